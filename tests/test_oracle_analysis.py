@@ -1,0 +1,142 @@
+"""Pins of the oracle's symbolic analysis (Sec. 2, Sec. 5.1, Sec. 5.2)."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle.analysis import analyze, bfs_nearest, cluster_tree_geometric, cluster_tree_balanced, \
+    front_neighbours, levels_of_fronts
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grid2d(n):
+    """n x n x 1 node lattice with the 5-point pattern (for Fig. 5)."""
+    import scipy.sparse as sp
+    idx = np.arange(n * n)
+    i, j = idx % n, idx // n
+    rows, cols = [idx], [idx]
+    for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+        ok = (i + di >= 0) & (i + di < n) & (j + dj >= 0) & (j + dj < n)
+        rows.append(idx[ok]); cols.append(idx[ok] + di + n * dj)
+    r = np.concatenate(rows); c = np.concatenate(cols)
+    A = sp.csr_matrix((np.ones(len(r), complex), (r, c)), shape=(n * n, n * n))
+    A.sort_indices()
+    coords = np.stack([i, j, np.zeros_like(i)], 1).astype(np.int32)
+    return w.SparseProblem("grid2d", n * n, A.indptr.astype(np.int64), A.indices.astype(np.int32),
+                           A.data, coords, w.LATTICE_NODE)
+
+
+def test_nested_dissection_matches_fig5_example():
+    p = _grid2d(11)
+    an = analyze(p, leaf_size=8, nmin_sep=10 ** 9)
+    spec = {}
+    for line in open(os.path.join(GOLDEN, "nd_11x11_fig5.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, xl, xh, yl, yh = line.split()
+        spec[name] = (int(xl), int(xh), int(yl), int(yh))
+    def box(f):
+        c = p.coords[an.perm[f.sep_begin:f.sep_end]]
+        return (c[:, 0].min(), c[:, 0].max(), c[:, 1].min(), c[:, 1].max()), len(c)
+    root = an.fronts[-1]
+    assert box(root) == (spec["S0"], 11)
+    kids = [an.fronts[c] for c in root.children]
+    assert [box(k)[0] for k in kids] == [spec["S1_0"], spec["S1_1"]]
+    g = [box(an.fronts[c])[0] for k in kids for c in k.children]
+    assert g == [spec["S2_00"], spec["S2_01"], spec["S2_10"], spec["S2_11"]]
+
+
+@pytest.mark.parametrize("gen", [lambda: w.helmholtz7(12, 8), lambda: w.yee_maxwell(6, 10)])
+def test_structure_invariants(gen):
+    p = gen()
+    an = analyze(p, leaf_size=16, nmin_sep=40, hodbf_leaf=8)
+    N = p.n
+    assert np.array_equal(np.sort(an.perm), np.arange(N))
+    assert sum(f.s for f in an.fronts) == N
+    A = p.to_scipy()[an.perm][:, an.perm].tocoo()
+    owner = np.empty(N, np.int64)
+    for f in an.fronts:
+        owner[f.sep_begin:f.sep_end] = f.id
+    anc = {}
+    for f in an.fronts:
+        a, q = set(), f.id
+        while q >= 0:
+            a.add(q); q = an.fronts[q].parent
+        anc[f.id] = a
+    # no entry of A couples two fronts neither of which is an ancestor of the other
+    for r, c in zip(A.row, A.col):
+        fr, fc = owner[r], owner[c]
+        assert fr in anc[fc] or fc in anc[fr]
+    for f in an.fronts:
+        ok = set(range(f.sep_begin, f.sep_end)) | set(f.upd.tolist())
+        for c in f.children:
+            assert set(an.fronts[c].upd.tolist()) <= ok
+        if f.compressed:
+            assert len(f.th_tree[-1]) == 2 ** (len(f.th_tree) - 1)
+            assert max(b - a for a, b in f.th_tree[-1]) <= 8
+
+
+def test_symbolic_equals_bruteforce_elimination():
+    """Fill pattern of L+U from a dense symbolic elimination == the fronts' structure."""
+    for p in (w.helmholtz7(6, 8), w.yee_maxwell(4, 10)):
+        an = analyze(p, leaf_size=10, nmin_sep=10 ** 9)
+        N = p.n
+        P = (p.to_scipy()[an.perm][:, an.perm].toarray() != 0)
+        S = P.copy()
+        for k in range(N):                      # symbolic Gaussian elimination
+            rows = np.nonzero(S[k + 1:, k])[0] + k + 1
+            cols = np.nonzero(S[k, k + 1:])[0] + k + 1
+            S[np.ix_(rows, cols)] = True
+        for f in an.fronts:
+            idx = list(range(f.sep_begin, f.sep_end))
+            below = set()
+            for k in idx:
+                below |= set((np.nonzero(S[k + 1:, k])[0] + k + 1).tolist())
+            assert below - set(idx) == set(f.upd.tolist())
+
+
+def test_survey_shape_table():
+    an = analyze(w.helmholtz7(16, 8), 64, 128, 64)
+    assert len(an.fronts) == 101 and len(levels_of_fronts(an)) == 7
+    assert an.fronts[-1].s == 256 and an.fronts[-1].u == 0
+    assert sorted((an.fronts[c].s, an.fronts[c].u) for c in an.fronts[-1].children) == [(112, 256), (128, 256)]
+    assert sum(f.compressed for f in an.fronts) == 2
+
+
+def test_cluster_trees():
+    order, lv = cluster_tree_geometric(np.array([[x, y, 0] for y in range(8) for x in range(16)]), 16)
+    assert len(lv) == 4 and all(b - a == 16 for a, b in lv[-1])
+    # first cut is at x = 8 (largest extent), every leaf is a 4 x 4 square
+    assert sorted(order[:64] % 16)[-1] == 7
+    bl = cluster_tree_balanced(10, 3)
+    assert bl[1] == [(0, 5), (5, 10)] and bl[2] == [(0, 3), (3, 5), (5, 8), (8, 10)]
+
+
+def test_bfs_nearest_order_and_cut():
+    # path 0-1-2-3-4 plus a star at 2: 2-5, 2-6
+    adj = {0: [1], 1: [0, 2], 2: [1, 3, 5, 6], 3: [2, 4], 4: [3], 5: [2], 6: [2]}
+    rp = [0]; ci = []
+    for v in range(7):
+        ci += adj[v]; rp.append(len(ci))
+    rp, ci = np.array(rp), np.array(ci)
+    allowed = np.ones(7, bool)
+    tgt = np.ones(7, bool)
+    assert bfs_nearest(rp, ci, 0, allowed, tgt, 3) == [1, 2, 3]
+    assert bfs_nearest(rp, ci, 1, allowed, tgt, 4) == [0, 2, 3, 5]     # distance 2 cut by vertex order
+    tgt2 = np.zeros(7, bool); tgt2[[4, 6]] = True
+    assert bfs_nearest(rp, ci, 0, allowed, tgt2, 8) == [6, 4]         # 6 at distance 3, 4 at distance 4
+    allowed[2] = False
+    assert bfs_nearest(rp, ci, 0, allowed, tgt, 8) == [1]
+
+
+def test_neighbour_lists_respect_targets():
+    p = w.helmholtz7(12, 8)
+    an = analyze(p, 32, 60, 16)
+    f = [f for f in an.fronts if f.compressed and f.u][0]
+    nn = front_neighbours(an, f, 4)
+    s_set = set(range(f.sep_begin, f.sep_end)); u_set = set(f.upd.tolist())
+    assert all(set(v) <= u_set and len(v) == 4 for v in nn["nn12"].values())
+    assert all(set(v) <= s_set and len(v) == 4 for v in nn["nn21"].values())
+    assert all(set(v) <= s_set for v in nn["nn11"].values())
