@@ -1,0 +1,210 @@
+/*
+ * mf.h -- C ABI of the GB300 butterfly-compressed multifrontal solver.
+ *
+ * The solver factors a sparse complex matrix A (N x N, CSR) by the
+ * multifrontal method in nested-dissection order (paper Sec. 2, Alg. 1) and
+ * compresses the large fronts in the hierarchically off-diagonal butterfly
+ * format (Sec. 4-5, Alg. 5), then solves A x = b to a relative residual
+ * ||b - A x|| / ||b|| <= rtol with FP64 GMRES(30) or iterative refinement
+ * preconditioned by the factorization (Sec. 6).
+ *
+ * Conventions
+ *  - Complex numbers are interleaved pairs of doubles (re, im) at this ABI.
+ *  - Right-hand sides and solutions are column-major N x nrhs with leading
+ *    dimension ld (in complex elements, ld >= N).
+ *  - Every call returns MF_OK (0) or a negative MF_ERR_* code; the message of
+ *    the last failure is available from mf_last_error().  A failed call
+ *    leaves the handle valid for mf_destroy().
+ *  - The caller owns every input array; the library copies what it keeps.
+ *    The handle owns all device memory it allocates and frees it in
+ *    mf_destroy().
+ *  - One handle is used by one host thread at a time; different handles may
+ *    be used concurrently on different CUDA streams.
+ */
+#ifndef MF_H_
+#define MF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MF_OK = 0,
+  MF_ERR_ARG = -1,            /* invalid argument                                        */
+  MF_ERR_STATE = -2,          /* call out of order (e.g. solve before factor)            */
+  MF_ERR_UNSUPPORTED = -3,    /* input outside what the ordering rule handles            */
+  MF_ERR_OOM = -4,            /* device or host allocation failed                        */
+  MF_ERR_SINGULAR = -5,       /* zero pivot in a front (front id in the message)         */
+  MF_ERR_NO_CONVERGENCE = -6, /* refinement stopped above rtol; x and info still written */
+  MF_ERR_TIMEOUT = -7,        /* a bounded device wait expired                           */
+  MF_ERR_CUDA = -8            /* CUDA runtime error                                      */
+};
+
+enum { MF_LATTICE_NODE = 0, MF_LATTICE_EDGE = 1 };
+enum { MF_PREC_C64 = 0 /* complex64 factors + FP64 refinement */, MF_PREC_C128 = 1 /* all complex128 */ };
+enum { MF_REFINE_NONE = 0, MF_REFINE_GMRES = 1, MF_REFINE_IR = 2 };
+
+#define MF_OPTIONS_V1 1
+
+/* Options.  mf_options_init() fills the defaults given in brackets. */
+typedef struct {
+  int32_t version;        /* MF_OPTIONS_V1                                                      */
+  int32_t leaf_size;      /* [64]   nested-dissection leaf (unknowns per leaf front)            */
+  int32_t nmin_sep;       /* [1024] fronts with |I^s| >= nmin_sep are HOD-BF compressed (Alg. 5) */
+  int32_t hodbf_leaf;     /* [64]   leaf size of the HOD-BF and butterfly cluster trees          */
+  int32_t max_rank;       /* [0]    cap on every ID rank, 0 = none                               */
+  int32_t alpha;          /* [2]    uniform proxy oversampling (Sec. 3.1)                        */
+  int32_t knn;            /* [8]    graph nearest neighbours per point (Sec. 5.2)                */
+  int32_t precision;      /* [MF_PREC_C64]                                                      */
+  int32_t refine;         /* [MF_REFINE_GMRES]                                                  */
+  int32_t gmres_restart;  /* [30]                                                               */
+  int32_t max_iters;      /* [300]  cap on Krylov iterations (or refinement steps) per column   */
+  int32_t lattice;        /* [MF_LATTICE_NODE] how coords are read (see mf_analyze)             */
+  double rtol;            /* [1e-8] target ||b - A x|| / ||b||                                  */
+  uint64_t seed;          /* [1]    seed of the random sketches                                 */
+  const int32_t* coords;  /* [NULL] N x 3 integer lattice coordinates, required                 */
+} mf_options;
+
+typedef struct {
+  int32_t iters;          /* Krylov iterations (or refinement steps), max over columns */
+  int32_t converged;      /* 1 if every column met rtol                                 */
+  double max_rel_residual;/* max over columns of ||b - A x|| / ||b|| (FP64, true residual) */
+} mf_solve_info;
+
+typedef struct {
+  int64_t n;              /* N                                                        */
+  int64_t nfronts;        /* fronts in the assembly tree                              */
+  int64_t ncompressed;    /* fronts factored in HOD-BF form                           */
+  int32_t tree_levels;    /* depth of the assembly tree + 1                           */
+  int32_t max_rank;       /* largest ID rank met in the factorization                 */
+  double factor_flops;    /* real floating-point operations of the numeric factorization */
+  double factor_bytes;    /* device bytes holding the factors                          */
+  double factor_seconds;  /* wall time of the last mf_factor                           */
+  int32_t precision;      /* MF_PREC_*                                                 */
+  int32_t gpu_launches_factor;  /* kernel launches of one factorization                */
+  int32_t gpu_launches_solve;   /* kernel launches of one preconditioner application   */
+  int32_t reserved;
+} mf_stats_t;
+
+typedef struct mf_handle mf_handle;
+
+/* Fill *opt with the defaults.  Returns MF_OK or MF_ERR_ARG (opt == NULL). */
+int mf_options_init(mf_options* opt);
+
+/*
+ * Symbolic analysis (Alg. 1 lines 2-3, Alg. 5 line 2; Sec. 2, 5.1, 5.2).
+ *   n, rowptr[n+1] (int64), colind[nnz] (int32, 0-based), vals[2*nnz] (re, im):
+ *     the CSR matrix A; the pattern must be structurally symmetric.
+ *   opt->coords (N x 3 int32, required): lattice coordinates of the unknowns.
+ *     MF_LATTICE_NODE: grid indices (separator planes are layers of unknowns);
+ *     MF_LATTICE_EDGE: doubled coordinates of a Yee edge lattice (an edge at
+ *     (i+1/2, j, k) is (2i+1, 2j, 2k)); separators are node planes.
+ *   cuda_stream: the CUDA stream all device work of this handle runs on (NULL = default).
+ * Computes the planar nested-dissection ordering, the assembly tree, the
+ * update sets, the HOD-BF cluster trees and the neighbour lists on the host;
+ * no device memory is touched until mf_factor.  *out receives a new handle.
+ * Errors: MF_ERR_ARG (bad pointers/sizes/CSR), MF_ERR_UNSUPPORTED (a box with
+ * an empty separator), MF_ERR_OOM.
+ */
+int mf_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+               const mf_options* opt, void* cuda_stream, mf_handle** out);
+
+/*
+ * Numeric factorization on the GPU (Alg. 1 for fronts with |I^s| < nmin_sep,
+ * Alg. 5 otherwise).  tol is the ID tolerance epsilon of the butterfly
+ * constructions (Sec. 6.1); it is ignored by dense fronts.  May be called
+ * again (refactorization with the same pattern).  Blocks until done.
+ * Errors: MF_ERR_STATE (no analysis), MF_ERR_SINGULAR, MF_ERR_OOM, MF_ERR_CUDA.
+ */
+int mf_factor(mf_handle* h, double tol);
+
+/*
+ * Solve A X = B for nrhs columns with host buffers (b: N x nrhs, ldb; x: N x
+ * nrhs, ldx; x may equal b).  The copies to and from the device are part of
+ * the call.  Uses the refinement of opt->refine.  info may be NULL.
+ * Errors: MF_ERR_STATE (not factored), MF_ERR_ARG, MF_ERR_NO_CONVERGENCE
+ * (x and info written), MF_ERR_CUDA.
+ */
+int mf_solve(mf_handle* h, int32_t nrhs, const double* b, int64_t ldb, double* x, int64_t ldx,
+             mf_solve_info* info);
+
+/* Same as mf_solve with device buffers (interleaved complex128, column-major, ld = N). */
+int mf_solve_device(mf_handle* h, int32_t nrhs, const void* d_b, void* d_x, mf_solve_info* info);
+
+/* Counters of the analysis and of the last factorization. */
+int mf_stats(const mf_handle* h, mf_stats_t* out);
+
+/* Message of the last failure on h (h == NULL: of the calling thread). Never NULL. */
+const char* mf_last_error(const mf_handle* h);
+
+/* Event timing of the dominant kernel of mf_factor (the batched front GEMM).
+ * mf_profile(h, 1) enables it and clears the counters; every following
+ * mf_factor records CUDA events around each of those launches on the handle's
+ * stream.  mf_profile_read returns the accumulated launches, device time and
+ * algorithmic flops (8 m n k per complex product). */
+typedef struct {
+  int64_t launches;
+  double ms;
+  double flops;
+} mf_kernel_profile_t;
+int mf_profile(mf_handle* h, int32_t enable);
+int mf_profile_read(const mf_handle* h, mf_kernel_profile_t* out);
+
+/* Kernel launches issued by the library since it was loaded (all handles, all streams). */
+int64_t mf_launch_counter(void);
+
+/* Frees everything owned by h (NULL is ignored). */
+void mf_destroy(mf_handle* h);
+
+/* ---------------- inspection of the analysis (host only, no GPU needed) ---------------- */
+
+typedef struct {
+  int64_t n;
+  int64_t nfronts;
+  int64_t upd_total;      /* sum of |I^u| over fronts */
+  int64_t tree_total;     /* sum over compressed fronts of the ranges of both cluster trees */
+  int64_t nn_total;       /* sum over compressed fronts of the lengths of the four neighbour lists */
+} mf_analysis_sizes_t;
+
+int mf_analysis_sizes(const mf_handle* h, mf_analysis_sizes_t* out);
+
+/*
+ * Copies the analysis into caller buffers (sizes from mf_analysis_sizes):
+ *   perm[n]                 perm[new] = old
+ *   front_parent[nfronts]   parent front id (-1 for the root), fronts in post-order
+ *   front_sep[2*nfronts]    [sep_begin, sep_end) in the new numbering
+ *   front_flags[nfronts]    bit 0: compressed
+ *   upd_ptr[nfronts+1], upd_idx[upd_total]   I^u of every front (sorted new indices)
+ * Any pointer may be NULL to skip that array.
+ */
+int mf_analysis_export(const mf_handle* h, int64_t* perm, int64_t* front_parent, int64_t* front_sep,
+                       int32_t* front_flags, int64_t* upd_ptr, int64_t* upd_idx);
+
+/*
+ * Cluster trees of front f (Sec. 5.1).  nlev[0], nlev[1] receive the number of
+ * levels (depth + 1) of the HOD-BF tree T_H of F11 and of the F22 tree (0 for a
+ * dense front).  If ranges != NULL it receives, for T_H then the F22 tree,
+ * level by level, the 2^l ranges (a, b) of level l as int64 pairs; its length
+ * is 2 * (2^nlev[0] - 1) + 2 * (2^nlev[1] - 1) values.
+ */
+int mf_front_trees(const mf_handle* h, int64_t f, int64_t* nlev, int64_t* ranges);
+
+/*
+ * Graph nearest-neighbour lists of front f (Sec. 5.2) with knn neighbours:
+ * nn11 (rows I^s, within the graph of A(I^s,I^s), outside the row's T_H leaf),
+ * nn22 (rows I^u, graph A(I^u,I^u), outside the row's F22 leaf),
+ * nn12 (rows I^s, nearest vertices of I^u) and nn21 (rows I^u, nearest of I^s),
+ * breadth-first, level by level, increasing vertex order within a level.
+ * counts[4] receives the total entries of each list.  If ptr != NULL it receives
+ * the four CSR row-pointer arrays back to back (lengths s+1, u+1, s+1, u+1) and
+ * idx the entries (new indices) back to back.
+ */
+int mf_front_neighbours(const mf_handle* h, int64_t f, int32_t knn, int64_t* counts, int64_t* ptr, int64_t* idx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H_ */

@@ -1,0 +1,561 @@
+// C ABI (include/mf.h): handle, analysis, factorization, solve with FP64
+// refinement (right-preconditioned GMRES(m) with modified Gram-Schmidt, or
+// iterative refinement; Sec. 6), statistics and inspection.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mf.h"
+#include "analysis.h"
+#include "engine.h"
+
+using mf::CudaError;
+using mf::DevMem;
+
+struct mf_handle {
+  mf_options opt{};
+  std::vector<int32_t> coords;
+  cudaStream_t stream = nullptr;
+  mf::Analysis an;
+  std::string err;
+  // host copy of the permuted matrix values (interleaved) for the device upload
+  std::vector<double> pvals;
+  std::vector<int32_t> pcol32;
+  mf::DeviceMatrix A;
+  bool on_device = false;
+  std::unique_ptr<mf::EngineBase> eng;
+  bool factored = false;
+  bool profile = false;
+  double factor_seconds = 0;
+  // solve work (FP64, new numbering)
+  DevMem wb, wx, wr, wz, wV, wH, wsc, wy;
+  DevMem perm_d, io_tmp, io_b, io_x;     // permutation and I/O staging of the solve calls
+  int64_t io_nrhs = 0;
+  int64_t work_nrhs = 0;
+  int32_t work_restart = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(mf_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  g_err = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(mf_handle* h, F&& fn) {
+  try {
+    return fn();
+  } catch (const mf::SingularError& e) {
+    return fail(h, MF_ERR_SINGULAR, e.what());
+  } catch (const CudaError& e) {
+    std::string m = e.what();
+    int code = (m.find("out of memory") != std::string::npos || m.find("cudaMalloc") != std::string::npos)
+                   ? MF_ERR_OOM
+                   : MF_ERR_CUDA;
+    return fail(h, code, m);
+  } catch (const std::bad_alloc&) {
+    return fail(h, MF_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(h, MF_ERR_ARG, e.what());
+  }
+}
+
+void ensure_device(mf_handle* h) {
+  if (h->on_device) return;
+  cudaStream_t st = h->stream;
+  auto& A = h->A;
+  A.n = h->an.n;
+  A.nnz = (int64_t)h->an.pcol.size();
+  mf::upload(A.rowptr, h->an.prow, st);
+  mf::upload(A.col64, h->an.pcol, st);
+  mf::upload(A.col32, h->pcol32, st);
+  mf::upload(A.vals, h->pvals, st);
+  mf::upload(h->perm_d, h->an.perm, st);
+  MF_CUDA(cudaStreamSynchronize(st));
+  h->on_device = true;
+}
+
+void ensure_work(mf_handle* h, int nrhs, int restart) {
+  if (h->work_nrhs >= nrhs && h->work_restart >= restart) return;
+  const int64_t n = h->an.n;
+  size_t vec = sizeof(double) * 2 * (size_t)n * nrhs;
+  h->wb.alloc(vec);
+  h->wx.alloc(vec);
+  h->wr.alloc(vec);
+  h->wz.alloc(vec);
+  h->wV.alloc(vec * (restart + 1));
+  h->wH.alloc(sizeof(double) * 2 * (size_t)(restart + 2) * (restart + 1) * nrhs);
+  h->wsc.alloc(sizeof(double) * 2 * (size_t)nrhs * 4);
+  h->wy.alloc(sizeof(double) * 2 * (size_t)nrhs * (restart + 1));
+  h->work_nrhs = nrhs;
+  h->work_restart = restart;
+}
+
+using cplx = std::complex<double>;
+
+// True residual norms ||b - A x|| per column; r receives b - A x.
+void residual(mf_handle* h, const double* b, const double* x, double* r, int nrhs, std::vector<double>& nrm) {
+  const int64_t n = h->an.n;
+  cudaStream_t st = h->stream;
+  mf::launch_spmv_residual(n, h->A.rowptr.as<int64_t>(), h->A.col32.as<int32_t>(), h->A.vals.as<double>(), x, b, r,
+                           nrhs, n, st);
+  double* d = h->wsc.as<double>();
+  mf::launch_colnorm2(n, nrhs, r, n, d, st);
+  nrm.resize(nrhs);
+  MF_CUDA(cudaMemcpyAsync(nrm.data(), d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  MF_CUDA(cudaStreamSynchronize(st));
+  for (auto& v : nrm) v = std::sqrt(v);
+}
+
+// Solve on device buffers in the new numbering: B (n x nrhs) -> X.
+int solve_new_numbering(mf_handle* h, int nrhs, const double* B, double* X, mf_solve_info* info) {
+  const int64_t n = h->an.n;
+  cudaStream_t st = h->stream;
+  const int restart = std::max(1, h->opt.gmres_restart);
+  const int refine = h->opt.refine;
+  ensure_work(h, nrhs, refine == MF_REFINE_GMRES ? restart : 1);
+  const size_t vec = sizeof(double) * 2 * (size_t)n * nrhs;
+  std::vector<double> bn;
+  double* R = h->wr.as<double>();
+  double* Z = h->wz.as<double>();
+  // ||b||
+  {
+    double* d = h->wsc.as<double>();
+    mf::launch_colnorm2(n, nrhs, B, n, d, st);
+    bn.resize(nrhs);
+    MF_CUDA(cudaMemcpyAsync(bn.data(), d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    for (auto& v : bn) v = std::sqrt(v);
+  }
+  const double rtol = h->opt.rtol;
+  int iters = 0;
+  std::vector<double> rn;
+  auto rel_ok = [&](const std::vector<double>& r, int c) { return bn[c] == 0 || r[c] <= rtol * bn[c]; };
+
+  if (refine == MF_REFINE_NONE || refine == MF_REFINE_IR) {
+    h->eng->apply_precond(B, X, nrhs);
+    residual(h, B, X, R, nrhs, rn);
+    if (refine == MF_REFINE_IR) {
+      while (iters < h->opt.max_iters) {
+        bool all = true;
+        for (int c = 0; c < nrhs; ++c) all = all && rel_ok(rn, c);
+        if (all) break;
+        h->eng->apply_precond(R, Z, nrhs);
+        // X += Z
+        std::vector<double> one(2 * nrhs, 0.0);
+        for (int c = 0; c < nrhs; ++c) one[2 * c] = -1.0;
+        MF_CUDA(cudaMemcpyAsync(h->wsc.as<double>(), one.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, st));
+        mf::launch_colaxpy(n, nrhs, h->wsc.as<double>(), Z, n, X, n, 1.0, st);
+        residual(h, B, X, R, nrhs, rn);
+        ++iters;
+      }
+    }
+  } else {
+    // right-preconditioned restarted GMRES, all columns in lockstep, per-column Givens
+    MF_CUDA(cudaMemsetAsync(X, 0, vec, st));
+    MF_CUDA(cudaMemcpyAsync(R, B, vec, cudaMemcpyDeviceToDevice, st));
+    rn = bn;
+    double* V = h->wV.as<double>();
+    double* Hd = h->wH.as<double>();
+    double* sc = h->wsc.as<double>();
+    double* yd = h->wy.as<double>();
+    const size_t vstride = (size_t)2 * n * nrhs;   // doubles per Krylov vector block
+    std::vector<int> its_col(nrhs, 0);
+    while (true) {
+      std::vector<int> active;
+      for (int c = 0; c < nrhs; ++c)
+        if (!rel_ok(rn, c) && its_col[c] < h->opt.max_iters) active.push_back(c);
+      if (active.empty()) break;
+      // v0 = r / ||r||  (all columns; converged ones are carried but not used)
+      std::vector<double> inv(2 * nrhs, 0.0);
+      for (int c = 0; c < nrhs; ++c) inv[2 * c] = rn[c] > 0 ? 1.0 / rn[c] : 0.0;
+      MF_CUDA(cudaMemcpyAsync(sc, inv.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, st));
+      mf::launch_colscale(n, nrhs, sc, R, n, V, n, st);
+      std::vector<std::vector<cplx>> Hh(nrhs, std::vector<cplx>((restart + 1) * restart));
+      std::vector<std::vector<cplx>> cs(nrhs, std::vector<cplx>(restart)), sn(nrhs, std::vector<cplx>(restart));
+      std::vector<std::vector<cplx>> g(nrhs, std::vector<cplx>(restart + 1));
+      std::vector<int> jused(nrhs, 0);
+      std::vector<char> live(nrhs, 0);
+      for (int c : active) { live[c] = 1; g[c][0] = rn[c]; }
+      std::vector<double> hcol(2 * (restart + 1) * nrhs);
+      for (int j = 0; j < restart; ++j) {
+        bool any = false;
+        for (int c = 0; c < nrhs; ++c) any = any || live[c];
+        if (!any) break;
+        double* vj = V + j * vstride;
+        double* w = V + (j + 1) * vstride;
+        h->eng->apply_precond(vj, Z, nrhs);
+        mf::launch_spmv(n, h->A.rowptr.as<int64_t>(), h->A.col32.as<int32_t>(), h->A.vals.as<double>(), Z, w, nrhs, n,
+                        st);
+        // modified Gram-Schmidt
+        for (int i = 0; i <= j; ++i) {
+          double* hij = Hd + (size_t)2 * nrhs * (i + (restart + 1) * j);
+          mf::launch_coldot(n, nrhs, V + i * vstride, n, w, n, hij, st);
+          mf::launch_colaxpy(n, nrhs, hij, V + i * vstride, n, w, n, 1.0, st);
+        }
+        mf::launch_colnorm2(n, nrhs, w, n, sc, st);
+        std::vector<double> wn(nrhs);
+        MF_CUDA(cudaMemcpyAsync(wn.data(), sc, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaMemcpyAsync(hcol.data(), Hd + (size_t)2 * nrhs * (restart + 1) * j,
+                                sizeof(double) * 2 * nrhs * (j + 1), cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        std::vector<double> scl(2 * nrhs, 0.0);
+        for (int c = 0; c < nrhs; ++c) {
+          double hn = std::sqrt(wn[c]);
+          scl[2 * c] = hn > 0 ? 1.0 / hn : 0.0;
+          if (!live[c]) continue;
+          auto& H = Hh[c];
+          for (int i = 0; i <= j; ++i)
+            H[i + (restart + 1) * j] = cplx(hcol[2 * (nrhs * i + c)], hcol[2 * (nrhs * i + c) + 1]);
+          H[j + 1 + (restart + 1) * j] = hn;
+          for (int i = 0; i < j; ++i) {
+            cplx a = H[i + (restart + 1) * j], bb = H[i + 1 + (restart + 1) * j];
+            H[i + (restart + 1) * j] = cs[c][i] * a + sn[c][i] * bb;
+            H[i + 1 + (restart + 1) * j] = -std::conj(sn[c][i]) * a + std::conj(cs[c][i]) * bb;
+          }
+          cplx a = H[j + (restart + 1) * j], bb = H[j + 1 + (restart + 1) * j];
+          double den = std::sqrt(std::norm(a) + std::norm(bb));
+          cs[c][j] = den > 0 ? a / den : cplx(1);
+          sn[c][j] = den > 0 ? bb / den : cplx(0);
+          H[j + (restart + 1) * j] = cs[c][j] * a + sn[c][j] * bb;
+          H[j + 1 + (restart + 1) * j] = 0;
+          g[c][j + 1] = -std::conj(sn[c][j]) * g[c][j];
+          g[c][j] = cs[c][j] * g[c][j];
+          jused[c] = j + 1;
+          its_col[c]++;
+          if (std::abs(g[c][j + 1]) <= rtol * bn[c] || its_col[c] >= h->opt.max_iters || hn == 0) live[c] = 0;
+        }
+        MF_CUDA(cudaMemcpyAsync(sc, scl.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, st));
+        mf::launch_colscale(n, nrhs, sc, w, n, w, n, st);
+        iters = std::max(iters, j + 1);
+      }
+      // y = H^-1 g per column; t = V y ; X += M^-1 t
+      int jmax = 0;
+      for (int c : active) jmax = std::max(jmax, jused[c]);
+      std::vector<double> yh(2 * (size_t)nrhs * jmax, 0.0);
+      for (int c : active) {
+        int m = jused[c];
+        std::vector<cplx> y(m);
+        for (int i = m - 1; i >= 0; --i) {
+          cplx acc = g[c][i];
+          for (int k = i + 1; k < m; ++k) acc -= Hh[c][i + (restart + 1) * k] * y[k];
+          y[i] = acc / Hh[c][i + (restart + 1) * i];
+        }
+        for (int i = 0; i < m; ++i) {
+          yh[2 * ((size_t)nrhs * i + c)] = -y[i].real();
+          yh[2 * ((size_t)nrhs * i + c) + 1] = -y[i].imag();
+        }
+      }
+      MF_CUDA(cudaMemcpyAsync(yd, yh.data(), sizeof(double) * yh.size(), cudaMemcpyHostToDevice, st));
+      MF_CUDA(cudaMemsetAsync(R, 0, vec, st));
+      for (int i = 0; i < jmax; ++i)
+        mf::launch_colaxpy(n, nrhs, yd + (size_t)2 * nrhs * i, V + i * vstride, n, R, n, 1.0, st);
+      h->eng->apply_precond(R, Z, nrhs);
+      std::vector<double> one(2 * nrhs, 0.0);
+      for (int c = 0; c < nrhs; ++c) one[2 * c] = -1.0;
+      MF_CUDA(cudaMemcpyAsync(sc, one.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, st));
+      mf::launch_colaxpy(n, nrhs, sc, Z, n, X, n, 1.0, st);
+      residual(h, B, X, R, nrhs, rn);
+      iters = 0;
+      for (int c = 0; c < nrhs; ++c) iters = std::max(iters, its_col[c]);
+    }
+    if (rn.size() != (size_t)nrhs) residual(h, B, X, R, nrhs, rn);
+  }
+  MF_CUDA(cudaGetLastError());
+  double worst = 0;
+  bool conv = true;
+  for (int c = 0; c < nrhs; ++c) {
+    double rr = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
+    worst = std::max(worst, rr);
+    conv = conv && rel_ok(rn, c);
+  }
+  if (info) {
+    info->iters = iters;
+    info->converged = conv ? 1 : 0;
+    info->max_rel_residual = worst;
+  }
+  if (!conv && refine != MF_REFINE_NONE)
+    return fail(h, MF_ERR_NO_CONVERGENCE, "refinement stopped above rtol (max rel. residual " + std::to_string(worst) + ")");
+  return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mf_options_init(mf_options* o) {
+  if (!o) return fail(nullptr, MF_ERR_ARG, "opt is NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->version = MF_OPTIONS_V1;
+  o->leaf_size = 64;
+  o->nmin_sep = 1024;
+  o->hodbf_leaf = 64;
+  o->max_rank = 0;
+  o->alpha = 2;
+  o->knn = 8;
+  o->precision = MF_PREC_C64;
+  o->refine = MF_REFINE_GMRES;
+  o->gmres_restart = 30;
+  o->max_iters = 300;
+  o->lattice = MF_LATTICE_NODE;
+  o->rtol = 1e-8;
+  o->seed = 1;
+  o->coords = nullptr;
+  return MF_OK;
+}
+
+int mf_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals, const mf_options* opt,
+               void* cuda_stream, mf_handle** out) {
+  if (!out) return fail(nullptr, MF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!opt || opt->version != MF_OPTIONS_V1) return fail(nullptr, MF_ERR_ARG, "options missing or wrong version");
+  if (n <= 0 || !rowptr || !colind || !vals) return fail(nullptr, MF_ERR_ARG, "invalid CSR arguments");
+  if (!opt->coords) return fail(nullptr, MF_ERR_UNSUPPORTED, "lattice coordinates are required for the ordering");
+  std::unique_ptr<mf_handle> h(new (std::nothrow) mf_handle());
+  if (!h) return fail(nullptr, MF_ERR_OOM, "host allocation failed");
+  int rc = guarded(h.get(), [&]() -> int {
+    h->opt = *opt;
+    h->coords.assign(opt->coords, opt->coords + 3 * n);
+    h->opt.coords = h->coords.data();
+    h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    try {
+      mf::analyze(n, rowptr, colind, h->coords.data(), opt->lattice, opt->leaf_size, opt->nmin_sep, opt->hodbf_leaf,
+                  h->an);
+    } catch (const std::runtime_error& e) {
+      std::string m = e.what();
+      if (m.find("empty separator") != std::string::npos) return fail(h.get(), MF_ERR_UNSUPPORTED, m);
+      return fail(h.get(), MF_ERR_ARG, m);
+    }
+    // permuted values, aligned with the permuted (sorted) pattern
+    const auto& an = h->an;
+    h->pvals.resize(2 * an.pcol.size());
+    h->pcol32.resize(an.pcol.size());
+    std::vector<std::pair<int64_t, int64_t>> row;
+    for (int64_t r = 0; r < n; ++r) {
+      int64_t o = an.perm[r];
+      row.clear();
+      for (int64_t k = rowptr[o]; k < rowptr[o + 1]; ++k) row.push_back({an.iperm[colind[k]], k});
+      std::sort(row.begin(), row.end());
+      int64_t p = an.prow[r];
+      for (auto& e : row) {
+        h->pvals[2 * p] = vals[2 * e.second];
+        h->pvals[2 * p + 1] = vals[2 * e.second + 1];
+        h->pcol32[p] = (int32_t)e.first;
+        ++p;
+      }
+    }
+    return MF_OK;
+  });
+  if (rc != MF_OK) return rc;
+  *out = h.release();
+  return MF_OK;
+}
+
+int mf_factor(mf_handle* h, double tol) {
+  if (!h) return fail(nullptr, MF_ERR_ARG, "handle is NULL");
+  if (!(tol > 0) && !(tol == 0)) return fail(h, MF_ERR_ARG, "tol must be >= 0");
+  return guarded(h, [&]() -> int {
+    auto t0 = std::chrono::steady_clock::now();
+    ensure_device(h);
+    if (!h->eng) {
+      h->eng = h->opt.precision == MF_PREC_C128 ? mf::make_engine_c128(h->an, h->A, h->stream)
+                                               : mf::make_engine_c64(h->an, h->A, h->stream);
+      h->eng->profiling = h->profile;
+    }
+    h->factored = false;
+    h->eng->factor(tol);
+    h->factored = true;
+    h->factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return MF_OK;
+  });
+}
+
+int mf_solve_device(mf_handle* h, int32_t nrhs, const void* d_b, void* d_x, mf_solve_info* info) {
+  if (!h) return fail(nullptr, MF_ERR_ARG, "handle is NULL");
+  if (!h->factored) return fail(h, MF_ERR_STATE, "mf_solve before mf_factor");
+  if (nrhs <= 0 || !d_b || !d_x) return fail(h, MF_ERR_ARG, "invalid solve arguments");
+  return guarded(h, [&]() -> int {
+    const int64_t n = h->an.n;
+    ensure_work(h, nrhs, h->opt.refine == MF_REFINE_GMRES ? std::max(1, h->opt.gmres_restart) : 1);
+    cudaStream_t st = h->stream;
+    // permute into the new numbering: wb[new] = b[perm[new]]
+    double* B = h->wb.as<double>();
+    double* X = h->wx.as<double>();
+    const int64_t* perm = h->perm_d.as<int64_t>();
+    if (h->io_nrhs < nrhs) {
+      h->io_tmp.alloc(sizeof(double) * 2 * n * nrhs);
+      h->io_b.alloc(sizeof(double) * 2 * n * nrhs);
+      h->io_x.alloc(sizeof(double) * 2 * n * nrhs);
+      h->io_nrhs = nrhs;
+    }
+    DevMem& tmp = h->io_tmp;
+    mf::launch_to_planar<double>(static_cast<const double*>(d_b), n, n, nrhs, perm, tmp.as<double>(), n * nrhs, st);
+    mf::launch_from_planar<double>(tmp.as<double>(), n * nrhs, n, nrhs, nullptr, B, n, st);
+    int rc = solve_new_numbering(h, nrhs, B, X, info);
+    mf::launch_to_planar<double>(X, n, n, nrhs, nullptr, tmp.as<double>(), n * nrhs, st);
+    mf::launch_from_planar<double>(tmp.as<double>(), n * nrhs, n, nrhs, perm, static_cast<double*>(d_x), n, st);
+    MF_CUDA(cudaStreamSynchronize(st));
+    return rc;
+  });
+}
+
+int mf_solve(mf_handle* h, int32_t nrhs, const double* b, int64_t ldb, double* x, int64_t ldx, mf_solve_info* info) {
+  if (!h) return fail(nullptr, MF_ERR_ARG, "handle is NULL");
+  if (!h->factored) return fail(h, MF_ERR_STATE, "mf_solve before mf_factor");
+  const int64_t n = h->an.n;
+  if (nrhs <= 0 || !b || !x || ldb < n || ldx < n) return fail(h, MF_ERR_ARG, "invalid solve arguments");
+  return guarded(h, [&]() -> int {
+    cudaStream_t st = h->stream;
+    if (h->io_nrhs < nrhs) {
+      h->io_tmp.alloc(sizeof(double) * 2 * n * nrhs);
+      h->io_b.alloc(sizeof(double) * 2 * n * nrhs);
+      h->io_x.alloc(sizeof(double) * 2 * n * nrhs);
+      h->io_nrhs = nrhs;
+    }
+    DevMem& db = h->io_b;
+    DevMem& dx = h->io_x;
+    MF_CUDA(cudaMemcpy2DAsync(db.p, sizeof(double) * 2 * n, b, sizeof(double) * 2 * ldb, sizeof(double) * 2 * n, nrhs,
+                              cudaMemcpyHostToDevice, st));
+    int rc = mf_solve_device(h, nrhs, db.p, dx.p, info);
+    if (rc != MF_OK && rc != MF_ERR_NO_CONVERGENCE) return rc;
+    MF_CUDA(cudaMemcpy2DAsync(x, sizeof(double) * 2 * ldx, dx.p, sizeof(double) * 2 * n, sizeof(double) * 2 * n, nrhs,
+                              cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    return rc;
+  });
+}
+
+int mf_stats(const mf_handle* h, mf_stats_t* out) {
+  if (!h || !out) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  out->n = h->an.n;
+  out->nfronts = (int64_t)h->an.fronts.size();
+  int lv = 0;
+  for (auto& f : h->an.fronts) {
+    out->ncompressed += f.compressed ? 1 : 0;
+    lv = std::max(lv, f.level + 1);
+  }
+  out->tree_levels = lv;
+  out->precision = h->opt.precision;
+  if (h->eng) {
+    out->factor_flops = h->eng->factor_flops();
+    out->factor_bytes = h->eng->factor_bytes();
+    out->gpu_launches_factor = h->eng->launches_factor();
+    out->max_rank = h->eng->max_rank();
+  }
+  out->factor_seconds = h->factor_seconds;
+  return MF_OK;
+}
+
+int mf_profile(mf_handle* h, int32_t enable) {
+  if (!h) return fail(nullptr, MF_ERR_ARG, "handle is NULL");
+  h->profile = enable != 0;
+  if (h->eng) {
+    h->eng->profiling = h->profile;
+    h->eng->prof = mf::EngineBase::Profile();
+  }
+  return MF_OK;
+}
+
+int mf_profile_read(const mf_handle* h, mf_kernel_profile_t* out) {
+  if (!h || !out) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  if (h->eng) {
+    out->launches = h->eng->prof.launches;
+    out->ms = h->eng->prof.ms;
+    out->flops = h->eng->prof.flops;
+  }
+  return MF_OK;
+}
+
+int64_t mf_launch_counter(void) { return mf::launch_count(); }
+
+const char* mf_last_error(const mf_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+void mf_destroy(mf_handle* h) {
+  if (!h) return;
+  delete h;
+}
+
+int mf_analysis_sizes(const mf_handle* h, mf_analysis_sizes_t* out) {
+  if (!h || !out) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  out->n = h->an.n;
+  out->nfronts = (int64_t)h->an.fronts.size();
+  for (auto& f : h->an.fronts) {
+    out->upd_total += f.u();
+    for (auto& l : f.th_tree) out->tree_total += (int64_t)l.size();
+    for (auto& l : f.f22_tree) out->tree_total += (int64_t)l.size();
+  }
+  return MF_OK;
+}
+
+int mf_analysis_export(const mf_handle* h, int64_t* perm, int64_t* front_parent, int64_t* front_sep,
+                       int32_t* front_flags, int64_t* upd_ptr, int64_t* upd_idx) {
+  if (!h) return fail(nullptr, MF_ERR_ARG, "handle is NULL");
+  const auto& an = h->an;
+  if (perm) std::copy(an.perm.begin(), an.perm.end(), perm);
+  int64_t p = 0;
+  if (upd_ptr) upd_ptr[0] = 0;
+  for (size_t i = 0; i < an.fronts.size(); ++i) {
+    const auto& f = an.fronts[i];
+    if (front_parent) front_parent[i] = f.parent;
+    if (front_sep) { front_sep[2 * i] = f.sep_begin; front_sep[2 * i + 1] = f.sep_end; }
+    if (front_flags) front_flags[i] = f.compressed ? 1 : 0;
+    if (upd_idx) std::copy(f.upd.begin(), f.upd.end(), upd_idx + p);
+    p += f.u();
+    if (upd_ptr) upd_ptr[i + 1] = p;
+  }
+  return MF_OK;
+}
+
+int mf_front_trees(const mf_handle* h, int64_t f, int64_t* nlev, int64_t* ranges) {
+  if (!h || !nlev) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "NULL argument");
+  if (f < 0 || f >= (int64_t)h->an.fronts.size()) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "bad front id");
+  const auto& fr = h->an.fronts[f];
+  nlev[0] = (int64_t)fr.th_tree.size();
+  nlev[1] = (int64_t)fr.f22_tree.size();
+  if (ranges) {
+    int64_t p = 0;
+    for (auto* t : {&fr.th_tree, &fr.f22_tree})
+      for (auto& l : *t)
+        for (auto& r : l) { ranges[p++] = r.a; ranges[p++] = r.b; }
+  }
+  return MF_OK;
+}
+
+int mf_front_neighbours(const mf_handle* h, int64_t f, int32_t knn, int64_t* counts, int64_t* ptr, int64_t* idx) {
+  if (!h || !counts || knn < 0) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "invalid argument");
+  if (f < 0 || f >= (int64_t)h->an.fronts.size()) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "bad front id");
+  return guarded(const_cast<mf_handle*>(h), [&]() -> int {
+    mf::FrontNeighbours nb;
+    mf::front_neighbours(h->an, h->an.fronts[f], knn, nb);
+    const std::vector<int64_t>* P[4] = {&nb.nn11_ptr, &nb.nn22_ptr, &nb.nn12_ptr, &nb.nn21_ptr};
+    const std::vector<int64_t>* I[4] = {&nb.nn11, &nb.nn22, &nb.nn12, &nb.nn21};
+    for (int k = 0; k < 4; ++k) counts[k] = (int64_t)I[k]->size();
+    if (ptr) {
+      int64_t p = 0;
+      for (int k = 0; k < 4; ++k)
+        for (int64_t v : *P[k]) ptr[p++] = v;
+    }
+    if (idx) {
+      int64_t p = 0;
+      for (int k = 0; k < 4; ++k)
+        for (int64_t v : *I[k]) idx[p++] = v;
+    }
+    return MF_OK;
+  });
+}
+
+}  // extern "C"

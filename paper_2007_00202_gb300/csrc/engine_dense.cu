@@ -1,0 +1,557 @@
+// Dense-front engine: the multifrontal factorization of Alg. 1 (Sec. 2), one
+// batched launch sequence per assembly-tree level (deepest level first), and
+// the forward/backward solve of Alg. 1's last line.
+//
+// Per level:  assemble A entries, extend-add children (Sec. 2 step 1);
+// blocked right-looking LU of F11 with partial pivoting inside F11 (step 2);
+// explicit L^-1 and U^-1 by recursive 2 x 2 block inversion; F12 <- L^-1 P^T F12,
+// F21 <- F21 U^-1 (step 3) and C = F22 - F21 F12 (step 4) as batched GEMMs.
+// The whole sequence is built once per analysis ("launch program") and
+// replayed by every factorization.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "engine.h"
+
+namespace mf {
+
+namespace {
+
+constexpr int LU_NB = 32;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <typename T>
+class DenseEngine : public EngineBase {
+ public:
+  DenseEngine(const Analysis& an, const DeviceMatrix& A, cudaStream_t st) : an_(an), A_(A), st_(st) { plan(); }
+
+  void factor(double) override {
+    MF_CUDA(cudaMemsetAsync(arena_.p, 0, zero_bytes_, st_));
+    MF_CUDA(cudaMemsetAsync(status_.p, 0, sizeof(int32_t), st_));
+    size_t ng = 0;
+    if (profiling) {
+      for (size_t i = 0; i < fops_.size(); ++i) ng += gemm_flops_[i] > 0 ? 1 : 0;
+      while (evs_.size() < 2 * ng) {
+        cudaEvent_t e;
+        MF_CUDA(cudaEventCreate(&e));
+        evs_.push_back(e);
+      }
+    }
+    size_t k = 0;
+    for (size_t i = 0; i < fops_.size(); ++i) {
+      bool timed = profiling && gemm_flops_[i] > 0;
+      if (timed) MF_CUDA(cudaEventRecord(evs_[2 * k], st_));
+      fops_[i](st_);
+      if (timed) { MF_CUDA(cudaEventRecord(evs_[2 * k + 1], st_)); ++k; }
+    }
+    MF_CUDA(cudaGetLastError());
+    if (profiling) {
+      MF_CUDA(cudaStreamSynchronize(st_));
+      k = 0;
+      for (size_t i = 0; i < fops_.size(); ++i) {
+        if (gemm_flops_[i] <= 0) continue;
+        float ms = 0;
+        MF_CUDA(cudaEventElapsedTime(&ms, evs_[2 * k], evs_[2 * k + 1]));
+        prof.ms += ms;
+        prof.flops += gemm_flops_[i];
+        prof.launches += 1;
+        ++k;
+      }
+    }
+    int32_t stat = 0;
+    MF_CUDA(cudaMemcpyAsync(&stat, status_.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
+    MF_CUDA(cudaStreamSynchronize(st_));
+    if (stat != DEV_OK) throw SingularError("zero pivot in a dense front");
+  }
+
+  void apply_precond(const double* x, double* y, int nrhs) override {
+    SolveProg& sp = solve_prog(nrhs);
+    const int64_t n = an_.n;
+    T* X = sp.X.template as<T>();
+    const int64_t xpl = n * nrhs;
+    launch_to_planar<T>(x, n, n, nrhs, nullptr, X, xpl, st_);
+    for (auto& op : sp.ops) op(st_);
+    launch_from_planar<T>(X, xpl, n, nrhs, nullptr, y, n, st_);
+    MF_CUDA(cudaGetLastError());
+  }
+
+  double factor_flops() const override { return flops_; }
+  double factor_bytes() const override { return factor_bytes_; }
+  int launches_factor() const override { return nlaunch_factor_; }
+  int launches_solve(int nrhs) override { return solve_prog(nrhs).nlaunch + 2; }
+
+ private:
+  struct SolveProg {
+    DevMem X, tmp, ptrs, descs, tiles;
+    std::vector<std::function<void(cudaStream_t)>> ops;
+    int nlaunch = 0;
+  };
+
+  const Analysis& an_;
+  const DeviceMatrix& A_;
+  cudaStream_t st_;
+  DevMem arena_, fronts_d_, flists_d_, status_, descs_d_, tiles_d_, ea_d_;
+  size_t zero_bytes_ = 0;
+  std::vector<FrontDev<T>> fr_;             // indexed by front id
+  std::vector<std::vector<int32_t>> levels_;  // front ids per level, deepest first
+  std::vector<size_t> level_off_;           // offsets of the level lists in flists_d_
+  std::vector<std::function<void(cudaStream_t)>> fops_;
+  std::vector<GemmDesc<T>> descs_;
+  std::vector<GemmTile> tiles_;
+  double flops_ = 0, factor_bytes_ = 0;
+  int nlaunch_factor_ = 0;
+  std::map<int, std::unique_ptr<SolveProg>> sprog_;
+  std::vector<double> gemm_flops_;          // per factor op: algorithmic flops if it is a GEMM launch, else 0
+  std::vector<cudaEvent_t> evs_;
+
+ public:
+  ~DenseEngine() override {
+    for (auto e : evs_) cudaEventDestroy(e);
+  }
+
+ private:
+
+  const int32_t* flist(size_t lv) const { return flists_d_.template as<int32_t>() + level_off_[lv]; }
+
+  // Register a batched GEMM launch in the program being built (descs, tiles collected in vectors).
+  struct GemmRef {
+    size_t d0, t0;
+    int nt;
+    size_t nd;
+  };
+  GemmRef add_gemm(std::vector<GemmDesc<T>>& D, std::vector<GemmTile>& Tl, const std::vector<GemmDesc<T>>& batch) {
+    GemmRef r{D.size(), Tl.size(), 0, 0};
+    for (auto& d : batch) {
+      if (d.m <= 0 || d.n <= 0) continue;
+      int idx = (int)(D.size() - r.d0);
+      D.push_back(d);
+      int tm = (d.m + GEMM_TILE - 1) / GEMM_TILE, tn = (d.n + GEMM_TILE - 1) / GEMM_TILE;
+      for (int i = 0; i < tm; ++i)
+        for (int j = 0; j < tn; ++j) Tl.push_back({idx, i, j, 0});
+    }
+    r.nt = (int)(Tl.size() - r.t0);
+    r.nd = D.size() - r.d0;
+    return r;
+  }
+
+  void push_op(std::function<void(cudaStream_t)> fn, double fl = 0) {
+    fops_.push_back(std::move(fn));
+    gemm_flops_.push_back(fl);
+  }
+
+  double ref_flops(const std::vector<GemmDesc<T>>& D, const GemmRef& g) const {
+    double f = 0;
+    for (size_t i = g.d0; i < g.d0 + g.nd; ++i) f += 8.0 * D[i].m * D[i].n * D[i].k;
+    return f;
+  }
+
+  static GemmDesc<T> gd(int m, int n, int k, int ta, int tb, T alpha, T beta, PMat<T> a, PMat<T> b, PMat<T> c) {
+    GemmDesc<T> d;
+    d.m = m; d.n = n; d.k = k; d.transA = ta; d.transB = tb; d.alpha = alpha; d.beta = beta;
+    d.A = a; d.B = b; d.C = c;
+    return d;
+  }
+
+  void plan() {
+    const auto& F = an_.fronts;
+    const size_t nf = F.size();
+    fr_.resize(nf);
+    // ---- memory plan: one arena; the zeroed part first
+    size_t off = 0;
+    auto take = [&](size_t elems) {
+      size_t o = off;
+      off = align_up(off + elems * sizeof(T), 256);
+      return o;
+    };
+    struct Offs { size_t LU, Linv, UinvT, F12w, F21w, C, UT, W, F12p, F12T, F21f, piv, perm, upd; };
+    std::vector<Offs> o(nf);
+    for (size_t i = 0; i < nf; ++i) {
+      int64_t s = F[i].s(), u = F[i].u();
+      o[i].LU = take(2 * s * s);
+      o[i].Linv = take(2 * s * s);
+      o[i].UinvT = take(2 * s * s);
+      o[i].F12w = take(2 * s * u);
+      o[i].F21w = take(2 * s * u);
+      o[i].C = take(F[i].parent >= 0 ? 2 * u * u : 0);
+    }
+    zero_bytes_ = off;
+    for (size_t i = 0; i < nf; ++i) {
+      int64_t s = F[i].s(), u = F[i].u();
+      o[i].UT = take(2 * s * s);
+      o[i].W = take(4 * s * s);   // two s x s planar work matrices (L and U inversions)
+      o[i].F12p = take(2 * s * u);
+      o[i].F12T = take(2 * s * u);
+      o[i].F21f = take(2 * s * u);
+      o[i].piv = off; off = align_up(off + s * 4, 256);
+      o[i].perm = off; off = align_up(off + s * 4, 256);
+      o[i].upd = off; off = align_up(off + u * 8, 256);
+      factor_bytes_ += sizeof(T) * 2.0 * (2.0 * s * s + 2.0 * s * u) + 8.0 * s;
+    }
+    arena_.alloc(off);
+    char* base = arena_.template as<char>();
+    for (size_t i = 0; i < nf; ++i) {
+      int64_t s = F[i].s(), u = F[i].u();
+      FrontDev<T>& f = fr_[i];
+      f.sep_begin = F[i].sep_begin;
+      f.s = (int32_t)s;
+      f.u = (int32_t)u;
+      f.upd = reinterpret_cast<const int64_t*>(base + o[i].upd);
+      f.LU = reinterpret_cast<T*>(base + o[i].LU);
+      f.UT = reinterpret_cast<T*>(base + o[i].UT);
+      f.Linv = reinterpret_cast<T*>(base + o[i].Linv);
+      f.UinvT = reinterpret_cast<T*>(base + o[i].UinvT);
+      f.F12w = reinterpret_cast<T*>(base + o[i].F12w);
+      f.F12p = reinterpret_cast<T*>(base + o[i].F12p);
+      f.F12T = reinterpret_cast<T*>(base + o[i].F12T);
+      f.F21w = reinterpret_cast<T*>(base + o[i].F21w);
+      f.F21f = reinterpret_cast<T*>(base + o[i].F21f);
+      f.C = reinterpret_cast<T*>(base + o[i].C);
+      f.W = reinterpret_cast<T*>(base + o[i].W);
+      f.piv = reinterpret_cast<int32_t*>(base + o[i].piv);
+      f.perm = reinterpret_cast<int32_t*>(base + o[i].perm);
+      f.pl_ss = s * s;
+      f.pl_us = u * s;
+      f.pl_uu = u * u;
+      if (u) MF_CUDA(cudaMemcpyAsync(base + o[i].upd, F[i].upd.data(), u * 8, cudaMemcpyHostToDevice, st_));
+      flops_ += 8.0 * ((double)s * s * s / 3.0 + (double)s * s * u + (double)s * u * u);
+    }
+    upload(fronts_d_, fr_, st_);
+    status_.alloc(sizeof(int32_t));
+    // ---- levels
+    int depth = 0;
+    for (auto& f : F) depth = std::max(depth, f.level + 1);
+    levels_.assign(depth, {});
+    for (auto& f : F) levels_[depth - 1 - f.level].push_back((int32_t)f.id);
+    std::vector<int32_t> all;
+    for (auto& lv : levels_) {
+      level_off_.push_back(all.size());
+      all.insert(all.end(), lv.begin(), lv.end());
+    }
+    upload(flists_d_, all, st_);
+    // ---- extend-add items (children of the fronts of each level; slot 0 / slot 1)
+    std::vector<ExtendAddItem<T>> items;
+    std::vector<int32_t> rel_all;
+    struct EaRef { size_t i0; int n; int maxuc; };
+    std::vector<std::array<EaRef, 2>> ea_refs(depth);
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> rel_spans;   // per item: rel offset
+    std::vector<size_t> rel_off_of_item;
+    for (int lv = 0; lv < depth; ++lv) {
+      for (int slot = 0; slot < 2; ++slot) {
+        EaRef r{items.size(), 0, 0};
+        for (int32_t fid : levels_[lv]) {
+          const auto& pf = F[fid];
+          if ((int)pf.children.size() <= slot) continue;
+          const auto& cf = F[pf.children[slot]];
+          // rel map: position of the child's I^u entries in the parent front
+          size_t ro = rel_all.size();
+          for (int64_t g : cf.upd) {
+            int64_t pos;
+            if (g >= pf.sep_begin && g < pf.sep_end) pos = g - pf.sep_begin;
+            else {
+              auto it = std::lower_bound(pf.upd.begin(), pf.upd.end(), g);
+              if (it == pf.upd.end() || *it != g) throw std::runtime_error("child update set not in parent front");
+              pos = pf.s() + (it - pf.upd.begin());
+            }
+            rel_all.push_back((int32_t)pos);
+          }
+          ExtendAddItem<T> it;
+          it.Cc = fr_[cf.id].C;
+          it.plane_c = cf.u() * cf.u();
+          it.rel = nullptr;
+          it.uc = (int32_t)cf.u();
+          it.parent = fid;
+          rel_off_of_item.push_back(ro);
+          items.push_back(it);
+          r.n++;
+          r.maxuc = std::max(r.maxuc, (int)cf.u());
+        }
+        ea_refs[lv][slot] = r;
+      }
+    }
+    upload(rel_, rel_all, st_);
+    for (size_t k = 0; k < items.size(); ++k) items[k].rel = rel_.template as<int32_t>() + rel_off_of_item[k];
+    upload(ea_d_, items, st_);
+
+    // ---- the factor program
+    std::vector<GemmDesc<T>> D;
+    std::vector<GemmTile> Tl;
+    struct PendingGemm { GemmRef r; };
+    for (int lv = 0; lv < depth; ++lv) {
+      const auto& L = levels_[lv];
+      const int nfl = (int)L.size();
+      int max_s = 0, max_u = 0, max_rows = 0;
+      for (int32_t fid : L) {
+        max_s = std::max<int>(max_s, (int)F[fid].s());
+        max_u = std::max<int>(max_u, (int)F[fid].u());
+      }
+      max_rows = max_s + max_u;
+      const int32_t* fl_lv = nullptr;   // resolved at run time
+      const size_t lvi = lv;
+      // assemble
+      push_op([this, lvi, nfl, max_rows](cudaStream_t st) {
+        launch_assemble_A<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, max_rows, A_.rowptr.template as<int64_t>(),
+                             A_.col64.template as<int64_t>(), A_.vals.template as<double>(), st);
+      });
+      nlaunch_factor_++;
+      for (int slot = 0; slot < 2; ++slot) {
+        EaRef r = ea_refs[lv][slot];
+        if (r.n == 0) continue;
+        push_op([this, r](cudaStream_t st) {
+          launch_extend_add<T>(ea_d_.template as<ExtendAddItem<T>>() + r.i0, r.n, fronts_d_.template as<FrontDev<T>>(), r.maxuc, st);
+        });
+        nlaunch_factor_++;
+      }
+      (void)fl_lv;
+      // blocked LU
+      for (int kb = 0; kb < max_s; kb += LU_NB) {
+        push_op([this, lvi, nfl, kb](cudaStream_t st) {
+          launch_panel_lu<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, kb, LU_NB, status_.template as<int32_t>(), st);
+        });
+        push_op([this, lvi, nfl, kb, max_s](cudaStream_t st) {
+          launch_panel_trsm<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, kb, LU_NB, max_s, st);
+        });
+        nlaunch_factor_ += 2;
+        std::vector<GemmDesc<T>> batch;
+        for (int32_t fid : L) {
+          const FrontDev<T>& f = fr_[fid];
+          int s = f.s;
+          int w = std::min(LU_NB, s - kb);
+          int rem = s - kb - w;
+          if (kb >= s || rem <= 0) continue;
+          PMat<T> a{f.LU + (int64_t)(kb + w) * s + kb, f.pl_ss, s};
+          PMat<T> b{f.LU + (int64_t)kb * s + kb + w, f.pl_ss, s};
+          PMat<T> c{f.LU + (int64_t)(kb + w) * s + kb + w, f.pl_ss, s};
+          batch.push_back(gd(rem, rem, w, 0, 0, T(-1), T(1), a, b, c));
+        }
+        GemmRef g = add_gemm(D, Tl, batch);
+        if (g.nt) {
+          push_op([this, g](cudaStream_t st) {
+            launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt, st);
+          }, ref_flops(D, g));
+          nlaunch_factor_++;
+        }
+      }
+      push_op([this, lvi, nfl, max_s, max_u](cudaStream_t st) {
+        launch_post_lu<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, max_s, max_u, st);
+      });
+      nlaunch_factor_ += 3;
+      for (int which = 0; which < 2; ++which) {
+        push_op([this, lvi, nfl, max_s, which](cudaStream_t st) {
+          launch_trinv_diag<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, max_s, which, nullptr, st);
+        });
+        nlaunch_factor_++;
+      }
+      // recursive 2 x 2 block inversion of the lower triangles, block 64 -> 128 -> ...
+      for (int h = 64; h < max_s; h *= 2) {
+        std::vector<GemmDesc<T>> b1, b2;
+        for (int32_t fid : L) {
+          const FrontDev<T>& f = fr_[fid];
+          int s = f.s;
+          for (int a0 = 0; a0 + h < s; a0 += 2 * h) {
+            int c0 = a0 + h, c1 = std::min(a0 + 2 * h, s);
+            int mc = c1 - c0;
+            for (int which = 0; which < 2; ++which) {
+              T* Tm = which == 0 ? f.LU : f.UT;
+              T* X = which == 0 ? f.Linv : f.UinvT;
+              T* W = f.W + (which == 0 ? 0 : 2 * f.pl_ss);   // separate work matrix per triangle
+              int64_t woff = (int64_t)c0 * s + a0;
+              PMat<T> tca{Tm + (int64_t)c0 * s + a0, f.pl_ss, s};
+              PMat<T> xaa{X + (int64_t)a0 * s + a0, f.pl_ss, s};
+              PMat<T> w{W + woff, f.pl_ss, s};
+              PMat<T> xcc{X + (int64_t)c0 * s + c0, f.pl_ss, s};
+              PMat<T> xca{X + (int64_t)c0 * s + a0, f.pl_ss, s};
+              b1.push_back(gd(mc, h, h, 0, 0, T(1), T(0), tca, xaa, w));
+              b2.push_back(gd(mc, h, mc, 0, 0, T(-1), T(0), xcc, w, xca));
+            }
+          }
+        }
+        GemmRef g1 = add_gemm(D, Tl, b1);
+        GemmRef g2 = add_gemm(D, Tl, b2);
+        if (g1.nt) {
+          push_op([this, g1](cudaStream_t st) {
+            launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g1.d0, tiles_d_.template as<GemmTile>() + g1.t0, g1.nt, st);
+          }, ref_flops(D, g1));
+          push_op([this, g2](cudaStream_t st) {
+            launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g2.d0, tiles_d_.template as<GemmTile>() + g2.t0, g2.nt, st);
+          }, ref_flops(D, g2));
+          nlaunch_factor_ += 2;
+        }
+      }
+      // F12^T <- (P^T F12)^T L^-T  and  F21 <- F21 U^-1
+      {
+        std::vector<GemmDesc<T>> b;
+        for (int32_t fid : L) {
+          const FrontDev<T>& f = fr_[fid];
+          if (f.u == 0) continue;
+          b.push_back(gd(f.u, f.s, f.s, 0, 1, T(1), T(0), PMat<T>{f.F12p, f.pl_us, f.s}, PMat<T>{f.Linv, f.pl_ss, f.s},
+                         PMat<T>{f.F12T, f.pl_us, f.s}));
+          b.push_back(gd(f.u, f.s, f.s, 0, 1, T(1), T(0), PMat<T>{f.F21w, f.pl_us, f.s},
+                         PMat<T>{f.UinvT, f.pl_ss, f.s}, PMat<T>{f.F21f, f.pl_us, f.s}));
+        }
+        GemmRef g = add_gemm(D, Tl, b);
+        if (g.nt) {
+          push_op([this, g](cudaStream_t st) {
+            launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt, st);
+          }, ref_flops(D, g));
+          nlaunch_factor_++;
+        }
+      }
+      // Schur complement C = F22 - F21 F12   (Sec. 2 step 4)
+      {
+        std::vector<GemmDesc<T>> b;
+        for (int32_t fid : L) {
+          const FrontDev<T>& f = fr_[fid];
+          if (f.u == 0 || F[fid].parent < 0) continue;
+          b.push_back(gd(f.u, f.u, f.s, 0, 1, T(-1), T(1), PMat<T>{f.F21f, f.pl_us, f.s},
+                         PMat<T>{f.F12T, f.pl_us, f.s}, PMat<T>{f.C, f.pl_uu, f.u}));
+        }
+        GemmRef g = add_gemm(D, Tl, b);
+        if (g.nt) {
+          push_op([this, g](cudaStream_t st) {
+            launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt, st);
+          }, ref_flops(D, g));
+          nlaunch_factor_++;
+        }
+      }
+    }
+    upload(descs_d_, D, st_);
+    upload(tiles_d_, Tl, st_);
+    MF_CUDA(cudaStreamSynchronize(st_));
+  }
+
+  SolveProg& solve_prog(int nrhs) {
+    auto it = sprog_.find(nrhs);
+    if (it != sprog_.end()) return *it->second;
+    auto sp = std::make_unique<SolveProg>();
+    const auto& F = an_.fronts;
+    const int64_t n = an_.n;
+    sp->X.alloc(sizeof(T) * 2 * n * nrhs);
+    // per-front temps ta (s x nrhs), tb (s x nrhs), tu (u x nrhs)
+    std::vector<size_t> ta(F.size()), tb(F.size()), tu(F.size());
+    size_t off = 0;
+    for (size_t i = 0; i < F.size(); ++i) {
+      ta[i] = off; off = align_up(off + sizeof(T) * 2 * F[i].s() * nrhs, 256);
+      tb[i] = off; off = align_up(off + sizeof(T) * 2 * F[i].s() * nrhs, 256);
+      tu[i] = off; off = align_up(off + sizeof(T) * 2 * F[i].u() * nrhs, 256);
+    }
+    sp->tmp.alloc(off);
+    char* tb0 = sp->tmp.template as<char>();
+    auto P = [&](size_t o) { return reinterpret_cast<T*>(tb0 + o); };
+    // pointer tables per level: ta, tb, tu in level order
+    std::vector<T*> ptab;
+    std::vector<size_t> poff_ta(levels_.size()), poff_tb(levels_.size()), poff_tu(levels_.size());
+    for (size_t lv = 0; lv < levels_.size(); ++lv) {
+      poff_ta[lv] = ptab.size();
+      for (int32_t f : levels_[lv]) ptab.push_back(P(ta[f]));
+      poff_tb[lv] = ptab.size();
+      for (int32_t f : levels_[lv]) ptab.push_back(P(tb[f]));
+      poff_tu[lv] = ptab.size();
+      for (int32_t f : levels_[lv]) ptab.push_back(P(tu[f]));
+    }
+    upload(sp->ptrs, ptab, st_);
+    T* const* pt = sp->ptrs.template as<T* const>();
+    std::vector<GemmDesc<T>> D;
+    std::vector<GemmTile> Tl;
+    T* X = sp->X.template as<T>();
+    const int64_t xpl = n * nrhs;
+    SolveProg* spp = sp.get();
+    auto gemm_op = [&](const std::vector<GemmDesc<T>>& b) {
+      GemmRef g = add_gemm(D, Tl, b);
+      if (g.nt) {
+        sp->ops.push_back([spp, g](cudaStream_t st) {
+          launch_gemm<T>(spp->descs.template as<GemmDesc<T>>() + g.d0, spp->tiles.template as<GemmTile>() + g.t0, g.nt, st);
+        });
+        sp->nlaunch++;
+      }
+    };
+    // forward: leaves -> root
+    for (size_t lv = 0; lv < levels_.size(); ++lv) {
+      const auto& L = levels_[lv];
+      int nfl = (int)L.size(), max_s = 0, max_u = 0;
+      for (int32_t f : L) { max_s = std::max<int>(max_s, fr_[f].s); max_u = std::max<int>(max_u, fr_[f].u); }
+      size_t lvi = lv;
+      sp->ops.push_back([this, lvi, nfl, max_s, X, xpl, nrhs, pt, poff_ta](cudaStream_t st) {
+        launch_fwd_gather<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, max_s, X, xpl, nrhs, pt + poff_ta[lvi], st);
+      });
+      sp->nlaunch++;
+      std::vector<GemmDesc<T>> b1, b2;
+      for (int32_t f : L) {
+        const FrontDev<T>& fd = fr_[f];
+        int64_t spl = (int64_t)fd.s * nrhs, upl = (int64_t)fd.u * nrhs;
+        b1.push_back(gd(fd.s, nrhs, fd.s, 0, 0, T(1), T(0), PMat<T>{fd.Linv, fd.pl_ss, fd.s},
+                        PMat<T>{P(ta[f]), spl, nrhs}, PMat<T>{P(tb[f]), spl, nrhs}));
+        if (fd.u)
+          b2.push_back(gd(fd.u, nrhs, fd.s, 0, 0, T(-1), T(0), PMat<T>{fd.F21f, fd.pl_us, fd.s},
+                          PMat<T>{P(tb[f]), spl, nrhs}, PMat<T>{P(tu[f]), upl, nrhs}));
+      }
+      gemm_op(b1);
+      sp->ops.push_back([this, lvi, nfl, max_s, X, xpl, nrhs, pt, poff_tb](cudaStream_t st) {
+        launch_scatter_sep<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, max_s, X, xpl, nrhs, pt + poff_tb[lvi], st);
+      });
+      sp->nlaunch++;
+      gemm_op(b2);
+      if (max_u) {
+        sp->ops.push_back([this, lvi, nfl, max_u, X, xpl, nrhs, pt, poff_tu](cudaStream_t st) {
+          launch_scatter_add_upd<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, max_u, X, xpl, nrhs,
+                                    pt + poff_tu[lvi], st);
+        });
+        sp->nlaunch++;
+      }
+    }
+    // backward: root -> leaves
+    for (size_t lvr = levels_.size(); lvr-- > 0;) {
+      const auto& L = levels_[lvr];
+      int nfl = (int)L.size(), max_s = 0, max_u = 0;
+      for (int32_t f : L) { max_s = std::max<int>(max_s, fr_[f].s); max_u = std::max<int>(max_u, fr_[f].u); }
+      size_t lvi = lvr;
+      if (max_u) {
+        sp->ops.push_back([this, lvi, nfl, max_u, X, xpl, nrhs, pt, poff_tu](cudaStream_t st) {
+          launch_gather_upd<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, max_u, X, xpl, nrhs, pt + poff_tu[lvi],
+                               st);
+        });
+        sp->nlaunch++;
+      }
+      sp->ops.push_back([this, lvi, nfl, max_s, X, xpl, nrhs, pt, poff_tb](cudaStream_t st) {
+        launch_gather_sep<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, max_s, X, xpl, nrhs, pt + poff_tb[lvi], st);
+      });
+      sp->nlaunch++;
+      std::vector<GemmDesc<T>> b1, b2;
+      for (int32_t f : L) {
+        const FrontDev<T>& fd = fr_[f];
+        int64_t spl = (int64_t)fd.s * nrhs, upl = (int64_t)fd.u * nrhs;
+        if (fd.u)
+          b1.push_back(gd(fd.s, nrhs, fd.u, 1, 0, T(-1), T(1), PMat<T>{fd.F12T, fd.pl_us, fd.s},
+                          PMat<T>{P(tu[f]), upl, nrhs}, PMat<T>{P(tb[f]), spl, nrhs}));
+        b2.push_back(gd(fd.s, nrhs, fd.s, 1, 0, T(1), T(0), PMat<T>{fd.UinvT, fd.pl_ss, fd.s},
+                        PMat<T>{P(tb[f]), spl, nrhs}, PMat<T>{P(ta[f]), spl, nrhs}));
+      }
+      gemm_op(b1);
+      gemm_op(b2);
+      sp->ops.push_back([this, lvi, nfl, max_s, X, xpl, nrhs, pt, poff_ta](cudaStream_t st) {
+        launch_scatter_sep<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, max_s, X, xpl, nrhs, pt + poff_ta[lvi], st);
+      });
+      sp->nlaunch++;
+    }
+    upload(sp->descs, D, st_);
+    upload(sp->tiles, Tl, st_);
+    MF_CUDA(cudaStreamSynchronize(st_));
+    auto& ref = *sp;
+    sprog_[nrhs] = std::move(sp);
+    return ref;
+  }
+
+  DevMem rel_;
+};
+
+}  // namespace
+
+std::unique_ptr<EngineBase> make_engine_c64(const Analysis& an, const DeviceMatrix& A, cudaStream_t st) {
+  return std::make_unique<DenseEngine<float>>(an, A, st);
+}
+std::unique_ptr<EngineBase> make_engine_c128(const Analysis& an, const DeviceMatrix& A, cudaStream_t st) {
+  return std::make_unique<DenseEngine<double>>(an, A, st);
+}
+
+}  // namespace mf

@@ -1,0 +1,91 @@
+// Host-callable launchers of the CUDA kernels (all asynchronous on `st`).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mf_device.h"
+
+namespace mf {
+
+// Number of kernel launches issued by this library since it was loaded.
+int64_t launch_count();
+void count_launches(int k);
+
+// Batched planar complex GEMM over a tile list (SIMT).
+template <typename T>
+void launch_gemm(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, cudaStream_t st);
+// Tile size of the SIMT GEMM (both dimensions).
+constexpr int GEMM_TILE = 64;
+
+// Dense front assembly and extend-add (Sec. 2 step 1).
+template <typename T>
+void launch_assemble_A(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int maxrows, const int64_t* rowptr,
+                       const int64_t* colind, const double* vals, cudaStream_t st);
+template <typename T>
+void launch_extend_add(const ExtendAddItem<T>* d_items, int nitems, const FrontDev<T>* d_fronts, int max_uc,
+                       cudaStream_t st);
+
+// Partial LU of F11 with partial pivoting (Sec. 2 step 2): one panel step.
+template <typename T>
+void launch_panel_lu(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int kb, int nb, int32_t* status,
+                     cudaStream_t st);
+template <typename T>
+void launch_panel_trsm(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int kb, int nb, int max_s,
+                       cudaStream_t st);
+
+// After the LU: UT <- U^T (lower, zero above), pivots applied to F12^T columns,
+// pivots turned into a gather permutation.
+template <typename T>
+void launch_post_lu(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int max_s, int max_u, cudaStream_t st);
+
+// Diagonal-block inverses of a lower triangular matrix (block 64) into X.
+// which = 0: T = strict lower of LU with unit diagonal, X = Linv (stored in W2 slot)
+// which = 1: T = UT, X = UinvT
+template <typename T>
+void launch_trinv_diag(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int max_s, int which, T* const* d_X,
+                       cudaStream_t st);
+
+// Gather / scatter of right-hand sides between the global vector and front work.
+template <typename T>
+void launch_fwd_gather(const FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int max_s, const T* X, int64_t xpl,
+                       int nrhs, T* const* d_tmp, cudaStream_t st);
+template <typename T>
+void launch_scatter_sep(const FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int max_s, T* X, int64_t xpl,
+                        int nrhs, T* const* d_src, cudaStream_t st);
+template <typename T>
+void launch_scatter_add_upd(const FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int max_u, T* X,
+                            int64_t xpl, int nrhs, T* const* d_src, cudaStream_t st);
+template <typename T>
+void launch_gather_upd(const FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int max_u, const T* X,
+                       int64_t xpl, int nrhs, T* const* d_dst, cudaStream_t st);
+template <typename T>
+void launch_gather_sep(const FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int max_s, const T* X,
+                       int64_t xpl, int nrhs, T* const* d_dst, cudaStream_t st);
+
+// Conversions between interleaved complex128 (column-major, original numbering)
+// and planar T (row-major N x nrhs, new numbering).
+template <typename T>
+void launch_to_planar(const double* src, int64_t ld, int64_t n, int nrhs, const int64_t* perm, T* dst, int64_t pl,
+                      cudaStream_t st);
+template <typename T>
+void launch_from_planar(const T* src, int64_t pl, int64_t n, int nrhs, const int64_t* perm, double* dst, int64_t ld,
+                        cudaStream_t st);
+
+// FP64 sparse residual and Krylov helpers (interleaved complex128, column-major n x nrhs).
+void launch_spmv_residual(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                          const double* x, const double* b, double* r, int nrhs, int64_t ld, cudaStream_t st);
+void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals, const double* x,
+                 double* y, int nrhs, int64_t ld, cudaStream_t st);
+// out[c] = sum_i conj(V[i,c]) W[i,c]  (complex, per column), written as (re, im) pairs
+void launch_coldot(int64_t n, int nrhs, const double* V, int64_t ldv, const double* W, int64_t ldw, double* out,
+                   cudaStream_t st);
+// W[:,c] -= h[c] V[:,c]  (complex h per column)
+void launch_colaxpy(int64_t n, int nrhs, const double* h, const double* V, int64_t ldv, double* W, int64_t ldw,
+                    double sign, cudaStream_t st);
+// Y[:,c] = X[:,c] * s[c] (complex s) ; Y may alias X
+void launch_colscale(int64_t n, int nrhs, const double* s, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                     cudaStream_t st);
+// out[c] = ||X[:,c]||_2^2
+void launch_colnorm2(int64_t n, int nrhs, const double* X, int64_t ldx, double* out, cudaStream_t st);
+
+}  // namespace mf

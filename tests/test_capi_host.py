@@ -1,0 +1,98 @@
+"""C-ABI tests that need no GPU: the library loads, exports every declared
+symbol, validates its arguments, and its host analysis equals the oracle's
+bit for bit (nested dissection, tree, update sets, cluster trees, neighbours)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle.analysis import analyze, front_neighbours
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_2007_00202_gb300 import build
+    build.build()
+    import paper_2007_00202_gb300 as pkg
+    return pkg
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mf.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int64_t|int|void|const char\*)\s+(mf_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_every_declared_symbol(g):
+    L = g.lib()
+    names = _declared()
+    assert "mf_analyze" in names and "mf_factor" in names and "mf_solve" in names
+    for n in names:
+        assert hasattr(L, n), n
+    from paper_2007_00202_gb300.mf import SIGNATURES
+    assert set(SIGNATURES) <= set(names)
+
+
+def test_argument_errors(g):
+    from paper_2007_00202_gb300.mf import MfError
+    p = w.helmholtz7(4, 8)
+    with pytest.raises(MfError) as e:
+        g.mf_analyze(p.n, p.rowptr, np.full_like(p.colind, p.n + 5), p.vals, p.coords)
+    assert e.value.code == -1
+    h = g.analyze_problem(p)
+    with pytest.raises(MfError) as e:
+        h.mf_solve(np.ones(p.n, complex))
+    assert e.value.code == -2          # solve before factor
+    o = g.mf_options_init()
+    assert (o.leaf_size, o.nmin_sep, o.gmres_restart, o.rtol) == (64, 1024, 30, 1e-8)
+
+
+def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True):
+    an = analyze(p, leaf, nmin, hleaf)
+    h = g.analyze_problem(p, leaf_size=leaf, nmin_sep=nmin, hodbf_leaf=hleaf)
+    e = h.mf_analysis_export()
+    assert np.array_equal(e["perm"], an.perm)
+    assert len(e["parent"]) == len(an.fronts)
+    for i, f in enumerate(an.fronts):
+        assert e["parent"][i] == f.parent
+        assert tuple(e["sep"][i]) == (f.sep_begin, f.sep_end)
+        assert bool(e["compressed"][i]) == f.compressed
+        assert np.array_equal(e["upd_idx"][e["upd_ptr"][i]:e["upd_ptr"][i + 1]], f.upd)
+        if f.compressed:
+            th, f22 = h.mf_front_trees(f.id)
+            assert th == [list(map(tuple, l)) for l in f.th_tree]
+            assert f22 == [list(map(tuple, l)) for l in f.f22_tree]
+            if check_nn:
+                nn = h.mf_front_neighbours(f.id, knn, f.s, f.u)
+                on = front_neighbours(an, f, knn)
+                S = range(f.sep_begin, f.sep_end)
+                U = [int(x) for x in f.upd]
+                assert nn["nn11"] == [on["nn11"][x] for x in S]
+                assert nn["nn12"] == [on["nn12"][x] for x in S]
+                assert nn["nn21"] == [on["nn21"][x] for x in U]
+                assert nn["nn22"] == [on["nn22"][x] for x in U]
+    return an
+
+
+def test_analysis_bit_exact_helmholtz(g):
+    an = _compare(g, w.helmholtz7(16, 8), 64, 128, 64)
+    assert sum(f.compressed for f in an.fronts) == 2
+
+
+def test_analysis_bit_exact_odd_sizes(g):
+    _compare(g, w.helmholtz7(13, 8), 20, 40, 16, knn=5)
+
+
+def test_analysis_bit_exact_yee(g):
+    _compare(g, w.yee_maxwell(8, 10), 32, 60, 16)
+
+
+def test_analysis_bit_exact_64cube_structure(g):
+    # full-size configuration of the 64^3 workload: ordering and tree only
+    p = w.helmholtz7(64, 10)
+    an = _compare(g, p, 64, 1024, 64, check_nn=False)
+    assert len(an.fronts) == 4817
+    assert sum(f.compressed for f in an.fronts) == 5
