@@ -152,6 +152,41 @@ typedef struct {
 int mf_profile(mf_handle* h, int32_t enable);
 int mf_profile_read(const mf_handle* h, mf_kernel_profile_t* out);
 
+/*
+ * Component entry point of the front-update GEMM kernels (the Schur update
+ * C = F22 - F21 F12 of Sec. 2 step 4 and the triangular products before it).
+ * One planar complex64 product on device memory:
+ *   C = alpha * A * B^T + beta * C,  A: m x k, B: n x k, C: m x n, all row-major,
+ *   each matrix given by its real plane (device pointer), leading dimension ld and
+ *   the element offset pl of its imaginary plane (im = re + pl).
+ * engine 0: SIMT FP32 kernel; engine 1: tcgen05 kind::tf32 tensor-core kernel, one
+ * TF32 pass; engine 2: the same kernel in split precision (three TF32 passes,
+ * hi*hi + hi*lo + lo*hi), the form used by mf_factor.  Engines 1 and 2 require
+ * lda, ldb, pla, plb multiples of 4 and 16-byte aligned planes.
+ * Runs on `stream` and waits for it.  Errors: MF_ERR_ARG, MF_ERR_TIMEOUT, MF_ERR_CUDA.
+ */
+int mf_gemm_c64(int32_t engine, int32_t m, int32_t n, int32_t k, const float* A, int64_t lda, int64_t pla,
+                const float* B, int64_t ldb, int64_t plb, float* C, int64_t ldc, int64_t plc, float alpha, float beta,
+                void* stream);
+
+/*
+ * Component entry point of the batched row interpolative decomposition (Sec. 3):
+ * for each of nmat complex64 matrices M_q (m x n), a column-pivoted Householder
+ * QR of M_q^T truncated at the first k with |R_{k+1,k+1}| <= tol |R_11| (at most
+ * kmax = min(m, n, max_rank > 0 ? max_rank : n) steps) gives the skeleton rows
+ * I_q (|I_q| = rank_q) and U_q with M_q ~= U_q M_q(I_q, :) and U_q(I_q, :) = I.
+ * Device buffers:
+ *   M     nmat matrices back to back, each a real m x n row-major plane followed by
+ *         its imaginary plane (2 m n floats per matrix); not modified
+ *   U     out, nmat blocks of 2 m kmax floats (real then imaginary m x kmax row-major;
+ *         columns >= rank_q are unspecified)
+ *   sk    out, nmat x kmax int32 (first rank_q entries valid), rank out, nmat int32.
+ * Scratch of 2 m n floats per matrix is allocated by the call.  Runs on `stream`
+ * and waits for it.  Errors: MF_ERR_ARG (sizes: n <= 8192, m <= 2048), MF_ERR_OOM, MF_ERR_CUDA.
+ */
+int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol, int32_t max_rank, float* U,
+                  int32_t* sk, int32_t* rank, void* stream);
+
 /* Kernel launches issued by the library since it was loaded (all handles, all streams). */
 int64_t mf_launch_counter(void);
 

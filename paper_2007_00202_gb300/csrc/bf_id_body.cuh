@@ -1,0 +1,186 @@
+// Device body of the batched row interpolative decomposition (Sec. 3), shared
+// by the batched kernel and its fixed-scratch variant.  One CTA (256 threads)
+// per matrix; dynamic shared memory of sizeof(T) * (2 n + m) + 4 m bytes.
+//
+// Row ID of M (m x n): column-pivoted Householder QR of M^T, truncated at the
+// first k with |R_{k+1,k+1}| <= tol |R_11| (or k = kmax), then
+// U = P [I; (R11^-1 R12)^T].  The columns of M^T are the rows of M, which are
+// contiguous: every reflection updates each remaining row with one dot product
+// and one axpy (a warp per row), and the remaining row norms are recomputed in
+// the same pass.  Pivot: largest remaining norm, lowest position on ties.
+#pragma once
+#include "bf_kernels.h"
+
+namespace mf {
+
+template <typename T>
+__device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t max_rank) {
+  const int m = jb.m, n = jb.n;
+  extern __shared__ unsigned char smraw[];
+  T* vr = reinterpret_cast<T*>(smraw);       // Householder vector, n entries (re, im)
+  T* vi = vr + n;
+  T* nrm = vi + n;                           // remaining squared norms, by position
+  int* perm = reinterpret_cast<int*>(nrm + m);
+  __shared__ T red_v[8];
+  __shared__ int red_i[8];
+  __shared__ T sh_alpha_r, sh_alpha_i, sh_scale, sh_ref;
+  __shared__ int sh_p, sh_stop;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  T* Wr = jb.work;
+  T* Wi = jb.work + jb.wplane;
+  // copy M to the work matrix (ld = n) and compute the row norms
+  for (int r = warp; r < m; r += nw) {
+    const T* mr = jb.M + (int64_t)r * jb.ld;
+    const T* mi = mr + jb.plane;
+    T s = 0;
+    for (int c = lane; c < n; c += 32) {
+      T a = mr[c], b = mi[c];
+      Wr[(int64_t)r * n + c] = a;
+      Wi[(int64_t)r * n + c] = b;
+      s += a * a + b * b;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) { nrm[r] = s; perm[r] = r; }
+  }
+  int kmax = m < n ? m : n;
+  if (max_rank > 0 && max_rank < kmax) kmax = max_rank;
+  if (tid == 0) sh_stop = 0;
+  __syncthreads();
+  int rank = 0;
+  for (int k = 0; k < kmax; ++k) {
+    // pivot: largest remaining norm among positions k..m-1
+    T best = T(-1);
+    int bi = m;
+    for (int q = k + tid; q < m; q += blockDim.x)
+      if (nrm[q] > best) { best = nrm[q]; bi = q; }
+    for (int o = 16; o > 0; o >>= 1) {
+      T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      best = red_v[0]; bi = red_i[0];
+      for (int w = 1; w < nw; ++w)
+        if (red_v[w] > best || (red_v[w] == best && red_i[w] < bi)) { best = red_v[w]; bi = red_i[w]; }
+      T nu = sqrt(best > T(0) ? best : T(0));
+      if (k == 0) sh_ref = nu;
+      if (sh_ref == T(0) || nu <= tol * sh_ref) sh_stop = 1;
+      else {
+        sh_p = bi;
+        T t = nrm[k]; nrm[k] = nrm[bi]; nrm[bi] = t;
+        int ti = perm[k]; perm[k] = perm[bi]; perm[bi] = ti;
+      }
+    }
+    __syncthreads();
+    if (sh_stop) break;
+    // Householder vector from the pivot row's coordinates k..n-1
+    const int pr = perm[k];
+    T* xr = Wr + (int64_t)pr * n;
+    T* xi = Wi + (int64_t)pr * n;
+    T s2 = 0;
+    for (int c = k + tid; c < n; c += blockDim.x) {
+      T a = xr[c], b = xi[c];
+      vr[c] = a; vi[c] = b;
+      s2 += a * a + b * b;
+    }
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) red_v[warp] = s2;
+    __syncthreads();
+    if (tid == 0) {
+      T tot = 0;
+      for (int w = 0; w < nw; ++w) tot += red_v[w];
+      T nx = sqrt(tot);
+      T x0r = vr[k], x0i = vi[k];
+      T ax0 = sqrt(x0r * x0r + x0i * x0i);
+      T phr = ax0 > T(0) ? x0r / ax0 : T(1), phi = ax0 > T(0) ? x0i / ax0 : T(0);
+      T alr = -phr * nx, ali = -phi * nx;
+      vr[k] = x0r - alr;
+      vi[k] = x0i - ali;
+      T vv = tot - (x0r * x0r + x0i * x0i) + vr[k] * vr[k] + vi[k] * vi[k];
+      sh_scale = vv > T(0) ? T(2) / vv : T(0);
+      sh_alpha_r = alr;
+      sh_alpha_i = ali;
+    }
+    __syncthreads();
+    // reflected pivot row: alpha e_k
+    for (int c = k + tid; c < n; c += blockDim.x) {
+      xr[c] = c == k ? sh_alpha_r : T(0);
+      xi[c] = c == k ? sh_alpha_i : T(0);
+    }
+    // apply H to the remaining rows, recompute their norms beyond coordinate k
+    const T sc = sh_scale;
+    for (int q = k + 1 + warp; q < m; q += nw) {
+      T* yr = Wr + (int64_t)perm[q] * n;
+      T* yi = Wi + (int64_t)perm[q] * n;
+      T dr = 0, di = 0;   // v^H y
+      for (int c = k + lane; c < n; c += 32) {
+        T a = vr[c], b = vi[c], p = yr[c], r = yi[c];
+        dr += a * p + b * r;
+        di += a * r - b * p;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        dr += __shfl_xor_sync(0xffffffffu, dr, o);
+        di += __shfl_xor_sync(0xffffffffu, di, o);
+      }
+      dr *= sc;
+      di *= sc;
+      T s = 0;
+      for (int c = k + lane; c < n; c += 32) {
+        T a = vr[c], b = vi[c];
+        T p = yr[c] - (a * dr - b * di);
+        T r = yi[c] - (a * di + b * dr);
+        yr[c] = p;
+        yi[c] = r;
+        if (c > k) s += p * p + r * r;
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) nrm[q] = s;
+    }
+    __syncthreads();
+    rank = k + 1;
+  }
+  __syncthreads();
+  // outputs: rank, skeleton (first rank pivots), U = P [I; (R11^-1 R12)^T]
+  const int r = rank;
+  if (tid == 0) *jb.rank = r;
+  for (int b = tid; b < r; b += blockDim.x) jb.sk[b] = perm[b];
+  const int ldu = jb.ldu;
+
+  T* Ur = jb.U;
+  T* Ui = jb.U + jb.uplane;
+  // identity rows
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    int b = e / r, c = e % r;
+    Ur[(int64_t)perm[b] * ldu + c] = b == c ? T(1) : T(0);
+    Ui[(int64_t)perm[b] * ldu + c] = T(0);
+  }
+  // non-pivot rows: back substitution with R11 (R11[a][b] = work[perm[b]][a], a <= b)
+  for (int j = r + tid; j < m; j += blockDim.x) {
+    const int q = perm[j];
+    const T* yr = Wr + (int64_t)q * n;
+    const T* yi = Wi + (int64_t)q * n;
+    T* ur = Ur + (int64_t)q * ldu;
+    T* ui = Ui + (int64_t)q * ldu;
+    for (int b = r - 1; b >= 0; --b) {
+      T accr = yr[b], acci = yi[b];
+      for (int c = b + 1; c < r; ++c) {
+        const int pc = perm[c];
+        T Rr = Wr[(int64_t)pc * n + b], Ri = Wi[(int64_t)pc * n + b];
+        T tr = ur[c], ti = ui[c];
+        accr -= Rr * tr - Ri * ti;
+        acci -= Rr * ti + Ri * tr;
+      }
+      const int pb = perm[b];
+      T dr = Wr[(int64_t)pb * n + b], di = Wi[(int64_t)pb * n + b];
+      T den = dr * dr + di * di;
+      if (den == T(0)) den = T(1);
+      ur[b] = (accr * dr + acci * di) / den;
+      ui[b] = (acci * dr - accr * di) / den;
+    }
+  }
+}
+
+
+}  // namespace mf

@@ -1,0 +1,116 @@
+// Device job descriptors and launchers of the butterfly-path kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace mf {
+
+// One row interpolative decomposition (Sec. 3) of M (m x n, planar, row-major, ld).
+// Outputs: *rank, sk[0..rank) (skeleton rows), U (m x rank used, ld = ldu).
+// work: scratch of m x n per plane (overwritten by the QR).
+template <typename T>
+struct IdJob {
+  const T* M;
+  int64_t plane, ld;
+  int32_t m, n;
+  T* U;
+  int64_t uplane;
+  int32_t ldu;
+  int32_t* sk;
+  int32_t* rank;
+  T* work;
+  int64_t wplane;
+};
+
+// A group of sketch columns: rows [a, b) x cols [c0, c0 + w) of a row-major
+// matrix; identity columns (w == b - a) or counter-based Gaussians keyed by key.
+struct SketchGroup {
+  int64_t a, b;
+  int32_t c0, w;
+  int32_t key;
+  int32_t identity;
+};
+
+// dst[i][c] = src[rows[i]][c0 + c]
+template <typename T>
+struct GatherJob {
+  const T* src;
+  int64_t splane, sld;
+  const int32_t* rows;
+  int32_t c0;
+  int32_t nrows, ncols;
+  T* dst;
+  int64_t dplane, dld;
+};
+
+// A dense contribution block of a child and the map front position -> child position (-1 if absent).
+template <typename T>
+struct DenseKid {
+  const T* C;
+  int64_t plane, ld;
+  const int32_t* inv;
+};
+
+template <typename T>
+struct FrontCtx {
+  int64_t sep_begin;
+  int32_t s, u;
+  const int64_t* upd;
+  int32_t nkids;
+  DenseKid<T> kids[2];
+};
+
+// Entries of the front at (X[a], Y[b]) (front-local positions): A-part (if with_A) + dense children.
+template <typename T>
+struct FrontEntryJob {
+  int32_t ctx;
+  const int32_t* X;
+  const int32_t* Y;
+  int32_t nx, ny;
+  T* dst;
+  int64_t dplane, dld;
+  int32_t with_A;
+  int32_t accumulate;
+};
+
+// dst[rows[a]][cols[b]] += sign * src[a][b]
+template <typename T>
+struct PlaceJob {
+  const T* src;
+  int64_t splane, sld;
+  const int32_t* rows;
+  const int32_t* cols;
+  int32_t nr, nc;
+  T* dst;
+  int64_t dplane, dld;
+  T sign;
+};
+
+template <typename T>
+struct InvJob {
+  const T* A;
+  int64_t aplane, lda;
+  int32_t n;
+  T* X;
+  int64_t xplane, ldx;
+};
+
+template <typename T>
+int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st);
+template <typename T>
+void launch_sketch(const SketchGroup* d_groups, int ngroups, int max_elems, T* out, int64_t plane, int ld,
+                   cudaStream_t st);
+template <typename T>
+void launch_gather_rows(const GatherJob<T>* d_jobs, int njobs, int64_t max_elems, cudaStream_t st);
+template <typename T>
+void launch_front_entries(const FrontEntryJob<T>* d_jobs, int njobs, int64_t max_elems, const FrontCtx<T>* d_ctx,
+                          const int64_t* rowptr, const int32_t* colind, const double* vals, cudaStream_t st);
+template <typename T>
+void launch_place(const PlaceJob<T>* d_jobs, int njobs, int64_t max_elems, cudaStream_t st);
+template <typename T>
+int launch_small_inverse(const InvJob<T>* d_jobs, int njobs, int max_n, int32_t* status, cudaStream_t st);
+
+}  // namespace mf

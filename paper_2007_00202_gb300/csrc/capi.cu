@@ -14,6 +14,7 @@
 
 #include "../../include/mf.h"
 #include "analysis.h"
+#include "bf_kernels.h"
 #include "engine.h"
 
 using mf::CudaError;
@@ -477,6 +478,77 @@ int mf_profile_read(const mf_handle* h, mf_kernel_profile_t* out) {
     out->flops = h->eng->prof.flops;
   }
   return MF_OK;
+}
+
+int mf_gemm_c64(int32_t engine, int32_t m, int32_t n, int32_t k, const float* A, int64_t lda, int64_t pla,
+                const float* B, int64_t ldb, int64_t plb, float* C, int64_t ldc, int64_t plc, float alpha, float beta,
+                void* stream) {
+  if (m <= 0 || n <= 0 || k <= 0 || !A || !B || !C || lda < k || ldb < k || ldc < n)
+    return fail(nullptr, MF_ERR_ARG, "invalid GEMM arguments");
+  if (engine < 0 || engine > 2) return fail(nullptr, MF_ERR_ARG, "engine must be 0, 1 or 2");
+  if (engine >= 1 && ((lda | ldb | pla | plb) % 4 != 0 || ((uintptr_t)A | (uintptr_t)B) % 16 != 0))
+    return fail(nullptr, MF_ERR_ARG, "tensor-core GEMM needs 16-byte aligned operands (ld, plane % 4 == 0)");
+  return guarded(nullptr, [&]() -> int {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    mf::GemmDesc<float> d;
+    d.m = m; d.n = n; d.k = k; d.transA = 0; d.transB = 1; d.alpha = alpha; d.beta = beta;
+    d.A = {const_cast<float*>(A), pla, lda};
+    d.B = {const_cast<float*>(B), plb, ldb};
+    d.C = {C, plc, ldc};
+    int tile = engine >= 1 ? mf::gemm_tc_tile() : mf::GEMM_TILE;
+    std::vector<mf::GemmTile> tl;
+    for (int i = 0; i < (m + tile - 1) / tile; ++i)
+      for (int j = 0; j < (n + tile - 1) / tile; ++j) tl.push_back({0, i, j, 0});
+    DevMem dd, dt, ds;
+    mf::upload(dd, std::vector<mf::GemmDesc<float>>{d}, st);
+    mf::upload(dt, tl, st);
+    ds.alloc(sizeof(int32_t));
+    MF_CUDA(cudaMemsetAsync(ds.p, 0, sizeof(int32_t), st));
+    if (engine >= 1) mf::launch_gemm_tc(dd.as<mf::GemmDesc<float>>(), dt.as<mf::GemmTile>(), (int)tl.size(),
+                                        ds.as<int32_t>(), st, engine == 2);
+    else mf::launch_gemm<float>(dd.as<mf::GemmDesc<float>>(), dt.as<mf::GemmTile>(), (int)tl.size(), st);
+    MF_CUDA(cudaGetLastError());
+    int32_t stat = 0;
+    MF_CUDA(cudaMemcpyAsync(&stat, ds.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (stat) return fail(nullptr, MF_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM expired");
+    return MF_OK;
+  });
+}
+
+int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol, int32_t max_rank, float* U,
+                  int32_t* sk, int32_t* rank, void* stream) {
+  if (nmat <= 0 || m <= 0 || n <= 0 || m > 2048 || n > 8192 || !M || !U || !sk || !rank || !(tol >= 0))
+    return fail(nullptr, MF_ERR_ARG, "invalid row-ID arguments");
+  return guarded(nullptr, [&]() -> int {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int kmax = std::min(m, n);
+    if (max_rank > 0) kmax = std::min(kmax, (int)max_rank);
+    DevMem work, jobs;
+    work.alloc(sizeof(float) * 2 * (size_t)m * n * nmat);
+    std::vector<mf::IdJob<float>> jb(nmat);
+    for (int q = 0; q < nmat; ++q) {
+      auto& j = jb[q];
+      j.M = M + (size_t)2 * m * n * q;
+      j.plane = (int64_t)m * n;
+      j.ld = n;
+      j.m = m;
+      j.n = n;
+      j.U = U + (size_t)2 * m * kmax * q;
+      j.uplane = (int64_t)m * kmax;
+      j.ldu = kmax;
+      j.sk = sk + (size_t)kmax * q;
+      j.rank = rank + q;
+      j.work = work.as<float>() + (size_t)2 * m * n * q;
+      j.wplane = (int64_t)m * n;
+    }
+    mf::upload(jobs, jb, st);
+    if (mf::launch_row_id<float>(jobs.as<mf::IdJob<float>>(), nmat, m, n, (float)tol, max_rank, st) != 0)
+      return fail(nullptr, MF_ERR_ARG, "matrix too large for the row-ID kernel");
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaStreamSynchronize(st));
+    return MF_OK;
+  });
 }
 
 int64_t mf_launch_counter(void) { return mf::launch_count(); }

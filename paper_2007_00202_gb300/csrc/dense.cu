@@ -138,19 +138,19 @@ __global__ void k_assemble_A(FrontDev<T>* fronts, const int32_t* flist, const in
     T vr = (T)vals[2 * k], vi = (T)vals[2 * k + 1];
     if (r < f.s) {
       if (c >= sb && c < se) {
-        int64_t off = (int64_t)r * f.s + (c - sb);
+        int64_t off = (int64_t)r * f.ls + (c - sb);
         f.LU[off] = vr;
         f.LU[off + f.pl_ss] = vi;
       } else if (c >= se) {
         int64_t p = find_sorted(f.upd, f.u, c);
         if (p >= 0) {
-          int64_t off = p * f.s + r;
+          int64_t off = p * f.ls + r;
           f.F12w[off] = vr;
           f.F12w[off + f.pl_us] = vi;
         }
       }
     } else if (c >= sb && c < se) {
-      int64_t off = (int64_t)(r - f.s) * f.s + (c - sb);
+      int64_t off = (int64_t)(r - f.s) * f.ls + (c - sb);
       f.F21w[off] = vr;
       f.F21w[off + f.pl_us] = vi;
     }
@@ -178,7 +178,7 @@ __global__ void k_extend_add(const ExtendAddItem<T>* items, const FrontDev<T>* f
   const int i = blockIdx.x * (blockDim.x >> 5) + warp;
   if (i >= it.uc) return;
   const int ri = it.rel[i];
-  const T* cr = it.Cc + (int64_t)i * it.uc;
+  const T* cr = it.Cc + (int64_t)i * it.ldc;
   const T* ci = cr + it.plane_c;
   for (int j = lane; j < it.uc; j += 32) {
     const int rj = it.rel[j];
@@ -186,11 +186,11 @@ __global__ void k_extend_add(const ExtendAddItem<T>* items, const FrontDev<T>* f
     T* dst;
     int64_t off, pl;
     if (ri < f.s) {
-      if (rj < f.s) { dst = f.LU; off = (int64_t)ri * f.s + rj; pl = f.pl_ss; }
-      else { dst = f.F12w; off = (int64_t)(rj - f.s) * f.s + ri; pl = f.pl_us; }
+      if (rj < f.s) { dst = f.LU; off = (int64_t)ri * f.ls + rj; pl = f.pl_ss; }
+      else { dst = f.F12w; off = (int64_t)(rj - f.s) * f.ls + ri; pl = f.pl_us; }
     } else {
-      if (rj < f.s) { dst = f.F21w; off = (int64_t)(ri - f.s) * f.s + rj; pl = f.pl_us; }
-      else { dst = f.C; off = (int64_t)(ri - f.s) * f.u + (rj - f.s); pl = f.pl_uu; }
+      if (rj < f.s) { dst = f.F21w; off = (int64_t)(ri - f.s) * f.ls + rj; pl = f.pl_us; }
+      else { dst = f.C; off = (int64_t)(ri - f.s) * f.lu + (rj - f.s); pl = f.pl_uu; }
     }
     dst[off] += vr;
     dst[off + pl] += vi;
@@ -209,29 +209,49 @@ void launch_extend_add(const ExtendAddItem<T>* d_items, int nitems, const FrontD
 // ---------------------------------------------------------------------------
 // Panel LU with partial pivoting inside F11 (Sec. 2 step 2; pivot search does
 // not look at F12/F21).  Pivot: largest modulus, lowest row on ties.
+// The panel (rows kb..s-1, columns kb..kb+w-1) is factored in shared memory
+// when it fits (cap_rows), with the pivots' row swaps applied to the columns
+// outside the panel afterwards; taller panels are factored in place in global
+// memory (L2-resident for the front sizes of the dense path).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(512) k_panel_lu(FrontDev<T>* fronts, const int32_t* flist, int kb, int nb,
-                                                  int32_t* status) {
+                                                  int cap_rows, int32_t* status) {
   FrontDev<T> f = fronts[flist[blockIdx.x]];
   const int s = f.s;
+  const int ld = f.ls;
   if (kb >= s) return;
   const int w = min(nb, s - kb);
+  const int rows = s - kb;
   T* Ar = f.LU;
   T* Ai = f.LU + f.pl_ss;
   __shared__ T redv[32];
   __shared__ int redi[32];
-  __shared__ T rowr[64], rowi[64];
   __shared__ int piv_sh;
+  __shared__ T best_sh;
+  extern __shared__ unsigned char pan_raw[];
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int j = kb; j < kb + w; ++j) {
-    // pivot search in column j, rows j..s-1
+  const bool in_smem = rows <= cap_rows;
+  // panel element accessors (row q = 0..rows-1 is global row kb + q, column c = 0..w-1)
+  T* Pr = reinterpret_cast<T*>(pan_raw);
+  T* Pi = Pr + (size_t)cap_rows * nb;
+  auto pr = [&](int q, int c) -> T& { return in_smem ? Pr[q * nb + c] : Ar[(int64_t)(kb + q) * ld + kb + c]; };
+  auto pi = [&](int q, int c) -> T& { return in_smem ? Pi[q * nb + c] : Ai[(int64_t)(kb + q) * ld + kb + c]; };
+  if (in_smem) {
+    for (int e = tid; e < rows * w; e += nt) {
+      int q = e / w, c = e % w;
+      Pr[q * nb + c] = Ar[(int64_t)(kb + q) * ld + kb + c];
+      Pi[q * nb + c] = Ai[(int64_t)(kb + q) * ld + kb + c];
+    }
+    __syncthreads();
+  }
+  for (int jj = 0; jj < w; ++jj) {
     T best = T(-1);
-    int bi = s;
-    for (int i = j + tid; i < s; i += nt) {
-      T a = Ar[(int64_t)i * s + j], b = Ai[(int64_t)i * s + j];
+    int bi = rows;
+    for (int q = jj + tid; q < rows; q += nt) {
+      T a = pr(q, jj), b = pi(q, jj);
       T m2 = a * a + b * b;
-      if (m2 > best) { best = m2; bi = i; }
+      if (m2 > best) { best = m2; bi = q; }
     }
     for (int o = 16; o > 0; o >>= 1) {
       T ob = __shfl_down_sync(0xffffffffu, best, o);
@@ -243,60 +263,89 @@ __global__ void __launch_bounds__(512) k_panel_lu(FrontDev<T>* fronts, const int
     if (tid < 32) {
       int nw = nt >> 5;
       best = tid < nw ? redv[tid] : T(-1);
-      bi = tid < nw ? redi[tid] : s;
+      bi = tid < nw ? redi[tid] : rows;
       for (int o = 16; o > 0; o >>= 1) {
         T ob = __shfl_down_sync(0xffffffffu, best, o);
         int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (tid == 0) {
-        piv_sh = bi < s ? bi : j;
-        f.piv[j] = piv_sh;
+        piv_sh = bi < rows ? bi : jj;
+        best_sh = best;
+        f.piv[kb + jj] = kb + piv_sh;
         if (!(best > T(0)) && status) atomicExch(status, (int32_t)DEV_ZERO_PIVOT);
       }
     }
     __syncthreads();
     const int p = piv_sh;
-    if (p != j) {
-      for (int c = tid; c < s; c += nt) {
-        int64_t o1 = (int64_t)j * s + c, o2 = (int64_t)p * s + c;
-        T t0 = Ar[o1]; Ar[o1] = Ar[o2]; Ar[o2] = t0;
-        t0 = Ai[o1]; Ai[o1] = Ai[o2]; Ai[o2] = t0;
+    if (p != jj) {
+      if (in_smem) {
+        for (int c = tid; c < w; c += nt) {
+          T t0 = Pr[jj * nb + c]; Pr[jj * nb + c] = Pr[p * nb + c]; Pr[p * nb + c] = t0;
+          t0 = Pi[jj * nb + c]; Pi[jj * nb + c] = Pi[p * nb + c]; Pi[p * nb + c] = t0;
+        }
+      } else {
+        for (int c = tid; c < s; c += nt) {
+          int64_t o1 = (int64_t)(kb + jj) * ld + c, o2 = (int64_t)(kb + p) * ld + c;
+          T t0 = Ar[o1]; Ar[o1] = Ar[o2]; Ar[o2] = t0;
+          t0 = Ai[o1]; Ai[o1] = Ai[o2]; Ai[o2] = t0;
+        }
       }
     }
     __syncthreads();
-    // pivot row segment of the panel
-    for (int c = j + tid; c < kb + w; c += nt) {
-      rowr[c - kb] = Ar[(int64_t)j * s + c];
-      rowi[c - kb] = Ai[(int64_t)j * s + c];
-    }
-    __syncthreads();
-    T dr = rowr[j - kb], di = rowi[j - kb];
+    T dr = pr(jj, jj), di = pi(jj, jj);
     T den = dr * dr + di * di;
     if (den == T(0)) { dr = T(1); di = T(0); den = T(1); }
     const T invr = dr / den, invi = -di / den;
-    for (int i = j + 1 + tid; i < s; i += nt) {
-      int64_t o = (int64_t)i * s;
-      T ar = Ar[o + j], ai = Ai[o + j];
+    for (int q = jj + 1 + tid; q < rows; q += nt) {
+      T ar = pr(q, jj), ai = pi(q, jj);
       T lr = ar * invr - ai * invi, li = ar * invi + ai * invr;
-      Ar[o + j] = lr;
-      Ai[o + j] = li;
-      for (int c = j + 1; c < kb + w; ++c) {
-        T ur = rowr[c - kb], ui = rowi[c - kb];
-        Ar[o + c] -= lr * ur - li * ui;
-        Ai[o + c] -= lr * ui + li * ur;
+      pr(q, jj) = lr;
+      pi(q, jj) = li;
+      for (int c = jj + 1; c < w; ++c) {
+        T ur = pr(jj, c), ui = pi(jj, c);
+        pr(q, c) -= lr * ur - li * ui;
+        pi(q, c) -= lr * ui + li * ur;
       }
     }
     __syncthreads();
   }
+  if (in_smem) {
+    for (int e = tid; e < rows * w; e += nt) {
+      int q = e / w, c = e % w;
+      Ar[(int64_t)(kb + q) * ld + kb + c] = Pr[q * nb + c];
+      Ai[(int64_t)(kb + q) * ld + kb + c] = Pi[q * nb + c];
+    }
+    // the panel's row swaps on the columns outside the panel, in pivot order
+    for (int c = tid; c < s; c += nt) {
+      if (c >= kb && c < kb + w) continue;
+      for (int jj = 0; jj < w; ++jj) {
+        int p = f.piv[kb + jj];
+        if (p != kb + jj) {
+          int64_t o1 = (int64_t)(kb + jj) * ld + c, o2 = (int64_t)p * ld + c;
+          T t0 = Ar[o1]; Ar[o1] = Ar[o2]; Ar[o2] = t0;
+          t0 = Ai[o1]; Ai[o1] = Ai[o2]; Ai[o2] = t0;
+        }
+      }
+    }
+  }
 }
 
 template <typename T>
-void launch_panel_lu(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int kb, int nb, int32_t* status,
-                     cudaStream_t st) {
+void launch_panel_lu(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int kb, int nb, int max_rows,
+                     int32_t* status, cudaStream_t st) {
   if (nf <= 0) return;
+  constexpr size_t budget = 192 * 1024;
+  int cap = (int)(budget / (2 * sizeof(T) * (size_t)nb));
+  if (max_rows < cap) cap = max_rows;
+  size_t sm = 2 * sizeof(T) * (size_t)nb * cap;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_panel_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
+    attr = true;
+  }
   g_launches++;
-  k_panel_lu<T><<<nf, 512, 0, st>>>(d_fronts, d_flist, kb, nb, status);
+  k_panel_lu<T><<<nf, 512, sm, st>>>(d_fronts, d_flist, kb, nb, cap, status);
 }
 
 // U12 <- L11^-1 A12 for the panel rows [kb, kb+w) and columns [kb+w, s).
@@ -304,6 +353,7 @@ template <typename T>
 __global__ void k_panel_trsm(FrontDev<T>* fronts, const int32_t* flist, int kb, int nb) {
   FrontDev<T> f = fronts[flist[blockIdx.y]];
   const int s = f.s;
+  const int ld = f.ls;
   if (kb >= s) return;
   const int w = min(nb, s - kb);
   __shared__ T Lr[64][65], Li[64][65];
@@ -311,8 +361,8 @@ __global__ void k_panel_trsm(FrontDev<T>* fronts, const int32_t* flist, int kb, 
   T* Ai = f.LU + f.pl_ss;
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
     int r = e / w, c = e % w;
-    Lr[r][c] = Ar[(int64_t)(kb + r) * s + kb + c];
-    Li[r][c] = Ai[(int64_t)(kb + r) * s + kb + c];
+    Lr[r][c] = Ar[(int64_t)(kb + r) * ld + kb + c];
+    Li[r][c] = Ai[(int64_t)(kb + r) * ld + kb + c];
   }
   __syncthreads();
   int col = kb + w + blockIdx.x * blockDim.x + threadIdx.x;
@@ -320,15 +370,15 @@ __global__ void k_panel_trsm(FrontDev<T>* fronts, const int32_t* flist, int kb, 
   T xr[64], xi[64];
 #pragma unroll 1
   for (int r = 0; r < w; ++r) {
-    T vr = Ar[(int64_t)(kb + r) * s + col], vi = Ai[(int64_t)(kb + r) * s + col];
+    T vr = Ar[(int64_t)(kb + r) * ld + col], vi = Ai[(int64_t)(kb + r) * ld + col];
     for (int t = 0; t < r; ++t) {
       vr -= Lr[r][t] * xr[t] - Li[r][t] * xi[t];
       vi -= Lr[r][t] * xi[t] + Li[r][t] * xr[t];
     }
     xr[r] = vr;
     xi[r] = vi;
-    Ar[(int64_t)(kb + r) * s + col] = vr;
-    Ai[(int64_t)(kb + r) * s + col] = vi;
+    Ar[(int64_t)(kb + r) * ld + col] = vr;
+    Ai[(int64_t)(kb + r) * ld + col] = vi;
   }
 }
 
@@ -348,6 +398,7 @@ template <typename T>
 __global__ void k_transpose_U(FrontDev<T>* fronts, const int32_t* flist) {
   FrontDev<T> f = fronts[flist[blockIdx.z]];
   const int s = f.s;
+  const int ld = f.ls;
   __shared__ T tr[32][33], ti[32][33];
   int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   if (r0 >= s || c0 >= s) return;
@@ -356,8 +407,8 @@ __global__ void k_transpose_U(FrontDev<T>* fronts, const int32_t* flist) {
     int r = r0 + k, c = c0 + tx;
     T vr = T(0), vi = T(0);
     if (r < s && c < s && c >= r) {
-      vr = f.LU[(int64_t)r * s + c];
-      vi = f.LU[(int64_t)r * s + c + f.pl_ss];
+      vr = f.LU[(int64_t)r * ld + c];
+      vi = f.LU[(int64_t)r * ld + c + f.pl_ss];
     }
     tr[k][tx] = vr;
     ti[k][tx] = vi;
@@ -366,8 +417,8 @@ __global__ void k_transpose_U(FrontDev<T>* fronts, const int32_t* flist) {
   for (int k = ty; k < 32; k += 8) {
     int r = c0 + k, c = r0 + tx;   // UT[r][c] = U[c][r]
     if (r < s && c < s) {
-      f.UT[(int64_t)r * s + c] = tr[tx][k];
-      f.UT[(int64_t)r * s + c + f.pl_ss] = ti[tx][k];
+      f.UT[(int64_t)r * ld + c] = tr[tx][k];
+      f.UT[(int64_t)r * ld + c + f.pl_ss] = ti[tx][k];
     }
   }
 }
@@ -390,9 +441,10 @@ __global__ void k_permute_F12(FrontDev<T>* fronts, const int32_t* flist) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)f.u * f.s) return;
   int64_t j = e / f.s, k = e % f.s;
-  int64_t src = j * f.s + f.perm[k];
-  f.F12p[e] = f.F12w[src];
-  f.F12p[e + f.pl_us] = f.F12w[src + f.pl_us];
+  int64_t dst = j * f.ls + k;
+  int64_t src = j * f.ls + f.perm[k];
+  f.F12p[dst] = f.F12w[src];
+  f.F12p[dst + f.pl_us] = f.F12w[src + f.pl_us];
 }
 
 template <typename T>
@@ -419,6 +471,7 @@ template <typename T>
 __global__ void k_trinv_diag(FrontDev<T>* fronts, const int32_t* flist, int which) {
   FrontDev<T> f = fronts[flist[blockIdx.y]];
   const int s = f.s;
+  const int ld = f.ls;
   const int b0 = blockIdx.x * 64;
   if (b0 >= s) return;
   const int w = min(64, s - b0);
@@ -433,8 +486,8 @@ __global__ void k_trinv_diag(FrontDev<T>* fronts, const int32_t* flist, int whic
     int r = e / w, c = e % w;
     T vr = T(0), vi = T(0);
     if (c < r || (c == r && which == 1)) {
-      vr = src[(int64_t)(b0 + r) * s + b0 + c];
-      vi = src[(int64_t)(b0 + r) * s + b0 + c + f.pl_ss];
+      vr = src[(int64_t)(b0 + r) * ld + b0 + c];
+      vi = src[(int64_t)(b0 + r) * ld + b0 + c + f.pl_ss];
     } else if (c == r) {
       vr = T(1);
     }
@@ -464,8 +517,8 @@ __global__ void k_trinv_diag(FrontDev<T>* fronts, const int32_t* flist, int whic
   __syncthreads();
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
     int r = e / w, cc = e % w;
-    dst[(int64_t)(b0 + r) * s + b0 + cc] = Xr[r * 65 + cc];
-    dst[(int64_t)(b0 + r) * s + b0 + cc + f.pl_ss] = Xi[r * 65 + cc];
+    dst[(int64_t)(b0 + r) * ld + b0 + cc] = Xr[r * 65 + cc];
+    dst[(int64_t)(b0 + r) * ld + b0 + cc + f.pl_ss] = Xi[r * 65 + cc];
   }
 }
 
@@ -803,7 +856,7 @@ void launch_colnorm2(int64_t n, int nrhs, const double* X, int64_t ldx, double* 
   template void launch_assemble_A<T>(FrontDev<T>*, const int32_t*, int, int, const int64_t*, const int64_t*,     \
                                      const double*, cudaStream_t);                                               \
   template void launch_extend_add<T>(const ExtendAddItem<T>*, int, const FrontDev<T>*, int, cudaStream_t);        \
-  template void launch_panel_lu<T>(FrontDev<T>*, const int32_t*, int, int, int, int32_t*, cudaStream_t);          \
+  template void launch_panel_lu<T>(FrontDev<T>*, const int32_t*, int, int, int, int, int32_t*, cudaStream_t);     \
   template void launch_panel_trsm<T>(FrontDev<T>*, const int32_t*, int, int, int, int, cudaStream_t);             \
   template void launch_post_lu<T>(FrontDev<T>*, const int32_t*, int, int, int, cudaStream_t);                     \
   template void launch_trinv_diag<T>(FrontDev<T>*, const int32_t*, int, int, int, T* const*, cudaStream_t);       \

@@ -10,6 +10,7 @@
 // replayed by every factorization.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 
 #include "engine.h"
@@ -28,6 +29,7 @@ class DenseEngine : public EngineBase {
   DenseEngine(const Analysis& an, const DeviceMatrix& A, cudaStream_t st) : an_(an), A_(A), st_(st) { plan(); }
 
   void factor(double) override {
+    const int64_t c0 = launch_count();
     MF_CUDA(cudaMemsetAsync(arena_.p, 0, zero_bytes_, st_));
     MF_CUDA(cudaMemsetAsync(status_.p, 0, sizeof(int32_t), st_));
     size_t ng = 0;
@@ -47,6 +49,7 @@ class DenseEngine : public EngineBase {
       if (timed) { MF_CUDA(cudaEventRecord(evs_[2 * k + 1], st_)); ++k; }
     }
     MF_CUDA(cudaGetLastError());
+    nlaunch_factor_ = (int)(launch_count() - c0);
     if (profiling) {
       MF_CUDA(cudaStreamSynchronize(st_));
       k = 0;
@@ -63,6 +66,7 @@ class DenseEngine : public EngineBase {
     int32_t stat = 0;
     MF_CUDA(cudaMemcpyAsync(&stat, status_.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     MF_CUDA(cudaStreamSynchronize(st_));
+    if (stat == 2) throw CudaError("a bounded wait in the tensor-core GEMM expired (MF_ERR_TIMEOUT)");
     if (stat != DEV_OK) throw SingularError("zero pivot in a dense front");
   }
 
@@ -121,13 +125,14 @@ class DenseEngine : public EngineBase {
     int nt;
     size_t nd;
   };
-  GemmRef add_gemm(std::vector<GemmDesc<T>>& D, std::vector<GemmTile>& Tl, const std::vector<GemmDesc<T>>& batch) {
+  GemmRef add_gemm(std::vector<GemmDesc<T>>& D, std::vector<GemmTile>& Tl, const std::vector<GemmDesc<T>>& batch,
+                   int tile = GEMM_TILE) {
     GemmRef r{D.size(), Tl.size(), 0, 0};
     for (auto& d : batch) {
       if (d.m <= 0 || d.n <= 0) continue;
       int idx = (int)(D.size() - r.d0);
       D.push_back(d);
-      int tm = (d.m + GEMM_TILE - 1) / GEMM_TILE, tn = (d.n + GEMM_TILE - 1) / GEMM_TILE;
+      int tm = (d.m + tile - 1) / tile, tn = (d.n + tile - 1) / tile;
       for (int i = 0; i < tm; ++i)
         for (int j = 0; j < tn; ++j) Tl.push_back({idx, i, j, 0});
     }
@@ -135,6 +140,25 @@ class DenseEngine : public EngineBase {
     r.nd = D.size() - r.d0;
     return r;
   }
+
+  // "NT" products (both operands K-contiguous): tcgen05 tensor cores for complex64, SIMT for complex128
+  static bool use_tc() {
+    if (sizeof(T) != 4) return false;
+    const char* e = getenv("MF_NO_TC");
+    return !(e && e[0] == '1');
+  }
+  void push_gemm_nt(std::vector<GemmDesc<T>>& D, std::vector<GemmTile>& Tl, const std::vector<GemmDesc<T>>& b) {
+    const bool tc = use_tc();
+    GemmRef g = add_gemm(D, Tl, b, tc ? gemm_tc_tile() : GEMM_TILE);
+    if (!g.nt) return;
+    if (tc)
+      push_op([this, g](cudaStream_t st) { launch_nt(g, st); }, ref_flops(D, g));
+    else
+      push_op([this, g](cudaStream_t st) {
+        launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt, st);
+      }, ref_flops(D, g));
+  }
+  void launch_nt(const GemmRef& g, cudaStream_t st);
 
   void push_op(std::function<void(cudaStream_t)> fn, double fl = 0) {
     fops_.push_back(std::move(fn));
@@ -169,21 +193,23 @@ class DenseEngine : public EngineBase {
     std::vector<Offs> o(nf);
     for (size_t i = 0; i < nf; ++i) {
       int64_t s = F[i].s(), u = F[i].u();
-      o[i].LU = take(2 * s * s);
-      o[i].Linv = take(2 * s * s);
-      o[i].UinvT = take(2 * s * s);
-      o[i].F12w = take(2 * s * u);
-      o[i].F21w = take(2 * s * u);
-      o[i].C = take(F[i].parent >= 0 ? 2 * u * u : 0);
+      const int64_t ls = (s + 3) & ~3ll, lu = (u + 3) & ~3ll;
+      o[i].LU = take(2 * s * ls);
+      o[i].Linv = take(2 * s * ls);
+      o[i].UinvT = take(2 * s * ls);
+      o[i].F12w = take(2 * u * ls);
+      o[i].F21w = take(2 * u * ls);
+      o[i].C = take(F[i].parent >= 0 ? 2 * u * lu : 0);
     }
     zero_bytes_ = off;
     for (size_t i = 0; i < nf; ++i) {
       int64_t s = F[i].s(), u = F[i].u();
-      o[i].UT = take(2 * s * s);
-      o[i].W = take(4 * s * s);   // two s x s planar work matrices (L and U inversions)
-      o[i].F12p = take(2 * s * u);
-      o[i].F12T = take(2 * s * u);
-      o[i].F21f = take(2 * s * u);
+      const int64_t ls = (s + 3) & ~3ll;
+      o[i].UT = take(2 * s * ls);
+      o[i].W = take(4 * s * ls);   // two s x s planar work matrices (L and U inversions)
+      o[i].F12p = take(2 * u * ls);
+      o[i].F12T = take(2 * u * ls);
+      o[i].F21f = take(2 * u * ls);
       o[i].piv = off; off = align_up(off + s * 4, 256);
       o[i].perm = off; off = align_up(off + s * 4, 256);
       o[i].upd = off; off = align_up(off + u * 8, 256);
@@ -211,9 +237,12 @@ class DenseEngine : public EngineBase {
       f.W = reinterpret_cast<T*>(base + o[i].W);
       f.piv = reinterpret_cast<int32_t*>(base + o[i].piv);
       f.perm = reinterpret_cast<int32_t*>(base + o[i].perm);
-      f.pl_ss = s * s;
-      f.pl_us = u * s;
-      f.pl_uu = u * u;
+      const int64_t ls = (s + 3) & ~3ll, lu = (u + 3) & ~3ll;
+      f.ls = (int32_t)ls;
+      f.lu = (int32_t)lu;
+      f.pl_ss = s * ls;
+      f.pl_us = u * ls;
+      f.pl_uu = u * lu;
       if (u) MF_CUDA(cudaMemcpyAsync(base + o[i].upd, F[i].upd.data(), u * 8, cudaMemcpyHostToDevice, st_));
       flops_ += 8.0 * ((double)s * s * s / 3.0 + (double)s * s * u + (double)s * u * u);
     }
@@ -258,7 +287,8 @@ class DenseEngine : public EngineBase {
           }
           ExtendAddItem<T> it;
           it.Cc = fr_[cf.id].C;
-          it.plane_c = cf.u() * cf.u();
+          it.plane_c = fr_[cf.id].pl_uu;
+          it.ldc = fr_[cf.id].lu;
           it.rel = nullptr;
           it.uc = (int32_t)cf.u();
           it.parent = fid;
@@ -306,8 +336,9 @@ class DenseEngine : public EngineBase {
       (void)fl_lv;
       // blocked LU
       for (int kb = 0; kb < max_s; kb += LU_NB) {
-        push_op([this, lvi, nfl, kb](cudaStream_t st) {
-          launch_panel_lu<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, kb, LU_NB, status_.template as<int32_t>(), st);
+        push_op([this, lvi, nfl, kb, max_s](cudaStream_t st) {
+          launch_panel_lu<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, kb, LU_NB, max_s - kb,
+                             status_.template as<int32_t>(), st);
         });
         push_op([this, lvi, nfl, kb, max_s](cudaStream_t st) {
           launch_panel_trsm<T>(fronts_d_.template as<FrontDev<T>>(), flist(lvi), nfl, kb, LU_NB, max_s, st);
@@ -320,9 +351,10 @@ class DenseEngine : public EngineBase {
           int w = std::min(LU_NB, s - kb);
           int rem = s - kb - w;
           if (kb >= s || rem <= 0) continue;
-          PMat<T> a{f.LU + (int64_t)(kb + w) * s + kb, f.pl_ss, s};
-          PMat<T> b{f.LU + (int64_t)kb * s + kb + w, f.pl_ss, s};
-          PMat<T> c{f.LU + (int64_t)(kb + w) * s + kb + w, f.pl_ss, s};
+          const int ls = f.ls;
+          PMat<T> a{f.LU + (int64_t)(kb + w) * ls + kb, f.pl_ss, ls};
+          PMat<T> b{f.LU + (int64_t)kb * ls + kb + w, f.pl_ss, ls};
+          PMat<T> c{f.LU + (int64_t)(kb + w) * ls + kb + w, f.pl_ss, ls};
           batch.push_back(gd(rem, rem, w, 0, 0, T(-1), T(1), a, b, c));
         }
         GemmRef g = add_gemm(D, Tl, batch);
@@ -356,12 +388,13 @@ class DenseEngine : public EngineBase {
               T* Tm = which == 0 ? f.LU : f.UT;
               T* X = which == 0 ? f.Linv : f.UinvT;
               T* W = f.W + (which == 0 ? 0 : 2 * f.pl_ss);   // separate work matrix per triangle
-              int64_t woff = (int64_t)c0 * s + a0;
-              PMat<T> tca{Tm + (int64_t)c0 * s + a0, f.pl_ss, s};
-              PMat<T> xaa{X + (int64_t)a0 * s + a0, f.pl_ss, s};
-              PMat<T> w{W + woff, f.pl_ss, s};
-              PMat<T> xcc{X + (int64_t)c0 * s + c0, f.pl_ss, s};
-              PMat<T> xca{X + (int64_t)c0 * s + a0, f.pl_ss, s};
+              const int ls = f.ls;
+              int64_t woff = (int64_t)c0 * ls + a0;
+              PMat<T> tca{Tm + (int64_t)c0 * ls + a0, f.pl_ss, ls};
+              PMat<T> xaa{X + (int64_t)a0 * ls + a0, f.pl_ss, ls};
+              PMat<T> w{W + woff, f.pl_ss, ls};
+              PMat<T> xcc{X + (int64_t)c0 * ls + c0, f.pl_ss, ls};
+              PMat<T> xca{X + (int64_t)c0 * ls + a0, f.pl_ss, ls};
               b1.push_back(gd(mc, h, h, 0, 0, T(1), T(0), tca, xaa, w));
               b2.push_back(gd(mc, h, mc, 0, 0, T(-1), T(0), xcc, w, xca));
             }
@@ -385,18 +418,12 @@ class DenseEngine : public EngineBase {
         for (int32_t fid : L) {
           const FrontDev<T>& f = fr_[fid];
           if (f.u == 0) continue;
-          b.push_back(gd(f.u, f.s, f.s, 0, 1, T(1), T(0), PMat<T>{f.F12p, f.pl_us, f.s}, PMat<T>{f.Linv, f.pl_ss, f.s},
-                         PMat<T>{f.F12T, f.pl_us, f.s}));
-          b.push_back(gd(f.u, f.s, f.s, 0, 1, T(1), T(0), PMat<T>{f.F21w, f.pl_us, f.s},
-                         PMat<T>{f.UinvT, f.pl_ss, f.s}, PMat<T>{f.F21f, f.pl_us, f.s}));
+          b.push_back(gd(f.u, f.s, f.s, 0, 1, T(1), T(0), PMat<T>{f.F12p, f.pl_us, f.ls}, PMat<T>{f.Linv, f.pl_ss, f.ls},
+                         PMat<T>{f.F12T, f.pl_us, f.ls}));
+          b.push_back(gd(f.u, f.s, f.s, 0, 1, T(1), T(0), PMat<T>{f.F21w, f.pl_us, f.ls},
+                         PMat<T>{f.UinvT, f.pl_ss, f.ls}, PMat<T>{f.F21f, f.pl_us, f.ls}));
         }
-        GemmRef g = add_gemm(D, Tl, b);
-        if (g.nt) {
-          push_op([this, g](cudaStream_t st) {
-            launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt, st);
-          }, ref_flops(D, g));
-          nlaunch_factor_++;
-        }
+        push_gemm_nt(D, Tl, b);
       }
       // Schur complement C = F22 - F21 F12   (Sec. 2 step 4)
       {
@@ -404,16 +431,10 @@ class DenseEngine : public EngineBase {
         for (int32_t fid : L) {
           const FrontDev<T>& f = fr_[fid];
           if (f.u == 0 || F[fid].parent < 0) continue;
-          b.push_back(gd(f.u, f.u, f.s, 0, 1, T(-1), T(1), PMat<T>{f.F21f, f.pl_us, f.s},
-                         PMat<T>{f.F12T, f.pl_us, f.s}, PMat<T>{f.C, f.pl_uu, f.u}));
+          b.push_back(gd(f.u, f.u, f.s, 0, 1, T(-1), T(1), PMat<T>{f.F21f, f.pl_us, f.ls},
+                         PMat<T>{f.F12T, f.pl_us, f.ls}, PMat<T>{f.C, f.pl_uu, f.lu}));
         }
-        GemmRef g = add_gemm(D, Tl, b);
-        if (g.nt) {
-          push_op([this, g](cudaStream_t st) {
-            launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt, st);
-          }, ref_flops(D, g));
-          nlaunch_factor_++;
-        }
+        push_gemm_nt(D, Tl, b);
       }
     }
     upload(descs_d_, D, st_);
@@ -480,10 +501,10 @@ class DenseEngine : public EngineBase {
       for (int32_t f : L) {
         const FrontDev<T>& fd = fr_[f];
         int64_t spl = (int64_t)fd.s * nrhs, upl = (int64_t)fd.u * nrhs;
-        b1.push_back(gd(fd.s, nrhs, fd.s, 0, 0, T(1), T(0), PMat<T>{fd.Linv, fd.pl_ss, fd.s},
+        b1.push_back(gd(fd.s, nrhs, fd.s, 0, 0, T(1), T(0), PMat<T>{fd.Linv, fd.pl_ss, fd.ls},
                         PMat<T>{P(ta[f]), spl, nrhs}, PMat<T>{P(tb[f]), spl, nrhs}));
         if (fd.u)
-          b2.push_back(gd(fd.u, nrhs, fd.s, 0, 0, T(-1), T(0), PMat<T>{fd.F21f, fd.pl_us, fd.s},
+          b2.push_back(gd(fd.u, nrhs, fd.s, 0, 0, T(-1), T(0), PMat<T>{fd.F21f, fd.pl_us, fd.ls},
                           PMat<T>{P(tb[f]), spl, nrhs}, PMat<T>{P(tu[f]), upl, nrhs}));
       }
       gemm_op(b1);
@@ -522,9 +543,9 @@ class DenseEngine : public EngineBase {
         const FrontDev<T>& fd = fr_[f];
         int64_t spl = (int64_t)fd.s * nrhs, upl = (int64_t)fd.u * nrhs;
         if (fd.u)
-          b1.push_back(gd(fd.s, nrhs, fd.u, 1, 0, T(-1), T(1), PMat<T>{fd.F12T, fd.pl_us, fd.s},
+          b1.push_back(gd(fd.s, nrhs, fd.u, 1, 0, T(-1), T(1), PMat<T>{fd.F12T, fd.pl_us, fd.ls},
                           PMat<T>{P(tu[f]), upl, nrhs}, PMat<T>{P(tb[f]), spl, nrhs}));
-        b2.push_back(gd(fd.s, nrhs, fd.s, 1, 0, T(1), T(0), PMat<T>{fd.UinvT, fd.pl_ss, fd.s},
+        b2.push_back(gd(fd.s, nrhs, fd.s, 1, 0, T(1), T(0), PMat<T>{fd.UinvT, fd.pl_ss, fd.ls},
                         PMat<T>{P(tb[f]), spl, nrhs}, PMat<T>{P(ta[f]), spl, nrhs}));
       }
       gemm_op(b1);
@@ -544,6 +565,17 @@ class DenseEngine : public EngineBase {
 
   DevMem rel_;
 };
+
+template <>
+void DenseEngine<float>::launch_nt(const GemmRef& g, cudaStream_t st) {
+  launch_gemm_tc(descs_d_.template as<GemmDesc<float>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt,
+                 status_.template as<int32_t>(), st);
+}
+template <>
+void DenseEngine<double>::launch_nt(const GemmRef& g, cudaStream_t st) {
+  launch_gemm<double>(descs_d_.template as<GemmDesc<double>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt,
+                      st);
+}
 
 }  // namespace
 

@@ -17,6 +17,14 @@ void launch_gemm(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles,
 // Tile size of the SIMT GEMM (both dimensions).
 constexpr int GEMM_TILE = 64;
 
+// tcgen05 (kind::tf32) planar complex GEMM, "NT" form only (transA = 0, transB = 1),
+// leading dimensions multiples of 4, 16-byte aligned planes; 128 x 128 tiles.
+// status receives 2 if a bounded wait expired.
+// split = true: three-pass split TF32 (hi*hi + hi*lo + lo*hi), close to FP32 accuracy.
+void launch_gemm_tc(const GemmDesc<float>* d_desc, const GemmTile* d_tiles, int ntiles, int32_t* status,
+                    cudaStream_t st, bool split = true);
+int gemm_tc_tile();
+
 // Dense front assembly and extend-add (Sec. 2 step 1).
 template <typename T>
 void launch_assemble_A(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int maxrows, const int64_t* rowptr,
@@ -27,8 +35,8 @@ void launch_extend_add(const ExtendAddItem<T>* d_items, int nitems, const FrontD
 
 // Partial LU of F11 with partial pivoting (Sec. 2 step 2): one panel step.
 template <typename T>
-void launch_panel_lu(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int kb, int nb, int32_t* status,
-                     cudaStream_t st);
+void launch_panel_lu(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int kb, int nb, int max_rows,
+                     int32_t* status, cudaStream_t st);
 template <typename T>
 void launch_panel_trsm(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int kb, int nb, int max_s,
                        cudaStream_t st);

@@ -53,6 +53,7 @@ struct FrontDev {
   T* W;                  // s x s work
   int32_t* piv;          // s pivots (LAPACK convention: row k swapped with piv[k] at step k)
   int32_t* perm;         // s gather permutation: (P^T b)[k] = b[perm[k]]
+  int32_t ls, lu;        // leading dimensions of s-wide and u-wide rows (s, u rounded up to 4)
   int64_t pl_ss, pl_us, pl_uu;   // plane strides of s x s, u x s and u x u matrices
 };
 
@@ -63,6 +64,7 @@ struct ExtendAddItem {
   int64_t plane_c;
   const int32_t* rel;    // u_c positions in the parent front (0..s_p+u_p-1)
   int32_t uc;
+  int32_t ldc;           // leading dimension of the child's block
   int32_t parent;        // index into the FrontDev array
 };
 

@@ -75,6 +75,9 @@ SIGNATURES = {
     "mf_destroy": (None, [_P]),
     "mf_launch_counter": (C.c_int64, []),
     "mf_profile": (C.c_int, [_P, C.c_int32]),
+    "mf_row_id_c64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, C.c_double, C.c_int32, _P, _P, _P, _P]),
+    "mf_gemm_c64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int64, C.c_int64, _P, C.c_int64,
+                              C.c_int64, _P, C.c_int64, C.c_int64, C.c_float, C.c_float, _P]),
     "mf_profile_read": (C.c_int, [_P, C.POINTER(mf_kernel_profile_t)]),
     "mf_analysis_sizes": (C.c_int, [_P, C.POINTER(mf_analysis_sizes_t)]),
     "mf_analysis_export": (C.c_int, [_P, _I64P, _I64P, _I64P, _I32P, _I64P, _I64P]),
@@ -148,8 +151,9 @@ class Handle:
         n, nrhs = B.shape
         X = np.empty_like(B, order="F")
         info = mf_solve_info()
-        rc = lib().mf_solve(self.ptr, nrhs, _p(B.view(np.float64), C.c_double), n,
-                            _p(X.view(np.float64), C.c_double), n, C.byref(info))
+        dp = C.POINTER(C.c_double)
+        rc = lib().mf_solve(self.ptr, nrhs, C.cast(B.ctypes.data, dp), n, C.cast(X.ctypes.data, dp), n,
+                            C.byref(info))
         if not (allow_no_convergence and rc == -6):
             _check(rc, self.ptr)
         return (X[:, 0] if vec else X), info
@@ -235,7 +239,7 @@ def mf_analyze(n, rowptr, colind, vals, coords, lattice=MF_LATTICE_NODE, stream=
     o = mf_options_init(lattice=lattice, **opts)
     o.coords = _p(coords, C.c_int32)
     h = C.c_void_p()
-    rc = lib().mf_analyze(n, _p(rowptr, C.c_int64), _p(colind, C.c_int32), _p(vals.view(np.float64), C.c_double),
+    rc = lib().mf_analyze(n, _p(rowptr, C.c_int64), _p(colind, C.c_int32), C.cast(vals.ctypes.data, C.POINTER(C.c_double)),
                           C.byref(o), C.c_void_p(stream), C.byref(h))
     _check(rc, None)
     return Handle(h, (rowptr, colind, vals, coords))
@@ -244,3 +248,15 @@ def mf_analyze(n, rowptr, colind, vals, coords, lattice=MF_LATTICE_NODE, stream=
 def analyze_problem(prob, **opts) -> Handle:
     """mf_analyze on a workloads.SparseProblem-like object (n, rowptr, colind, vals, coords, lattice)."""
     return mf_analyze(prob.n, prob.rowptr, prob.colind, prob.vals, prob.coords, prob.lattice, **opts)
+
+
+def mf_gemm_c64(engine, m, n, k, A, lda, pla, B, ldb, plb, C_, ldc, plc, alpha, beta, stream=0):
+    """Component GEMM on device pointers (ints); see include/mf.h."""
+    _check(lib().mf_gemm_c64(engine, m, n, k, C.c_void_p(A), lda, pla, C.c_void_p(B), ldb, plb, C.c_void_p(C_), ldc,
+                             plc, alpha, beta, C.c_void_p(stream)))
+
+
+def mf_row_id_c64(nmat, m, n, M, tol, max_rank, U, sk, rank, stream=0):
+    """Component batched row ID on device pointers (ints); see include/mf.h."""
+    _check(lib().mf_row_id_c64(nmat, m, n, C.c_void_p(M), tol, max_rank, C.c_void_p(U), C.c_void_p(sk),
+                               C.c_void_p(rank), C.c_void_p(stream)))

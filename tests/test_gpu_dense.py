@@ -75,7 +75,6 @@ def test_solve_device_and_refactor(g):
     h = g.analyze_problem(p, leaf_size=32, nmin_sep=10 ** 9)
     h.mf_factor(0.0)
     h.mf_factor(0.0)                                  # refactorization reuses the plan
-    bd = torch.from_numpy(np.asfortranarray(b).view(np.float64).reshape(-1)).cuda()
     bd = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()      # column-major N x nrhs == row-major nrhs x N
     xd = torch.empty_like(bd)
     info = h.mf_solve_device(4, bd.data_ptr(), xd.data_ptr())
@@ -93,4 +92,4 @@ def test_launch_counter_moves(g):
     c0 = g.lib().mf_launch_counter()
     h.mf_factor(0.0)
     st = h.mf_stats()
-    assert g.lib().mf_launch_counter() - c0 >= st["gpu_launches_factor"] > 0
+    assert g.lib().mf_launch_counter() - c0 == st["gpu_launches_factor"] > 0

@@ -1,0 +1,50 @@
+"""Front-update GEMM kernels (Sec. 2 step 4: C = F22 - F21 F12) against an FP64 product."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2007_00202_gb300 import build
+    build.build()
+    return torch
+
+
+def _planar(torch, M, ld):
+    rows, cols = M.shape
+    buf = torch.zeros(2, rows, ld, dtype=torch.float32, device="cuda")
+    buf[0, :, :cols] = torch.from_numpy(M.real.astype(np.float32))
+    buf[1, :, :cols] = torch.from_numpy(M.imag.astype(np.float32))
+    return buf
+
+
+@pytest.mark.parametrize("engine", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k,beta", [(300, 257, 100, 1.0), (128, 128, 32, 0.0), (1, 5, 3, 1.0),
+                                        (520, 390, 961, 1.0)])
+def test_gemm_nt_against_fp64(tk, engine, m, n, k, beta):
+    import paper_2007_00202_gb300.mf as mf
+    torch = tk
+    rng = np.random.default_rng(m + n + k)
+    A = rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))
+    B = rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))
+    C0 = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+    lda = (k + 3) // 4 * 4
+    ldc = n + 3
+    dA, dB, dC = _planar(torch, A, lda), _planar(torch, B, lda), _planar(torch, C0, ldc)
+    mf.mf_gemm_c64(engine, m, n, k, dA.data_ptr(), lda, m * lda, dB.data_ptr(), lda, n * lda, dC.data_ptr(), ldc,
+                   m * ldc, -1.0, beta, 0)
+    torch.cuda.synchronize()
+    out = dC[0, :, :n].double().cpu().numpy() + 1j * dC[1, :, :n].double().cpu().numpy()
+    ref = -(A @ B.T) + beta * C0
+    scale = np.sqrt(k) * np.abs(A).max() * np.abs(B).max()
+    err = np.abs(out - ref).max() / scale
+    # FP32 SIMT: ~1e-6; one TF32 pass (10-bit mantissa inputs, FP32 accumulate): ~1e-3;
+    # split TF32 (three passes): FP32-like
+    assert err < {0: 2e-5, 1: 4e-3, 2: 2e-5}[engine], err
+    # the padding column of C (beyond n) is untouched
+    assert float(dC[0, :, n:].abs().max()) == float(_planar(torch, C0, ldc)[0, :, n:].abs().max())
