@@ -187,6 +187,29 @@ int mf_gemm_c64(int32_t engine, int32_t m, int32_t n, int32_t k, const float* A,
 int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol, int32_t max_rank, float* U,
                   int32_t* sk, int32_t* rank, void* stream);
 
+/*
+ * mf_row_id_c64 without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory where
+ * they need the decomposition -- code that runs while a CUDA graph is being
+ * captured (cudaMalloc/cudaFree cannot be captured), or embedders whose device
+ * memory is fully reserved up front.  Same arguments, layouts and results as
+ * mf_row_id_c64; the QR work matrix lives in a fixed array inside the library
+ * (8 MiB per GPU, held by every GPU that loads the library until the process
+ * exits) instead of a per-call allocation.
+ *  - Limit: 2 * m * n * nmat <= 2^21 floats (e.g. 16 matrices of 128 x 512);
+ *    larger batches return MF_ERR_ARG and do nothing.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current) and sets the kernel's shared-memory limit; make that first
+ *    call before any stream capture.
+ *  - All calls share the one array and the work matrix is fully rewritten by
+ *    every call, so calls that overlap on the GPU (different streams or
+ *    threads without ordering) race and give wrong results.
+ *  - Calls no cudaMalloc, cudaFree or allocating library routine.  Waits for `stream`.
+ * Errors: MF_ERR_ARG, MF_ERR_CUDA.
+ */
+int mf_row_id_c64_noalloc(int32_t nmat, int32_t m, int32_t n, const float* M, double tol, int32_t max_rank,
+                          float* U, int32_t* sk, int32_t* rank, void* stream);
+
 /* Kernel launches issued by the library since it was loaded (all handles, all streams). */
 int64_t mf_launch_counter(void);
 

@@ -76,6 +76,8 @@ SIGNATURES = {
     "mf_launch_counter": (C.c_int64, []),
     "mf_profile": (C.c_int, [_P, C.c_int32]),
     "mf_row_id_c64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, C.c_double, C.c_int32, _P, _P, _P, _P]),
+    "mf_row_id_c64_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, C.c_double, C.c_int32, _P, _P, _P,
+                                        _P]),
     "mf_gemm_c64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int64, C.c_int64, _P, C.c_int64,
                               C.c_int64, _P, C.c_int64, C.c_int64, C.c_float, C.c_float, _P]),
     "mf_profile_read": (C.c_int, [_P, C.POINTER(mf_kernel_profile_t)]),
@@ -260,3 +262,9 @@ def mf_row_id_c64(nmat, m, n, M, tol, max_rank, U, sk, rank, stream=0):
     """Component batched row ID on device pointers (ints); see include/mf.h."""
     _check(lib().mf_row_id_c64(nmat, m, n, C.c_void_p(M), tol, max_rank, C.c_void_p(U), C.c_void_p(sk),
                                C.c_void_p(rank), C.c_void_p(stream)))
+
+
+def mf_row_id_c64_noalloc(nmat, m, n, M, tol, max_rank, U, sk, rank, stream=0):
+    """mf_row_id_c64 with the library's fixed scratch array (no device allocation); see include/mf.h."""
+    _check(lib().mf_row_id_c64_noalloc(nmat, m, n, C.c_void_p(M), tol, max_rank, C.c_void_p(U), C.c_void_p(sk),
+                                       C.c_void_p(rank), C.c_void_p(stream)))
