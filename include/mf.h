@@ -210,6 +210,35 @@ int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol
 int mf_row_id_c64_noalloc(int32_t nmat, int32_t m, int32_t n, const float* M, double tol, int32_t max_rank,
                           float* U, int32_t* sk, int32_t* rank, void* stream);
 
+/* ---------------- butterfly component: Green's-function block sets ---------------- */
+
+/*
+ * HOD-BF compression of nblk blocks of the 3-D Helmholtz Green's function
+ * G(x, y) = exp(i k |x - y|) / (4 pi |x - y|) (Sec. 3.1) between two parallel
+ * m_b x m_b point grids of spacing h, at z = 0 and z = h.  Each block is an
+ * m_b^2 x m_b^2 HOD-BF matrix (Sec. 4) over a uniform-depth geometric bisection
+ * of the plane with leaves of at most `leaf` points; its off-diagonal blocks
+ * are butterflies built by entry evaluation (Alg. 2, ID tolerance tol, rank cap
+ * max_rank (0 = none), alpha uniform + knn nearest proxies), complex64, on the
+ * GPU.  Rows of block b occupy [off_b, off_b + m_b^2) of the set, points in the
+ * set's order (see mf_green_points).  *out receives the set (owns its memory).
+ */
+typedef struct mf_bfset mf_bfset;
+int mf_green_build(int32_t nblk, const int32_t* m, double k, double h, double tol, int32_t leaf, int32_t max_rank,
+                   int32_t alpha, int32_t knn, void* stream, mf_bfset** out);
+/* rows of the set, stored complex entries, largest ID rank, build wall time */
+int mf_green_info(const mf_bfset* s, int64_t* rows, double* storage_entries, int32_t* max_rank,
+                  double* build_seconds);
+/* host copies of the source (z = 0) and target (z = h) points, rows x 3 each, in the set's row order */
+int mf_green_points(const mf_bfset* s, double* P, double* Q);
+/*
+ * y_b = H_b x_b for every block (the butterfly apply of Sec. 3.1, level by level).
+ * x, y: device, planar complex64 rows x nrhs row-major (real plane, then the
+ * imaginary plane at offset rows * nrhs).  Waits for the set's stream.
+ */
+int mf_green_apply(mf_bfset* s, int32_t nrhs, const float* x, float* y);
+void mf_green_destroy(mf_bfset* s);
+
 /* Kernel launches issued by the library since it was loaded (all handles, all streams). */
 int64_t mf_launch_counter(void);
 

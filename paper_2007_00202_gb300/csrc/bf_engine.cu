@@ -1,0 +1,1722 @@
+// Butterfly and HOD-BF algorithms on the GPU (Sec. 3-4; Alg. 2, 3, 4), host-driven:
+// index sets, ranks and skeletons are host data; every product, ID, gather
+// and solve is a batched device launch on the context's stream.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "bf_engine.h"
+
+namespace mf {
+
+namespace {
+
+// splitmix64 (Steele, Lea, Flood 2014) for reproducible uniform sampling of proxies
+inline uint64_t splitmix(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  uint64_t z = x;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// cnt indices of [a, b) uniformly without replacement: the cnt smallest hashes
+// h(c) = splitmix64(salt ^ (c * golden)), salt = (a << 32) | b, returned sorted.
+IdxVec uniform_sample(int64_t a, int64_t b, int64_t cnt) {
+  const uint64_t salt = ((uint64_t)(a & 0xFFFFFFFF) << 32) | (uint64_t)(b & 0xFFFFFFFF);
+  std::vector<std::pair<uint64_t, int32_t>> h;
+  h.reserve(b - a);
+  for (int64_t c = a; c < b; ++c) h.push_back({splitmix(salt ^ ((uint64_t)c * 0x9E3779B97F4A7C15ull)), (int32_t)c});
+  if (cnt < (int64_t)h.size()) std::partial_sort(h.begin(), h.begin() + cnt, h.end());
+  IdxVec out;
+  for (int64_t k = 0; k < cnt && k < (int64_t)h.size(); ++k) out.push_back(h[k].second);
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+// Proxy columns for rows X inside [a, b): alpha |X| uniform samples plus the
+// knn nearest neighbours of each row that fall in [a, b); all of [a, b) when
+// (alpha + knn) |X| >= b - a.
+IdxVec proxies(const IdxVec& X, int64_t a, int64_t b, const std::vector<IdxVec>& nn, int alpha, int knn) {
+  const int64_t size = b - a;
+  IdxVec out;
+  if ((int64_t)(alpha + knn) * (int64_t)X.size() >= size) {
+    out.resize(size);
+    std::iota(out.begin(), out.end(), (int32_t)a);
+    return out;
+  }
+  out = uniform_sample(a, b, (int64_t)alpha * X.size());
+  for (int32_t x : X) {
+    if (x < 0 || x >= (int32_t)nn.size()) continue;
+    int k = 0;
+    for (int32_t c : nn[x]) {
+      if (k++ >= knn) break;
+      if (c >= a && c < b) out.push_back(c);
+    }
+  }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+  return out;
+}
+
+IdxVec cat(const IdxVec& a, const IdxVec& b) {
+  IdxVec o(a);
+  o.insert(o.end(), b.begin(), b.end());
+  return o;
+}
+
+IdxVec range_vec(int64_t a, int64_t b) {
+  IdxVec o(b - a);
+  std::iota(o.begin(), o.end(), (int32_t)a);
+  return o;
+}
+
+template <typename T>
+GemmDesc<T> gdesc(int m, int n, int k, int ta, int tb, T alpha, T beta, const Blk<T>& A, const Blk<T>& B,
+                  const Blk<T>& C) {
+  GemmDesc<T> d;
+  d.m = m; d.n = n; d.k = k; d.transA = ta; d.transB = tb; d.alpha = alpha; d.beta = beta;
+  d.A = A.pm(); d.B = B.pm(); d.C = C.pm();
+  return d;
+}
+
+}  // namespace
+
+Tree subtree(const Tree& t, int l0, int i0, int depth);
+Tree extend_tree(const Tree& t, int depth);
+
+Tree subtree(const Tree& t, int l0, int i0, int depth) {
+  const int64_t a0 = t[l0][i0].a;
+  Tree out;
+  for (int d = 0; d <= depth; ++d) {
+    std::vector<Range> lv;
+    for (int k = i0 * (1 << d); k < (i0 + 1) * (1 << d); ++k) lv.push_back({t[l0 + d][k].a - a0, t[l0 + d][k].b - a0});
+    out.push_back(std::move(lv));
+  }
+  return out;
+}
+
+Tree extend_tree(const Tree& t, int depth) {
+  Tree out(t.begin(), t.begin() + std::min<size_t>(t.size(), depth + 1));
+  while ((int)out.size() < depth + 1) {
+    std::vector<Range> nw;
+    for (auto& r : out.back()) {
+      int64_t m = r.a + (r.b - r.a + 1) / 2;
+      nw.push_back({r.a, m});
+      nw.push_back({m, r.b});
+    }
+    out.push_back(std::move(nw));
+  }
+  return out;
+}
+
+template <typename T>
+int DBF<T>::max_rank() const {
+  int r = 0;
+  for (auto& lv : Osk)
+    for (auto& s : lv) r = std::max(r, (int)s.size());
+  for (auto& lv : Ssk)
+    for (auto& s : lv) r = std::max(r, (int)s.size());
+  return r;
+}
+
+template <typename T>
+double DBF<T>::storage() const {
+  double s = 0;
+  for (auto& lv : U)
+    for (auto& b : lv) s += (double)b.rows * b.cols;
+  for (auto& lv : V)
+    for (auto& b : lv) s += (double)b.rows * b.cols;
+  for (auto& b : B) s += (double)b.rows * b.cols;
+  return s;
+}
+
+template <typename T>
+int DHODBF<T>::max_rank() const {
+  int r = 0;
+  for (auto& lv : off)
+    for (auto& b : lv)
+      if (b) r = std::max(r, b->max_rank());
+  return r;
+}
+
+template <typename T>
+double DHODBF<T>::storage() const {
+  double s = 0;
+  for (auto& d : D) s += (double)d.rows * d.cols;
+  for (auto& lv : off)
+    for (auto& b : lv)
+      if (b) s += b->storage();
+  return s;
+}
+
+template <typename T>
+double DHODBFInv<T>::storage() const {
+  double s = 0;
+  for (auto& d : Dinv) s += (double)d.rows * d.cols;
+  for (auto& lv : M)
+    for (auto& b : lv)
+      if (b) s += b->storage();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// context and primitives
+// ---------------------------------------------------------------------------
+template <typename T>
+BFContext<T>::BFContext(cudaStream_t s, size_t pb, size_t sb) : st(s) {
+  persist.init(pb);
+  scratch.init(sb);
+  status.alloc(sizeof(int32_t));
+  MF_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int32_t), st));
+}
+
+template <typename T>
+void BFContext<T>::check_status() {
+  int32_t v = 0;
+  MF_CUDA(cudaMemcpyAsync(&v, status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MF_CUDA(cudaStreamSynchronize(st));
+  if (v != 0) throw SingularError("singular block in a compressed front (zero pivot or indefinite normal equations)");
+}
+
+template <typename T>
+void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
+  std::vector<GemmDesc<T>> D;
+  std::vector<GemmTile> tl;
+  for (auto& d : descs) {
+    if (d.m <= 0 || d.n <= 0) continue;
+    int idx = (int)D.size();
+    D.push_back(d);
+    flops += 8.0 * d.m * d.n * d.k;
+    for (int i = 0; i < (d.m + GEMM_TILE - 1) / GEMM_TILE; ++i)
+      for (int j = 0; j < (d.n + GEMM_TILE - 1) / GEMM_TILE; ++j) tl.push_back({idx, i, j, 0});
+  }
+  if (tl.empty()) return;
+  auto* dd = scratch.takeT<GemmDesc<T>>(D.size());
+  auto* dt = scratch.takeT<GemmTile>(tl.size());
+  MF_CUDA(cudaMemcpyAsync(dd, D.data(), D.size() * sizeof(GemmDesc<T>), cudaMemcpyHostToDevice, st));
+  MF_CUDA(cudaMemcpyAsync(dt, tl.data(), tl.size() * sizeof(GemmTile), cudaMemcpyHostToDevice, st));
+  launch_gemm<T>(dd, dt, (int)tl.size(), st);
+}
+
+template <typename T>
+void BFContext<T>::zero(Blk<T>& b) {
+  if (b.rows <= 0 || b.cols <= 0) return;
+  MF_CUDA(cudaMemsetAsync(b.p, 0, sizeof(T) * (size_t)b.rows * b.ld, st));
+  MF_CUDA(cudaMemsetAsync(b.p + b.plane, 0, sizeof(T) * (size_t)b.rows * b.ld, st));
+}
+
+template <typename T>
+static void run_blk2(BFContext<T>& cx, std::vector<Blk2Job<T>>& jobs) {
+  if (jobs.empty()) return;
+  int64_t mx = 0;
+  for (auto& j : jobs) mx = std::max<int64_t>(mx, (int64_t)j.rows * j.cols);
+  auto* dj = cx.scratch.template takeT<Blk2Job<T>>(jobs.size());
+  MF_CUDA(cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(Blk2Job<T>), cudaMemcpyHostToDevice, cx.st));
+  launch_blk2<T>(dj, (int)jobs.size(), mx, cx.st);
+}
+
+template <typename T>
+static const int32_t* dev_idx(BFContext<T>& cx, const IdxVec& v) {
+  auto* d = cx.scratch.template takeT<int32_t>(std::max<size_t>(v.size(), 1));
+  if (!v.empty()) MF_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * 4, cudaMemcpyHostToDevice, cx.st));
+  return d;
+}
+
+template <typename T>
+void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_rank, std::vector<IdxVec>& sk,
+                           std::vector<Blk<T>>& Us) {
+  const size_t nj = Ms.size();
+  sk.assign(nj, {});
+  Us.assign(nj, Blk<T>());
+  if (!nj) return;
+  std::vector<IdJob<T>> jobs;
+  std::vector<size_t> which;
+  int32_t* dsk = nullptr;
+  int32_t* drk = scratch.takeT<int32_t>(nj);
+  std::vector<int> kmaxv(nj, 0);
+  size_t sktot = 0;
+  for (size_t q = 0; q < nj; ++q) {
+    int m = Ms[q].rows, n = Ms[q].cols;
+    int kmax = std::min(m, n);
+    if (max_rank > 0) kmax = std::min(kmax, max_rank);
+    kmaxv[q] = kmax;
+    sktot += std::max(kmax, 1);
+  }
+  dsk = scratch.takeT<int32_t>(sktot);
+  size_t skoff = 0;
+  int max_m = 1, max_n = 1;
+  std::vector<size_t> skoffv(nj);
+  for (size_t q = 0; q < nj; ++q) {
+    skoffv[q] = skoff;
+    int m = Ms[q].rows, n = Ms[q].cols, kmax = kmaxv[q];
+    skoff += std::max(kmax, 1);
+    Blk<T> U;
+    U.rows = m;
+    U.cols = 0;
+    U.ld = std::max(1, (kmax + 3) & ~3);
+    U.plane = (int64_t)std::max(m, 1) * U.ld;
+    U.p = persist.takeT<T>(2 * (size_t)U.plane);
+    Us[q] = U;
+    if (m == 0 || n == 0 || kmax == 0) continue;
+    IdJob<T> j;
+    j.M = Ms[q].p;
+    j.plane = Ms[q].plane;
+    j.ld = Ms[q].ld;
+    j.m = m;
+    j.n = n;
+    j.U = U.p;
+    j.uplane = U.plane;
+    j.ldu = (int32_t)U.ld;
+    j.sk = dsk + skoffv[q];
+    j.rank = drk + q;
+    j.work = scratch.takeT<T>(2 * (size_t)m * n);
+    j.wplane = (int64_t)m * n;
+    jobs.push_back(j);
+    which.push_back(q);
+    max_m = std::max(max_m, m);
+    max_n = std::max(max_n, n);
+  }
+  MF_CUDA(cudaMemsetAsync(drk, 0, nj * 4, st));
+  if (!jobs.empty()) {
+    auto* dj = scratch.takeT<IdJob<T>>(jobs.size());
+    MF_CUDA(cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(IdJob<T>), cudaMemcpyHostToDevice, st));
+    if (launch_row_id<T>(dj, (int)jobs.size(), max_m, max_n, (T)tol, max_rank, st) != 0)
+      throw std::runtime_error("ID block too large for the row-ID kernel (" + std::to_string(max_m) + " x " +
+                               std::to_string(max_n) + ")");
+    n_id += (int64_t)jobs.size();
+  }
+  std::vector<int32_t> hr(nj), hs(sktot);
+  MF_CUDA(cudaMemcpyAsync(hr.data(), drk, nj * 4, cudaMemcpyDeviceToHost, st));
+  MF_CUDA(cudaMemcpyAsync(hs.data(), dsk, sktot * 4, cudaMemcpyDeviceToHost, st));
+  MF_CUDA(cudaStreamSynchronize(st));
+  for (size_t q = 0; q < nj; ++q) {
+    int r = hr[q];
+    Us[q].cols = r;
+    sk[q].assign(hs.begin() + skoffv[q], hs.begin() + skoffv[q] + r);
+    max_rank_seen = std::max(max_rank_seen, r);
+    flops += 8.0 * 2.0 * Ms[q].rows * (double)Ms[q].cols * r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// apply: Y (=|+=) K X for several butterflies at once (stage-merged launches)
+// ---------------------------------------------------------------------------
+template <typename T>
+void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vector<Blk<T>>& X, std::vector<Blk<T>>& Y,
+                         bool transpose, bool accumulate) {
+  const size_t nb = bfs.size();
+  if (!nb) return;
+  const int k = X[0].cols;
+  std::map<int, std::vector<GemmDesc<T>>> stages;   // stage index -> descs
+  const T one = T(1), zero = T(0), beta_out = accumulate ? T(1) : T(0);
+  for (size_t q = 0; q < nb; ++q) {
+    const DBF<T>& bf = *bfs[q];
+    const int L = bf.L, lc = bf.lc;
+    auto vec_buf = [&](const std::vector<int>& ranks, std::vector<Blk<T>>& out) {
+      size_t tot = 0;
+      for (int r : ranks) tot += (size_t)r;
+      Blk<T> all;
+      all.rows = (int)tot;
+      all.cols = k;
+      all.ld = k;
+      all.plane = (int64_t)std::max<size_t>(tot, 1) * k;
+      all.p = scratch.takeT<T>(2 * (size_t)all.plane);
+      out.resize(ranks.size());
+      size_t o = 0;
+      for (size_t p = 0; p < ranks.size(); ++p) {
+        out[p] = all.sub((int)o, 0, ranks[p], k);
+        o += ranks[p];
+      }
+    };
+    int stg = 0;
+    if (!transpose) {
+      // right half: level 0 (V), levels 1..lc (W)
+      std::vector<Blk<T>> prev, cur;
+      {
+        std::vector<int> rk;
+        for (int j = 0; j < (1 << L); ++j) rk.push_back(bf.rc(0, 0, j));
+        vec_buf(rk, cur);
+        for (int j = 0; j < (1 << L); ++j) {
+          const Range r = bf.ct[L][j];
+          const Blk<T>& V = bf.V[0][j];
+          stages[stg].push_back(gdesc<T>(bf.rc(0, 0, j), k, (int)(r.b - r.a), 1, 0, one, zero, V,
+                                         X[q].sub((int)r.a, 0, (int)(r.b - r.a), k), cur[j]));
+        }
+        ++stg;
+      }
+      for (int l = 1; l <= lc; ++l) {
+        prev.swap(cur);
+        std::vector<int> rk;
+        for (int i = 0; i < (1 << l); ++i)
+          for (int j = 0; j < (1 << (L - l)); ++j) rk.push_back(bf.rc(l, i, j));
+        vec_buf(rk, cur);
+        for (int i = 0; i < (1 << l); ++i)
+          for (int j = 0; j < (1 << (L - l)); ++j) {
+            const int p = bf.pidx(l, i, j);
+            const int p1 = bf.pidx(l - 1, i / 2, 2 * j);
+            const int c1 = bf.rc(l - 1, i / 2, 2 * j), c2 = bf.rc(l - 1, i / 2, 2 * j + 1);
+            Blk<T> in = prev[p1];
+            in.rows = c1 + c2;   // (i/2, 2j) and (i/2, 2j+1) are adjacent in the level buffer
+            stages[stg].push_back(gdesc<T>(bf.rc(l, i, j), k, c1 + c2, 1, 0, one, zero, bf.V[l][p], in, cur[p]));
+          }
+        ++stg;
+      }
+      // centre
+      std::vector<Blk<T>> ys;
+      {
+        std::vector<int> rk;
+        for (int i = 0; i < (1 << lc); ++i)
+          for (int j = 0; j < (1 << (L - lc)); ++j) rk.push_back(bf.rr(lc, i, j));
+        vec_buf(rk, ys);
+        for (int i = 0; i < (1 << lc); ++i)
+          for (int j = 0; j < (1 << (L - lc)); ++j) {
+            const int p = bf.pidx(lc, i, j);
+            stages[stg].push_back(gdesc<T>(bf.rr(lc, i, j), k, bf.rc(lc, i, j), 0, 0, one, zero, bf.B[p], cur[p], ys[p]));
+          }
+        ++stg;
+      }
+      // left half: levels lc .. L-1 -> l+1, pulled per output pair, two accumulation stages
+      for (int l = lc; l < L; ++l) {
+        std::vector<Blk<T>> nxt;
+        std::vector<int> rk;
+        for (int i = 0; i < (1 << (l + 1)); ++i)
+          for (int j = 0; j < (1 << (L - l - 1)); ++j) rk.push_back(bf.rr(l + 1, i, j));
+        vec_buf(rk, nxt);
+        for (int t = 0; t < 2; ++t) {
+          for (int i2 = 0; i2 < (1 << (l + 1)); ++i2)
+            for (int j2 = 0; j2 < (1 << (L - l - 1)); ++j2) {
+              const int i = i2 / 2, nu = 2 * j2 + t;
+              const int p = bf.pidx(l, i, nu);
+              const int r1 = bf.rr(l + 1, 2 * i, j2);
+              const int rows0 = (i2 % 2 == 0) ? 0 : r1;
+              const int nrow = bf.rr(l + 1, i2, j2);
+              const Blk<T>& R = bf.U[l][p];
+              stages[stg + t].push_back(gdesc<T>(nrow, k, bf.rr(l, i, nu), 0, 0, one, t == 0 ? zero : one,
+                                                 R.sub(rows0, 0, nrow, R.cols), ys[p], nxt[bf.pidx(l + 1, i2, j2)]));
+            }
+        }
+        stg += 2;
+        ys.swap(nxt);
+      }
+      for (int i = 0; i < (1 << L); ++i) {
+        const Range r = bf.rt[L][i];
+        const Blk<T>& U = bf.U[L][i];
+        stages[stg].push_back(gdesc<T>((int)(r.b - r.a), k, bf.rr(L, i, 0), 0, 0, one, beta_out, U, ys[i],
+                                       Y[q].sub((int)r.a, 0, (int)(r.b - r.a), k)));
+      }
+    } else {
+      // transpose: U^T, R^T (two stages), B^T, W (pulled, two stages), V
+      std::vector<Blk<T>> cur;
+      {
+        std::vector<int> rk;
+        for (int i = 0; i < (1 << L); ++i) rk.push_back(bf.rr(L, i, 0));
+        vec_buf(rk, cur);
+        for (int i = 0; i < (1 << L); ++i) {
+          const Range r = bf.rt[L][i];
+          stages[stg].push_back(gdesc<T>(bf.rr(L, i, 0), k, (int)(r.b - r.a), 1, 0, one, zero, bf.U[L][i],
+                                         X[q].sub((int)r.a, 0, (int)(r.b - r.a), k), cur[i]));
+        }
+        ++stg;
+      }
+      for (int l = L - 1; l >= lc; --l) {
+        std::vector<Blk<T>> nxt;
+        std::vector<int> rk;
+        for (int i = 0; i < (1 << l); ++i)
+          for (int j = 0; j < (1 << (L - l)); ++j) rk.push_back(bf.rr(l, i, j));
+        vec_buf(rk, nxt);
+        for (int t = 0; t < 2; ++t) {
+          for (int i = 0; i < (1 << l); ++i)
+            for (int j = 0; j < (1 << (L - l)); ++j) {
+              const int p = bf.pidx(l, i, j);
+              const int r1 = bf.rr(l + 1, 2 * i, j / 2);
+              const int rows0 = t == 0 ? 0 : r1;
+              const int nrow = bf.rr(l + 1, 2 * i + t, j / 2);
+              const Blk<T>& R = bf.U[l][p];
+              stages[stg + t].push_back(gdesc<T>(bf.rr(l, i, j), k, nrow, 1, 0, one, t == 0 ? zero : one,
+                                                 R.sub(rows0, 0, nrow, R.cols), cur[bf.pidx(l + 1, 2 * i + t, j / 2)],
+                                                 nxt[p]));
+            }
+        }
+        stg += 2;
+        cur.swap(nxt);
+      }
+      std::vector<Blk<T>> ys;
+      {
+        std::vector<int> rk;
+        for (int i = 0; i < (1 << lc); ++i)
+          for (int j = 0; j < (1 << (L - lc)); ++j) rk.push_back(bf.rc(lc, i, j));
+        vec_buf(rk, ys);
+        for (int i = 0; i < (1 << lc); ++i)
+          for (int j = 0; j < (1 << (L - lc)); ++j) {
+            const int p = bf.pidx(lc, i, j);
+            stages[stg].push_back(gdesc<T>(bf.rc(lc, i, j), k, bf.rr(lc, i, j), 1, 0, one, zero, bf.B[p], cur[p], ys[p]));
+          }
+        ++stg;
+      }
+      for (int l = lc; l >= 1; --l) {
+        std::vector<Blk<T>> nxt;
+        std::vector<int> rk;
+        for (int i = 0; i < (1 << (l - 1)); ++i)
+          for (int j = 0; j < (1 << (L - l + 1)); ++j) rk.push_back(bf.rc(l - 1, i, j));
+        vec_buf(rk, nxt);
+        for (int t = 0; t < 2; ++t) {
+          for (int i2 = 0; i2 < (1 << (l - 1)); ++i2)
+            for (int j2 = 0; j2 < (1 << (L - l + 1)); ++j2) {
+              const int i = 2 * i2 + t, j = j2 / 2;
+              const int p = bf.pidx(l, i, j);
+              const int c1 = bf.rc(l - 1, i2, 2 * j);
+              const int rows0 = (j2 % 2 == 0) ? 0 : c1;
+              const int nrow = bf.rc(l - 1, i2, j2);
+              const Blk<T>& W = bf.V[l][p];
+              stages[stg + t].push_back(gdesc<T>(nrow, k, bf.rc(l, i, j), 0, 0, one, t == 0 ? zero : one,
+                                                 W.sub(rows0, 0, nrow, W.cols), ys[p], nxt[bf.pidx(l - 1, i2, j2)]));
+            }
+        }
+        stg += 2;
+        ys.swap(nxt);
+      }
+      for (int j = 0; j < (1 << L); ++j) {
+        const Range r = bf.ct[L][j];
+        stages[stg].push_back(gdesc<T>((int)(r.b - r.a), k, bf.rc(0, 0, j), 0, 0, one, beta_out, bf.V[0][j], ys[j],
+                                       Y[q].sub((int)r.a, 0, (int)(r.b - r.a), k)));
+      }
+    }
+  }
+  // The final stage of each butterfly writes its output; butterflies with fewer stages finish earlier,
+  // which is fine because outputs of different butterflies in one call are disjoint or accumulated in
+  // separate calls by the callers.
+  for (auto& kv : stages) gemm(kv.second);
+}
+
+template <typename T>
+void BFContext<T>::right_transform(const DBF<T>& bf, const Blk<T>& X, std::vector<Blk<T>>& xs) {
+  const int L = bf.L, lc = bf.lc, k = X.cols;
+  std::vector<Blk<T>> prev, cur;
+  auto buf = [&](std::vector<Blk<T>>& out, int l) {
+    out.assign((size_t)1 << L, Blk<T>());
+    size_t tot = 0;
+    for (int p = 0; p < (1 << L); ++p) tot += (size_t)bf.Ssk[l][p].size();
+    Blk<T> all;
+    all.rows = (int)tot; all.cols = k; all.ld = k; all.plane = (int64_t)std::max<size_t>(tot, 1) * k;
+    all.p = scratch.takeT<T>(2 * (size_t)all.plane);
+    size_t o = 0;
+    for (int p = 0; p < (1 << L); ++p) {
+      out[p] = all.sub((int)o, 0, (int)bf.Ssk[l][p].size(), k);
+      o += bf.Ssk[l][p].size();
+    }
+  };
+  buf(cur, 0);
+  std::vector<GemmDesc<T>> g;
+  for (int j = 0; j < (1 << L); ++j) {
+    const Range r = bf.ct[L][j];
+    g.push_back(gdesc<T>(bf.rc(0, 0, j), k, (int)(r.b - r.a), 1, 0, T(1), T(0), bf.V[0][j],
+                         X.sub((int)r.a, 0, (int)(r.b - r.a), k), cur[j]));
+  }
+  gemm(g);
+  for (int l = 1; l <= lc; ++l) {
+    prev.swap(cur);
+    buf(cur, l);
+    g.clear();
+    for (int i = 0; i < (1 << l); ++i)
+      for (int j = 0; j < (1 << (L - l)); ++j) {
+        const int p = bf.pidx(l, i, j);
+        const int p1 = bf.pidx(l - 1, i / 2, 2 * j);
+        const int c1 = bf.rc(l - 1, i / 2, 2 * j), c2 = bf.rc(l - 1, i / 2, 2 * j + 1);
+        Blk<T> in = prev[p1];
+        in.rows = c1 + c2;
+        g.push_back(gdesc<T>(bf.rc(l, i, j), k, c1 + c2, 1, 0, T(1), T(0), bf.V[l][p], in, cur[p]));
+      }
+    gemm(g);
+  }
+  xs.swap(cur);
+}
+
+// ---------------------------------------------------------------------------
+// construction from entry extraction (Alg. 2), many butterflies with the same
+// number of levels in lockstep: per level one extraction call (all blocks of
+// all problems) and one batched ID launch.  Problem q's local indices are
+// shifted by (row_off, col_off) into the index space of the extractor.
+// ---------------------------------------------------------------------------
+template <typename T>
+void BFContext<T>::entry_eval_batch(const DExtract<T>& ext, std::vector<BFProblem<T>>& probs, const BFParams& P) {
+  if (probs.empty()) return;
+  const int L = probs[0].L, lc = L / 2;
+  for (auto& pb : probs) {
+    if (pb.L != L) throw std::runtime_error("entry_eval_batch: problems must share the level count");
+    pb.out = std::make_unique<DBF<T>>();
+    pb.out->init(pb.m, pb.n, pb.rt, pb.ct, L);
+  }
+  const size_t mk = scratch.mark();
+  auto shifted = [&](const std::vector<std::pair<IdxVec, IdxVec>>& lst, const BFProblem<T>& pb,
+                     std::vector<std::pair<IdxVec, IdxVec>>& g) {
+    for (auto pr : lst) {
+      for (auto& x : pr.first) x += (int32_t)pb.row_off;
+      for (auto& y : pr.second) y += (int32_t)pb.col_off;
+      g.push_back(std::move(pr));
+    }
+  };
+  for (int l = L; l >= lc; --l) {                         // left to middle
+    std::vector<std::pair<IdxVec, IdxVec>> all;
+    std::vector<std::vector<std::pair<IdxVec, IdxVec>>> loc(probs.size());
+    for (size_t q = 0; q < probs.size(); ++q) {
+      DBF<T>& bf = *probs[q].out;
+      for (int i = 0; i < (1 << l); ++i)
+        for (int j = 0; j < (1 << (L - l)); ++j) {
+          IdxVec X = l == L ? range_vec(bf.rt[L][i].a, bf.rt[L][i].b)
+                            : cat(bf.Osk[l + 1][bf.pidx(l + 1, 2 * i, j / 2)],
+                                  bf.Osk[l + 1][bf.pidx(l + 1, 2 * i + 1, j / 2)]);
+          const Range c = bf.ct[L - l][j];
+          loc[q].push_back({X, proxies(X, c.a, c.b, probs[q].nn_r, P.alpha, P.knn)});
+        }
+      shifted(loc[q], probs[q], all);
+    }
+    std::vector<Blk<T>> blocks(all.size());
+    for (size_t t = 0; t < all.size(); ++t) blocks[t] = new_blk<T>(scratch, (int)all[t].first.size(), (int)all[t].second.size());
+    ext(all, blocks);
+    std::vector<IdxVec> sk;
+    std::vector<Blk<T>> Us;
+    row_ids(blocks, P.tol, P.max_rank, sk, Us);
+    size_t t = 0;
+    for (size_t q = 0; q < probs.size(); ++q) {
+      DBF<T>& bf = *probs[q].out;
+      for (size_t p = 0; p < loc[q].size(); ++p, ++t) {
+        bf.U[l][p] = Us[t];
+        IdxVec o;
+        for (int32_t x : sk[t]) o.push_back(loc[q][p].first[x]);
+        bf.Osk[l][p] = o;
+      }
+    }
+    scratch.release(mk);
+  }
+  for (int l = 0; l <= lc; ++l) {                         // right to middle (column IDs)
+    std::vector<std::pair<IdxVec, IdxVec>> all;
+    std::vector<std::vector<std::pair<IdxVec, IdxVec>>> loc(probs.size());
+    for (size_t q = 0; q < probs.size(); ++q) {
+      DBF<T>& bf = *probs[q].out;
+      for (int i = 0; i < (1 << l); ++i)
+        for (int j = 0; j < (1 << (L - l)); ++j) {
+          IdxVec Y = l == 0 ? range_vec(bf.ct[L][j].a, bf.ct[L][j].b)
+                            : cat(bf.Ssk[l - 1][bf.pidx(l - 1, i / 2, 2 * j)],
+                                  bf.Ssk[l - 1][bf.pidx(l - 1, i / 2, 2 * j + 1)]);
+          const Range r = bf.rt[l][i];
+          loc[q].push_back({proxies(Y, r.a, r.b, probs[q].nn_c, P.alpha, P.knn), Y});
+        }
+      shifted(loc[q], probs[q], all);
+    }
+    std::vector<Blk<T>> blocks(all.size()), tblocks(all.size());
+    for (size_t t = 0; t < all.size(); ++t) {
+      blocks[t] = new_blk<T>(scratch, (int)all[t].first.size(), (int)all[t].second.size());
+      tblocks[t] = new_blk<T>(scratch, (int)all[t].second.size(), (int)all[t].first.size());
+    }
+    ext(all, blocks);
+    std::vector<Blk2Job<T>> tj;
+    for (size_t t = 0; t < all.size(); ++t) {
+      Blk2Job<T> jb{};
+      jb.src = blocks[t].p; jb.splane = blocks[t].plane; jb.sld = blocks[t].ld;
+      jb.dst = tblocks[t].p; jb.dplane = tblocks[t].plane; jb.dld = tblocks[t].ld;
+      jb.rows = blocks[t].rows; jb.cols = blocks[t].cols; jb.mode = 0; jb.alpha = T(1);
+      if (jb.rows && jb.cols) tj.push_back(jb);
+    }
+    run_blk2(*this, tj);
+    std::vector<IdxVec> sk;
+    std::vector<Blk<T>> Vs;
+    row_ids(tblocks, P.tol, P.max_rank, sk, Vs);
+    size_t t = 0;
+    for (size_t q = 0; q < probs.size(); ++q) {
+      DBF<T>& bf = *probs[q].out;
+      for (size_t p = 0; p < loc[q].size(); ++p, ++t) {
+        bf.V[l][p] = Vs[t];
+        IdxVec o;
+        for (int32_t y : sk[t]) o.push_back(loc[q][p].second[y]);
+        bf.Ssk[l][p] = o;
+      }
+    }
+    scratch.release(mk);
+  }
+  {                                                       // centre
+    std::vector<std::pair<IdxVec, IdxVec>> all, loc;
+    std::vector<Blk<T>> blocks;
+    for (size_t q = 0; q < probs.size(); ++q) {
+      DBF<T>& bf = *probs[q].out;
+      loc.clear();
+      for (int p = 0; p < (1 << L); ++p) loc.push_back({bf.Osk[lc][p], bf.Ssk[lc][p]});
+      shifted(loc, probs[q], all);
+      for (int p = 0; p < (1 << L); ++p) {
+        bf.B[p] = new_blk<T>(persist, (int)bf.Osk[lc][p].size(), (int)bf.Ssk[lc][p].size());
+        blocks.push_back(bf.B[p]);
+      }
+    }
+    ext(all, blocks);
+  }
+  MF_CUDA(cudaStreamSynchronize(st));
+  scratch.release(mk);
+}
+
+template <typename T>
+std::unique_ptr<DBF<T>> BFContext<T>::entry_eval(const DExtract<T>& ext, int m, int n, const Tree& rt, const Tree& ct,
+                                                  int L, const std::vector<IdxVec>& nn_r,
+                                                  const std::vector<IdxVec>& nn_c, const BFParams& P) {
+  std::vector<BFProblem<T>> pr(1);
+  pr[0].m = m; pr[0].n = n; pr[0].L = L; pr[0].rt = rt; pr[0].ct = ct; pr[0].nn_r = nn_r; pr[0].nn_c = nn_c;
+  entry_eval_batch(ext, pr, P);
+  return std::move(pr[0].out);
+}
+
+// ---------------------------------------------------------------------------
+// construction from products (Sec. 3.2; reading: ID-based sketching variant of Alg. 2)
+// ---------------------------------------------------------------------------
+template <typename T>
+std::unique_ptr<DBF<T>> BFContext<T>::random_matvec(const DOp<T>& op, const Tree& rt, const Tree& ct, int L,
+                                                     const BFParams& P, uint32_t key) {
+  const int m = op.rows, n = op.cols;
+  auto bf = std::make_unique<DBF<T>>();
+  bf->init(m, n, rt, ct, L);
+  const int lc = bf->lc;
+  const int q0 = (P.max_rank > 0 ? P.max_rank : P.q_start) + P.p;
+  const size_t mk = scratch.mark();
+  Blk<T> cOm, cY;
+  std::vector<std::pair<int, int>> ccols;
+  auto sketch = [&](int rows, const std::vector<Range>& groups, int q, int level, int side,
+                    std::vector<std::pair<int, int>>& cols) -> Blk<T> {
+    cols.clear();
+    int tot = 0;
+    std::vector<SketchGroup> sg;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      int size = (int)(groups[g].b - groups[g].a);
+      int w = size <= q ? size : q;
+      cols.push_back({tot, tot + w});
+      SketchGroup s;
+      s.a = groups[g].a; s.b = groups[g].b; s.c0 = tot; s.w = w;
+      s.key = (int32_t)((key * 1000003u + (uint32_t)level * 7919u + (uint32_t)side * 104729u + (uint32_t)g) & 0xFFFFFF);
+      s.identity = (w == size) ? 1 : 0;
+      if (w > 0) sg.push_back(s);
+      tot += w;
+    }
+    Blk<T> Om = new_blk<T>(scratch, rows, std::max(tot, 1));
+    Om.cols = tot;
+    zero(Om);
+    if (!sg.empty()) {
+      int mx = 0;
+      for (auto& s : sg) mx = std::max<int>(mx, (int)((s.b - s.a) * s.w));
+      auto* dg = scratch.takeT<SketchGroup>(sg.size());
+      MF_CUDA(cudaMemcpyAsync(dg, sg.data(), sg.size() * sizeof(SketchGroup), cudaMemcpyHostToDevice, st));
+      launch_sketch<T>(dg, (int)sg.size(), mx, Om.p, Om.plane, (int)Om.ld, st);
+    }
+    return Om;
+  };
+  auto gather = [&](const Blk<T>& Y, const IdxVec& rows, std::pair<int, int> cols) -> std::pair<Blk<T>, GatherJob<T>> {
+    Blk<T> M = new_blk<T>(scratch, (int)rows.size(), cols.second - cols.first);
+    GatherJob<T> g;
+    g.src = Y.p; g.splane = Y.plane; g.sld = Y.ld;
+    g.rows = dev_idx(*this, rows);
+    g.c0 = cols.first;
+    g.nrows = (int)rows.size();
+    g.ncols = cols.second - cols.first;
+    g.dst = M.p; g.dplane = M.plane; g.dld = M.ld;
+    return {M, g};
+  };
+  auto run_gathers = [&](std::vector<GatherJob<T>>& gj) {
+    if (gj.empty()) return;
+    int64_t mx = 0;
+    for (auto& g : gj) mx = std::max<int64_t>(mx, (int64_t)g.nrows * g.ncols);
+    auto* d = scratch.takeT<GatherJob<T>>(gj.size());
+    MF_CUDA(cudaMemcpyAsync(d, gj.data(), gj.size() * sizeof(GatherJob<T>), cudaMemcpyHostToDevice, st));
+    launch_gather_rows<T>(d, (int)gj.size(), mx, st);
+  };
+  for (int l = L; l >= lc; --l) {                         // left half: sketches of K(X, S_nu)
+    const auto& groups = bf->ct[L - l];
+    int q = q0;
+    for (;;) {
+      std::vector<std::pair<int, int>> cols;
+      Blk<T> Om = sketch(n, groups, q, l, 0, cols);
+      Blk<T> Y = new_blk<T>(scratch, m, std::max(Om.cols, 1));
+      Y.cols = Om.cols;
+      if (Om.cols > 0) op.apply(Om, Y, false);
+      std::vector<Blk<T>> Ms;
+      std::vector<GatherJob<T>> gj;
+      std::vector<IdxVec> Xs;
+      for (int i = 0; i < (1 << l); ++i)
+        for (int j = 0; j < (1 << (L - l)); ++j) {
+          IdxVec X = l == L ? range_vec(bf->rt[L][i].a, bf->rt[L][i].b)
+                            : cat(bf->Osk[l + 1][bf->pidx(l + 1, 2 * i, j / 2)],
+                                  bf->Osk[l + 1][bf->pidx(l + 1, 2 * i + 1, j / 2)]);
+          auto pr = gather(Y, X, cols[j]);
+          Ms.push_back(pr.first);
+          if (pr.second.nrows && pr.second.ncols) gj.push_back(pr.second);
+          Xs.push_back(X);
+        }
+      run_gathers(gj);
+      std::vector<IdxVec> sk;
+      std::vector<Blk<T>> Us;
+      row_ids(Ms, P.tol, P.max_rank, sk, Us);
+      bool grow = false;
+      if (P.max_rank <= 0)
+        for (size_t p = 0; p < Ms.size(); ++p) {
+          int j = (int)(p % (1 << (L - l)));
+          int w = cols[j].second - cols[j].first, size = (int)(groups[j].b - groups[j].a);
+          if (w < size && (int)sk[p].size() > w - P.p) grow = true;
+        }
+      if (grow && q < 4096) {
+        q *= 2;
+        continue;
+      }
+      for (size_t p = 0; p < Ms.size(); ++p) {
+        bf->U[l][p] = Us[p];
+        IdxVec o;
+        for (int32_t s : sk[p]) o.push_back(Xs[p][s]);
+        bf->Osk[l][p] = o;
+      }
+      if (l == lc) { cOm = Om; cY = Y; ccols = cols; }
+      break;
+    }
+  }
+  const size_t mk2 = scratch.mark();
+  for (int l = 0; l <= lc; ++l) {                         // right half: sketches of K(O_tau, Y)^T
+    const auto& groups = bf->rt[l];
+    int q = q0;
+    for (;;) {
+      std::vector<std::pair<int, int>> cols;
+      Blk<T> Ps = sketch(m, groups, q, l, 1, cols);
+      Blk<T> Z = new_blk<T>(scratch, n, std::max(Ps.cols, 1));
+      Z.cols = Ps.cols;
+      if (Ps.cols > 0) op.apply(Ps, Z, true);
+      std::vector<Blk<T>> Ms;
+      std::vector<GatherJob<T>> gj;
+      std::vector<IdxVec> Ys;
+      for (int i = 0; i < (1 << l); ++i)
+        for (int j = 0; j < (1 << (L - l)); ++j) {
+          IdxVec Yc = l == 0 ? range_vec(bf->ct[L][j].a, bf->ct[L][j].b)
+                             : cat(bf->Ssk[l - 1][bf->pidx(l - 1, i / 2, 2 * j)],
+                                   bf->Ssk[l - 1][bf->pidx(l - 1, i / 2, 2 * j + 1)]);
+          auto pr = gather(Z, Yc, cols[i]);
+          Ms.push_back(pr.first);
+          if (pr.second.nrows && pr.second.ncols) gj.push_back(pr.second);
+          Ys.push_back(Yc);
+        }
+      run_gathers(gj);
+      std::vector<IdxVec> sk;
+      std::vector<Blk<T>> Vs;
+      row_ids(Ms, P.tol, P.max_rank, sk, Vs);
+      bool grow = false;
+      if (P.max_rank <= 0)
+        for (size_t p = 0; p < Ms.size(); ++p) {
+          int i = (int)(p / (1 << (L - l)));
+          int w = cols[i].second - cols[i].first, size = (int)(groups[i].b - groups[i].a);
+          if (w < size && (int)sk[p].size() > w - P.p) grow = true;
+        }
+      if (grow && q < 4096) {
+        q *= 2;
+        continue;
+      }
+      for (size_t p = 0; p < Ms.size(); ++p) {
+        bf->V[l][p] = Vs[p];
+        IdxVec o;
+        for (int32_t s : sk[p]) o.push_back(Ys[p][s]);
+        bf->Ssk[l][p] = o;
+      }
+      break;
+    }
+    scratch.release(mk2);
+  }
+  // centre: B (V^T Omega_nu) = Y(Obar, cols(nu)) in the least-squares sense
+  {
+    std::vector<Blk<T>> xs;
+    right_transform(*bf, cOm, xs);
+    std::vector<LstsqJob<T>> lj;
+    std::vector<GatherJob<T>> gj;
+    std::vector<Blk<T>> Yr(xs.size());
+    int maxc = 1;
+    for (int i = 0; i < (1 << lc); ++i)
+      for (int j = 0; j < (1 << (L - lc)); ++j) {
+        const int p = bf->pidx(lc, i, j);
+        const int r = bf->rr(lc, i, j), c = bf->rc(lc, i, j);
+        Blk<T> Bm = new_blk<T>(persist, r, c);
+        bf->B[p] = Bm;
+        if (r == 0 || c == 0) continue;
+        auto pr = gather(cY, bf->Osk[lc][p], ccols[j]);
+        Yr[p] = pr.first;
+        gj.push_back(pr.second);
+        LstsqJob<T> L1;
+        Blk<T> Tm = xs[p];
+        L1.Tm = Tm.p + ccols[j].first; L1.tplane = Tm.plane; L1.tld = Tm.ld;
+        L1.Y = Yr[p].p; L1.yplane = Yr[p].plane; L1.yld = Yr[p].ld;
+        L1.B = Bm.p; L1.bplane = Bm.plane; L1.bld = Bm.ld;
+        L1.c = c; L1.r = r; L1.w = ccols[j].second - ccols[j].first;
+        lj.push_back(L1);
+        maxc = std::max(maxc, c);
+        flops += 8.0 * ((double)c * c * L1.w + (double)r * c * L1.w);
+      }
+    run_gathers(gj);
+    if (!lj.empty()) {
+      auto* d = scratch.takeT<LstsqJob<T>>(lj.size());
+      MF_CUDA(cudaMemcpyAsync(d, lj.data(), lj.size() * sizeof(LstsqJob<T>), cudaMemcpyHostToDevice, st));
+      if (launch_lstsq<T>(d, (int)lj.size(), maxc, status.as<int32_t>(), st) != 0)
+        throw std::runtime_error("centre block too large for the least-squares kernel");
+    }
+  }
+  MF_CUDA(cudaStreamSynchronize(st));
+  scratch.release(mk);
+  return bf;
+}
+
+// ---------------------------------------------------------------------------
+// extraction of a list of sub-blocks (Alg. 3, loops reordered so each block
+// of the butterfly is multiplied at most once per list item and level)
+// dst[q] += sign * K(X_q, Y_q)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ExtractPlan {
+  std::vector<PlaceJob<T>> pj;
+  std::map<int, std::vector<GemmDesc<T>>> Estage, Fstage;
+  std::vector<Blk2Job<T>> gather0;
+  std::vector<GemmDesc<T>> centre1, centre2;
+};
+
+template <typename T>
+static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vector<std::pair<IdxVec, IdxVec>>& lst,
+                            std::vector<Blk<T>>& dst, T sign, ExtractPlan<T>& EP) {
+  const int L = bf.L, lc = bf.lc;
+  struct Part {
+    int p0, p1;   // positions [p0, p1) in the sorted list
+  };
+  auto& pj = EP.pj;
+  auto& Estage = EP.Estage;
+  auto& Fstage = EP.Fstage;
+  auto& gather0 = EP.gather0;
+  auto& centre1 = EP.centre1;
+  auto& centre2 = EP.centre2;
+  auto& scratch = cx.scratch;
+  auto zero = [&](Blk<T>& b) { cx.zero(b); };
+  for (size_t q = 0; q < lst.size(); ++q) {
+    const IdxVec& X0 = lst[q].first;
+    const IdxVec& Y0 = lst[q].second;
+    if (X0.empty() || Y0.empty()) continue;
+    // sorted copies and their original positions
+    std::vector<int> xo(X0.size()), yo(Y0.size());
+    std::iota(xo.begin(), xo.end(), 0);
+    std::iota(yo.begin(), yo.end(), 0);
+    std::sort(xo.begin(), xo.end(), [&](int a, int b) { return X0[a] < X0[b]; });
+    std::sort(yo.begin(), yo.end(), [&](int a, int b) { return Y0[a] < Y0[b]; });
+    IdxVec X(X0.size()), Y(Y0.size());
+    for (size_t t = 0; t < xo.size(); ++t) X[t] = X0[xo[t]];
+    for (size_t t = 0; t < yo.size(); ++t) Y[t] = Y0[yo[t]];
+    auto parts = [&](const Tree& tr, int l, const IdxVec& v) {
+      std::vector<Part> out(tr[l].size());
+      for (size_t k = 0; k < tr[l].size(); ++k) {
+        out[k].p0 = (int)(std::lower_bound(v.begin(), v.end(), (int32_t)tr[l][k].a) - v.begin());
+        out[k].p1 = (int)(std::lower_bound(v.begin(), v.end(), (int32_t)tr[l][k].b) - v.begin());
+      }
+      return out;
+    };
+    std::vector<std::vector<Part>> Xp(L + 1), Yp(L + 1);
+    for (int l = 0; l <= L; ++l) { Xp[l] = parts(bf.rt, l, X); Yp[l] = parts(bf.ct, l, Y); }
+    auto nonempty = [](const Part& p) { return p.p1 > p.p0; };
+    // E^l blocks, l = L .. lc : rows = positions of X in O_i, cols = r(l,i,j)
+    std::vector<std::map<int, Blk<T>>> E(L + 1), F(L + 1);
+    const IdxVec* Xptr = &X;
+    for (int i = 0; i < (1 << L); ++i) {
+      if (!nonempty(Xp[L][i]) || !nonempty(Yp[0][0])) continue;
+      const int r = bf.rr(L, i, 0);
+      const int nr = Xp[L][i].p1 - Xp[L][i].p0;
+      Blk<T> e = new_blk<T>(scratch, nr, std::max(r, 1));
+      e.cols = r;
+      E[L][i] = e;
+      if (r == 0) continue;
+      IdxVec rows;
+      for (int t = Xp[L][i].p0; t < Xp[L][i].p1; ++t) rows.push_back((*Xptr)[t] - (int32_t)bf.rt[L][i].a);
+      zero(e);
+      Blk2Job<T> j{};
+      j.src = bf.U[L][i].p; j.splane = bf.U[L][i].plane; j.sld = bf.U[L][i].ld;
+      j.dst = e.p; j.dplane = e.plane; j.dld = e.ld; j.rows = nr; j.cols = r; j.alpha = T(1);
+      j.ridx = dev_idx(cx, rows);
+      j.cidx = dev_idx(cx, range_vec(0, r));
+      j.mode = 1;
+      gather0.push_back(j);
+    }
+    for (int l = L - 1; l >= lc; --l)
+      for (int i = 0; i < (1 << l); ++i)
+        for (int jj = 0; jj < (1 << (L - l)); ++jj) {
+          if (!nonempty(Xp[l][i]) || !nonempty(Yp[L - l][jj])) continue;
+          const int p = bf.pidx(l, i, jj);
+          const int r = bf.rr(l, i, jj);
+          const int nr = Xp[l][i].p1 - Xp[l][i].p0;
+          Blk<T> e = new_blk<T>(scratch, nr, std::max(r, 1));
+          e.cols = r;
+          E[l][p] = e;
+          const int r1 = bf.rr(l + 1, 2 * i, jj / 2);
+          int roff = 0;
+          for (int t = 0; t < 2; ++t) {
+            const int ci = 2 * i + t;
+            if (!nonempty(Xp[l + 1][ci])) continue;
+            const int cp = bf.pidx(l + 1, ci, jj / 2);
+            auto it = E[l + 1].find(cp);
+            const int nrc = Xp[l + 1][ci].p1 - Xp[l + 1][ci].p0;
+            const int rc = bf.rr(l + 1, ci, jj / 2);
+            const Blk<T>& R = bf.U[l][p];
+            const int off = Xp[l + 1][ci].p0 - Xp[l][i].p0;
+            if (it == E[l + 1].end()) continue;
+            Estage[L - 1 - l].push_back(gdesc<T>(nrc, r, rc, 0, 0, T(1), T(0), it->second,
+                                         R.sub(t == 0 ? 0 : r1, 0, rc, R.cols), e.sub(off, 0, nrc, r)));
+            (void)roff;
+          }
+        }
+    // F^l blocks stored transposed: rows = positions of Y in S_j, cols = c(l,i,j)
+    for (int jj = 0; jj < (1 << L); ++jj) {
+      if (!nonempty(Yp[L][jj]) || !nonempty(Xp[0][0])) continue;
+      const int c = bf.rc(0, 0, jj);
+      const int nr = Yp[L][jj].p1 - Yp[L][jj].p0;
+      Blk<T> f = new_blk<T>(scratch, nr, std::max(c, 1));
+      f.cols = c;
+      F[0][jj] = f;
+      if (c == 0) continue;
+      IdxVec rows;
+      for (int t = Yp[L][jj].p0; t < Yp[L][jj].p1; ++t) rows.push_back(Y[t] - (int32_t)bf.ct[L][jj].a);
+      zero(f);
+      Blk2Job<T> j{};
+      j.src = bf.V[0][jj].p; j.splane = bf.V[0][jj].plane; j.sld = bf.V[0][jj].ld;
+      j.dst = f.p; j.dplane = f.plane; j.dld = f.ld; j.rows = nr; j.cols = c; j.alpha = T(1);
+      j.ridx = dev_idx(cx, rows);
+      j.cidx = dev_idx(cx, range_vec(0, c));
+      j.mode = 1;
+      gather0.push_back(j);
+    }
+    for (int l = 1; l <= lc; ++l)
+      for (int i = 0; i < (1 << l); ++i)
+        for (int jj = 0; jj < (1 << (L - l)); ++jj) {
+          if (!nonempty(Xp[l][i]) || !nonempty(Yp[L - l][jj])) continue;
+          const int p = bf.pidx(l, i, jj);
+          const int c = bf.rc(l, i, jj);
+          const int nr = Yp[L - l][jj].p1 - Yp[L - l][jj].p0;
+          Blk<T> f = new_blk<T>(scratch, nr, std::max(c, 1));
+          f.cols = c;
+          F[l][p] = f;
+          const int c1 = bf.rc(l - 1, i / 2, 2 * jj);
+          for (int t = 0; t < 2; ++t) {
+            const int cj = 2 * jj + t;
+            if (!nonempty(Yp[L - l + 1][cj])) continue;
+            const int cp = bf.pidx(l - 1, i / 2, cj);
+            auto it = F[l - 1].find(cp);
+            if (it == F[l - 1].end()) continue;
+            const int nrc = Yp[L - l + 1][cj].p1 - Yp[L - l + 1][cj].p0;
+            const int cc = bf.rc(l - 1, i / 2, cj);
+            const Blk<T>& W = bf.V[l][p];
+            const int off = Yp[L - l + 1][cj].p0 - Yp[L - l][jj].p0;
+            Fstage[l - 1].push_back(gdesc<T>(nrc, c, cc, 0, 0, T(1), T(0), it->second,
+                                         W.sub(t == 0 ? 0 : c1, 0, cc, W.cols), f.sub(off, 0, nrc, c)));
+          }
+        }
+    // centre: out(X in O_i, Y in S_j) = E B F = (E B) Ft^T
+    for (int i = 0; i < (1 << lc); ++i)
+      for (int jj = 0; jj < (1 << (L - lc)); ++jj) {
+        if (!nonempty(Xp[lc][i]) || !nonempty(Yp[L - lc][jj])) continue;
+        const int p = bf.pidx(lc, i, jj);
+        auto ie = E[lc].find(p);
+        auto iff = F[lc].find(p);
+        if (ie == E[lc].end() || iff == F[lc].end()) continue;
+        const int r = bf.rr(lc, i, jj), c = bf.rc(lc, i, jj);
+        const int nx = Xp[lc][i].p1 - Xp[lc][i].p0, ny = Yp[L - lc][jj].p1 - Yp[L - lc][jj].p0;
+        Blk<T> tmp = new_blk<T>(scratch, nx, std::max(c, 1));
+        Blk<T> out = new_blk<T>(scratch, nx, ny);
+        if (r == 0 || c == 0) continue;
+        centre1.push_back(gdesc<T>(nx, c, r, 0, 0, T(1), T(0), ie->second, bf.B[p], tmp));
+        centre2.push_back(gdesc<T>(nx, ny, c, 0, 1, T(1), T(0), tmp, iff->second, out));
+        IdxVec rows, cols;
+        for (int t = Xp[lc][i].p0; t < Xp[lc][i].p1; ++t) rows.push_back(xo[t]);
+        for (int t = Yp[L - lc][jj].p0; t < Yp[L - lc][jj].p1; ++t) cols.push_back(yo[t]);
+        PlaceJob<T> pl;
+        pl.src = out.p; pl.splane = out.plane; pl.sld = out.ld;
+        pl.rows = dev_idx(cx, rows);
+        pl.cols = dev_idx(cx, cols);
+        pl.nr = nx; pl.nc = ny;
+        pl.dst = dst[q].p; pl.dplane = dst[q].plane; pl.dld = dst[q].ld;
+        pl.sign = sign;
+        pj.push_back(pl);
+      }
+  }
+}
+
+template <typename T>
+static void extract_run(BFContext<T>& cx, ExtractPlan<T>& EP) {
+  run_blk2(cx, EP.gather0);
+  for (auto& kv : EP.Estage) cx.gemm(kv.second);
+  for (auto& kv : EP.Fstage) cx.gemm(kv.second);
+  cx.gemm(EP.centre1);
+  cx.gemm(EP.centre2);
+  if (!EP.pj.empty()) {
+    int64_t mx = 0;
+    for (auto& p : EP.pj) mx = std::max<int64_t>(mx, (int64_t)p.nr * p.nc);
+    auto* d = cx.scratch.template takeT<PlaceJob<T>>(EP.pj.size());
+    MF_CUDA(cudaMemcpyAsync(d, EP.pj.data(), EP.pj.size() * sizeof(PlaceJob<T>), cudaMemcpyHostToDevice, cx.st));
+    launch_place<T>(d, (int)EP.pj.size(), mx, cx.st);
+  }
+}
+
+template <typename T>
+void BFContext<T>::extract_bf(const DBF<T>& bf, const std::vector<std::pair<IdxVec, IdxVec>>& lst,
+                              std::vector<Blk<T>>& dst, T sign) {
+  ExtractPlan<T> EP;
+  extract_collect(*this, bf, lst, dst, sign, EP);
+  extract_run(*this, EP);
+}
+
+template <typename T>
+void BFContext<T>::extract_multi(const std::vector<const DBF<T>*>& bfs,
+                                 const std::vector<const std::vector<std::pair<IdxVec, IdxVec>>*>& lsts,
+                                 const std::vector<std::vector<Blk<T>>*>& dsts) {
+  ExtractPlan<T> EP;
+  for (size_t q = 0; q < bfs.size(); ++q) extract_collect(*this, *bfs[q], *lsts[q], *dsts[q], T(1), EP);
+  extract_run(*this, EP);
+}
+
+// ---------------------------------------------------------------------------
+// split of an L-level butterfly into the (L-2)-level child on quadrant (a, b) (Alg. 4, BF_SMW)
+// ---------------------------------------------------------------------------
+template <typename T>
+std::unique_ptr<DBF<T>> BFContext<T>::split_child(const DBF<T>& bf, int a, int b) {
+  const int L = bf.L, Lp = L - 2;
+  const int64_t ra0 = bf.rt[1][a].a, cb0 = bf.ct[1][b].a;
+  Tree rt = subtree(bf.rt, 1, a, Lp), ct = subtree(bf.ct, 1, b, Lp);
+  auto ch = std::make_unique<DBF<T>>();
+  ch->init((int)(rt[0][0].b), (int)(ct[0][0].b), rt, ct, Lp);
+  std::vector<GemmDesc<T>> g;
+  for (int lp = ch->lc; lp <= Lp; ++lp) {
+    const int l = lp + 1;
+    for (int ip = 0; ip < (1 << lp); ++ip)
+      for (int jp = 0; jp < (1 << (Lp - lp)); ++jp) {
+        const int i = a * (1 << lp) + ip, j = b * (1 << (Lp - lp)) + jp;
+        const int p = bf.pidx(l, i, j), pp = ch->pidx(lp, ip, jp);
+        const Blk<T>& R = bf.U[l][p];
+        if (l == L - 1) {
+          const int r1 = bf.rr(L, 2 * i, 0), r2 = bf.rr(L, 2 * i + 1, 0);
+          const Blk<T>& U1 = bf.U[L][2 * i];
+          const Blk<T>& U2 = bf.U[L][2 * i + 1];
+          Blk<T> out = new_blk<T>(persist, U1.rows + U2.rows, std::max(R.cols, 1));
+          out.cols = R.cols;
+          if (R.cols > 0) {
+            g.push_back(gdesc<T>(U1.rows, R.cols, r1, 0, 0, T(1), T(0), U1, R.sub(0, 0, r1, R.cols),
+                                 out.sub(0, 0, U1.rows, R.cols)));
+            g.push_back(gdesc<T>(U2.rows, R.cols, r2, 0, 0, T(1), T(0), U2, R.sub(r1, 0, r2, R.cols),
+                                 out.sub(U1.rows, 0, U2.rows, R.cols)));
+          }
+          ch->U[lp][pp] = out;
+        } else {
+          ch->U[lp][pp] = R;
+        }
+        IdxVec o;
+        for (int32_t x : bf.Osk[l][p]) o.push_back(x - (int32_t)ra0);
+        ch->Osk[lp][pp] = o;
+      }
+  }
+  for (int lp = 0; lp <= ch->lc; ++lp) {
+    const int l = lp + 1;
+    for (int ip = 0; ip < (1 << lp); ++ip)
+      for (int jp = 0; jp < (1 << (Lp - lp)); ++jp) {
+        const int i = a * (1 << lp) + ip, j = b * (1 << (Lp - lp)) + jp;
+        const int p = bf.pidx(l, i, j), pp = ch->pidx(lp, ip, jp);
+        const Blk<T>& W = bf.V[l][p];
+        if (l == 1) {
+          const int c1 = bf.rc(0, 0, 2 * j), c2 = bf.rc(0, 0, 2 * j + 1);
+          const Blk<T>& V1 = bf.V[0][2 * j];
+          const Blk<T>& V2 = bf.V[0][2 * j + 1];
+          Blk<T> out = new_blk<T>(persist, V1.rows + V2.rows, std::max(W.cols, 1));
+          out.cols = W.cols;
+          if (W.cols > 0) {
+            g.push_back(gdesc<T>(V1.rows, W.cols, c1, 0, 0, T(1), T(0), V1, W.sub(0, 0, c1, W.cols),
+                                 out.sub(0, 0, V1.rows, W.cols)));
+            g.push_back(gdesc<T>(V2.rows, W.cols, c2, 0, 0, T(1), T(0), V2, W.sub(c1, 0, c2, W.cols),
+                                 out.sub(V1.rows, 0, V2.rows, W.cols)));
+          }
+          ch->V[lp][pp] = out;
+        } else {
+          ch->V[lp][pp] = W;
+        }
+        IdxVec o;
+        for (int32_t x : bf.Ssk[l][p]) o.push_back(x - (int32_t)cb0);
+        ch->Ssk[lp][pp] = o;
+      }
+  }
+  for (int ip = 0; ip < (1 << ch->lc); ++ip)
+    for (int jp = 0; jp < (1 << (Lp - ch->lc)); ++jp) {
+      const int i = a * (1 << ch->lc) + ip, j = b * (1 << (Lp - ch->lc)) + jp;
+      ch->B[ch->pidx(ch->lc, ip, jp)] = bf.B[bf.pidx(bf.lc, i, j)];
+    }
+  gemm(g);
+  return ch;
+}
+
+// ---------------------------------------------------------------------------
+// HOD-BF (Sec. 4)
+// ---------------------------------------------------------------------------
+template <typename T>
+void BFContext<T>::hodbf_entry_eval_batch(const DExtract<T>& ext, std::vector<HProblem<T>>& probs, const BFParams& P) {
+  // leaves of every problem in one extraction call
+  {
+    std::vector<std::pair<IdxVec, IdxVec>> lst;
+    std::vector<Blk<T>> blocks;
+    for (auto& hp : probs) {
+      hp.out = std::make_unique<DHODBF<T>>();
+      DHODBF<T>& H = *hp.out;
+      H.n = hp.n;
+      H.tree = hp.tree;
+      H.LH = (int)hp.tree.size() - 1;
+      for (auto& r : hp.tree[H.LH]) {
+        IdxVec v = range_vec(r.a + hp.off, r.b + hp.off);
+        lst.push_back({v, v});
+        H.D.push_back(new_blk<T>(persist, (int)(r.b - r.a), (int)(r.b - r.a)));
+        blocks.push_back(H.D.back());
+      }
+      H.off.clear();
+      H.off.resize(H.LH + 1);
+    }
+    ext(lst, blocks);
+  }
+  // off-diagonal butterflies grouped by level count
+  std::map<int, std::vector<BFProblem<T>>> groups;
+  std::map<int, std::vector<std::pair<size_t, std::pair<int, int>>>> where;
+  for (size_t q = 0; q < probs.size(); ++q) {
+    const HProblem<T>& hp = probs[q];
+    const Tree& tree = hp.tree;
+    const int LH = (int)tree.size() - 1;
+    for (int l = 1; l <= LH; ++l) {
+      probs[q].out->off[l].resize((size_t)1 << l);
+      for (int i = 0; i < (1 << l); ++i) {
+        const Range rr = tree[l][i], cr = tree[l][i ^ 1];
+        const int a = (int)rr.a, c = (int)cr.a, nr = (int)(rr.b - rr.a), nc = (int)(cr.b - cr.a);
+        BFProblem<T> bp;
+        bp.m = nr; bp.n = nc; bp.L = LH - l;
+        bp.rt = subtree(tree, l, i, bp.L);
+        bp.ct = subtree(tree, l, i ^ 1, bp.L);
+        bp.row_off = hp.off + a;
+        bp.col_off = hp.off + c;
+        bp.nn_r.resize(nr);
+        bp.nn_c.resize(nc);
+        for (int x = 0; x < nr; ++x)
+          if (a + x < (int)hp.nn.size())
+            for (int32_t v : hp.nn[a + x])
+              if (v >= c && v < c + nc) bp.nn_r[x].push_back(v - c);
+        for (int y = 0; y < nc; ++y)
+          if (c + y < (int)hp.nn.size())
+            for (int32_t v : hp.nn[c + y])
+              if (v >= a && v < a + nr) bp.nn_c[y].push_back(v - a);
+        where[bp.L].push_back({q, {l, i}});
+        groups[bp.L].push_back(std::move(bp));
+      }
+    }
+  }
+  for (auto& kv : groups) {
+    entry_eval_batch(ext, kv.second, P);
+    auto& wh = where[kv.first];
+    for (size_t t = 0; t < kv.second.size(); ++t)
+      probs[wh[t].first].out->off[wh[t].second.first][wh[t].second.second] = std::move(kv.second[t].out);
+  }
+}
+
+template <typename T>
+std::unique_ptr<DHODBF<T>> BFContext<T>::hodbf_entry_eval(const DExtract<T>& ext, int n, const Tree& tree,
+                                                           const std::vector<IdxVec>& nn, const BFParams& P) {
+  std::vector<HProblem<T>> hp(1);
+  hp[0].n = n; hp[0].tree = tree; hp[0].nn = nn; hp[0].off = 0;
+  hodbf_entry_eval_batch(ext, hp, P);
+  return std::move(hp[0].out);
+}
+
+template <typename T>
+void BFContext<T>::hodbf_apply(const DHODBF<T>& H, const Blk<T>& X, Blk<T>& Y, bool transpose) {
+  const int LH = H.LH, k = X.cols;
+  std::vector<GemmDesc<T>> g;
+  for (size_t q = 0; q < H.D.size(); ++q) {
+    const Range r = H.tree[LH][q];
+    const int nr = (int)(r.b - r.a);
+    g.push_back(gdesc<T>(nr, k, nr, transpose ? 1 : 0, 0, T(1), T(0), H.D[q], X.sub((int)r.a, 0, nr, k),
+                         Y.sub((int)r.a, 0, nr, k)));
+  }
+  gemm(g);
+  for (int l = 1; l <= LH; ++l) {
+    std::vector<const DBF<T>*> bfs;
+    std::vector<Blk<T>> xs, ys;
+    for (int i = 0; i < (1 << l); ++i) {
+      const Range rr = H.tree[l][i], cr = H.tree[l][i ^ 1];
+      bfs.push_back(H.off[l][i].get());
+      if (!transpose) {
+        xs.push_back(X.sub((int)cr.a, 0, (int)(cr.b - cr.a), k));
+        ys.push_back(Y.sub((int)rr.a, 0, (int)(rr.b - rr.a), k));
+      } else {
+        xs.push_back(X.sub((int)rr.a, 0, (int)(rr.b - rr.a), k));
+        ys.push_back(Y.sub((int)cr.a, 0, (int)(cr.b - cr.a), k));
+      }
+    }
+    apply(bfs, xs, ys, transpose, true);
+  }
+}
+
+template <typename T>
+void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair<IdxVec, IdxVec>>& lst,
+                                 std::vector<Blk<T>>& dst, T sign) {
+  const int LH = H.LH;
+  std::vector<Blk2Job<T>> gj;
+  std::vector<PlaceJob<T>> pj;
+  struct Req {
+    const DBF<T>* bf;
+    std::vector<std::pair<IdxVec, IdxVec>> lst;
+    std::vector<Blk<T>> tmp;
+    std::vector<IdxVec> px, py;
+    int q;
+  };
+  std::vector<Req> reqs;
+  std::map<const DBF<T>*, size_t> req_of;
+  for (size_t q = 0; q < lst.size(); ++q) {
+    const IdxVec& X = lst[q].first;
+    const IdxVec& Y = lst[q].second;
+    if (X.empty() || Y.empty()) continue;
+    // leaves
+    for (size_t li = 0; li < H.tree[LH].size(); ++li) {
+      const Range r = H.tree[LH][li];
+      IdxVec px, py, rx, ry;
+      for (size_t a = 0; a < X.size(); ++a)
+        if (X[a] >= r.a && X[a] < r.b) { px.push_back((int32_t)a); rx.push_back(X[a] - (int32_t)r.a); }
+      for (size_t b = 0; b < Y.size(); ++b)
+        if (Y[b] >= r.a && Y[b] < r.b) { py.push_back((int32_t)b); ry.push_back(Y[b] - (int32_t)r.a); }
+      if (px.empty() || py.empty()) continue;
+      Blk<T> t = new_blk<T>(scratch, (int)px.size(), (int)py.size());
+      zero(t);
+      Blk2Job<T> j{};
+      j.src = H.D[li].p; j.splane = H.D[li].plane; j.sld = H.D[li].ld;
+      j.dst = t.p; j.dplane = t.plane; j.dld = t.ld; j.rows = t.rows; j.cols = t.cols; j.alpha = T(1);
+      j.ridx = dev_idx(*this, rx); j.cidx = dev_idx(*this, ry); j.mode = 1;
+      gj.push_back(j);
+      PlaceJob<T> pl;
+      pl.src = t.p; pl.splane = t.plane; pl.sld = t.ld;
+      pl.rows = dev_idx(*this, px); pl.cols = dev_idx(*this, py); pl.nr = t.rows; pl.nc = t.cols;
+      pl.dst = dst[q].p; pl.dplane = dst[q].plane; pl.dld = dst[q].ld; pl.sign = sign;
+      pj.push_back(pl);
+    }
+    // off-diagonal butterflies
+    for (int l = 1; l <= LH; ++l)
+      for (int i = 0; i < (1 << l); ++i) {
+        const Range rr = H.tree[l][i], cr = H.tree[l][i ^ 1];
+        IdxVec px, py, rx, ry;
+        for (size_t a = 0; a < X.size(); ++a)
+          if (X[a] >= rr.a && X[a] < rr.b) { px.push_back((int32_t)a); rx.push_back(X[a] - (int32_t)rr.a); }
+        if (px.empty()) continue;
+        for (size_t b = 0; b < Y.size(); ++b)
+          if (Y[b] >= cr.a && Y[b] < cr.b) { py.push_back((int32_t)b); ry.push_back(Y[b] - (int32_t)cr.a); }
+        if (py.empty()) continue;
+        const DBF<T>* bf = H.off[l][i].get();
+        auto it = req_of.find(bf);
+        if (it == req_of.end()) {
+          req_of[bf] = reqs.size();
+          reqs.push_back(Req{bf, {}, {}, {}, {}, 0});
+          it = req_of.find(bf);
+        }
+        Req& R = reqs[it->second];
+        R.lst.push_back({rx, ry});
+        Blk<T> t = new_blk<T>(scratch, (int)rx.size(), (int)ry.size());
+        zero(t);
+        R.tmp.push_back(t);
+        PlaceJob<T> pl;
+        pl.src = t.p; pl.splane = t.plane; pl.sld = t.ld;
+        pl.rows = dev_idx(*this, px); pl.cols = dev_idx(*this, py); pl.nr = t.rows; pl.nc = t.cols;
+        pl.dst = dst[q].p; pl.dplane = dst[q].plane; pl.dld = dst[q].ld; pl.sign = sign;
+        pj.push_back(pl);
+      }
+  }
+  run_blk2(*this, gj);
+  std::vector<const DBF<T>*> bfs;
+  std::vector<const std::vector<std::pair<IdxVec, IdxVec>>*> ls;
+  std::vector<std::vector<Blk<T>>*> ds;
+  for (auto& R : reqs) {
+    bfs.push_back(R.bf);
+    ls.push_back(&R.lst);
+    ds.push_back(&R.tmp);
+  }
+  extract_multi(bfs, ls, ds);
+  if (!pj.empty()) {
+    int64_t mx = 0;
+    for (auto& p : pj) mx = std::max<int64_t>(mx, (int64_t)p.nr * p.nc);
+    auto* d = scratch.takeT<PlaceJob<T>>(pj.size());
+    MF_CUDA(cudaMemcpyAsync(d, pj.data(), pj.size() * sizeof(PlaceJob<T>), cudaMemcpyHostToDevice, st));
+    launch_place<T>(d, (int)pj.size(), mx, st);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// HOD-BF inversion (Alg. 4) and BF_SMW
+// ---------------------------------------------------------------------------
+template <typename T>
+void BFContext<T>::inv_apply(const DHODBFInv<T>& Hi, const Blk<T>& X, Blk<T>& Y, bool transpose, int l0, int i0) {
+  const int LH = Hi.LH, k = X.cols;
+  const int64_t a0 = Hi.tree[l0][i0].a;
+  const int nsub = 1 << (LH - l0);
+  auto leaves = [&](const Blk<T>& src, Blk<T>& out) {
+    std::vector<GemmDesc<T>> g;
+    for (int li = i0 * nsub; li < (i0 + 1) * nsub; ++li) {
+      const Range r = Hi.tree[LH][li];
+      const int nr = (int)(r.b - r.a);
+      if (nr == 0) continue;
+      g.push_back(gdesc<T>(nr, k, nr, transpose ? 1 : 0, 0, T(1), T(0), Hi.Dinv[li], src.sub((int)(r.a - a0), 0, nr, k),
+                           out.sub((int)(r.a - a0), 0, nr, k)));
+    }
+    gemm(g);
+  };
+  const size_t mk = scratch.mark();
+  Blk<T> Z = new_blk<T>(scratch, X.rows, k);
+  auto level = [&](int l) {
+    const int span = 1 << (l - l0);
+    std::vector<const DBF<T>*> bfs;
+    std::vector<Blk<T>> xs, zs;
+    for (int i = i0 * span; i < (i0 + 1) * span; ++i) {
+      const Range r = Hi.tree[l][i];
+      bfs.push_back(Hi.M[l][i].get());
+      xs.push_back(Y.sub((int)(r.a - a0), 0, (int)(r.b - r.a), k));
+      zs.push_back(Z.sub((int)(r.a - a0), 0, (int)(r.b - r.a), k));
+    }
+    apply(bfs, xs, zs, transpose, false);
+    std::vector<Blk2Job<T>> aj;
+    Blk2Job<T> j{};
+    j.src = Z.p; j.splane = Z.plane; j.sld = Z.ld;
+    j.dst = Y.p; j.dplane = Y.plane; j.dld = Y.ld; j.rows = X.rows; j.cols = k; j.alpha = T(1); j.mode = 2;
+    aj.push_back(j);
+    run_blk2(*this, aj);
+  };
+  if (!transpose) {
+    leaves(X, Y);
+    for (int l = LH - 1; l >= l0; --l) level(l);
+  } else {
+    // Y = X first, then the level factors in reverse order, then the leaves
+    std::vector<Blk2Job<T>> cj;
+    Blk2Job<T> j{};
+    j.src = X.p; j.splane = X.plane; j.sld = X.ld;
+    j.dst = Y.p; j.dplane = Y.plane; j.dld = Y.ld; j.rows = X.rows; j.cols = k; j.alpha = T(1); j.mode = 3;
+    cj.push_back(j);
+    run_blk2(*this, cj);
+    for (int l = l0; l <= LH - 1; ++l) level(l);
+    leaves(Y, Z);
+    std::vector<Blk2Job<T>> bj;
+    Blk2Job<T> b{};
+    b.src = Z.p; b.splane = Z.plane; b.sld = Z.ld;
+    b.dst = Y.p; b.dplane = Y.plane; b.dld = Y.ld; b.rows = X.rows; b.cols = k; b.alpha = T(1); b.mode = 3;
+    bj.push_back(b);
+    run_blk2(*this, bj);
+  }
+  (void)mk;   // Z stays reserved until the caller releases its scratch mark
+}
+
+template <typename T>
+static void small_inverse(BFContext<T>& cx, const std::vector<Blk<T>>& A, std::vector<Blk<T>>& X) {
+  std::vector<InvJob<T>> jobs;
+  int mx = 1;
+  for (size_t q = 0; q < A.size(); ++q) {
+    if (A[q].rows == 0) continue;
+    InvJob<T> j;
+    j.A = A[q].p; j.aplane = A[q].plane; j.lda = A[q].ld; j.n = A[q].rows;
+    j.X = X[q].p; j.xplane = X[q].plane; j.ldx = X[q].ld;
+    jobs.push_back(j);
+    mx = std::max(mx, A[q].rows);
+    cx.flops += 8.0 * A[q].rows * (double)A[q].rows * A[q].rows;
+  }
+  if (jobs.empty()) return;
+  auto* d = cx.scratch.template takeT<InvJob<T>>(jobs.size());
+  MF_CUDA(cudaMemcpyAsync(d, jobs.data(), jobs.size() * sizeof(InvJob<T>), cudaMemcpyHostToDevice, cx.st));
+  if (launch_small_inverse<T>(d, (int)jobs.size(), mx, cx.status.template as<int32_t>(), cx.st) != 0)
+    throw std::runtime_error("block too large for the small dense inverse (" + std::to_string(mx) + ")");
+}
+
+template <typename T>
+std::unique_ptr<DBF<T>> BFContext<T>::bf_smw(const DBF<T>& K, const BFParams& P, uint32_t key) {
+  const int L = K.L;
+  if (L == 0) {
+    // (I + U B V^T)^-1 = I - U B (I + V^T U B)^-1 V^T
+    auto out = std::make_unique<DBF<T>>();
+    out->init(K.m, K.n, K.rt, K.ct, 0);
+    out->U = K.U; out->Osk = K.Osk; out->V = K.V; out->Ssk = K.Ssk;
+    const Blk<T>& U = K.U[0][0];
+    const Blk<T>& V = K.V[0][0];
+    const Blk<T>& B = K.B[0];
+    const int r = B.rows, c = B.cols;
+    Blk<T> Bn = new_blk<T>(persist, r, std::max(c, 1));
+    Bn.cols = c;
+    out->B[0] = Bn;
+    if (r == 0 || c == 0) return out;
+    const size_t mk = scratch.mark();
+    Blk<T> VU = new_blk<T>(scratch, c, r), G = new_blk<T>(scratch, c, c), Gi = new_blk<T>(scratch, c, c);
+    std::vector<GemmDesc<T>> g{gdesc<T>(c, r, V.rows, 1, 0, T(1), T(0), V, U, VU)};
+    gemm(g);
+    // G = I + VU B : set G = I then G += VU B
+    {
+      std::vector<T> eye(2 * (size_t)G.plane, T(0));
+      for (int a = 0; a < c; ++a) eye[(size_t)a * G.ld + a] = T(1);
+      MF_CUDA(cudaMemcpyAsync(G.p, eye.data(), eye.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+      MF_CUDA(cudaStreamSynchronize(st));
+    }
+    g = {gdesc<T>(c, c, r, 0, 0, T(1), T(1), VU, B, G)};
+    gemm(g);
+    std::vector<Blk<T>> A1{G}, X1{Gi};
+    small_inverse(*this, A1, X1);
+    g = {gdesc<T>(r, c, c, 0, 0, T(-1), T(0), B, Gi, Bn)};
+    gemm(g);
+    MF_CUDA(cudaStreamSynchronize(st));
+    scratch.release(mk);
+    return out;
+  }
+  if (L == 1) {
+    // K = Ubar Mbar, Ubar = diag(U_0, U_1); R'_j = -(I + Mbar Ubar)^-1 R_j
+    auto out = std::make_unique<DBF<T>>();
+    out->init(K.m, K.n, K.rt, K.ct, 1);
+    out->U = K.U; out->Osk = K.Osk; out->V = K.V; out->Ssk = K.Ssk; out->B = K.B;
+    const int r0 = K.rr(1, 0, 0), r1 = K.rr(1, 1, 0), rs = r0 + r1;
+    if (rs == 0) return out;
+    const size_t mk = scratch.mark();
+    Blk<T> G = new_blk<T>(scratch, rs, rs), Gi = new_blk<T>(scratch, rs, rs);
+    {
+      std::vector<T> eye(2 * (size_t)G.plane, T(0));
+      for (int a = 0; a < rs; ++a) eye[(size_t)a * G.ld + a] = T(1);
+      MF_CUDA(cudaMemcpyAsync(G.p, eye.data(), eye.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+      MF_CUDA(cudaStreamSynchronize(st));
+    }
+    for (int j = 0; j < 2; ++j) {
+      // column block j of Mbar Ubar:  R_j B_j (V_j^T U_j)  into G[:, off_j : off_j + r_j]
+      const Blk<T>& V = K.V[0][j];
+      const Blk<T>& Uj = K.U[1][j];
+      const Blk<T>& Bj = K.B[j];
+      const Blk<T>& Rj = K.U[0][j];
+      const int c = V.cols, rj = j == 0 ? r0 : r1, off = j == 0 ? 0 : r0;
+      if (c == 0 || rj == 0 || Bj.rows == 0) continue;
+      Blk<T> VU = new_blk<T>(scratch, c, rj), BVU = new_blk<T>(scratch, Bj.rows, rj);
+      std::vector<GemmDesc<T>> g{gdesc<T>(c, rj, V.rows, 1, 0, T(1), T(0), V, Uj, VU)};
+      gemm(g);
+      g = {gdesc<T>(Bj.rows, rj, c, 0, 0, T(1), T(0), Bj, VU, BVU)};
+      gemm(g);
+      g = {gdesc<T>(rs, rj, Bj.rows, 0, 0, T(1), T(1), Rj, BVU, G.sub(0, off, rs, rj))};
+      gemm(g);
+    }
+    std::vector<Blk<T>> A1{G}, X1{Gi};
+    small_inverse(*this, A1, X1);
+    for (int j = 0; j < 2; ++j) {
+      const Blk<T>& Rj = K.U[0][j];
+      Blk<T> Rn = new_blk<T>(persist, rs, std::max(Rj.cols, 1));
+      Rn.cols = Rj.cols;
+      if (Rj.cols > 0) {
+        std::vector<GemmDesc<T>> g{gdesc<T>(rs, Rj.cols, rs, 0, 0, T(-1), T(0), Gi, Rj, Rn)};
+        gemm(g);
+      }
+      out->U[0][j] = Rn;
+    }
+    MF_CUDA(cudaStreamSynchronize(st));
+    scratch.release(mk);
+    return out;
+  }
+  auto K11 = split_child(K, 0, 0), K12 = split_child(K, 0, 1), K21 = split_child(K, 1, 0), K22 = split_child(K, 1, 1);
+  auto K22i = bf_smw(*K22, P, key * 4u + 1u);
+  return smw_assemble(K.m, K.rt, L, K11.get(), *K12, *K21, K22i.get(), P, key);
+}
+
+template <typename T>
+std::unique_ptr<DBF<T>> BFContext<T>::smw_assemble(int n, const Tree& tr, int L, const DBF<T>* K11, const DBF<T>& K12,
+                                                    const DBF<T>& K21, const DBF<T>* K22i, const BFParams& P,
+                                                    uint32_t key) {
+  const int n1 = (int)tr[1][0].b, n2 = n - n1;
+  // z = (I + K22i) y, into a new scratch block (y unchanged)
+  auto inv22 = [this, K22i](const Blk<T>& y, bool tr_) -> Blk<T> {
+    Blk<T> z = new_blk<T>(scratch, y.rows, y.cols);
+    std::vector<Blk2Job<T>> cj;
+    Blk2Job<T> j{};
+    j.src = y.p; j.splane = y.plane; j.sld = y.ld; j.dst = z.p; j.dplane = z.plane; j.dld = z.ld;
+    j.rows = y.rows; j.cols = y.cols; j.alpha = T(1); j.mode = 3;
+    cj.push_back(j);
+    run_blk2(*this, cj);
+    if (K22i) {
+      std::vector<const DBF<T>*> b{K22i};
+      std::vector<Blk<T>> xs{y}, ys{z};
+      apply(b, xs, ys, tr_, true);
+    }
+    return z;
+  };
+  auto app = [this](const DBF<T>& K, const Blk<T>& x, Blk<T>& y, bool tr_, bool acc) {
+    std::vector<const DBF<T>*> b{&K};
+    std::vector<Blk<T>> xs{x}, ys{y};
+    apply(b, xs, ys, tr_, acc);
+  };
+  auto axpy = [this](const Blk<T>& x, Blk<T>& y, T alpha) {
+    std::vector<Blk2Job<T>> cj;
+    Blk2Job<T> j{};
+    j.src = x.p; j.splane = x.plane; j.sld = x.ld; j.dst = y.p; j.dplane = y.plane; j.dld = y.ld;
+    j.rows = x.rows; j.cols = x.cols; j.alpha = alpha; j.mode = 2;
+    cj.push_back(j);
+    run_blk2(*this, cj);
+  };
+  // S = K11 - K12 (I + K22i) K21, an (L-2)-level butterfly on the first child's trees
+  DOp<T> sop;
+  sop.rows = n1;
+  sop.cols = n1;
+  sop.apply = [&, this](const Blk<T>& X, Blk<T>& Y, bool tr_) {
+    const int k = X.cols;
+    if (!tr_) {
+      Blk<T> t = new_blk<T>(scratch, n2, k);
+      app(K21, X, t, false, false);
+      Blk<T> u = inv22(t, false);
+      app(K12, u, Y, false, false);
+      std::vector<Blk2Job<T>> neg;
+      Blk2Job<T> j{};
+      j.src = Y.p; j.splane = Y.plane; j.sld = Y.ld; j.dst = Y.p; j.dplane = Y.plane; j.dld = Y.ld;
+      j.rows = Y.rows; j.cols = k; j.alpha = T(-2); j.mode = 2;   // Y <- Y - 2Y = -Y
+      neg.push_back(j);
+      run_blk2(*this, neg);
+      if (K11) app(*K11, X, Y, false, true);
+    } else {
+      Blk<T> t = new_blk<T>(scratch, n2, k);
+      app(K12, X, t, true, false);
+      Blk<T> u = inv22(t, true);
+      app(K21, u, Y, true, false);
+      std::vector<Blk2Job<T>> neg;
+      Blk2Job<T> j{};
+      j.src = Y.p; j.splane = Y.plane; j.sld = Y.ld; j.dst = Y.p; j.dplane = Y.plane; j.dld = Y.ld;
+      j.rows = Y.rows; j.cols = k; j.alpha = T(-2); j.mode = 2;
+      neg.push_back(j);
+      run_blk2(*this, neg);
+      if (K11) app(*K11, X, Y, true, true);
+    }
+  };
+  Tree rt1 = subtree(tr, 1, 0, L - 2);
+  auto S = random_matvec(sop, rt1, rt1, L - 2, P, key * 4u + 2u);
+  auto K11i = bf_smw(*S, P, key * 4u + 3u);
+  const DBF<T>* K11ip = K11i.get();
+  // A^-1 - I with A^-1 = [I 0; -A22^-1 A21 I] diag(A11^-1, A22^-1) [I -A12 A22^-1; 0 I]
+  DOp<T> fop;
+  fop.rows = n;
+  fop.cols = n;
+  fop.apply = [&, this](const Blk<T>& X, Blk<T>& Y, bool tr_) {
+    const int k = X.cols;
+    Blk<T> x1 = X.sub(0, 0, n1, k), x2 = X.sub(n1, 0, n2, k);
+    Blk<T> y1 = Y.sub(0, 0, n1, k), y2 = Y.sub(n1, 0, n2, k);
+    if (!tr_) {
+      Blk<T> w = inv22(x2, false);                    // A22^-1 x2
+      Blk<T> t1 = new_blk<T>(scratch, n1, k);
+      app(K12, w, t1, false, false);                  // K12 A22^-1 x2
+      std::vector<Blk2Job<T>> cj;                     // t1 = x1 - t1
+      Blk2Job<T> j{};
+      j.src = t1.p; j.splane = t1.plane; j.sld = t1.ld; j.dst = t1.p; j.dplane = t1.plane; j.dld = t1.ld;
+      j.rows = n1; j.cols = k; j.alpha = T(-2); j.mode = 2;
+      cj.push_back(j);
+      run_blk2(*this, cj);
+      axpy(x1, t1, T(1));
+      // u1 = t1 + K11i t1 -> y1 ; y1 currently = u1
+      std::vector<Blk2Job<T>> c2;
+      Blk2Job<T> j2{};
+      j2.src = t1.p; j2.splane = t1.plane; j2.sld = t1.ld; j2.dst = y1.p; j2.dplane = y1.plane; j2.dld = y1.ld;
+      j2.rows = n1; j2.cols = k; j2.alpha = T(1); j2.mode = 3;
+      c2.push_back(j2);
+      run_blk2(*this, c2);
+      app(*K11ip, t1, y1, false, true);
+      // y2 = A22^-1 x2 - A22^-1 K21 u1
+      Blk<T> v = new_blk<T>(scratch, n2, k);
+      app(K21, y1, v, false, false);
+      Blk<T> vv = inv22(v, false);
+      std::vector<Blk2Job<T>> c3;
+      Blk2Job<T> j3{};
+      j3.src = w.p; j3.splane = w.plane; j3.sld = w.ld; j3.dst = y2.p; j3.dplane = y2.plane; j3.dld = y2.ld;
+      j3.rows = n2; j3.cols = k; j3.alpha = T(1); j3.mode = 3;
+      c3.push_back(j3);
+      run_blk2(*this, c3);
+      axpy(vv, y2, T(-1));
+    } else {
+      Blk<T> w = inv22(x2, true);                     // A22^-T x2
+      Blk<T> t1 = new_blk<T>(scratch, n1, k);
+      app(K21, w, t1, true, false);                   // K21^T A22^-T x2
+      std::vector<Blk2Job<T>> cj;
+      Blk2Job<T> j{};
+      j.src = t1.p; j.splane = t1.plane; j.sld = t1.ld; j.dst = t1.p; j.dplane = t1.plane; j.dld = t1.ld;
+      j.rows = n1; j.cols = k; j.alpha = T(-2); j.mode = 2;
+      cj.push_back(j);
+      run_blk2(*this, cj);
+      axpy(x1, t1, T(1));                             // v1 = x1 - K21^T A22^-T x2
+      std::vector<Blk2Job<T>> c2;
+      Blk2Job<T> j2{};
+      j2.src = t1.p; j2.splane = t1.plane; j2.sld = t1.ld; j2.dst = y1.p; j2.dplane = y1.plane; j2.dld = y1.ld;
+      j2.rows = n1; j2.cols = k; j2.alpha = T(1); j2.mode = 3;
+      c2.push_back(j2);
+      run_blk2(*this, c2);
+      app(*K11ip, t1, y1, true, true);                // w1 = A11^-T v1
+      Blk<T> v = new_blk<T>(scratch, n2, k);
+      app(K12, y1, v, true, false);                   // K12^T w1
+      Blk<T> vv = inv22(v, true);
+      std::vector<Blk2Job<T>> c3;
+      Blk2Job<T> j3{};
+      j3.src = w.p; j3.splane = w.plane; j3.sld = w.ld; j3.dst = y2.p; j3.dplane = y2.plane; j3.dld = y2.ld;
+      j3.rows = n2; j3.cols = k; j3.alpha = T(1); j3.mode = 3;
+      c3.push_back(j3);
+      run_blk2(*this, c3);
+      axpy(vv, y2, T(-1));
+    }
+    axpy(X, Y, T(-1));                                // minus the identity
+  };
+  return random_matvec(fop, tr, tr, L, P, key * 4u);
+}
+
+template <typename T>
+std::unique_ptr<DHODBFInv<T>> BFContext<T>::hodbf_invert(const DHODBF<T>& H, const BFParams& P, uint32_t key) {
+  auto inv = std::make_unique<DHODBFInv<T>>();
+  inv->n = H.n;
+  inv->tree = H.tree;
+  inv->LH = H.LH;
+  const int LH = H.LH;
+  inv->Dinv.resize(H.D.size());
+  for (size_t q = 0; q < H.D.size(); ++q) inv->Dinv[q] = new_blk<T>(persist, H.D[q].rows, H.D[q].rows);
+  small_inverse(*this, H.D, inv->Dinv);
+  inv->M.clear();
+  inv->M.resize(LH + 1);
+  for (int l = LH - 1; l >= 0; --l) {
+    inv->M[l].resize((size_t)1 << l);
+    for (int i = 0; i < (1 << l); ++i) {
+      const int t1 = 2 * i, t2 = 2 * i + 1;
+      const Range r1 = H.tree[l + 1][t1], r2 = H.tree[l + 1][t2];
+      const int n1 = (int)(r1.b - r1.a), n2 = (int)(r2.b - r2.a);
+      const int Lq = LH - l - 1;
+      std::unique_ptr<DBF<T>> Bs[2];
+      for (int side = 0; side < 2; ++side) {
+        const int tt = side == 0 ? t1 : t2, ts = side == 0 ? t2 : t1;
+        const int na = side == 0 ? n1 : n2, nb = side == 0 ? n2 : n1;
+        const DBF<T>* Boff = H.off[l + 1][tt].get();
+        DHODBFInv<T>* ip = inv.get();
+        DOp<T> op;
+        op.rows = na;
+        op.cols = nb;
+        op.apply = [this, Boff, ip, l, tt, na](const Blk<T>& X, Blk<T>& Y, bool tr_) {
+          const int k = X.cols;
+          Blk<T> t = new_blk<T>(scratch, na, k);
+          if (!tr_) {
+            std::vector<const DBF<T>*> b{Boff};
+            std::vector<Blk<T>> xs{X}, ys{t};
+            apply(b, xs, ys, false, false);
+            inv_apply(*ip, t, Y, false, l + 1, tt);
+          } else {
+            inv_apply(*ip, X, t, true, l + 1, tt);
+            std::vector<const DBF<T>*> b{Boff};
+            std::vector<Blk<T>> xs{t}, ys{Y};
+            apply(b, xs, ys, true, false);
+          }
+        };
+        Tree rt = subtree(H.tree, l + 1, tt, Lq), ct = subtree(H.tree, l + 1, ts, Lq);
+        Bs[side] = random_matvec(op, rt, ct, Lq, P, (key * 131u + (uint32_t)l * 17u + (uint32_t)tt) & 0xFFFFFu);
+      }
+      const int L = Lq + 2;
+      Tree tr = extend_tree(subtree(H.tree, l, i, LH - l), L);
+      inv->M[l][i] = smw_assemble(n1 + n2, tr, L, nullptr, *Bs[0], *Bs[1], nullptr, P,
+                                  (key * 977u + (uint32_t)l * 31u + (uint32_t)i) & 0xFFFFFu);
+    }
+  }
+  check_status();
+  return inv;
+}
+
+template struct DBF<float>;
+template struct DBF<double>;
+template struct DHODBF<float>;
+template struct DHODBF<double>;
+template struct DHODBFInv<float>;
+template struct DHODBFInv<double>;
+template class BFContext<float>;
+template class BFContext<double>;
+
+}  // namespace mf

@@ -1,0 +1,231 @@
+// Device butterfly and HOD-BF matrices (Sec. 3-4) and their algorithms on the GPU:
+// apply / transpose apply, extraction of sub-block lists (Alg. 3), construction
+// from entry extraction (Alg. 2) and from products (Sec. 3.2), HOD-BF
+// construction, extraction and inversion (Alg. 4 with BF_SMW).
+//
+// Control flow runs on the host (index sets, ranks and skeletons are host
+// data, exactly as the oracle keeps them); every numerical step is a batched
+// device launch: one GEMM launch per butterfly level for all blocks of all
+// butterflies involved, one batched ID launch per construction level.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cstdint>
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "analysis.h"
+#include "bf_kernels.h"
+#include "engine.h"
+
+namespace mf {
+
+using Tree = std::vector<std::vector<Range>>;   // levels of index ranges
+
+// Bump allocator over one device allocation; mark/release for scratch phases.
+class Arena {
+ public:
+  void init(size_t bytes) {
+    mem_.alloc(bytes);
+    off_ = 0;
+  }
+  bool ready() const { return mem_.p != nullptr; }
+  void* take(size_t bytes) {
+    size_t o = (off_ + 255) & ~size_t(255);
+    if (o + bytes > mem_.bytes)
+      throw CudaError("device arena exhausted (cudaMalloc: out of memory): need " + std::to_string(o + bytes) +
+                      " of " + std::to_string(mem_.bytes) + " bytes");
+    off_ = o + bytes;
+    peak_ = std::max(peak_, off_);
+    return static_cast<char*>(mem_.p) + o;
+  }
+  template <typename T>
+  T* takeT(size_t n) { return static_cast<T*>(take(n * sizeof(T))); }
+  size_t mark() const { return off_; }
+  void release(size_t m) { off_ = m; }
+  size_t used() const { return off_; }
+  size_t peak() const { return peak_; }
+  size_t capacity() const { return mem_.bytes; }
+
+ private:
+  DevMem mem_;
+  size_t off_ = 0, peak_ = 0;
+};
+
+// A planar complex block in device memory: rows x cols, row-major, leading dim ld.
+template <typename T>
+struct Blk {
+  T* p = nullptr;
+  int64_t plane = 0;
+  int32_t rows = 0, cols = 0;
+  int64_t ld = 0;
+  PMat<T> pm() const { return PMat<T>{p, plane, ld}; }
+  Blk sub(int r0, int c0, int nr, int nc) const {
+    Blk b = *this;
+    b.p = p + (int64_t)r0 * ld + c0;
+    b.rows = nr;
+    b.cols = nc;
+    return b;
+  }
+};
+
+template <typename T>
+Blk<T> new_blk(Arena& a, int rows, int cols) {
+  Blk<T> b;
+  b.rows = rows;
+  b.cols = cols;
+  b.ld = std::max(1, (cols + 3) & ~3);
+  b.plane = (int64_t)std::max(rows, 1) * b.ld;
+  b.p = a.takeT<T>(2 * (size_t)b.plane);
+  return b;
+}
+
+using IdxVec = std::vector<int32_t>;
+
+// Device butterfly (hybrid form, centre at l_c = floor(L/2)).
+template <typename T>
+struct DBF {
+  int m = 0, n = 0, L = 0, lc = 0;
+  Tree rt, ct;
+  // index of pair (i, j) at level l: i * 2^(L-l) + j
+  std::vector<std::vector<Blk<T>>> U;     // l in [lc, L]   (U at L, R below)
+  std::vector<std::vector<IdxVec>> Osk;
+  std::vector<std::vector<Blk<T>>> V;     // l in [0, lc]   (V at 0, W above)
+  std::vector<std::vector<IdxVec>> Ssk;
+  std::vector<Blk<T>> B;                  // pairs at lc
+  void init(int m_, int n_, const Tree& r, const Tree& c, int L_) {
+    m = m_; n = n_; L = L_; lc = L_ / 2;
+    rt.assign(r.begin(), r.begin() + L_ + 1);
+    ct.assign(c.begin(), c.begin() + L_ + 1);
+    U.assign(L + 1, {}); Osk.assign(L + 1, {});
+    V.assign(L + 1, {}); Ssk.assign(L + 1, {});
+    for (int l = 0; l <= L; ++l) {
+      size_t np = (size_t)1 << L;
+      if (l >= lc) { U[l].resize(np); Osk[l].resize(np); }
+      if (l <= lc) { V[l].resize(np); Ssk[l].resize(np); }
+    }
+    B.resize((size_t)1 << L);
+  }
+  int pidx(int l, int i, int j) const { return i * (1 << (L - l)) + j; }
+  int rr(int l, int i, int j) const { return (int)Osk[l][pidx(l, i, j)].size(); }
+  int rc(int l, int i, int j) const { return (int)Ssk[l][pidx(l, i, j)].size(); }
+  int max_rank() const;
+  double storage() const;   // complex entries
+};
+
+// HOD-BF matrix over a uniform-depth cluster tree.
+template <typename T>
+struct DHODBF {
+  int n = 0, LH = 0;
+  Tree tree;
+  std::vector<Blk<T>> D;                   // leaves
+  std::vector<std::vector<std::unique_ptr<DBF<T>>>> off;   // off[l][i], l = 1..LH: K(node i, sibling)
+  int max_rank() const;
+  double storage() const;
+};
+
+// HOD-BF inverse in the product form of Alg. 4:
+// D^-1 = M_root diag(M_level1) ... diag(M_level(LH-1)) diag(D_leaf^-1), M = I + K.
+template <typename T>
+struct DHODBFInv {
+  int n = 0, LH = 0;
+  Tree tree;
+  std::vector<Blk<T>> Dinv;
+  std::vector<std::vector<std::unique_ptr<DBF<T>>>> M;    // M[l][i], l = 0..LH-1
+  double storage() const;
+};
+
+// A black-box operator on device vectors: Y = K X (or K^T X); X is cols x k,
+// Y rows x k, both row-major planar (ld = k, plane = rows * k).
+template <typename T>
+struct DOp {
+  int rows = 0, cols = 0;
+  std::function<void(const Blk<T>& X, Blk<T>& Y, bool transpose)> apply;
+};
+
+// Extraction callback: fills dst blocks (allocated by the caller, X.size() x Y.size()).
+template <typename T>
+using DExtract = std::function<void(const std::vector<std::pair<IdxVec, IdxVec>>& lst, std::vector<Blk<T>>& dst)>;
+
+// One butterfly construction problem of a batch (Alg. 2 in lockstep).
+template <typename T>
+struct BFProblem {
+  int m = 0, n = 0, L = 0;
+  int64_t row_off = 0, col_off = 0;   // shift of local indices into the extractor's index space
+  Tree rt, ct;
+  std::vector<IdxVec> nn_r, nn_c;     // neighbour lists in local indices
+  std::unique_ptr<DBF<T>> out;
+};
+
+// One HOD-BF construction problem: square block of size n at offset off of the extractor's index space.
+template <typename T>
+struct HProblem {
+  int n = 0;
+  int64_t off = 0;
+  Tree tree;
+  std::vector<IdxVec> nn;             // neighbours in local indices
+  std::unique_ptr<DHODBF<T>> out;
+};
+
+struct BFParams {
+  double tol = 1e-4;
+  int max_rank = 0;
+  int alpha = 2, knn = 8;
+  int p = 8;            // oversampling of the randomized construction
+  int q_start = 64;     // sketch width without a rank cap
+};
+
+// Everything the butterfly algorithms need: stream, arenas, counters.
+template <typename T>
+class BFContext {
+ public:
+  BFContext(cudaStream_t st, size_t persist_bytes, size_t scratch_bytes);
+  cudaStream_t st;
+  Arena persist, scratch;
+  DevMem status;
+  double flops = 0;
+  int max_rank_seen = 0;
+  int64_t n_id = 0;
+
+  // ---- primitives
+  void gemm(std::vector<GemmDesc<T>>& descs);             // one launch for all descs
+  void zero(Blk<T>& b);
+  // row IDs of the given matrices (device); results on host (ranks, skeletons) and U in persist
+  void row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_rank, std::vector<IdxVec>& sk,
+               std::vector<Blk<T>>& Us);
+  // ---- butterfly algorithms
+  void apply(const std::vector<const DBF<T>*>& bfs, const std::vector<Blk<T>>& X, std::vector<Blk<T>>& Y,
+             bool transpose, bool accumulate);
+  void extract_bf(const DBF<T>& bf, const std::vector<std::pair<IdxVec, IdxVec>>& lst, std::vector<Blk<T>>& dst,
+                  T sign);
+  // several butterflies at once, stage-merged; dst blocks receive += K(X, Y)
+  void extract_multi(const std::vector<const DBF<T>*>& bfs,
+                     const std::vector<const std::vector<std::pair<IdxVec, IdxVec>>*>& lsts,
+                     const std::vector<std::vector<Blk<T>>*>& dsts);
+  void entry_eval_batch(const DExtract<T>& ext, std::vector<BFProblem<T>>& probs, const BFParams& P);
+  void hodbf_entry_eval_batch(const DExtract<T>& ext, std::vector<HProblem<T>>& probs, const BFParams& P);
+  std::unique_ptr<DBF<T>> entry_eval(const DExtract<T>& ext, int m, int n, const Tree& rt, const Tree& ct, int L,
+                                      const std::vector<IdxVec>& nn_r, const std::vector<IdxVec>& nn_c,
+                                      const BFParams& P);
+  std::unique_ptr<DBF<T>> random_matvec(const DOp<T>& op, const Tree& rt, const Tree& ct, int L, const BFParams& P,
+                                         uint32_t key);
+  void right_transform(const DBF<T>& bf, const Blk<T>& X, std::vector<Blk<T>>& xs);
+  std::unique_ptr<DBF<T>> split_child(const DBF<T>& bf, int a, int b);
+  // ---- HOD-BF
+  std::unique_ptr<DHODBF<T>> hodbf_entry_eval(const DExtract<T>& ext, int n, const Tree& tree,
+                                               const std::vector<IdxVec>& nn, const BFParams& P);
+  void hodbf_apply(const DHODBF<T>& H, const Blk<T>& X, Blk<T>& Y, bool transpose);
+  void hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair<IdxVec, IdxVec>>& lst, std::vector<Blk<T>>& dst,
+                     T sign);
+  std::unique_ptr<DHODBFInv<T>> hodbf_invert(const DHODBF<T>& H, const BFParams& P, uint32_t key);
+  void inv_apply(const DHODBFInv<T>& Hi, const Blk<T>& X, Blk<T>& Y, bool transpose, int l0 = 0, int i0 = 0);
+  std::unique_ptr<DBF<T>> bf_smw(const DBF<T>& K, const BFParams& P, uint32_t key);
+  std::unique_ptr<DBF<T>> smw_assemble(int n, const Tree& tr, int L, const DBF<T>* K11, const DBF<T>& K12,
+                                       const DBF<T>& K21, const DBF<T>* K22i, const BFParams& P, uint32_t key);
+  void check_status();
+};
+
+}  // namespace mf

@@ -279,6 +279,157 @@ int launch_small_inverse(const InvJob<T>* d_jobs, int njobs, int max_n, int32_t*
   return 0;
 }
 
+template <typename T>
+__global__ void k_blk2(const Blk2Job<T>* jobs) {
+  const Blk2Job<T> j = jobs[blockIdx.y];
+  const int64_t total = (int64_t)j.rows * j.cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / j.cols), c = (int)(e % j.cols);
+    if (j.mode == 0) {
+      const int64_t so = (int64_t)r * j.sld + c, dof = (int64_t)c * j.dld + r;
+      j.dst[dof] = j.src[so];
+      j.dst[dof + j.dplane] = j.src[so + j.splane];
+    } else if (j.mode == 1) {
+      const int64_t so = (int64_t)j.ridx[r] * j.sld + j.cidx[c], dof = (int64_t)r * j.dld + c;
+      j.dst[dof] += j.alpha * j.src[so];
+      j.dst[dof + j.dplane] += j.alpha * j.src[so + j.splane];
+    } else if (j.mode == 2) {
+      const int64_t so = (int64_t)r * j.sld + c, dof = (int64_t)r * j.dld + c;
+      j.dst[dof] += j.alpha * j.src[so];
+      j.dst[dof + j.dplane] += j.alpha * j.src[so + j.splane];
+    } else {
+      const int64_t so = (int64_t)r * j.sld + c, dof = (int64_t)r * j.dld + c;
+      j.dst[dof] = j.src[so];
+      j.dst[dof + j.dplane] = j.src[so + j.splane];
+    }
+  }
+}
+
+template <typename T>
+void launch_blk2(const Blk2Job<T>* d_jobs, int njobs, int64_t max_elems, cudaStream_t st) {
+  if (njobs <= 0 || max_elems <= 0) return;
+  int bx = (int)((max_elems + 255) / 256);
+  if (bx > 512) bx = 512;
+  count_launches(1);
+  k_blk2<T><<<dim3(bx, njobs), 256, 0, st>>>(d_jobs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lstsq(const LstsqJob<T>* jobs, int32_t* status) {
+  const LstsqJob<T> j = jobs[blockIdx.x];
+  const int c = j.c, r = j.r, w = j.w;
+  extern __shared__ double lsq[];
+  double* Gr = lsq;              // c x c, Hermitian, then its Cholesky factor (lower)
+  double* Gi = Gr + c * c;
+  double* zr = Gi + c * c;       // per-thread-block solve vector
+  double* zi = zr + c;
+  const T* Tr = j.Tm;
+  const T* Ti = j.Tm + j.tplane;
+  // G = Tm Tm^H
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    int a = e / c, b = e % c;
+    if (b > a) continue;
+    double sr = 0, si = 0;
+    for (int t = 0; t < w; ++t) {
+      double ar = Tr[(int64_t)a * j.tld + t], ai = Ti[(int64_t)a * j.tld + t];
+      double br = Tr[(int64_t)b * j.tld + t], bi = Ti[(int64_t)b * j.tld + t];
+      sr += ar * br + ai * bi;      // a * conj(b)
+      si += ai * br - ar * bi;
+    }
+    Gr[a * c + b] = sr; Gi[a * c + b] = si;
+    Gr[b * c + a] = sr; Gi[b * c + a] = -si;
+  }
+  __syncthreads();
+  // Cholesky G = L L^H (in place, lower), by one thread per column step
+  for (int k = 0; k < c; ++k) {
+    if (threadIdx.x == 0) {
+      double d = Gr[k * c + k];
+      if (!(d > 0)) {
+        if (status) atomicExch(status, (int32_t)DEV_ZERO_PIVOT);
+        d = 1e-300;
+      }
+      Gr[k * c + k] = sqrt(d);
+      Gi[k * c + k] = 0;
+    }
+    __syncthreads();
+    const double dk = Gr[k * c + k];
+    for (int i = k + 1 + threadIdx.x; i < c; i += blockDim.x) {
+      Gr[i * c + k] /= dk;
+      Gi[i * c + k] /= dk;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (c - k - 1) * (c - k - 1); e += blockDim.x) {
+      int i = k + 1 + e / (c - k - 1), l = k + 1 + e % (c - k - 1);
+      if (l > i) continue;
+      // G[i][l] -= L[i][k] conj(L[l][k])
+      double ar = Gr[i * c + k], ai = Gi[i * c + k], br = Gr[l * c + k], bi = Gi[l * c + k];
+      Gr[i * c + l] -= ar * br + ai * bi;
+      Gi[i * c + l] -= ai * br - ar * bi;
+    }
+    __syncthreads();
+  }
+  // rows of B: b_i = h_i G^-1, h_i = y_i Tm^H ; solve G b_i^H = h_i^H
+  const T* Yr = j.Y;
+  const T* Yi = j.Y + j.yplane;
+  for (int i = 0; i < r; ++i) {
+    for (int a = threadIdx.x; a < c; a += blockDim.x) {
+      double sr = 0, si = 0;   // h_i[a] = sum_t y[t] conj(T[a][t]) ; store conj -> h^H
+      for (int t = 0; t < w; ++t) {
+        double yr = Yr[(int64_t)i * j.yld + t], yi = Yi[(int64_t)i * j.yld + t];
+        double tr = Tr[(int64_t)a * j.tld + t], ti = Ti[(int64_t)a * j.tld + t];
+        sr += yr * tr + yi * ti;
+        si += yi * tr - yr * ti;
+      }
+      zr[a] = sr;
+      zi[a] = -si;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int a = 0; a < c; ++a) {          // L z = h^H
+        double vr = zr[a], vi = zi[a];
+        for (int b = 0; b < a; ++b) {
+          double lr = Gr[a * c + b], li = Gi[a * c + b];
+          vr -= lr * zr[b] - li * zi[b];
+          vi -= lr * zi[b] + li * zr[b];
+        }
+        zr[a] = vr / Gr[a * c + a];
+        zi[a] = vi / Gr[a * c + a];
+      }
+      for (int a = c - 1; a >= 0; --a) {     // L^H x = z
+        double vr = zr[a], vi = zi[a];
+        for (int b = a + 1; b < c; ++b) {
+          double lr = Gr[b * c + a], li = -Gi[b * c + a];
+          vr -= lr * zr[b] - li * zi[b];
+          vi -= lr * zi[b] + li * zr[b];
+        }
+        zr[a] = vr / Gr[a * c + a];
+        zi[a] = vi / Gr[a * c + a];
+      }
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < c; a += blockDim.x) {
+      j.B[(int64_t)i * j.bld + a] = (T)zr[a];
+      j.B[(int64_t)i * j.bld + a + j.bplane] = (T)(-zi[a]);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int32_t* status, cudaStream_t st) {
+  if (njobs <= 0) return 0;
+  size_t sm = sizeof(double) * (2 * (size_t)max_c * max_c + 2 * (size_t)max_c);
+  if (sm > 200 * 1024) return -1;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_lstsq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  count_launches(1);
+  k_lstsq<T><<<njobs, 256, sm, st>>>(d_jobs, status);
+  return 0;
+}
+
 #define MF_BF_INST(T)                                                                                            \
   template int launch_row_id<T>(const IdJob<T>*, int, int, int, T, int, cudaStream_t);                          \
   template void launch_sketch<T>(const SketchGroup*, int, int, T*, int64_t, int, cudaStream_t);                 \
@@ -286,7 +437,9 @@ int launch_small_inverse(const InvJob<T>* d_jobs, int njobs, int max_n, int32_t*
   template void launch_front_entries<T>(const FrontEntryJob<T>*, int, int64_t, const FrontCtx<T>*, const int64_t*, \
                                         const int32_t*, const double*, cudaStream_t);                           \
   template void launch_place<T>(const PlaceJob<T>*, int, int64_t, cudaStream_t);                                \
-  template int launch_small_inverse<T>(const InvJob<T>*, int, int, int32_t*, cudaStream_t);
+  template int launch_small_inverse<T>(const InvJob<T>*, int, int, int32_t*, cudaStream_t);                     \
+  template void launch_blk2<T>(const Blk2Job<T>*, int, int64_t, cudaStream_t);                                   \
+  template int launch_lstsq<T>(const LstsqJob<T>*, int, int, int32_t*, cudaStream_t);
 
 MF_BF_INST(float)
 MF_BF_INST(double)

@@ -98,6 +98,42 @@ struct InvJob {
   int64_t xplane, ldx;
 };
 
+// Block-to-block operations on planar row-major blocks:
+//   mode 0: dst = src^T (plain transpose), dst is cols x rows
+//   mode 1: dst[a][b] += alpha * src[ridx[a]][cidx[b]]   (gather of a sub-block)
+//   mode 2: dst += alpha * src
+//   mode 3: dst = src
+template <typename T>
+struct Blk2Job {
+  const T* src;
+  int64_t splane, sld;
+  T* dst;
+  int64_t dplane, dld;
+  int32_t rows, cols;
+  T alpha;
+  const int32_t* ridx;
+  const int32_t* cidx;
+  int32_t mode;
+};
+
+// B (r x c) minimising ||B Tm - Y||_F for Tm (c x w), Y (r x w): normal equations
+// in FP64 with a Cholesky factorization (c <= 110).
+template <typename T>
+struct LstsqJob {
+  const T* Tm;
+  int64_t tplane, tld;
+  const T* Y;
+  int64_t yplane, yld;
+  T* B;
+  int64_t bplane, bld;
+  int32_t c, r, w;
+};
+
+template <typename T>
+void launch_blk2(const Blk2Job<T>* d_jobs, int njobs, int64_t max_elems, cudaStream_t st);
+template <typename T>
+int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int32_t* status, cudaStream_t st);
+
 template <typename T>
 int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st);
 template <typename T>

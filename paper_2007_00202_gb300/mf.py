@@ -75,6 +75,12 @@ SIGNATURES = {
     "mf_destroy": (None, [_P]),
     "mf_launch_counter": (C.c_int64, []),
     "mf_profile": (C.c_int, [_P, C.c_int32]),
+    "mf_green_build": (C.c_int, [C.c_int32, _I32P, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                 C.c_int32, C.c_int32, _P, C.POINTER(_P)]),
+    "mf_green_info": (C.c_int, [_P, _I64P, _DP, _I32P, _DP]),
+    "mf_green_points": (C.c_int, [_P, _DP, _DP]),
+    "mf_green_apply": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "mf_green_destroy": (None, [_P]),
     "mf_row_id_c64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, C.c_double, C.c_int32, _P, _P, _P, _P]),
     "mf_row_id_c64_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, C.c_double, C.c_int32, _P, _P, _P,
                                         _P]),
@@ -268,3 +274,29 @@ def mf_row_id_c64_noalloc(nmat, m, n, M, tol, max_rank, U, sk, rank, stream=0):
     """mf_row_id_c64 with the library's fixed scratch array (no device allocation); see include/mf.h."""
     _check(lib().mf_row_id_c64_noalloc(nmat, m, n, C.c_void_p(M), tol, max_rank, C.c_void_p(U), C.c_void_p(sk),
                                        C.c_void_p(rank), C.c_void_p(stream)))
+
+
+class GreenSet:
+    """Set of HOD-BF compressed Green's-function blocks built on the GPU (mf_green_*)."""
+
+    def __init__(self, m_list, k, h=1.0, tol=1e-4, leaf=64, max_rank=0, alpha=2, knn=8, stream=0):
+        m = np.ascontiguousarray(m_list, dtype=np.int32)
+        self.ptr = C.c_void_p()
+        _check(lib().mf_green_build(len(m), _p(m, C.c_int32), k, h, tol, leaf, max_rank, alpha, knn,
+                                    C.c_void_p(stream), C.byref(self.ptr)))
+        rows = C.c_int64(); st = C.c_double(); mr = C.c_int32(); bs = C.c_double()
+        _check(lib().mf_green_info(self.ptr, C.byref(rows), C.byref(st), C.byref(mr), C.byref(bs)))
+        self.rows, self.storage, self.max_rank, self.build_seconds = rows.value, st.value, mr.value, bs.value
+
+    def points(self):
+        P = np.empty((self.rows, 3)); Q = np.empty((self.rows, 3))
+        _check(lib().mf_green_points(self.ptr, _p(P, C.c_double), _p(Q, C.c_double)))
+        return P, Q
+
+    def apply(self, nrhs, d_x, d_y):
+        _check(lib().mf_green_apply(self.ptr, nrhs, C.c_void_p(d_x), C.c_void_p(d_y)))
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            lib().mf_green_destroy(self.ptr)
+            self.ptr = None
