@@ -370,8 +370,21 @@ int mf_factor(mf_handle* h, double tol) {
     auto t0 = std::chrono::steady_clock::now();
     ensure_device(h);
     if (!h->eng) {
-      h->eng = h->opt.precision == MF_PREC_C128 ? mf::make_engine_c128(h->an, h->A, h->stream)
-                                               : mf::make_engine_c64(h->an, h->A, h->stream);
+      mf::EngineOptions eo;
+      eo.max_rank = h->opt.max_rank;
+      eo.alpha = h->opt.alpha;
+      eo.knn = h->opt.knn;
+      eo.seed = h->opt.seed;
+      bool any_comp = false;
+      size_t comp_n = 0;
+      for (auto& f : h->an.fronts)
+        if (f.compressed) { any_comp = true; comp_n += (size_t)(f.s() + f.u()); }
+      // arenas for the compressed fronts, sized from their dimensions (generous: 280 GB devices)
+      size_t el = h->opt.precision == MF_PREC_C128 ? 16 : 8;
+      eo.persist_bytes = any_comp ? std::max<size_t>(size_t(8) << 30, comp_n * 20000 * el) : 0;
+      eo.scratch_bytes = any_comp ? std::max<size_t>(size_t(4) << 30, comp_n * 10000 * el) : 0;
+      h->eng = h->opt.precision == MF_PREC_C128 ? mf::make_engine_c128(h->an, h->A, h->stream, eo)
+                                               : mf::make_engine_c64(h->an, h->A, h->stream, eo);
       h->eng->profiling = h->profile;
     }
     h->factored = false;

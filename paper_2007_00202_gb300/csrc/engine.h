@@ -39,6 +39,11 @@ struct DevMem {
   DevMem() = default;
   DevMem(const DevMem&) = delete;
   DevMem& operator=(const DevMem&) = delete;
+  DevMem(DevMem&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevMem& operator=(DevMem&& o) noexcept {
+    if (this != &o) { reset(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
   ~DevMem() { reset(); }
   void reset() {
     if (p) cudaFree(p);
@@ -83,6 +88,7 @@ class EngineBase {
   virtual int launches_factor() const = 0;
   virtual int launches_solve(int nrhs) = 0;
   virtual int max_rank() const { return 0; }
+  virtual double compressed_seconds() const { return 0; }
   // Event timing of the dominant kernel (the batched front GEMM) inside factor().
   struct Profile {
     int64_t launches = 0;
@@ -92,7 +98,18 @@ class EngineBase {
   Profile prof;
 };
 
-std::unique_ptr<EngineBase> make_engine_c64(const Analysis& an, const DeviceMatrix& A, cudaStream_t st);
-std::unique_ptr<EngineBase> make_engine_c128(const Analysis& an, const DeviceMatrix& A, cudaStream_t st);
+// Parameters of the compressed fronts (Alg. 2-5).
+struct EngineOptions {
+  int max_rank = 0;
+  int alpha = 2, knn = 8;
+  uint64_t seed = 1;
+  size_t persist_bytes = size_t(24) << 30;   // device arena for compressed factors
+  size_t scratch_bytes = size_t(12) << 30;   // device arena for construction work
+};
+
+std::unique_ptr<EngineBase> make_engine_c64(const Analysis& an, const DeviceMatrix& A, cudaStream_t st,
+                                            const EngineOptions& eo);
+std::unique_ptr<EngineBase> make_engine_c128(const Analysis& an, const DeviceMatrix& A, cudaStream_t st,
+                                             const EngineOptions& eo);
 
 }  // namespace mf

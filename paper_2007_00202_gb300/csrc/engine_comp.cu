@@ -1,0 +1,293 @@
+// Compressed fronts (Alg. 5) on the GPU; see engine_comp.h.
+#include <algorithm>
+#include <chrono>
+#include <numeric>
+
+#include "engine_comp.h"
+
+namespace mf {
+
+namespace {
+
+IdxVec iota_vec(int n) {
+  IdxVec v(n);
+  std::iota(v.begin(), v.end(), 0);
+  return v;
+}
+
+}  // namespace
+
+template <typename T>
+void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr, const BFParams& P, uint64_t seed) {
+  auto t0 = std::chrono::steady_clock::now();
+  const FrontInfo& f = an_.fronts[fid];
+  const int s = (int)f.s(), u = (int)f.u();
+  auto cfp = std::make_unique<CompFront<T>>();
+  CompFront<T>& cf = *cfp;
+  cf.fid = fid;
+  cf.s = s;
+  cf.u = u;
+  cf.sep_begin = f.sep_begin;
+  // position of each global index in this front: I^s -> [0, s), I^u -> s + index
+  auto front_pos = [&](int64_t g) -> int32_t {
+    if (g >= f.sep_begin && g < f.sep_end) return (int32_t)(g - f.sep_begin);
+    auto it = std::lower_bound(f.upd.begin(), f.upd.end(), g);
+    if (it == f.upd.end() || *it != g) return -1;
+    return (int32_t)(s + (it - f.upd.begin()));
+  };
+  // children: inverse relative maps (front position -> child position, -1 if absent)
+  struct Kid {
+    int id;
+    bool compressed;
+    std::vector<int32_t> inv;
+    DevMem d_inv;
+  };
+  std::vector<Kid> kids;
+  for (int64_t c : f.children) {
+    Kid k;
+    k.id = (int)c;
+    k.compressed = an_.fronts[c].compressed;
+    k.inv.assign(s + u, -1);
+    const auto& cu = an_.fronts[c].upd;
+    for (size_t i = 0; i < cu.size(); ++i) {
+      int32_t p = front_pos(cu[i]);
+      if (p < 0) throw std::runtime_error("child update set not in the parent front");
+      k.inv[p] = (int32_t)i;
+    }
+    upload(k.d_inv, k.inv, st_);
+    kids.push_back(std::move(k));
+  }
+  // device context of the gathers: A entries and dense children
+  FrontCtx<T> ctx{};
+  ctx.sep_begin = f.sep_begin;
+  ctx.s = s;
+  ctx.u = u;
+  ctx.upd = fr[fid].upd;
+  ctx.nkids = 0;
+  for (auto& k : kids)
+    if (!k.compressed) {
+      DenseKid<T> dk;
+      dk.C = fr[k.id].C;
+      dk.plane = fr[k.id].pl_uu;
+      dk.ld = fr[k.id].lu;
+      dk.inv = k.d_inv.template as<int32_t>();
+      ctx.kids[ctx.nkids++] = dk;
+    }
+  DevMem d_ctx;
+  upload(d_ctx, std::vector<FrontCtx<T>>{ctx}, st_);
+  const FrontCtx<T>* dctx = d_ctx.template as<FrontCtx<T>>();
+  const DBF<T>* Sptr = nullptr;
+  // extraction over front positions; shifts map the caller's local indices to front positions
+  auto make_ext = [&, dctx](int rs, int cs, bool with_A, bool minus_S) -> DExtract<T> {
+    return [&, dctx, rs, cs, with_A, minus_S](const std::vector<std::pair<IdxVec, IdxVec>>& lst,
+                                              std::vector<Blk<T>>& dst) {
+      std::vector<FrontEntryJob<T>> jobs;
+      int64_t mx = 0;
+      std::vector<std::pair<IdxVec, IdxVec>> g(lst);
+      for (auto& pr : g) {
+        for (auto& x : pr.first) x += rs;
+        for (auto& y : pr.second) y += cs;
+      }
+      for (size_t q = 0; q < g.size(); ++q) {
+        if (g[q].first.empty() || g[q].second.empty()) continue;
+        FrontEntryJob<T> j;
+        j.ctx = 0;
+        auto* dx = cx.scratch.template takeT<int32_t>(g[q].first.size());
+        auto* dy = cx.scratch.template takeT<int32_t>(g[q].second.size());
+        MF_CUDA(cudaMemcpyAsync(dx, g[q].first.data(), g[q].first.size() * 4, cudaMemcpyHostToDevice, st_));
+        MF_CUDA(cudaMemcpyAsync(dy, g[q].second.data(), g[q].second.size() * 4, cudaMemcpyHostToDevice, st_));
+        j.X = dx; j.Y = dy;
+        j.nx = (int)g[q].first.size(); j.ny = (int)g[q].second.size();
+        j.dst = dst[q].p; j.dplane = dst[q].plane; j.dld = dst[q].ld;
+        j.with_A = with_A ? 1 : 0;
+        j.accumulate = 0;
+        jobs.push_back(j);
+        mx = std::max<int64_t>(mx, (int64_t)j.nx * j.ny);
+      }
+      if (!jobs.empty()) {
+        auto* dj = cx.scratch.template takeT<FrontEntryJob<T>>(jobs.size());
+        MF_CUDA(cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(jobs[0]), cudaMemcpyHostToDevice, st_));
+        launch_front_entries<T>(dj, (int)jobs.size(), mx, dctx, A_.rowptr.template as<int64_t>(),
+                                A_.col32.template as<int32_t>(), A_.vals.template as<double>(), st_);
+      }
+      for (auto& k : kids) {
+        if (!k.compressed) continue;
+        std::vector<std::pair<IdxVec, IdxVec>> m(g.size());
+        bool any = false;
+        for (size_t q = 0; q < g.size(); ++q) {
+          for (int32_t x : g[q].first) m[q].first.push_back(x >= 0 && x < s + u ? k.inv[x] : -1);
+          for (int32_t y : g[q].second) m[q].second.push_back(y >= 0 && y < s + u ? k.inv[y] : -1);
+          any = true;
+        }
+        if (any) cx.hodbf_extract(*fronts.at(k.id)->C, m, dst, T(1));
+      }
+      if (minus_S && Sptr) {
+        std::vector<std::pair<IdxVec, IdxVec>> m(g);
+        for (auto& pr : m) {
+          for (auto& x : pr.first) x -= s;
+          for (auto& y : pr.second) y -= s;
+        }
+        cx.extract_bf(*Sptr, m, dst, T(-1));
+      }
+    };
+  };
+  // neighbour lists in front positions
+  FrontNeighbours nb;
+  front_neighbours(an_, f, P.knn, nb);
+  auto to_local = [&](const std::vector<int64_t>& ptr, const std::vector<int64_t>& idx, int rows, int base) {
+    std::vector<IdxVec> out(rows);
+    for (int r = 0; r < rows; ++r)
+      for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) {
+        int32_t p = front_pos(idx[k]);
+        if (p >= 0) out[r].push_back(p - base);
+      }
+    return out;
+  };
+  std::vector<IdxVec> nn11 = to_local(nb.nn11_ptr, nb.nn11, s, 0);
+  std::vector<IdxVec> nn12 = to_local(nb.nn12_ptr, nb.nn12, s, s);   // I^s row -> I^u local
+  std::vector<IdxVec> nn21 = to_local(nb.nn21_ptr, nb.nn21, u, 0);   // I^u row -> I^s local
+  std::vector<IdxVec> nn22 = to_local(nb.nn22_ptr, nb.nn22, u, s);
+  Tree th = f.th_tree, t22 = f.f22_tree;
+  cf.F11 = cx.hodbf_entry_eval(make_ext(0, 0, true, false), s, th, nn11, P);
+  cf.F11inv = cx.hodbf_invert(*cf.F11, P, (uint32_t)((seed * 7 + fid) & 0xFFFFF));
+  if (u > 0) {
+    const int LH = (int)th.size() - 1, L22 = (int)t22.size() - 1, L = std::min(LH, L22);
+    cf.F12 = cx.entry_eval(make_ext(0, s, true, false), s, u, th, t22, L, nn12, nn21, P);
+    cf.F21 = cx.entry_eval(make_ext(s, 0, true, false), u, s, t22, th, L, nn21, nn12, P);
+    const DBF<T>* F12p = cf.F12.get();
+    const DBF<T>* F21p = cf.F21.get();
+    const DHODBFInv<T>* Ip = cf.F11inv.get();
+    DOp<T> op;
+    op.rows = u;
+    op.cols = u;
+    op.apply = [this, F12p, F21p, Ip, s, u](const Blk<T>& X, Blk<T>& Y, bool tr) {
+      const int k = X.cols;
+      Blk<T> a = new_blk<T>(cx.scratch, s, k), b = new_blk<T>(cx.scratch, s, k);
+      std::vector<Blk<T>> xs{X}, as{a};
+      std::vector<const DBF<T>*> one{tr ? F21p : F12p};
+      cx.apply(one, xs, as, tr, false);                 // F12 x   (or F21^T x)
+      cx.inv_apply(*Ip, a, b, tr, 0, 0);                // F11^-1 . (or F11^-T .)
+      std::vector<Blk<T>> bs{b}, ys{Y};
+      std::vector<const DBF<T>*> two{tr ? F12p : F21p};
+      cx.apply(two, bs, ys, tr, false);                 // F21 .   (or F12^T .)
+    };
+    auto S = cx.random_matvec(op, t22, t22, L22, P, (uint32_t)((seed * 13 + fid) & 0xFFFFF));
+    Sptr = S.get();
+    if (f.parent >= 0) cf.C = cx.hodbf_entry_eval(make_ext(s, s, false, true), u, t22, nn22, P);
+    Sptr = nullptr;
+    cf.max_rank = std::max({cf.F11->max_rank(), cf.F12->max_rank(), cf.F21->max_rank(), S->max_rank(),
+                            cf.C ? cf.C->max_rank() : 0});
+  } else {
+    cf.max_rank = cf.F11->max_rank();
+  }
+  cf.upd32.resize(u);
+  for (int i = 0; i < u; ++i) cf.upd32[i] = (int32_t)f.upd[i];
+  upload(cf.d_upd32, cf.upd32, st_);
+  MF_CUDA(cudaStreamSynchronize(st_));
+  cx.check_status();
+  cf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  fronts[fid] = std::move(cfp);
+}
+
+template <typename T>
+void CompressedPart<T>::densify_C(int fid, const FrontDev<T>& fd) {
+  CompFront<T>& cf = *fronts.at(fid);
+  if (!cf.C || cf.u == 0) return;
+  const int u = cf.u;
+  const size_t mk = cx.scratch.mark();
+  Blk<T> I = new_blk<T>(cx.scratch, u, u);
+  cx.zero(I);
+  {
+    std::vector<T> ones(u, T(1));
+    // identity: set the diagonal of the real plane through strided copies
+    MF_CUDA(cudaMemcpy2DAsync(I.p, (I.ld + 1) * sizeof(T), ones.data(), sizeof(T), sizeof(T), u,
+                              cudaMemcpyHostToDevice, st_));
+    MF_CUDA(cudaStreamSynchronize(st_));
+  }
+  Blk<T> Cd;
+  Cd.p = fd.C; Cd.rows = u; Cd.cols = u; Cd.ld = fd.lu; Cd.plane = fd.pl_uu;
+  cx.hodbf_apply(*cf.C, I, Cd, false);
+  MF_CUDA(cudaStreamSynchronize(st_));
+  cx.scratch.release(mk);
+}
+
+template <typename T>
+void CompressedPart<T>::forward(int fid, Blk<T>& X) {
+  CompFront<T>& cf = *fronts.at(fid);
+  const int s = cf.s, u = cf.u, k = X.cols;
+  const size_t mk = cx.scratch.mark();
+  Blk<T> xs = X.sub((int)cf.sep_begin, 0, s, k);
+  Blk<T> w = new_blk<T>(cx.scratch, s, k);
+  cx.inv_apply(*cf.F11inv, xs, w, false, 0, 0);
+  std::vector<Blk2Job<T>> cp;
+  Blk2Job<T> j{};
+  j.src = w.p; j.splane = w.plane; j.sld = w.ld; j.dst = xs.p; j.dplane = xs.plane; j.dld = xs.ld;
+  j.rows = s; j.cols = k; j.alpha = T(1); j.mode = 3;
+  cp.push_back(j);
+  {
+    auto* d = cx.scratch.template takeT<Blk2Job<T>>(1);
+    MF_CUDA(cudaMemcpyAsync(d, cp.data(), sizeof(Blk2Job<T>), cudaMemcpyHostToDevice, st_));
+    launch_blk2<T>(d, 1, (int64_t)s * k, st_);
+  }
+  if (u > 0) {
+    Blk<T> t = new_blk<T>(cx.scratch, u, k);
+    std::vector<const DBF<T>*> b{cf.F21.get()};
+    std::vector<Blk<T>> xsv{w}, ys{t};
+    cx.apply(b, xsv, ys, false, false);
+    PlaceJob<T> pl;
+    pl.src = t.p; pl.splane = t.plane; pl.sld = t.ld;
+    IdxVec cols = iota_vec(k);
+    auto* dc = cx.scratch.template takeT<int32_t>(k);
+    MF_CUDA(cudaMemcpyAsync(dc, cols.data(), k * 4, cudaMemcpyHostToDevice, st_));
+    pl.rows = cf.d_upd32.template as<int32_t>(); pl.cols = dc; pl.nr = u; pl.nc = k;
+    pl.dst = X.p; pl.dplane = X.plane; pl.dld = X.ld; pl.sign = T(-1);
+    auto* d = cx.scratch.template takeT<PlaceJob<T>>(1);
+    MF_CUDA(cudaMemcpyAsync(d, &pl, sizeof(pl), cudaMemcpyHostToDevice, st_));
+    launch_place<T>(d, 1, (int64_t)u * k, st_);
+  }
+  MF_CUDA(cudaStreamSynchronize(st_));
+  cx.scratch.release(mk);
+}
+
+template <typename T>
+void CompressedPart<T>::backward(int fid, Blk<T>& X) {
+  CompFront<T>& cf = *fronts.at(fid);
+  const int s = cf.s, u = cf.u, k = X.cols;
+  if (u == 0) return;
+  const size_t mk = cx.scratch.mark();
+  Blk<T> xs = X.sub((int)cf.sep_begin, 0, s, k);
+  Blk<T> g = new_blk<T>(cx.scratch, u, k);
+  cx.zero(g);
+  IdxVec cols = iota_vec(k);
+  auto* dc = cx.scratch.template takeT<int32_t>(k);
+  MF_CUDA(cudaMemcpyAsync(dc, cols.data(), k * 4, cudaMemcpyHostToDevice, st_));
+  Blk2Job<T> j{};
+  j.src = X.p; j.splane = X.plane; j.sld = X.ld; j.dst = g.p; j.dplane = g.plane; j.dld = g.ld;
+  j.rows = u; j.cols = k; j.alpha = T(1); j.mode = 1;
+  j.ridx = cf.d_upd32.template as<int32_t>(); j.cidx = dc;
+  {
+    auto* d = cx.scratch.template takeT<Blk2Job<T>>(1);
+    MF_CUDA(cudaMemcpyAsync(d, &j, sizeof(j), cudaMemcpyHostToDevice, st_));
+    launch_blk2<T>(d, 1, (int64_t)u * k, st_);
+  }
+  Blk<T> v = new_blk<T>(cx.scratch, s, k), z = new_blk<T>(cx.scratch, s, k);
+  std::vector<const DBF<T>*> b{cf.F12.get()};
+  std::vector<Blk<T>> gs{g}, vs{v};
+  cx.apply(b, gs, vs, false, false);
+  cx.inv_apply(*cf.F11inv, v, z, false, 0, 0);
+  Blk2Job<T> a{};
+  a.src = z.p; a.splane = z.plane; a.sld = z.ld; a.dst = xs.p; a.dplane = xs.plane; a.dld = xs.ld;
+  a.rows = s; a.cols = k; a.alpha = T(-1); a.mode = 2;
+  {
+    auto* d = cx.scratch.template takeT<Blk2Job<T>>(1);
+    MF_CUDA(cudaMemcpyAsync(d, &a, sizeof(a), cudaMemcpyHostToDevice, st_));
+    launch_blk2<T>(d, 1, (int64_t)s * k, st_);
+  }
+  MF_CUDA(cudaStreamSynchronize(st_));
+  cx.scratch.release(mk);
+}
+
+template class CompressedPart<float>;
+template class CompressedPart<double>;
+
+}  // namespace mf

@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "engine.h"
+#include "engine_comp.h"
 
 namespace mf {
 
@@ -26,9 +27,15 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 template <typename T>
 class DenseEngine : public EngineBase {
  public:
-  DenseEngine(const Analysis& an, const DeviceMatrix& A, cudaStream_t st) : an_(an), A_(A), st_(st) { plan(); }
+  DenseEngine(const Analysis& an, const DeviceMatrix& A, cudaStream_t st, const EngineOptions& eo)
+      : an_(an), A_(A), st_(st), eo_(eo) {
+    plan();
+  }
 
-  void factor(double) override {
+  int max_rank() const override { return max_rank_; }
+  double compressed_seconds() const override { return comp_seconds_; }
+
+  void factor(double tol) override {
     const int64_t c0 = launch_count();
     MF_CUDA(cudaMemsetAsync(arena_.p, 0, zero_bytes_, st_));
     MF_CUDA(cudaMemsetAsync(status_.p, 0, sizeof(int32_t), st_));
@@ -42,12 +49,36 @@ class DenseEngine : public EngineBase {
       }
     }
     size_t k = 0;
-    for (size_t i = 0; i < fops_.size(); ++i) {
-      bool timed = profiling && gemm_flops_[i] > 0;
-      if (timed) MF_CUDA(cudaEventRecord(evs_[2 * k], st_));
-      fops_[i](st_);
-      if (timed) { MF_CUDA(cudaEventRecord(evs_[2 * k + 1], st_)); ++k; }
+    BFParams P;
+    P.tol = tol > 0 ? tol : 1e-12;
+    P.max_rank = eo_.max_rank;
+    P.alpha = eo_.alpha;
+    P.knn = eo_.knn;
+    comp_flops_ = 0;
+    comp_seconds_ = 0;
+    if (comp_) {
+      comp_->fronts.clear();
+      comp_->cx.persist.release(0);
+      comp_->cx.scratch.release(0);
+      comp_->cx.flops = 0;
     }
+    for (size_t lv = 0; lv < levels_.size(); ++lv) {
+      for (size_t i = lvl_begin_[lv]; i < lvl_begin_[lv + 1]; ++i) {
+        bool timed = profiling && gemm_flops_[i] > 0;
+        if (timed) MF_CUDA(cudaEventRecord(evs_[2 * k], st_));
+        fops_[i](st_);
+        if (timed) { MF_CUDA(cudaEventRecord(evs_[2 * k + 1], st_)); ++k; }
+      }
+      for (int32_t fid : comp_levels_[lv]) {
+        auto t0 = std::chrono::steady_clock::now();
+        comp_->factor_front(fid, fr_, P, eo_.seed);
+        const auto& F = an_.fronts;
+        if (F[fid].parent >= 0 && !F[F[fid].parent].compressed) comp_->densify_C(fid, fr_[fid]);
+        max_rank_ = std::max(max_rank_, comp_->fronts.at(fid)->max_rank);
+        comp_seconds_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      }
+    }
+    if (comp_) comp_flops_ = comp_->cx.flops;
     MF_CUDA(cudaGetLastError());
     nlaunch_factor_ = (int)(launch_count() - c0);
     if (profiling) {
@@ -81,7 +112,7 @@ class DenseEngine : public EngineBase {
     MF_CUDA(cudaGetLastError());
   }
 
-  double factor_flops() const override { return flops_; }
+  double factor_flops() const override { return flops_ + comp_flops_; }
   double factor_bytes() const override { return factor_bytes_; }
   int launches_factor() const override { return nlaunch_factor_; }
   int launches_solve(int nrhs) override { return solve_prog(nrhs).nlaunch + 2; }
@@ -108,6 +139,12 @@ class DenseEngine : public EngineBase {
   int nlaunch_factor_ = 0;
   std::map<int, std::unique_ptr<SolveProg>> sprog_;
   std::vector<double> gemm_flops_;          // per factor op: algorithmic flops if it is a GEMM launch, else 0
+  EngineOptions eo_;
+  std::vector<std::vector<int32_t>> comp_levels_;   // compressed fronts per level
+  std::vector<size_t> lvl_begin_;           // factor ops of level lv: [lvl_begin_[lv], lvl_begin_[lv+1])
+  std::unique_ptr<CompressedPart<T>> comp_;
+  double comp_flops_ = 0, comp_seconds_ = 0;
+  int max_rank_ = 0;
   std::vector<cudaEvent_t> evs_;
 
  public:
@@ -192,18 +229,18 @@ class DenseEngine : public EngineBase {
     struct Offs { size_t LU, Linv, UinvT, F12w, F21w, C, UT, W, F12p, F12T, F21f, piv, perm, upd; };
     std::vector<Offs> o(nf);
     for (size_t i = 0; i < nf; ++i) {
-      int64_t s = F[i].s(), u = F[i].u();
+      int64_t s = F[i].compressed ? 0 : F[i].s(), u = F[i].u();
       const int64_t ls = (s + 3) & ~3ll, lu = (u + 3) & ~3ll;
       o[i].LU = take(2 * s * ls);
       o[i].Linv = take(2 * s * ls);
       o[i].UinvT = take(2 * s * ls);
-      o[i].F12w = take(2 * u * ls);
-      o[i].F21w = take(2 * u * ls);
+      o[i].F12w = take(2 * (s ? u : 0) * ls);
+      o[i].F21w = take(2 * (s ? u : 0) * ls);
       o[i].C = take(F[i].parent >= 0 ? 2 * u * lu : 0);
     }
     zero_bytes_ = off;
     for (size_t i = 0; i < nf; ++i) {
-      int64_t s = F[i].s(), u = F[i].u();
+      int64_t s = F[i].compressed ? 0 : F[i].s(), u = F[i].compressed ? 0 : F[i].u();
       const int64_t ls = (s + 3) & ~3ll;
       o[i].UT = take(2 * s * ls);
       o[i].W = take(4 * s * ls);   // two s x s planar work matrices (L and U inversions)
@@ -212,13 +249,14 @@ class DenseEngine : public EngineBase {
       o[i].F21f = take(2 * u * ls);
       o[i].piv = off; off = align_up(off + s * 4, 256);
       o[i].perm = off; off = align_up(off + s * 4, 256);
-      o[i].upd = off; off = align_up(off + u * 8, 256);
+      o[i].upd = off; off = align_up(off + F[i].u() * 8, 256);
       factor_bytes_ += sizeof(T) * 2.0 * (2.0 * s * s + 2.0 * s * u) + 8.0 * s;
     }
     arena_.alloc(off);
     char* base = arena_.template as<char>();
     for (size_t i = 0; i < nf; ++i) {
       int64_t s = F[i].s(), u = F[i].u();
+      const int64_t sa = F[i].compressed ? 0 : s;   // dense buffers of compressed fronts are empty
       FrontDev<T>& f = fr_[i];
       f.sep_begin = F[i].sep_begin;
       f.s = (int32_t)s;
@@ -237,14 +275,14 @@ class DenseEngine : public EngineBase {
       f.W = reinterpret_cast<T*>(base + o[i].W);
       f.piv = reinterpret_cast<int32_t*>(base + o[i].piv);
       f.perm = reinterpret_cast<int32_t*>(base + o[i].perm);
-      const int64_t ls = (s + 3) & ~3ll, lu = (u + 3) & ~3ll;
+      const int64_t ls = (sa + 3) & ~3ll, lu = (u + 3) & ~3ll;
       f.ls = (int32_t)ls;
       f.lu = (int32_t)lu;
-      f.pl_ss = s * ls;
-      f.pl_us = u * ls;
+      f.pl_ss = sa * ls;
+      f.pl_us = (sa ? u : 0) * ls;
       f.pl_uu = u * lu;
       if (u) MF_CUDA(cudaMemcpyAsync(base + o[i].upd, F[i].upd.data(), u * 8, cudaMemcpyHostToDevice, st_));
-      flops_ += 8.0 * ((double)s * s * s / 3.0 + (double)s * s * u + (double)s * u * u);
+      if (!F[i].compressed) flops_ += 8.0 * ((double)s * s * s / 3.0 + (double)s * s * u + (double)s * u * u);
     }
     upload(fronts_d_, fr_, st_);
     status_.alloc(sizeof(int32_t));
@@ -252,7 +290,13 @@ class DenseEngine : public EngineBase {
     int depth = 0;
     for (auto& f : F) depth = std::max(depth, f.level + 1);
     levels_.assign(depth, {});
-    for (auto& f : F) levels_[depth - 1 - f.level].push_back((int32_t)f.id);
+    comp_levels_.assign(depth, {});
+    bool any_comp = false;
+    for (auto& f : F) {
+      if (f.compressed) { comp_levels_[depth - 1 - f.level].push_back((int32_t)f.id); any_comp = true; }
+      else levels_[depth - 1 - f.level].push_back((int32_t)f.id);
+    }
+    if (any_comp) comp_ = std::make_unique<CompressedPart<T>>(an_, A_, st_, eo_.persist_bytes, eo_.scratch_bytes);
     std::vector<int32_t> all;
     for (auto& lv : levels_) {
       level_off_.push_back(all.size());
@@ -309,6 +353,7 @@ class DenseEngine : public EngineBase {
     std::vector<GemmTile> Tl;
     struct PendingGemm { GemmRef r; };
     for (int lv = 0; lv < depth; ++lv) {
+      lvl_begin_.push_back(fops_.size());
       const auto& L = levels_[lv];
       const int nfl = (int)L.size();
       int max_s = 0, max_u = 0, max_rows = 0;
@@ -437,6 +482,7 @@ class DenseEngine : public EngineBase {
         push_gemm_nt(D, Tl, b);
       }
     }
+    lvl_begin_.push_back(fops_.size());
     upload(descs_d_, D, st_);
     upload(tiles_d_, Tl, st_);
     MF_CUDA(cudaStreamSynchronize(st_));
@@ -487,8 +533,19 @@ class DenseEngine : public EngineBase {
         sp->nlaunch++;
       }
     };
+    auto comp_op = [&](size_t lv, bool fwd) {
+      for (int32_t fid : comp_levels_[lv]) {
+        sp->ops.push_back([this, fid, fwd, X, n, nrhs](cudaStream_t) {
+          Blk<T> Xb;
+          Xb.p = X; Xb.rows = (int)n; Xb.cols = nrhs; Xb.ld = nrhs; Xb.plane = n * nrhs;
+          if (fwd) comp_->forward(fid, Xb);
+          else comp_->backward(fid, Xb);
+        });
+      }
+    };
     // forward: leaves -> root
     for (size_t lv = 0; lv < levels_.size(); ++lv) {
+      comp_op(lv, true);
       const auto& L = levels_[lv];
       int nfl = (int)L.size(), max_s = 0, max_u = 0;
       for (int32_t f : L) { max_s = std::max<int>(max_s, fr_[f].s); max_u = std::max<int>(max_u, fr_[f].u); }
@@ -523,6 +580,7 @@ class DenseEngine : public EngineBase {
     }
     // backward: root -> leaves
     for (size_t lvr = levels_.size(); lvr-- > 0;) {
+      comp_op(lvr, false);
       const auto& L = levels_[lvr];
       int nfl = (int)L.size(), max_s = 0, max_u = 0;
       for (int32_t f : L) { max_s = std::max<int>(max_s, fr_[f].s); max_u = std::max<int>(max_u, fr_[f].u); }
@@ -579,11 +637,13 @@ void DenseEngine<double>::launch_nt(const GemmRef& g, cudaStream_t st) {
 
 }  // namespace
 
-std::unique_ptr<EngineBase> make_engine_c64(const Analysis& an, const DeviceMatrix& A, cudaStream_t st) {
-  return std::make_unique<DenseEngine<float>>(an, A, st);
+std::unique_ptr<EngineBase> make_engine_c64(const Analysis& an, const DeviceMatrix& A, cudaStream_t st,
+                                            const EngineOptions& eo) {
+  return std::make_unique<DenseEngine<float>>(an, A, st, eo);
 }
-std::unique_ptr<EngineBase> make_engine_c128(const Analysis& an, const DeviceMatrix& A, cudaStream_t st) {
-  return std::make_unique<DenseEngine<double>>(an, A, st);
+std::unique_ptr<EngineBase> make_engine_c128(const Analysis& an, const DeviceMatrix& A, cudaStream_t st,
+                                             const EngineOptions& eo) {
+  return std::make_unique<DenseEngine<double>>(an, A, st, eo);
 }
 
 }  // namespace mf

@@ -1,0 +1,68 @@
+"""GPU compressed multifrontal factorization (Alg. 5: HOD-BF F11 and its Alg. 4 inverse,
+butterfly F12/F21, randomized S, HOD-BF contribution blocks) against the oracle."""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle.analysis import analyze
+from oracle import dense_mf as dm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2007_00202_gb300 import build
+    build.build()
+    import paper_2007_00202_gb300 as pkg
+    return pkg
+
+
+def _exact(p, b, leaf):
+    an = analyze(p, leaf, 10 ** 9)
+    return dm.solve(p, an, dm.multifrontal_factor(p, an)[0], b)
+
+
+def test_16cube_fp64_tol1e6_direct(g):
+    # 16^3 Helmholtz, separators >= 128 compressed at tol 1e-6, complex128, no refinement:
+    # a direct solver to 1e-4 (error and residual), as the oracle is
+    p = w.helmholtz7(16, 8)
+    b = w.rhs_point_plus_gaussian(p, 42)
+    h = g.analyze_problem(p, nmin_sep=128, precision=g.MF_PREC_C128, refine=g.MF_REFINE_NONE)
+    h.mf_factor(1e-6)
+    st = h.mf_stats()
+    assert st["ncompressed"] == 2 and st["max_rank"] > 0
+    x, info = h.mf_solve(b)
+    xe = _exact(p, b, 64)
+    A = p.to_scipy()
+    assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-4
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) <= 1e-4
+
+
+def test_mixed_compressed_gmres_to_1e8(g):
+    p = w.helmholtz7(16, 8)
+    b = w.rhs_gaussian(p, 4, 7)
+    h = g.analyze_problem(p, nmin_sep=64, leaf_size=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES)
+    h.mf_factor(1e-4)
+    assert h.mf_stats()["ncompressed"] >= 3
+    x, info = h.mf_solve(b)
+    A = p.to_scipy()
+    assert info.converged == 1
+    assert np.max(np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)) <= 1e-8
+    xe = _exact(p, b, 64)
+    assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-6
+
+
+def test_compressed_yee(g):
+    p = w.yee_maxwell(10, 10)
+    b = w.rhs_dipoles(p, 3, 11)
+    h = g.analyze_problem(p, leaf_size=32, nmin_sep=100, hodbf_leaf=32,
+                          precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES)
+    h.mf_factor(1e-4)
+    assert h.mf_stats()["ncompressed"] >= 1
+    x, info = h.mf_solve(b)
+    A = p.to_scipy()
+    assert np.max(np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)) <= 1e-8
