@@ -210,6 +210,40 @@ int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol
 int mf_row_id_c64_noalloc(int32_t nmat, int32_t m, int32_t n, const float* M, double tol, int32_t max_rank,
                           float* U, int32_t* sk, int32_t* rank, void* stream);
 
+/* ---------------- serving: continuous batching over resident factorizations ---------------- */
+
+/*
+ * A solve server over nproblems resident factorizations (handles already
+ * factored; each should have its own CUDA stream).  One worker thread per
+ * handle batches every request waiting for that handle when its previous batch
+ * ends (requests that arrive during a solve join the next batch), admits
+ * requests while the batch's device workspace, estimated as 40 * N * nrhs * 16
+ * bytes, fits mem_budget_bytes together with the other batches in flight, and
+ * runs the batch as one mf_solve.  The handles stay owned by the caller and must
+ * not be used elsewhere while the server lives.
+ */
+typedef struct mf_server mf_server;
+typedef struct {
+  int64_t id;
+  int32_t problem, nrhs;
+  int32_t iters, converged;
+  int32_t batch_rhs;          /* right-hand sides of the batch the request ran in */
+  int32_t reserved;
+  double max_rel_residual;    /* of the batch */
+  double t_arrival, t_start, t_done;   /* seconds since the server was created */
+} mf_request_info;
+
+int mf_server_create(int32_t nproblems, mf_handle* const* handles, int32_t max_batch_rhs, int64_t mem_budget_bytes,
+                     mf_server** out);
+/* Queue nrhs right-hand sides b (host, N x nrhs column-major, interleaved) for problem `problem`;
+ * x (host, same shape) is written when the request completes; *id identifies it.  b and x must
+ * stay valid until mf_server_wait returns.  MF_ERR_OOM if the request alone exceeds the budget. */
+int mf_server_submit(mf_server* s, int32_t problem, int32_t nrhs, const double* b, double* x, int64_t* id);
+/* Block until request id is done; returns the request's mf_solve status and fills *info. */
+int mf_server_wait(mf_server* s, int64_t id, mf_request_info* info);
+/* Finish queued requests and stop the workers. */
+void mf_server_destroy(mf_server* s);
+
 /* ---------------- butterfly component: Green's-function block sets ---------------- */
 
 /*

@@ -1,0 +1,207 @@
+// Continuous-batching solve server over resident factorizations.
+//
+// Several factorizations stay resident on the device (one mf_handle each, each
+// on its own CUDA stream).  Requests carry right-hand sides for one of them.
+// One worker thread per factorization takes every request that is waiting for
+// it when the previous batch finishes (continuous batching: requests that
+// arrive while a batch is on the GPU join the next batch), admits them while
+// the device workspace of the batch fits the memory budget, solves the batch
+// with one mf_solve call (columns converge independently inside GMRES), and
+// completes each request.  Batches of different factorizations overlap on the
+// device because the workers run concurrently on different streams.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/mf.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  int64_t id;
+  int32_t problem, nrhs;
+  const double* b;
+  double* x;
+  double t_arrival = 0, t_start = 0, t_done = 0;
+  int32_t iters = 0, converged = 0, batch_rhs = 0, status = 1;   // status 1 = pending
+  double max_rel_residual = 0;
+};
+
+struct Worker {
+  mf_handle* h = nullptr;
+  int64_t n = 0;
+  std::deque<std::shared_ptr<Request>> q;
+  std::thread th;
+  std::vector<double> bbuf, xbuf;
+};
+
+}  // namespace
+
+struct mf_server {
+  std::vector<std::unique_ptr<Worker>> w;
+  int32_t max_batch = 256;
+  int64_t budget = 0;
+  std::atomic<int64_t> reserved{0};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  int64_t next_id = 0;
+  std::map<int64_t, std::shared_ptr<Request>> reqs;
+  Clock::time_point t0 = Clock::now();
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+  int64_t bytes_for(int64_t n, int32_t nrhs) const { return (int64_t)(30 + 10) * n * nrhs * 16; }
+  void run(int p);
+};
+
+void mf_server::run(int p) {
+  Worker& wk = *w[p];
+  for (;;) {
+    std::vector<std::shared_ptr<Request>> batch;
+    int64_t bytes = 0;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_work.wait(lk, [&] { return stop || !wk.q.empty(); });
+      if (stop && wk.q.empty()) return;
+      int tot = 0;
+      while (!wk.q.empty()) {
+        auto& r = wk.q.front();
+        int64_t need = bytes_for(wk.n, tot + r->nrhs) - bytes;
+        bool first = batch.empty();
+        if (!first && (tot + r->nrhs > max_batch || reserved.load() + need > budget)) break;
+        if (first && reserved.load() + need > budget && reserved.load() > 0) break;   // wait for memory
+        bytes += need;
+        reserved += need;
+        tot += r->nrhs;
+        batch.push_back(r);
+        wk.q.pop_front();
+      }
+      if (batch.empty()) {
+        cv_done.wait_for(lk, std::chrono::milliseconds(1));
+        continue;
+      }
+    }
+    const double ts = now();
+    int tot = 0;
+    for (auto& r : batch) tot += r->nrhs;
+    wk.bbuf.resize((size_t)2 * wk.n * tot);
+    wk.xbuf.resize((size_t)2 * wk.n * tot);
+    size_t off = 0;
+    for (auto& r : batch) {
+      std::memcpy(wk.bbuf.data() + off, r->b, sizeof(double) * 2 * wk.n * r->nrhs);
+      off += (size_t)2 * wk.n * r->nrhs;
+    }
+    mf_solve_info info{};
+    int rc = mf_solve(wk.h, tot, wk.bbuf.data(), wk.n, wk.xbuf.data(), wk.n, &info);
+    const double td = now();
+    off = 0;
+    for (auto& r : batch) {
+      if (rc == MF_OK || rc == MF_ERR_NO_CONVERGENCE)
+        std::memcpy(r->x, wk.xbuf.data() + off, sizeof(double) * 2 * wk.n * r->nrhs);
+      off += (size_t)2 * wk.n * r->nrhs;
+    }
+    reserved -= bytes;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (auto& r : batch) {
+        r->t_start = ts;
+        r->t_done = td;
+        r->iters = info.iters;
+        r->converged = info.converged;
+        r->max_rel_residual = info.max_rel_residual;
+        r->batch_rhs = tot;
+        r->status = rc;
+      }
+    }
+    cv_done.notify_all();
+    cv_work.notify_all();
+  }
+}
+
+extern "C" {
+
+int mf_server_create(int32_t nproblems, mf_handle* const* handles, int32_t max_batch_rhs, int64_t mem_budget_bytes,
+                     mf_server** out) {
+  if (!out || nproblems <= 0 || !handles || max_batch_rhs <= 0 || mem_budget_bytes <= 0) return MF_ERR_ARG;
+  auto s = std::make_unique<mf_server>();
+  s->max_batch = max_batch_rhs;
+  s->budget = mem_budget_bytes;
+  for (int p = 0; p < nproblems; ++p) {
+    mf_stats_t st;
+    if (!handles[p] || mf_stats(handles[p], &st) != MF_OK) return MF_ERR_ARG;
+    auto wk = std::make_unique<Worker>();
+    wk->h = handles[p];
+    wk->n = st.n;
+    s->w.push_back(std::move(wk));
+  }
+  mf_server* sp = s.get();
+  for (int p = 0; p < nproblems; ++p) sp->w[p]->th = std::thread([sp, p] { sp->run(p); });
+  *out = s.release();
+  return MF_OK;
+}
+
+int mf_server_submit(mf_server* s, int32_t problem, int32_t nrhs, const double* b, double* x, int64_t* id) {
+  if (!s || problem < 0 || problem >= (int32_t)s->w.size() || nrhs <= 0 || !b || !x || !id) return MF_ERR_ARG;
+  if (s->bytes_for(s->w[problem]->n, nrhs) > s->budget) return MF_ERR_OOM;
+  auto r = std::make_shared<Request>();
+  r->problem = problem;
+  r->nrhs = nrhs;
+  r->b = b;
+  r->x = x;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    r->t_arrival = s->now();
+    s->reqs[r->id] = r;
+    s->w[problem]->q.push_back(r);
+    *id = r->id;
+  }
+  s->cv_work.notify_all();
+  return MF_OK;
+}
+
+int mf_server_wait(mf_server* s, int64_t id, mf_request_info* info) {
+  if (!s) return MF_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return MF_ERR_ARG;
+  auto r = it->second;
+  s->cv_done.wait(lk, [&] { return r->status != 1; });
+  if (info) {
+    info->id = r->id;
+    info->problem = r->problem;
+    info->nrhs = r->nrhs;
+    info->iters = r->iters;
+    info->converged = r->converged;
+    info->batch_rhs = r->batch_rhs;
+    info->max_rel_residual = r->max_rel_residual;
+    info->t_arrival = r->t_arrival;
+    info->t_start = r->t_start;
+    info->t_done = r->t_done;
+  }
+  s->reqs.erase(it);
+  return r->status;
+}
+
+void mf_server_destroy(mf_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& w : s->w)
+    if (w->th.joinable()) w->th.join();
+  delete s;
+}
+
+}  // extern "C"

@@ -53,6 +53,13 @@ class mf_kernel_profile_t(C.Structure):
     _fields_ = [("launches", C.c_int64), ("ms", C.c_double), ("flops", C.c_double)]
 
 
+class mf_request_info(C.Structure):
+    _fields_ = [("id", C.c_int64), ("problem", C.c_int32), ("nrhs", C.c_int32), ("iters", C.c_int32),
+                ("converged", C.c_int32), ("batch_rhs", C.c_int32), ("reserved", C.c_int32),
+                ("max_rel_residual", C.c_double), ("t_arrival", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double)]
+
+
 class mf_analysis_sizes_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("nfronts", C.c_int64), ("upd_total", C.c_int64), ("tree_total", C.c_int64),
                 ("nn_total", C.c_int64)]
@@ -75,6 +82,10 @@ SIGNATURES = {
     "mf_destroy": (None, [_P]),
     "mf_launch_counter": (C.c_int64, []),
     "mf_profile": (C.c_int, [_P, C.c_int32]),
+    "mf_server_create": (C.c_int, [C.c_int32, C.POINTER(_P), C.c_int32, C.c_int64, C.POINTER(_P)]),
+    "mf_server_submit": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _I64P]),
+    "mf_server_wait": (C.c_int, [_P, C.c_int64, C.POINTER(mf_request_info)]),
+    "mf_server_destroy": (None, [_P]),
     "mf_green_build": (C.c_int, [C.c_int32, _I32P, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32,
                                  C.c_int32, C.c_int32, _P, C.POINTER(_P)]),
     "mf_green_info": (C.c_int, [_P, _I64P, _DP, _I32P, _DP]),
@@ -300,3 +311,40 @@ class GreenSet:
         if getattr(self, "ptr", None):
             lib().mf_green_destroy(self.ptr)
             self.ptr = None
+
+
+class Server:
+    """Continuous-batching solve server over resident factorizations (mf_server_*)."""
+
+    def __init__(self, handles, max_batch_rhs=256, mem_budget_bytes=64 << 30):
+        self.handles = list(handles)
+        arr = (C.c_void_p * len(self.handles))(*[h.ptr for h in self.handles])
+        self.ptr = C.c_void_p()
+        _check(lib().mf_server_create(len(self.handles), arr, max_batch_rhs, mem_budget_bytes, C.byref(self.ptr)))
+        self._bufs = {}
+
+    def submit(self, problem, b):
+        """b: (N, nrhs) complex128 host array; returns a request id."""
+        B = np.asfortranarray(np.asarray(b, dtype=np.complex128).reshape(b.shape[0], -1))
+        X = np.empty_like(B, order="F")
+        rid = C.c_int64()
+        _check(lib().mf_server_submit(self.ptr, problem, B.shape[1], C.c_void_p(B.ctypes.data),
+                                      C.c_void_p(X.ctypes.data), C.byref(rid)))
+        self._bufs[rid.value] = (B, X)
+        return rid.value
+
+    def wait(self, rid):
+        info = mf_request_info()
+        rc = lib().mf_server_wait(self.ptr, rid, C.byref(info))
+        B, X = self._bufs.pop(rid)
+        if rc not in (0, -6):
+            _check(rc)
+        return X, {k: getattr(info, k) for k, _ in info._fields_}
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().mf_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        self.close()

@@ -1,0 +1,75 @@
+"""Serving: continuous batching over resident factorizations.  Each result must be
+the same alone and in the mix (both at the 1e-8 residual, and close to each other)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2007_00202_gb300 import build
+    build.build()
+    import paper_2007_00202_gb300 as g
+    probs = [w.helmholtz7(12, 8), w.helmholtz7(16, 8)]
+    streams = [torch.cuda.Stream() for _ in probs]
+    hs = []
+    for p, s in zip(probs, streams):
+        h = g.analyze_problem(p, nmin_sep=128, leaf_size=64, stream=s.cuda_stream)
+        h.mf_factor(1e-4)
+        hs.append(h)
+    return g, probs, hs, streams
+
+
+def test_results_same_alone_and_in_the_mix(env):
+    g, probs, hs, streams = env
+    import paper_2007_00202_gb300.mf as mf
+    rng = np.random.default_rng(5)
+    reqs = []
+    for r in range(24):
+        pi = int(rng.integers(len(probs)))
+        nrhs = int(rng.integers(1, 6))
+        reqs.append((pi, w.complex_gaussian(rng, probs[pi].n, nrhs)))
+    alone = [hs[pi].mf_solve(b)[0] for pi, b in reqs]
+    srv = mf.Server(hs, max_batch_rhs=32, mem_budget_bytes=8 << 30)
+    ids = [None] * len(reqs)
+
+    def client(lo, hi):
+        for k in range(lo, hi):
+            ids[k] = srv.submit(reqs[k][0], reqs[k][1])
+            time.sleep(0.001)
+
+    th = [threading.Thread(target=client, args=(a, a + 8)) for a in (0, 8, 16)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    out = [srv.wait(i) for i in ids]
+    srv.close()
+    batched = 0
+    for (pi, b), xa, (xm, info) in zip(reqs, alone, out):
+        A = probs[pi].to_scipy()
+        for x in (xa, xm):
+            assert np.max(np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)) <= 1e-8
+        assert np.linalg.norm(xm - xa) / np.linalg.norm(xa) <= 1e-6
+        assert info["t_done"] >= info["t_start"] >= info["t_arrival"]
+        batched += info["batch_rhs"] > info["nrhs"]
+    assert batched > 0          # some requests shared a batch with others
+
+
+def test_admission_rejects_oversized_request(env):
+    g, probs, hs, streams = env
+    import paper_2007_00202_gb300.mf as mf
+    srv = mf.Server(hs[:1], max_batch_rhs=8, mem_budget_bytes=1 << 20)
+    with pytest.raises(mf.MfError) as e:
+        srv.submit(0, np.ones((probs[0].n, 4), complex))
+    assert e.value.code == -4
+    srv.close()
