@@ -173,6 +173,36 @@ BFContext<T>::BFContext(cudaStream_t s, size_t pb, size_t sb) : st(s) {
 }
 
 template <typename T>
+BFContext<T>::~BFContext() {
+  if (ring) cudaFreeHost(ring);
+}
+
+template <typename T>
+void BFContext<T>::h2d(void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return;
+  if (!ring) {
+    ring_cap = size_t(128) << 20;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&ring), ring_cap, cudaHostAllocDefault) != cudaSuccess) {
+      ring = nullptr;
+      ring_cap = 0;
+    }
+  }
+  if (!ring || bytes > ring_cap / 4) {
+    MF_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    return;
+  }
+  size_t o = (ring_off + 255) & ~size_t(255);
+  if (o + bytes > ring_cap) {          // wrap: every earlier copy out of the ring has completed after this
+    MF_CUDA(cudaStreamSynchronize(st));
+    o = 0;
+  }
+  std::memcpy(ring + o, src, bytes);
+  MF_CUDA(cudaMemcpyAsync(dst, ring + o, bytes, cudaMemcpyHostToDevice, st));
+  ring_off = o + bytes;
+}
+
+template <typename T>
 void BFContext<T>::check_status() {
   int32_t v = 0;
   MF_CUDA(cudaMemcpyAsync(&v, status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -195,8 +225,8 @@ void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
   if (tl.empty()) return;
   auto* dd = scratch.takeT<GemmDesc<T>>(D.size());
   auto* dt = scratch.takeT<GemmTile>(tl.size());
-  MF_CUDA(cudaMemcpyAsync(dd, D.data(), D.size() * sizeof(GemmDesc<T>), cudaMemcpyHostToDevice, st));
-  MF_CUDA(cudaMemcpyAsync(dt, tl.data(), tl.size() * sizeof(GemmTile), cudaMemcpyHostToDevice, st));
+  h2d(dd, D.data(), D.size() * sizeof(GemmDesc<T>));
+  h2d(dt, tl.data(), tl.size() * sizeof(GemmTile));
   launch_gemm<T>(dd, dt, (int)tl.size(), st);
 }
 
@@ -213,14 +243,14 @@ static void run_blk2(BFContext<T>& cx, std::vector<Blk2Job<T>>& jobs) {
   int64_t mx = 0;
   for (auto& j : jobs) mx = std::max<int64_t>(mx, (int64_t)j.rows * j.cols);
   auto* dj = cx.scratch.template takeT<Blk2Job<T>>(jobs.size());
-  MF_CUDA(cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(Blk2Job<T>), cudaMemcpyHostToDevice, cx.st));
+  cx.h2d(dj, jobs.data(), jobs.size() * sizeof(Blk2Job<T>));
   launch_blk2<T>(dj, (int)jobs.size(), mx, cx.st);
 }
 
 template <typename T>
 static const int32_t* dev_idx(BFContext<T>& cx, const IdxVec& v) {
   auto* d = cx.scratch.template takeT<int32_t>(std::max<size_t>(v.size(), 1));
-  if (!v.empty()) MF_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * 4, cudaMemcpyHostToDevice, cx.st));
+  if (!v.empty()) cx.h2d(d, v.data(), v.size() * 4);
   return d;
 }
 
@@ -281,7 +311,7 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
   MF_CUDA(cudaMemsetAsync(drk, 0, nj * 4, st));
   if (!jobs.empty()) {
     auto* dj = scratch.takeT<IdJob<T>>(jobs.size());
-    MF_CUDA(cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(IdJob<T>), cudaMemcpyHostToDevice, st));
+    h2d(dj, jobs.data(), jobs.size() * sizeof(IdJob<T>));
     if (launch_row_id<T>(dj, (int)jobs.size(), max_m, max_n, (T)tol, max_rank, st) != 0)
       throw std::runtime_error("ID block too large for the row-ID kernel (" + std::to_string(max_m) + " x " +
                                std::to_string(max_n) + ")");
@@ -308,11 +338,11 @@ void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vecto
                          bool transpose, bool accumulate) {
   const size_t nb = bfs.size();
   if (!nb) return;
-  const int k = X[0].cols;
   std::map<int, std::vector<GemmDesc<T>>> stages;   // stage index -> descs
   const T one = T(1), zero = T(0), beta_out = accumulate ? T(1) : T(0);
   for (size_t q = 0; q < nb; ++q) {
     const DBF<T>& bf = *bfs[q];
+    const int k = X[q].cols;   // block widths may differ between butterflies
     const int L = bf.L, lc = bf.lc;
     auto vec_buf = [&](const std::vector<int>& ranks, std::vector<Blk<T>>& out) {
       size_t tot = 0;
@@ -701,7 +731,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::random_matvec(const DOp<T>& op, const Tree
       int mx = 0;
       for (auto& s : sg) mx = std::max<int>(mx, (int)((s.b - s.a) * s.w));
       auto* dg = scratch.takeT<SketchGroup>(sg.size());
-      MF_CUDA(cudaMemcpyAsync(dg, sg.data(), sg.size() * sizeof(SketchGroup), cudaMemcpyHostToDevice, st));
+      h2d(dg, sg.data(), sg.size() * sizeof(SketchGroup));
       launch_sketch<T>(dg, (int)sg.size(), mx, Om.p, Om.plane, (int)Om.ld, st);
     }
     return Om;
@@ -722,7 +752,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::random_matvec(const DOp<T>& op, const Tree
     int64_t mx = 0;
     for (auto& g : gj) mx = std::max<int64_t>(mx, (int64_t)g.nrows * g.ncols);
     auto* d = scratch.takeT<GatherJob<T>>(gj.size());
-    MF_CUDA(cudaMemcpyAsync(d, gj.data(), gj.size() * sizeof(GatherJob<T>), cudaMemcpyHostToDevice, st));
+    h2d(d, gj.data(), gj.size() * sizeof(GatherJob<T>));
     launch_gather_rows<T>(d, (int)gj.size(), mx, st);
   };
   for (int l = L; l >= lc; --l) {                         // left half: sketches of K(X, S_nu)
@@ -827,7 +857,6 @@ std::unique_ptr<DBF<T>> BFContext<T>::random_matvec(const DOp<T>& op, const Tree
     std::vector<LstsqJob<T>> lj;
     std::vector<GatherJob<T>> gj;
     std::vector<Blk<T>> Yr(xs.size());
-    int maxc = 1;
     for (int i = 0; i < (1 << lc); ++i)
       for (int j = 0; j < (1 << (L - lc)); ++j) {
         const int p = bf->pidx(lc, i, j);
@@ -844,17 +873,12 @@ std::unique_ptr<DBF<T>> BFContext<T>::random_matvec(const DOp<T>& op, const Tree
         L1.Y = Yr[p].p; L1.yplane = Yr[p].plane; L1.yld = Yr[p].ld;
         L1.B = Bm.p; L1.bplane = Bm.plane; L1.bld = Bm.ld;
         L1.c = c; L1.r = r; L1.w = ccols[j].second - ccols[j].first;
+        L1.W = nullptr;
         lj.push_back(L1);
-        maxc = std::max(maxc, c);
         flops += 8.0 * ((double)c * c * L1.w + (double)r * c * L1.w);
       }
     run_gathers(gj);
-    if (!lj.empty()) {
-      auto* d = scratch.takeT<LstsqJob<T>>(lj.size());
-      MF_CUDA(cudaMemcpyAsync(d, lj.data(), lj.size() * sizeof(LstsqJob<T>), cudaMemcpyHostToDevice, st));
-      if (launch_lstsq<T>(d, (int)lj.size(), maxc, status.as<int32_t>(), st) != 0)
-        throw std::runtime_error("centre block too large for the least-squares kernel");
-    }
+    run_lstsq(lj);
   }
   MF_CUDA(cudaStreamSynchronize(st));
   scratch.release(mk);
@@ -1048,7 +1072,7 @@ static void extract_run(BFContext<T>& cx, ExtractPlan<T>& EP) {
     int64_t mx = 0;
     for (auto& p : EP.pj) mx = std::max<int64_t>(mx, (int64_t)p.nr * p.nc);
     auto* d = cx.scratch.template takeT<PlaceJob<T>>(EP.pj.size());
-    MF_CUDA(cudaMemcpyAsync(d, EP.pj.data(), EP.pj.size() * sizeof(PlaceJob<T>), cudaMemcpyHostToDevice, cx.st));
+    cx.h2d(d, EP.pj.data(), EP.pj.size() * sizeof(PlaceJob<T>));
     launch_place<T>(d, (int)EP.pj.size(), mx, cx.st);
   }
 }
@@ -1336,7 +1360,7 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
     int64_t mx = 0;
     for (auto& p : pj) mx = std::max<int64_t>(mx, (int64_t)p.nr * p.nc);
     auto* d = scratch.takeT<PlaceJob<T>>(pj.size());
-    MF_CUDA(cudaMemcpyAsync(d, pj.data(), pj.size() * sizeof(PlaceJob<T>), cudaMemcpyHostToDevice, st));
+    h2d(d, pj.data(), pj.size() * sizeof(PlaceJob<T>));
     launch_place<T>(d, (int)pj.size(), mx, st);
   }
 }
@@ -1412,14 +1436,18 @@ static void small_inverse(BFContext<T>& cx, const std::vector<Blk<T>>& A, std::v
     InvJob<T> j;
     j.A = A[q].p; j.aplane = A[q].plane; j.lda = A[q].ld; j.n = A[q].rows;
     j.X = X[q].p; j.xplane = X[q].plane; j.ldx = X[q].ld;
+    j.W = nullptr;
     jobs.push_back(j);
     mx = std::max(mx, A[q].rows);
     cx.flops += 8.0 * A[q].rows * (double)A[q].rows * A[q].rows;
   }
   if (jobs.empty()) return;
+  const bool in_smem = small_inverse_smem_bytes(mx, sizeof(double)) <= kSmallInvSmemCap;
+  if (!in_smem)
+    for (auto& j : jobs) j.W = cx.scratch.template takeT<double>(4 * (size_t)j.n * j.n);
   auto* d = cx.scratch.template takeT<InvJob<T>>(jobs.size());
-  MF_CUDA(cudaMemcpyAsync(d, jobs.data(), jobs.size() * sizeof(InvJob<T>), cudaMemcpyHostToDevice, cx.st));
-  if (launch_small_inverse<T>(d, (int)jobs.size(), mx, cx.status.template as<int32_t>(), cx.st) != 0)
+  cx.h2d(d, jobs.data(), jobs.size() * sizeof(InvJob<T>));
+  if (launch_small_inverse<T>(d, (int)jobs.size(), mx, in_smem, cx.status.template as<int32_t>(), cx.st) != 0)
     throw std::runtime_error("block too large for the small dense inverse (" + std::to_string(mx) + ")");
 }
 
@@ -1447,7 +1475,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::bf_smw(const DBF<T>& K, const BFParams& P,
     {
       std::vector<T> eye(2 * (size_t)G.plane, T(0));
       for (int a = 0; a < c; ++a) eye[(size_t)a * G.ld + a] = T(1);
-      MF_CUDA(cudaMemcpyAsync(G.p, eye.data(), eye.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+      h2d(G.p, eye.data(), eye.size() * sizeof(T));
       MF_CUDA(cudaStreamSynchronize(st));
     }
     g = {gdesc<T>(c, c, r, 0, 0, T(1), T(1), VU, B, G)};
@@ -1472,7 +1500,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::bf_smw(const DBF<T>& K, const BFParams& P,
     {
       std::vector<T> eye(2 * (size_t)G.plane, T(0));
       for (int a = 0; a < rs; ++a) eye[(size_t)a * G.ld + a] = T(1);
-      MF_CUDA(cudaMemcpyAsync(G.p, eye.data(), eye.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+      h2d(G.p, eye.data(), eye.size() * sizeof(T));
       MF_CUDA(cudaStreamSynchronize(st));
     }
     for (int j = 0; j < 2; ++j) {
@@ -1666,48 +1694,499 @@ std::unique_ptr<DHODBFInv<T>> BFContext<T>::hodbf_invert(const DHODBF<T>& H, con
   small_inverse(*this, H.D, inv->Dinv);
   inv->M.clear();
   inv->M.resize(LH + 1);
+  DHODBFInv<T>* ip = inv.get();
   for (int l = LH - 1; l >= 0; --l) {
-    inv->M[l].resize((size_t)1 << l);
-    for (int i = 0; i < (1 << l); ++i) {
-      const int t1 = 2 * i, t2 = 2 * i + 1;
-      const Range r1 = H.tree[l + 1][t1], r2 = H.tree[l + 1][t2];
-      const int n1 = (int)(r1.b - r1.a), n2 = (int)(r2.b - r2.a);
-      const int Lq = LH - l - 1;
-      std::unique_ptr<DBF<T>> Bs[2];
+    const int nn = 1 << l, Lq = LH - l - 1;
+    inv->M[l].resize((size_t)nn);
+    // B_tau_i <- D_tau_i^-1 B_tau_i for both children of every node of level l, in lockstep
+    std::vector<RMProblem<T>> probs(2 * (size_t)nn);
+    std::vector<int> tt(2 * (size_t)nn);
+    std::vector<const DBF<T>*> Boff(2 * (size_t)nn);
+    for (int i = 0; i < nn; ++i)
       for (int side = 0; side < 2; ++side) {
-        const int tt = side == 0 ? t1 : t2, ts = side == 0 ? t2 : t1;
-        const int na = side == 0 ? n1 : n2, nb = side == 0 ? n2 : n1;
-        const DBF<T>* Boff = H.off[l + 1][tt].get();
-        DHODBFInv<T>* ip = inv.get();
-        DOp<T> op;
-        op.rows = na;
-        op.cols = nb;
-        op.apply = [this, Boff, ip, l, tt, na](const Blk<T>& X, Blk<T>& Y, bool tr_) {
-          const int k = X.cols;
-          Blk<T> t = new_blk<T>(scratch, na, k);
-          if (!tr_) {
-            std::vector<const DBF<T>*> b{Boff};
-            std::vector<Blk<T>> xs{X}, ys{t};
-            apply(b, xs, ys, false, false);
-            inv_apply(*ip, t, Y, false, l + 1, tt);
-          } else {
-            inv_apply(*ip, X, t, true, l + 1, tt);
-            std::vector<const DBF<T>*> b{Boff};
-            std::vector<Blk<T>> xs{t}, ys{Y};
-            apply(b, xs, ys, true, false);
-          }
-        };
-        Tree rt = subtree(H.tree, l + 1, tt, Lq), ct = subtree(H.tree, l + 1, ts, Lq);
-        Bs[side] = random_matvec(op, rt, ct, Lq, P, (key * 131u + (uint32_t)l * 17u + (uint32_t)tt) & 0xFFFFFu);
+        const size_t q = 2 * (size_t)i + side;
+        const int t = 2 * i + side, ts = 2 * i + 1 - side;
+        tt[q] = t;
+        Boff[q] = H.off[l + 1][t].get();
+        const Range ra = H.tree[l + 1][t], rb = H.tree[l + 1][ts];
+        probs[q].m = (int)(ra.b - ra.a);
+        probs[q].n = (int)(rb.b - rb.a);
+        probs[q].rt = subtree(H.tree, l + 1, t, Lq);
+        probs[q].ct = subtree(H.tree, l + 1, ts, Lq);
+        probs[q].key = (key * 131u + (uint32_t)l * 17u + (uint32_t)t) & 0xFFFFFu;
       }
-      const int L = Lq + 2;
-      Tree tr = extend_tree(subtree(H.tree, l, i, LH - l), L);
-      inv->M[l][i] = smw_assemble(n1 + n2, tr, L, nullptr, *Bs[0], *Bs[1], nullptr, P,
-                                  (key * 977u + (uint32_t)l * 31u + (uint32_t)i) & 0xFFFFFu);
+    DOpB<T> op = [&, ip, l](const std::vector<Blk<T>>& X, std::vector<Blk<T>>& Y, bool tr) {
+      std::vector<Blk<T>> tmp(X.size());
+      for (size_t q = 0; q < X.size(); ++q) tmp[q] = new_blk<T>(scratch, probs[q].m, X[q].cols);
+      if (!tr) {
+        apply(Boff, X, tmp, false, false);
+        inv_apply_b(*ip, l + 1, tt, tmp, Y, false);
+      } else {
+        inv_apply_b(*ip, l + 1, tt, X, tmp, true);
+        apply(Boff, tmp, Y, true, false);
+      }
+    };
+    random_matvec_batch(op, probs, Lq, P);
+    // BF_SMW([I B1; B2 I]) as an (Lq + 2)-level butterfly per node, all nodes of the level in lockstep
+    std::vector<SmwItem<T>> items(nn);
+    for (int i = 0; i < nn; ++i) {
+      const Range r = H.tree[l][i];
+      items[i].n = (int)(r.b - r.a);
+      items[i].tr = extend_tree(subtree(H.tree, l, i, LH - l), Lq + 2);
+      items[i].K12 = probs[2 * (size_t)i].out.get();
+      items[i].K21 = probs[2 * (size_t)i + 1].out.get();
+      items[i].key = (key * 977u + (uint32_t)l * 31u + (uint32_t)i) & 0xFFFFFu;
     }
+    smw_assemble_batch(items, Lq + 2, P);
+    for (int i = 0; i < nn; ++i) inv->M[l][i] = std::move(items[i].out);
   }
   check_status();
   return inv;
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms: every problem of a call runs in lockstep, one launch per step
+// for all of them (the HOD-BF inversion treats all nodes of a T_H level at once).
+// ---------------------------------------------------------------------------
+template <typename T>
+void BFContext<T>::run_lstsq(std::vector<LstsqJob<T>>& lj) {
+  if (lj.empty()) return;
+  int mc = 1, mr = 1, mw = 1;
+  for (auto& j : lj) {
+    mc = std::max(mc, (int)j.c);
+    mr = std::max(mr, (int)j.r);
+    mw = std::max(mw, (int)j.w);
+  }
+  const bool in_smem = lstsq_smem_bytes<T>(mc, mr, mw, true) <= kLstsqSmemCap;
+  if (!in_smem)
+    for (auto& j : lj) j.W = scratch.takeT<T>((size_t)lstsq_work_elems(j.c, j.r, j.w));
+  auto* d = scratch.takeT<LstsqJob<T>>(lj.size());
+  h2d(d, lj.data(), lj.size() * sizeof(LstsqJob<T>));
+  if (launch_lstsq<T>(d, (int)lj.size(), mc, mr, mw, in_smem, status.as<int32_t>(), st) != 0)
+    throw std::runtime_error("centre block too large for the least-squares kernel");
+}
+
+template <typename T>
+Blk<T> BFContext<T>::make_sketch(int rows, const std::vector<Range>& groups, int q, int level, int side, uint32_t key,
+                                 std::vector<std::pair<int, int>>& cols) {
+  cols.clear();
+  int tot = 0;
+  std::vector<SketchGroup> sg;
+  for (size_t g = 0; g < groups.size(); ++g) {
+    int size = (int)(groups[g].b - groups[g].a);
+    int w = size <= q ? size : q;
+    cols.push_back({tot, tot + w});
+    SketchGroup sgr;
+    sgr.a = groups[g].a; sgr.b = groups[g].b; sgr.c0 = tot; sgr.w = w;
+    sgr.key = (int32_t)((key * 1000003u + (uint32_t)level * 7919u + (uint32_t)side * 104729u + (uint32_t)g) & 0xFFFFFF);
+    sgr.identity = (w == size) ? 1 : 0;
+    if (w > 0) sg.push_back(sgr);
+    tot += w;
+  }
+  Blk<T> Om = new_blk<T>(scratch, rows, std::max(tot, 1));
+  Om.cols = tot;
+  zero(Om);
+  if (!sg.empty()) {
+    int mx = 0;
+    for (auto& g : sg) mx = std::max<int>(mx, (int)((g.b - g.a) * g.w));
+    auto* dg = scratch.takeT<SketchGroup>(sg.size());
+    h2d(dg, sg.data(), sg.size() * sizeof(SketchGroup));
+    launch_sketch<T>(dg, (int)sg.size(), mx, Om.p, Om.plane, (int)Om.ld, st);
+  }
+  return Om;
+}
+
+template <typename T>
+std::vector<Blk<T>> BFContext<T>::copy_b(const std::vector<Blk<T>>& x) {
+  std::vector<Blk<T>> out(x.size());
+  std::vector<Blk2Job<T>> jobs;
+  for (size_t q = 0; q < x.size(); ++q) {
+    out[q] = new_blk<T>(scratch, x[q].rows, x[q].cols);
+    Blk2Job<T> j{};
+    j.src = x[q].p; j.splane = x[q].plane; j.sld = x[q].ld;
+    j.dst = out[q].p; j.dplane = out[q].plane; j.dld = out[q].ld;
+    j.rows = x[q].rows; j.cols = x[q].cols; j.alpha = T(1); j.mode = 3;
+    if (j.rows && j.cols) jobs.push_back(j);
+  }
+  run_blk2(*this, jobs);
+  return out;
+}
+
+template <typename T>
+void BFContext<T>::axpy_b(const std::vector<Blk<T>>& x, std::vector<Blk<T>>& y, T alpha) {
+  std::vector<Blk2Job<T>> jobs;
+  for (size_t q = 0; q < x.size(); ++q) {
+    Blk2Job<T> j{};
+    j.src = x[q].p; j.splane = x[q].plane; j.sld = x[q].ld;
+    j.dst = y[q].p; j.dplane = y[q].plane; j.dld = y[q].ld;
+    j.rows = x[q].rows; j.cols = x[q].cols; j.alpha = alpha; j.mode = 2;
+    if (j.rows && j.cols) jobs.push_back(j);
+  }
+  run_blk2(*this, jobs);
+}
+
+template <typename T>
+void BFContext<T>::random_matvec_batch(const DOpB<T>& op, std::vector<RMProblem<T>>& probs, int L,
+                                       const BFParams& P) {
+  const size_t nq = probs.size();
+  if (!nq) return;
+  const int lc = L / 2;
+  const int q0 = (P.max_rank > 0 ? P.max_rank : P.q_start) + P.p;
+  for (auto& pb : probs) {
+    pb.out = std::make_unique<DBF<T>>();
+    pb.out->init(pb.m, pb.n, pb.rt, pb.ct, L);
+  }
+  const size_t mk = scratch.mark();
+  std::vector<Blk<T>> cOm(nq), cY(nq);
+  std::vector<std::vector<std::pair<int, int>>> ccols(nq);
+  auto gather_blk = [&](const Blk<T>& Y, const IdxVec& rows, std::pair<int, int> cols, std::vector<GatherJob<T>>& gj) {
+    Blk<T> M = new_blk<T>(scratch, (int)rows.size(), cols.second - cols.first);
+    GatherJob<T> g;
+    g.src = Y.p; g.splane = Y.plane; g.sld = Y.ld;
+    g.rows = dev_idx(*this, rows);
+    g.c0 = cols.first;
+    g.nrows = (int)rows.size();
+    g.ncols = cols.second - cols.first;
+    g.dst = M.p; g.dplane = M.plane; g.dld = M.ld;
+    if (g.nrows && g.ncols) gj.push_back(g);
+    return M;
+  };
+  auto run_gathers = [&](std::vector<GatherJob<T>>& gj) {
+    if (gj.empty()) return;
+    int64_t mx = 0;
+    for (auto& g : gj) mx = std::max<int64_t>(mx, (int64_t)g.nrows * g.ncols);
+    auto* d = scratch.takeT<GatherJob<T>>(gj.size());
+    h2d(d, gj.data(), gj.size() * sizeof(GatherJob<T>));
+    launch_gather_rows<T>(d, (int)gj.size(), mx, st);
+  };
+  for (int side = 0; side < 2; ++side) {
+    const int lfirst = side == 0 ? L : 0, llast = lc, step = side == 0 ? -1 : 1;
+    for (int l = lfirst;; l += step) {
+      int q = q0;
+      const size_t mkl = scratch.mark();
+      for (;;) {
+        std::vector<Blk<T>> Om(nq), Yb(nq);
+        std::vector<std::vector<std::pair<int, int>>> cols(nq);
+        for (size_t t = 0; t < nq; ++t) {
+          DBF<T>& bf = *probs[t].out;
+          const auto& groups = side == 0 ? bf.ct[L - l] : bf.rt[l];
+          Om[t] = make_sketch(side == 0 ? bf.n : bf.m, groups, q, l, side, probs[t].key, cols[t]);
+          Yb[t] = new_blk<T>(scratch, side == 0 ? bf.m : bf.n, std::max(Om[t].cols, 1));
+          Yb[t].cols = Om[t].cols;
+        }
+        op(Om, Yb, side == 1);
+        std::vector<Blk<T>> Ms;
+        std::vector<GatherJob<T>> gj;
+        std::vector<IdxVec> sets;
+        std::vector<std::pair<size_t, int>> owner;
+        for (size_t t = 0; t < nq; ++t) {
+          DBF<T>& bf = *probs[t].out;
+          for (int i = 0; i < (1 << l); ++i)
+            for (int j = 0; j < (1 << (L - l)); ++j) {
+              IdxVec X;
+              int grp;
+              if (side == 0) {
+                X = l == L ? range_vec(bf.rt[L][i].a, bf.rt[L][i].b)
+                           : cat(bf.Osk[l + 1][bf.pidx(l + 1, 2 * i, j / 2)],
+                                 bf.Osk[l + 1][bf.pidx(l + 1, 2 * i + 1, j / 2)]);
+                grp = j;
+              } else {
+                X = l == 0 ? range_vec(bf.ct[L][j].a, bf.ct[L][j].b)
+                           : cat(bf.Ssk[l - 1][bf.pidx(l - 1, i / 2, 2 * j)],
+                                 bf.Ssk[l - 1][bf.pidx(l - 1, i / 2, 2 * j + 1)]);
+                grp = i;
+              }
+              Ms.push_back(gather_blk(Yb[t], X, cols[t][grp], gj));
+              sets.push_back(X);
+              owner.push_back({t, grp});
+            }
+        }
+        run_gathers(gj);
+        std::vector<IdxVec> sk;
+        std::vector<Blk<T>> Us;
+        row_ids(Ms, P.tol, P.max_rank, sk, Us);
+        bool grow = false;
+        if (P.max_rank <= 0)
+          for (size_t p = 0; p < Ms.size(); ++p) {
+            const size_t t = owner[p].first;
+            const int grp = owner[p].second;
+            const DBF<T>& bf = *probs[t].out;
+            const Range g = side == 0 ? bf.ct[L - l][grp] : bf.rt[l][grp];
+            const int w = cols[t][grp].second - cols[t][grp].first;
+            if (w < (int)(g.b - g.a) && (int)sk[p].size() > w - P.p) grow = true;
+          }
+        if (grow && q < 4096) {
+          q *= 2;
+          scratch.release(mkl);
+          continue;
+        }
+        size_t p = 0;
+        for (size_t t = 0; t < nq; ++t) {
+          DBF<T>& bf = *probs[t].out;
+          for (int k = 0; k < (1 << L); ++k, ++p) {
+            IdxVec o;
+            for (int32_t x : sk[p]) o.push_back(sets[p][x]);
+            if (side == 0) { bf.U[l][k] = Us[p]; bf.Osk[l][k] = o; }
+            else { bf.V[l][k] = Us[p]; bf.Ssk[l][k] = o; }
+          }
+        }
+        if (side == 0 && l == lc) {
+          cOm = Om;
+          cY = Yb;
+          ccols = cols;
+        }
+        break;
+      }
+      if (side == 1) scratch.release(mkl);
+      if (l == llast) break;
+    }
+  }
+  // centre blocks by least squares, all problems in one launch
+  std::vector<LstsqJob<T>> lj;
+  std::vector<GatherJob<T>> gj;
+  for (size_t t = 0; t < nq; ++t) {
+    DBF<T>& bf = *probs[t].out;
+    std::vector<Blk<T>> xs;
+    right_transform(bf, cOm[t], xs);
+    for (int i = 0; i < (1 << lc); ++i)
+      for (int j = 0; j < (1 << (L - lc)); ++j) {
+        const int p = bf.pidx(lc, i, j);
+        const int r = bf.rr(lc, i, j), c = bf.rc(lc, i, j);
+        Blk<T> Bm = new_blk<T>(persist, r, std::max(c, 1));
+        Bm.cols = c;
+        bf.B[p] = Bm;
+        if (r == 0 || c == 0) continue;
+        Blk<T> Yr = gather_blk(cY[t], bf.Osk[lc][p], ccols[t][j], gj);
+        LstsqJob<T> L1;
+        L1.Tm = xs[p].p + ccols[t][j].first; L1.tplane = xs[p].plane; L1.tld = xs[p].ld;
+        L1.Y = Yr.p; L1.yplane = Yr.plane; L1.yld = Yr.ld;
+        L1.B = Bm.p; L1.bplane = Bm.plane; L1.bld = Bm.ld;
+        L1.c = c; L1.r = r; L1.w = ccols[t][j].second - ccols[t][j].first;
+        L1.W = nullptr;
+        lj.push_back(L1);
+        flops += 8.0 * ((double)c * c * L1.w + (double)r * c * L1.w);
+      }
+  }
+  run_gathers(gj);
+  run_lstsq(lj);
+  MF_CUDA(cudaStreamSynchronize(st));
+  scratch.release(mk);
+}
+
+template <typename T>
+void BFContext<T>::inv_apply_b(const DHODBFInv<T>& Hi, int l0, const std::vector<int>& i0s, const std::vector<Blk<T>>& X,
+                               std::vector<Blk<T>>& Y, bool transpose) {
+  const int LH = Hi.LH;
+  const size_t nq = i0s.size();
+  if (!nq) return;
+  const int nsub = 1 << (LH - l0);
+  std::vector<Blk<T>> Z(nq);
+  for (size_t q = 0; q < nq; ++q) Z[q] = new_blk<T>(scratch, X[q].rows, X[q].cols);
+  auto leaves = [&](const std::vector<Blk<T>>& src, std::vector<Blk<T>>& out) {
+    std::vector<GemmDesc<T>> g;
+    for (size_t q = 0; q < nq; ++q) {
+      const int64_t a0 = Hi.tree[l0][i0s[q]].a;
+      const int k = X[q].cols;
+      for (int li = i0s[q] * nsub; li < (i0s[q] + 1) * nsub; ++li) {
+        const Range r = Hi.tree[LH][li];
+        const int nr = (int)(r.b - r.a);
+        if (nr == 0) continue;
+        g.push_back(gdesc<T>(nr, k, nr, transpose ? 1 : 0, 0, T(1), T(0), Hi.Dinv[li],
+                             src[q].sub((int)(r.a - a0), 0, nr, k), out[q].sub((int)(r.a - a0), 0, nr, k)));
+      }
+    }
+    gemm(g);
+  };
+  auto level = [&](int l) {
+    const int span = 1 << (l - l0);
+    std::vector<const DBF<T>*> bfs;
+    std::vector<Blk<T>> xs, zs;
+    for (size_t q = 0; q < nq; ++q) {
+      const int64_t a0 = Hi.tree[l0][i0s[q]].a;
+      const int k = X[q].cols;
+      for (int i = i0s[q] * span; i < (i0s[q] + 1) * span; ++i) {
+        const Range r = Hi.tree[l][i];
+        bfs.push_back(Hi.M[l][i].get());
+        xs.push_back(Y[q].sub((int)(r.a - a0), 0, (int)(r.b - r.a), k));
+        zs.push_back(Z[q].sub((int)(r.a - a0), 0, (int)(r.b - r.a), k));
+      }
+    }
+    apply(bfs, xs, zs, transpose, false);
+    axpy_b(Z, Y, T(1));
+  };
+  if (!transpose) {
+    leaves(X, Y);
+    for (int l = LH - 1; l >= l0; --l) level(l);
+  } else {
+    std::vector<Blk2Job<T>> cj;
+    for (size_t q = 0; q < nq; ++q) {
+      Blk2Job<T> j{};
+      j.src = X[q].p; j.splane = X[q].plane; j.sld = X[q].ld;
+      j.dst = Y[q].p; j.dplane = Y[q].plane; j.dld = Y[q].ld; j.rows = X[q].rows; j.cols = X[q].cols; j.alpha = T(1);
+      j.mode = 3;
+      cj.push_back(j);
+    }
+    run_blk2(*this, cj);
+    for (int l = l0; l <= LH - 1; ++l) {
+      // Z must not carry the previous level's values into the axpy: level() overwrites Z first
+      level(l);
+    }
+    leaves(Y, Z);
+    std::vector<Blk2Job<T>> bj;
+    for (size_t q = 0; q < nq; ++q) {
+      Blk2Job<T> j{};
+      j.src = Z[q].p; j.splane = Z[q].plane; j.sld = Z[q].ld;
+      j.dst = Y[q].p; j.dplane = Y[q].plane; j.dld = Y[q].ld; j.rows = X[q].rows; j.cols = X[q].cols; j.alpha = T(1);
+      j.mode = 3;
+      bj.push_back(j);
+    }
+    run_blk2(*this, bj);
+  }
+}
+
+template <typename T>
+std::vector<std::unique_ptr<DBF<T>>> BFContext<T>::bf_smw_batch(const std::vector<const DBF<T>*>& Ks,
+                                                               const std::vector<uint32_t>& keys,
+                                                               const BFParams& P) {
+  std::vector<std::unique_ptr<DBF<T>>> out(Ks.size());
+  if (Ks.empty()) return out;
+  const int L = Ks[0]->L;
+  if (L <= 1) {
+    for (size_t q = 0; q < Ks.size(); ++q) out[q] = bf_smw(*Ks[q], P, keys[q]);
+    return out;
+  }
+  std::vector<std::unique_ptr<DBF<T>>> k11(Ks.size()), k12(Ks.size()), k21(Ks.size()), k22(Ks.size());
+  std::vector<const DBF<T>*> k22p;
+  std::vector<uint32_t> k22keys;
+  for (size_t q = 0; q < Ks.size(); ++q) {
+    k11[q] = split_child(*Ks[q], 0, 0);
+    k12[q] = split_child(*Ks[q], 0, 1);
+    k21[q] = split_child(*Ks[q], 1, 0);
+    k22[q] = split_child(*Ks[q], 1, 1);
+    k22p.push_back(k22[q].get());
+    k22keys.push_back(keys[q] * 4u + 1u);
+  }
+  auto k22i = bf_smw_batch(k22p, k22keys, P);
+  std::vector<SmwItem<T>> items(Ks.size());
+  for (size_t q = 0; q < Ks.size(); ++q) {
+    items[q].n = Ks[q]->m;
+    items[q].tr = Ks[q]->rt;
+    items[q].K11 = k11[q].get();
+    items[q].K12 = k12[q].get();
+    items[q].K21 = k21[q].get();
+    items[q].K22i = k22i[q].get();
+    items[q].key = keys[q];
+  }
+  smw_assemble_batch(items, L, P);
+  for (size_t q = 0; q < Ks.size(); ++q) out[q] = std::move(items[q].out);
+  return out;
+}
+
+template <typename T>
+void BFContext<T>::smw_assemble_batch(std::vector<SmwItem<T>>& items, int L, const BFParams& P) {
+  const size_t nq = items.size();
+  if (!nq) return;
+  std::vector<int> n1(nq), n2(nq);
+  for (size_t q = 0; q < nq; ++q) {
+    n1[q] = (int)items[q].tr[1][0].b;
+    n2[q] = items[q].n - n1[q];
+  }
+  auto apply_list = [&](const std::vector<const DBF<T>*>& K, const std::vector<Blk<T>>& x, std::vector<Blk<T>>& y,
+                        bool tr, bool acc) {
+    std::vector<const DBF<T>*> b;
+    std::vector<Blk<T>> xs, ys;
+    for (size_t q = 0; q < K.size(); ++q)
+      if (K[q]) { b.push_back(K[q]); xs.push_back(x[q]); ys.push_back(y[q]); }
+    apply(b, xs, ys, tr, acc);
+  };
+  std::vector<const DBF<T>*> K11(nq), K12(nq), K21(nq), K22i(nq);
+  for (size_t q = 0; q < nq; ++q) {
+    K11[q] = items[q].K11; K12[q] = items[q].K12; K21[q] = items[q].K21; K22i[q] = items[q].K22i;
+  }
+  // z = (I + K22i) y
+  auto inv22 = [&](const std::vector<Blk<T>>& y, bool tr) {
+    std::vector<Blk<T>> z = copy_b(y);
+    apply_list(K22i, y, z, tr, true);
+    return z;
+  };
+  auto newb = [&](const std::vector<int>& rows, const std::vector<Blk<T>>& like) {
+    std::vector<Blk<T>> v(nq);
+    for (size_t q = 0; q < nq; ++q) v[q] = new_blk<T>(scratch, rows[q], like[q].cols);
+    return v;
+  };
+  // S = K11 - K12 (I + K22i) K21
+  DOpB<T> sop = [&](const std::vector<Blk<T>>& X, std::vector<Blk<T>>& Y, bool tr) {
+    std::vector<Blk<T>> t = newb(n2, X);
+    apply_list(tr ? K12 : K21, X, t, tr, false);
+    std::vector<Blk<T>> u = inv22(t, tr);
+    apply_list(tr ? K21 : K12, u, Y, tr, false);
+    axpy_b(Y, Y, T(-2));
+    apply_list(K11, X, Y, tr, true);
+  };
+  std::vector<RMProblem<T>> sp(nq);
+  for (size_t q = 0; q < nq; ++q) {
+    sp[q].m = sp[q].n = n1[q];
+    sp[q].rt = subtree(items[q].tr, 1, 0, L - 2);
+    sp[q].ct = sp[q].rt;
+    sp[q].key = items[q].key * 4u + 2u;
+  }
+  random_matvec_batch(sop, sp, L - 2, P);
+  std::vector<const DBF<T>*> Sl;
+  std::vector<uint32_t> skeys;
+  for (size_t q = 0; q < nq; ++q) {
+    Sl.push_back(sp[q].out.get());
+    skeys.push_back(items[q].key * 4u + 3u);
+  }
+  auto K11i = bf_smw_batch(Sl, skeys, P);
+  std::vector<const DBF<T>*> K11ip(nq);
+  for (size_t q = 0; q < nq; ++q) K11ip[q] = K11i[q].get();
+  // A^-1 - I, A^-1 = [I 0; -A22^-1 A21 I] diag(A11^-1, A22^-1) [I -A12 A22^-1; 0 I]
+  DOpB<T> fop = [&](const std::vector<Blk<T>>& X, std::vector<Blk<T>>& Y, bool tr) {
+    std::vector<Blk<T>> x1(nq), x2(nq), y1(nq), y2(nq);
+    for (size_t q = 0; q < nq; ++q) {
+      const int k = X[q].cols;
+      x1[q] = X[q].sub(0, 0, n1[q], k); x2[q] = X[q].sub(n1[q], 0, n2[q], k);
+      y1[q] = Y[q].sub(0, 0, n1[q], k); y2[q] = Y[q].sub(n1[q], 0, n2[q], k);
+    }
+    std::vector<Blk<T>> w = inv22(x2, tr);                 // A22^-1 x2   (or A22^-T x2)
+    std::vector<Blk<T>> t1 = newb(n1, X);
+    apply_list(tr ? K21 : K12, w, t1, tr, false);         // K12 w  (or K21^T w)
+    axpy_b(t1, t1, T(-2));                                // t1 = -t1
+    axpy_b(x1, t1, T(1));                                 // t1 = x1 - K12 A22^-1 x2
+    std::vector<Blk2Job<T>> cj;
+    for (size_t q = 0; q < nq; ++q) {
+      Blk2Job<T> j{};
+      j.src = t1[q].p; j.splane = t1[q].plane; j.sld = t1[q].ld;
+      j.dst = y1[q].p; j.dplane = y1[q].plane; j.dld = y1[q].ld; j.rows = n1[q]; j.cols = X[q].cols; j.alpha = T(1);
+      j.mode = 3;
+      cj.push_back(j);
+    }
+    run_blk2(*this, cj);
+    apply_list(K11ip, t1, y1, tr, true);                  // y1 = A11^-1 t1
+    std::vector<Blk<T>> v = newb(n2, X);
+    apply_list(tr ? K12 : K21, y1, v, tr, false);         // K21 y1  (or K12^T y1)
+    std::vector<Blk<T>> vv = inv22(v, tr);
+    std::vector<Blk2Job<T>> c3;
+    for (size_t q = 0; q < nq; ++q) {
+      Blk2Job<T> j{};
+      j.src = w[q].p; j.splane = w[q].plane; j.sld = w[q].ld;
+      j.dst = y2[q].p; j.dplane = y2[q].plane; j.dld = y2[q].ld; j.rows = n2[q]; j.cols = X[q].cols; j.alpha = T(1);
+      j.mode = 3;
+      c3.push_back(j);
+    }
+    run_blk2(*this, c3);
+    axpy_b(vv, y2, T(-1));
+    axpy_b(X, Y, T(-1));                                  // minus the identity
+  };
+  std::vector<RMProblem<T>> fp(nq);
+  for (size_t q = 0; q < nq; ++q) {
+    fp[q].m = fp[q].n = items[q].n;
+    fp[q].rt = items[q].tr;
+    fp[q].ct = items[q].tr;
+    fp[q].key = items[q].key * 4u;
+  }
+  random_matvec_batch(fop, fp, L, P);
+  for (size_t q = 0; q < nq; ++q) items[q].out = std::move(fp[q].out);
 }
 
 template struct DBF<float>;

@@ -170,6 +170,32 @@ struct HProblem {
   std::unique_ptr<DHODBF<T>> out;
 };
 
+// Batched black-box operator: Y[q] = K_q X[q] (or K_q^T X[q]) for every problem q of a batch.
+template <typename T>
+using DOpB = std::function<void(const std::vector<Blk<T>>& X, std::vector<Blk<T>>& Y, bool transpose)>;
+
+// One randomized construction problem of a batch (all problems of a batch share L).
+template <typename T>
+struct RMProblem {
+  int m = 0, n = 0;
+  Tree rt, ct;
+  uint32_t key = 0;
+  std::unique_ptr<DBF<T>> out;
+};
+
+// One BF_SMW assembly problem: quadrants of K (K11, K22i may be null) on tree tr.
+template <typename T>
+struct SmwItem {
+  int n = 0;
+  Tree tr;
+  const DBF<T>* K11 = nullptr;
+  const DBF<T>* K12 = nullptr;
+  const DBF<T>* K21 = nullptr;
+  const DBF<T>* K22i = nullptr;
+  uint32_t key = 0;
+  std::unique_ptr<DBF<T>> out;
+};
+
 struct BFParams {
   double tol = 1e-4;
   int max_rank = 0;
@@ -183,7 +209,10 @@ template <typename T>
 class BFContext {
  public:
   BFContext(cudaStream_t st, size_t persist_bytes, size_t scratch_bytes);
+  ~BFContext();
   cudaStream_t st;
+  char* ring = nullptr;
+  size_t ring_cap = 0, ring_off = 0;
   Arena persist, scratch;
   DevMem status;
   double flops = 0;
@@ -191,9 +220,14 @@ class BFContext {
   int64_t n_id = 0;
 
   // ---- primitives
+  // Asynchronous host -> device copy of small host data through a pinned staging ring (the
+  // host data may be reused as soon as the call returns).
+  void h2d(void* dst, const void* src, size_t bytes);
   void gemm(std::vector<GemmDesc<T>>& descs);             // one launch for all descs
   void zero(Blk<T>& b);
   // row IDs of the given matrices (device); results on host (ranks, skeletons) and U in persist
+  // centre blocks by least squares, one launch for all jobs (work from scratch when shared memory is short)
+  void run_lstsq(std::vector<LstsqJob<T>>& lj);
   void row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_rank, std::vector<IdxVec>& sk,
                std::vector<Blk<T>>& Us);
   // ---- butterfly algorithms
@@ -226,6 +260,17 @@ class BFContext {
   std::unique_ptr<DBF<T>> smw_assemble(int n, const Tree& tr, int L, const DBF<T>* K11, const DBF<T>& K12,
                                        const DBF<T>& K21, const DBF<T>* K22i, const BFParams& P, uint32_t key);
   void check_status();
+  // ---- batched forms (all problems of one call in lockstep)
+  Blk<T> make_sketch(int rows, const std::vector<Range>& groups, int q, int level, int side, uint32_t key,
+                     std::vector<std::pair<int, int>>& cols);
+  void random_matvec_batch(const DOpB<T>& op, std::vector<RMProblem<T>>& probs, int L, const BFParams& P);
+  void inv_apply_b(const DHODBFInv<T>& Hi, int l0, const std::vector<int>& i0s, const std::vector<Blk<T>>& X,
+                   std::vector<Blk<T>>& Y, bool transpose);
+  std::vector<std::unique_ptr<DBF<T>>> bf_smw_batch(const std::vector<const DBF<T>*>& Ks,
+                                                    const std::vector<uint32_t>& keys, const BFParams& P);
+  void smw_assemble_batch(std::vector<SmwItem<T>>& items, int L, const BFParams& P);
+  std::vector<Blk<T>> copy_b(const std::vector<Blk<T>>& x);
+  void axpy_b(const std::vector<Blk<T>>& x, std::vector<Blk<T>>& y, T alpha);
 };
 
 }  // namespace mf

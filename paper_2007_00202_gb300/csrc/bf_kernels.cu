@@ -190,71 +190,78 @@ void launch_place(const PlaceJob<T>* d_jobs, int njobs, int64_t max_elems, cudaS
 }
 
 // Dense inverse of small square blocks by Gauss-Jordan elimination with
-// partial pivoting (largest modulus), computed in FP64 and stored as T.  One
-// CTA per block, n <= 128.  Used for the leaf blocks D_tau of HOD-BF
+// partial pivoting (largest modulus), computed in FP64 (work matrix in global
+// memory, L2-resident) and stored as T.  One CTA per block.  Used for the leaf blocks D_tau of HOD-BF
 // inverses (Alg. 4, "directly compute D_tau^-1").
 template <typename T>
-__global__ void __launch_bounds__(256) k_small_inverse(const InvJob<T>* jobs, int32_t* status) {
+__global__ void __launch_bounds__(256) k_small_inverse(const InvJob<T>* jobs, int work_in_smem, int32_t* status) {
   const InvJob<T> j = jobs[blockIdx.x];
+  using R = double;   // arithmetic in FP64 whatever the storage precision
   const int n = j.n;
-  extern __shared__ double sm_d[];
-  double* Ar = sm_d;                   // n x 2n augmented [A | I]
-  double* Ai = Ar + n * 2 * n;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* Ar = work_in_smem ? reinterpret_cast<R*>(smraw) : j.W;   // n x 2n augmented [A | I]
+  R* Ai = Ar + n * 2 * n;
   __shared__ int piv;
   const int w = 2 * n;
   for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
     int r = e / w, c = e % w;
     if (c < n) {
-      Ar[e] = (double)j.A[(int64_t)r * j.lda + c];
-      Ai[e] = (double)j.A[(int64_t)r * j.lda + c + j.aplane];
+      Ar[e] = (R)j.A[(int64_t)r * j.lda + c];
+      Ai[e] = (R)j.A[(int64_t)r * j.lda + c + j.aplane];
     } else {
-      Ar[e] = (c - n == r) ? 1.0 : 0.0;
-      Ai[e] = 0.0;
+      Ar[e] = (c - n == r) ? R(1) : R(0);
+      Ai[e] = R(0);
     }
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      double best = -1;
-      int bi = k;
-      for (int r = k; r < n; ++r) {
-        double m2 = Ar[r * w + k] * Ar[r * w + k] + Ai[r * w + k] * Ai[r * w + k];
+    if (threadIdx.x < 32) {   // pivot: largest modulus in column k at or below the diagonal, lowest row on ties
+      R best = R(-1);
+      int bi = n;
+      for (int r = k + threadIdx.x; r < n; r += 32) {
+        R m2 = Ar[r * w + k] * Ar[r * w + k] + Ai[r * w + k] * Ai[r * w + k];
         if (m2 > best) { best = m2; bi = r; }
       }
-      piv = bi;
-      if (!(best > 0) && status) atomicExch(status, (int32_t)DEV_ZERO_PIVOT);
+      for (int o = 16; o > 0; o >>= 1) {
+        R ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) {
+        piv = bi < n ? bi : k;
+        if (!(best > R(0)) && status) atomicExch(status, (int32_t)DEV_ZERO_PIVOT);
+      }
     }
     __syncthreads();
     const int p = piv;
     if (p != k)
       for (int c = threadIdx.x; c < w; c += blockDim.x) {
-        double t = Ar[k * w + c]; Ar[k * w + c] = Ar[p * w + c]; Ar[p * w + c] = t;
+        R t = Ar[k * w + c]; Ar[k * w + c] = Ar[p * w + c]; Ar[p * w + c] = t;
         t = Ai[k * w + c]; Ai[k * w + c] = Ai[p * w + c]; Ai[p * w + c] = t;
       }
     __syncthreads();
-    double dr = Ar[k * w + k], di = Ai[k * w + k];
-    double den = dr * dr + di * di;
-    if (den == 0) { dr = 1; di = 0; den = 1; }
-    const double ir = dr / den, ii = -di / den;
+    R dr = Ar[k * w + k], di = Ai[k * w + k];
+    R den = dr * dr + di * di;
+    if (den == R(0)) { dr = R(1); di = R(0); den = R(1); }
+    const R ir = dr / den, ii = -di / den;
     __syncthreads();
     for (int c = threadIdx.x; c < w; c += blockDim.x) {
-      double a = Ar[k * w + c], b = Ai[k * w + c];
+      R a = Ar[k * w + c], b = Ai[k * w + c];
       Ar[k * w + c] = a * ir - b * ii;
       Ai[k * w + c] = a * ii + b * ir;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
       int r = e / w, c = e % w;
-      if (r == k) continue;
-      double fr = Ar[r * w + k], fi = Ai[r * w + k];
-      if (c == k) continue;
-      double a = Ar[k * w + c], b = Ai[k * w + c];
+      if (r == k || c == k) continue;
+      R fr = Ar[r * w + k], fi = Ai[r * w + k];
+      R a = Ar[k * w + c], b = Ai[k * w + c];
       Ar[e] -= fr * a - fi * b;
       Ai[e] -= fr * b + fi * a;
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x)
-      if (r != k) { Ar[r * w + k] = 0; Ai[r * w + k] = 0; }
+      if (r != k) { Ar[r * w + k] = R(0); Ai[r * w + k] = R(0); }
     __syncthreads();
   }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -265,17 +272,18 @@ __global__ void __launch_bounds__(256) k_small_inverse(const InvJob<T>* jobs, in
 }
 
 template <typename T>
-int launch_small_inverse(const InvJob<T>* d_jobs, int njobs, int max_n, int32_t* status, cudaStream_t st) {
+int launch_small_inverse(const InvJob<T>* d_jobs, int njobs, int max_n, bool work_in_smem, int32_t* status,
+                         cudaStream_t st) {
   if (njobs <= 0) return 0;
-  size_t sm = sizeof(double) * 4 * (size_t)max_n * max_n;
-  if (sm > 200 * 1024) return -1;
+  const size_t smem = work_in_smem ? small_inverse_smem_bytes(max_n, sizeof(double)) : 0;
+  if (smem > kSmallInvSmemCap) return -1;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_small_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_small_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallInvSmemCap);
     attr = true;
   }
   count_launches(1);
-  k_small_inverse<T><<<njobs, 256, sm, st>>>(d_jobs, status);
+  k_small_inverse<T><<<njobs, 256, smem, st>>>(d_jobs, work_in_smem ? 1 : 0, status);
   return 0;
 }
 
@@ -315,118 +323,178 @@ void launch_blk2(const Blk2Job<T>* d_jobs, int njobs, int64_t max_elems, cudaStr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_lstsq(const LstsqJob<T>* jobs, int32_t* status) {
+__global__ void __launch_bounds__(256) k_lstsq(const LstsqJob<T>* jobs, int work_in_smem) {
   const LstsqJob<T> j = jobs[blockIdx.x];
   const int c = j.c, r = j.r, w = j.w;
-  extern __shared__ double lsq[];
-  double* Gr = lsq;              // c x c, Hermitian, then its Cholesky factor (lower)
-  double* Gi = Gr + c * c;
-  double* zr = Gi + c * c;       // per-thread-block solve vector
-  double* zi = zr + c;
-  const T* Tr = j.Tm;
-  const T* Ti = j.Tm + j.tplane;
-  // G = Tm Tm^H
-  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
-    int a = e / c, b = e % c;
-    if (b > a) continue;
-    double sr = 0, si = 0;
-    for (int t = 0; t < w; ++t) {
-      double ar = Tr[(int64_t)a * j.tld + t], ai = Ti[(int64_t)a * j.tld + t];
-      double br = Tr[(int64_t)b * j.tld + t], bi = Ti[(int64_t)b * j.tld + t];
-      sr += ar * br + ai * bi;      // a * conj(b)
-      si += ai * br - ar * bi;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int64_t wplane = (int64_t)(c + r) * w;
+  T* Wr = work_in_smem ? reinterpret_cast<T*>(smraw) : j.W;
+  T* Wi = Wr + wplane;
+  T* vr = reinterpret_cast<T*>(smraw) + (work_in_smem ? 2 * wplane : 0);   // Householder vector
+  T* vi = vr + w;
+  T* nrm = vi + w;                                 // remaining squared column norms, by position
+  int* perm = reinterpret_cast<int*>(nrm + c);     // position -> column of Tm^T (row of Tm)
+  __shared__ T red_v[8];
+  __shared__ int red_i[8];
+  __shared__ T sh_alpha_r, sh_alpha_i, sh_scale, sh_ref;
+  __shared__ int sh_stop;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const T eps = sizeof(T) == 4 ? T(1.1920929e-7) : T(2.220446049250313e-16);
+  // rows 0..c-1 of the work: the rows of Tm (columns of Tm^T); rows c..c+r-1: the rows of Y
+  for (int q = warp; q < c + r; q += nw) {
+    const bool isT = q < c;
+    const T* sr = isT ? j.Tm + (int64_t)q * j.tld : j.Y + (int64_t)(q - c) * j.yld;
+    const T* si = sr + (isT ? j.tplane : j.yplane);
+    T s = 0;
+    for (int t = lane; t < w; t += 32) {
+      T x = sr[t], y = si[t];
+      Wr[(int64_t)q * w + t] = x;
+      Wi[(int64_t)q * w + t] = y;
+      s += x * x + y * y;
     }
-    Gr[a * c + b] = sr; Gi[a * c + b] = si;
-    Gr[b * c + a] = sr; Gi[b * c + a] = -si;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (isT && lane == 0) { nrm[q] = s; perm[q] = q; }
   }
+  const int kmax = c < w ? c : w;
+  if (tid == 0) sh_stop = 0;
   __syncthreads();
-  // Cholesky G = L L^H (in place, lower), by one thread per column step
-  for (int k = 0; k < c; ++k) {
-    if (threadIdx.x == 0) {
-      double d = Gr[k * c + k];
-      if (!(d > 0)) {
-        if (status) atomicExch(status, (int32_t)DEV_ZERO_PIVOT);
-        d = 1e-300;
+  int rank = 0;
+  for (int k = 0; k < kmax; ++k) {
+    T best = T(-1);
+    int bi = c;
+    for (int q = k + tid; q < c; q += blockDim.x)
+      if (nrm[q] > best) { best = nrm[q]; bi = q; }
+    for (int o = 16; o > 0; o >>= 1) {
+      T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      best = red_v[0]; bi = red_i[0];
+      for (int u = 1; u < nw; ++u)
+        if (red_v[u] > best || (red_v[u] == best && red_i[u] < bi)) { best = red_v[u]; bi = red_i[u]; }
+      T nu = sqrt(best > T(0) ? best : T(0));
+      if (k == 0) sh_ref = nu;
+      if (sh_ref == T(0) || nu <= T(64) * eps * sh_ref) sh_stop = 1;
+      else {
+        T t = nrm[k]; nrm[k] = nrm[bi]; nrm[bi] = t;
+        int ti = perm[k]; perm[k] = perm[bi]; perm[bi] = ti;
       }
-      Gr[k * c + k] = sqrt(d);
-      Gi[k * c + k] = 0;
     }
     __syncthreads();
-    const double dk = Gr[k * c + k];
-    for (int i = k + 1 + threadIdx.x; i < c; i += blockDim.x) {
-      Gr[i * c + k] /= dk;
-      Gi[i * c + k] /= dk;
+    if (sh_stop) break;
+    T* xr = Wr + (int64_t)perm[k] * w;
+    T* xi = Wi + (int64_t)perm[k] * w;
+    T s2 = 0;
+    for (int t = k + tid; t < w; t += blockDim.x) {
+      T x = xr[t], y = xi[t];
+      vr[t] = x; vi[t] = y;
+      s2 += x * x + y * y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) red_v[warp] = s2;
+    __syncthreads();
+    if (tid == 0) {
+      T tot = 0;
+      for (int u = 0; u < nw; ++u) tot += red_v[u];
+      T nx = sqrt(tot);
+      T x0r = vr[k], x0i = vi[k];
+      T ax0 = sqrt(x0r * x0r + x0i * x0i);
+      T phr = ax0 > T(0) ? x0r / ax0 : T(1), phi = ax0 > T(0) ? x0i / ax0 : T(0);
+      T alr = -phr * nx, ali = -phi * nx;
+      vr[k] = x0r - alr;
+      vi[k] = x0i - ali;
+      T vv = tot - (x0r * x0r + x0i * x0i) + vr[k] * vr[k] + vi[k] * vi[k];
+      sh_scale = vv > T(0) ? T(2) / vv : T(0);
+      sh_alpha_r = alr;
+      sh_alpha_i = ali;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < (c - k - 1) * (c - k - 1); e += blockDim.x) {
-      int i = k + 1 + e / (c - k - 1), l = k + 1 + e % (c - k - 1);
-      if (l > i) continue;
-      // G[i][l] -= L[i][k] conj(L[l][k])
-      double ar = Gr[i * c + k], ai = Gi[i * c + k], br = Gr[l * c + k], bi = Gi[l * c + k];
-      Gr[i * c + l] -= ar * br + ai * bi;
-      Gi[i * c + l] -= ai * br - ar * bi;
+    for (int t = k + tid; t < w; t += blockDim.x) {
+      xr[t] = t == k ? sh_alpha_r : T(0);
+      xi[t] = t == k ? sh_alpha_i : T(0);
+    }
+    // reflect the remaining columns (positions k+1..c-1, norms updated) and every right-hand side
+    const T sc = sh_scale;
+    const int nrem = c - k - 1;
+    for (int q = warp; q < nrem + r; q += nw) {
+      const bool isT = q < nrem;
+      const int row = isT ? perm[k + 1 + q] : c + (q - nrem);
+      T* yr = Wr + (int64_t)row * w;
+      T* yi = Wi + (int64_t)row * w;
+      T dr = 0, di = 0;   // v^H y
+      for (int t = k + lane; t < w; t += 32) {
+        T a = vr[t], b = vi[t], p = yr[t], s = yi[t];
+        dr += a * p + b * s;
+        di += a * s - b * p;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        dr += __shfl_xor_sync(0xffffffffu, dr, o);
+        di += __shfl_xor_sync(0xffffffffu, di, o);
+      }
+      dr *= sc;
+      di *= sc;
+      T s = 0;
+      for (int t = k + lane; t < w; t += 32) {
+        T a = vr[t], b = vi[t];
+        T p = yr[t] - (a * dr - b * di);
+        T u = yi[t] - (a * di + b * dr);
+        yr[t] = p;
+        yi[t] = u;
+        if (t > k) s += p * p + u * u;
+      }
+      if (isT) {
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) nrm[k + 1 + q] = s;
+      }
     }
     __syncthreads();
+    rank = k + 1;
   }
-  // rows of B: b_i = h_i G^-1, h_i = y_i Tm^H ; solve G b_i^H = h_i^H
-  const T* Yr = j.Y;
-  const T* Yi = j.Y + j.yplane;
-  for (int i = 0; i < r; ++i) {
-    for (int a = threadIdx.x; a < c; a += blockDim.x) {
-      double sr = 0, si = 0;   // h_i[a] = sum_t y[t] conj(T[a][t]) ; store conj -> h^H
-      for (int t = 0; t < w; ++t) {
-        double yr = Yr[(int64_t)i * j.yld + t], yi = Yi[(int64_t)i * j.yld + t];
-        double tr = Tr[(int64_t)a * j.tld + t], ti = Ti[(int64_t)a * j.tld + t];
-        sr += yr * tr + yi * ti;
-        si += yi * tr - yr * ti;
+  // R11 z = (Q^H y)[0:rank] per right-hand side (one thread each, in place), B[i][perm[b]] = z[b]
+  for (int i = tid; i < r; i += blockDim.x) {
+    T* yr = Wr + (int64_t)(c + i) * w;
+    T* yi = Wi + (int64_t)(c + i) * w;
+    for (int b = rank - 1; b >= 0; --b) {
+      T accr = yr[b], acci = yi[b];
+      for (int cc = b + 1; cc < rank; ++cc) {
+        const int64_t pc = (int64_t)perm[cc] * w;
+        T Rr = Wr[pc + b], Ri = Wi[pc + b];
+        T zr = yr[cc], zi = yi[cc];
+        accr -= Rr * zr - Ri * zi;
+        acci -= Rr * zi + Ri * zr;
       }
-      zr[a] = sr;
-      zi[a] = -si;
+      const int64_t pb = (int64_t)perm[b] * w;
+      T dr = Wr[pb + b], di = Wi[pb + b];
+      T den = dr * dr + di * di;
+      yr[b] = (accr * dr + acci * di) / den;
+      yi[b] = (acci * dr - accr * di) / den;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int a = 0; a < c; ++a) {          // L z = h^H
-        double vr = zr[a], vi = zi[a];
-        for (int b = 0; b < a; ++b) {
-          double lr = Gr[a * c + b], li = Gi[a * c + b];
-          vr -= lr * zr[b] - li * zi[b];
-          vi -= lr * zi[b] + li * zr[b];
-        }
-        zr[a] = vr / Gr[a * c + a];
-        zi[a] = vi / Gr[a * c + a];
-      }
-      for (int a = c - 1; a >= 0; --a) {     // L^H x = z
-        double vr = zr[a], vi = zi[a];
-        for (int b = a + 1; b < c; ++b) {
-          double lr = Gr[b * c + a], li = -Gi[b * c + a];
-          vr -= lr * zr[b] - li * zi[b];
-          vi -= lr * zi[b] + li * zr[b];
-        }
-        zr[a] = vr / Gr[a * c + a];
-        zi[a] = vi / Gr[a * c + a];
-      }
+    T* br = j.B + (int64_t)i * j.bld;
+    T* bim = br + j.bplane;
+    for (int b = 0; b < c; ++b) {
+      br[perm[b]] = b < rank ? yr[b] : T(0);
+      bim[perm[b]] = b < rank ? yi[b] : T(0);
     }
-    __syncthreads();
-    for (int a = threadIdx.x; a < c; a += blockDim.x) {
-      j.B[(int64_t)i * j.bld + a] = (T)zr[a];
-      j.B[(int64_t)i * j.bld + a + j.bplane] = (T)(-zi[a]);
-    }
-    __syncthreads();
   }
 }
 
 template <typename T>
-int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int32_t* status, cudaStream_t st) {
+int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int max_r, int max_w, bool work_in_smem,
+                 int32_t* status, cudaStream_t st) {
+  (void)status;
   if (njobs <= 0) return 0;
-  size_t sm = sizeof(double) * (2 * (size_t)max_c * max_c + 2 * (size_t)max_c);
-  if (sm > 200 * 1024) return -1;
+  const size_t smem = lstsq_smem_bytes<T>(max_c, max_r, max_w, work_in_smem);
+  if (smem > kLstsqSmemCap) return -1;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_lstsq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_lstsq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLstsqSmemCap);
     attr = true;
   }
   count_launches(1);
-  k_lstsq<T><<<njobs, 256, sm, st>>>(d_jobs, status);
+  k_lstsq<T><<<njobs, 256, smem, st>>>(d_jobs, work_in_smem ? 1 : 0);
   return 0;
 }
 
@@ -437,9 +505,9 @@ int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int32_t* statu
   template void launch_front_entries<T>(const FrontEntryJob<T>*, int, int64_t, const FrontCtx<T>*, const int64_t*, \
                                         const int32_t*, const double*, cudaStream_t);                           \
   template void launch_place<T>(const PlaceJob<T>*, int, int64_t, cudaStream_t);                                \
-  template int launch_small_inverse<T>(const InvJob<T>*, int, int, int32_t*, cudaStream_t);                     \
+  template int launch_small_inverse<T>(const InvJob<T>*, int, int, bool, int32_t*, cudaStream_t);                     \
   template void launch_blk2<T>(const Blk2Job<T>*, int, int64_t, cudaStream_t);                                   \
-  template int launch_lstsq<T>(const LstsqJob<T>*, int, int, int32_t*, cudaStream_t);
+  template int launch_lstsq<T>(const LstsqJob<T>*, int, int, int, int, bool, int32_t*, cudaStream_t);
 
 MF_BF_INST(float)
 MF_BF_INST(double)

@@ -96,7 +96,12 @@ struct InvJob {
   int32_t n;
   T* X;
   int64_t xplane, ldx;
+  double* W;           // work of 4 n^2 doubles (augmented [A | I], real and imaginary planes) when not in shared memory
 };
+// Gauss-Jordan elimination with partial pivoting in FP64 (stored in T); the
+// augmented matrix sits in shared memory when the launch's largest job fits.
+inline size_t small_inverse_smem_bytes(int max_n, size_t elem) { return 4 * (size_t)max_n * max_n * elem; }
+constexpr size_t kSmallInvSmemCap = 200 * 1024;
 
 // Block-to-block operations on planar row-major blocks:
 //   mode 0: dst = src^T (plain transpose), dst is cols x rows
@@ -116,8 +121,12 @@ struct Blk2Job {
   int32_t mode;
 };
 
-// B (r x c) minimising ||B Tm - Y||_F for Tm (c x w), Y (r x w): normal equations
-// in FP64 with a Cholesky factorization (c <= 110).
+// B (r x c) minimising ||B Tm - Y||_F for Tm (c x w), Y (r x w), row by row:
+// Tm^T B[i,:]^T = Y[i,:]^T in the least-squares sense, by Householder QR with
+// column pivoting of Tm^T (whose columns are the contiguous rows of Tm), with
+// the reflections applied to the rows of Y in the same pass; columns of Tm^T
+// below a relative pivot of 64 eps get a zero coefficient.  Work in shared
+// memory when the launch's largest job fits, else in W.
 template <typename T>
 struct LstsqJob {
   const T* Tm;
@@ -127,12 +136,25 @@ struct LstsqJob {
   T* B;
   int64_t bplane, bld;
   int32_t c, r, w;
+  T* W;                // work of lstsq_work_elems(c, r, w) T values, used only when the launch says so
 };
+
+inline int64_t lstsq_work_elems(int c, int r, int w) { return 2 * (int64_t)(c + r) * w; }
+// Dynamic shared memory of one k_lstsq CTA: the work (if held there), the
+// Householder vector, the column norms and the column permutation.
+template <typename T>
+inline size_t lstsq_smem_bytes(int max_c, int max_r, int max_w, bool work_in_smem) {
+  size_t b = (size_t)(2 * max_w + max_c) * sizeof(T) + (size_t)max_c * 4 + 16;
+  if (work_in_smem) b += (size_t)lstsq_work_elems(max_c, max_r, max_w) * sizeof(T);
+  return b;
+}
+constexpr size_t kLstsqSmemCap = 200 * 1024;
 
 template <typename T>
 void launch_blk2(const Blk2Job<T>* d_jobs, int njobs, int64_t max_elems, cudaStream_t st);
 template <typename T>
-int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int32_t* status, cudaStream_t st);
+int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int max_r, int max_w, bool work_in_smem,
+                 int32_t* status, cudaStream_t st);
 
 template <typename T>
 int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st);
@@ -147,6 +169,7 @@ void launch_front_entries(const FrontEntryJob<T>* d_jobs, int njobs, int64_t max
 template <typename T>
 void launch_place(const PlaceJob<T>* d_jobs, int njobs, int64_t max_elems, cudaStream_t st);
 template <typename T>
-int launch_small_inverse(const InvJob<T>* d_jobs, int njobs, int max_n, int32_t* status, cudaStream_t st);
+int launch_small_inverse(const InvJob<T>* d_jobs, int njobs, int max_n, bool work_in_smem, int32_t* status,
+                         cudaStream_t st);
 
 }  // namespace mf
