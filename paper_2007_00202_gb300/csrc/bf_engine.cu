@@ -2,6 +2,7 @@
 // index sets, ranks and skeletons are host data; every product, ID, gather
 // and solve is a batched device launch on the context's stream.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -177,28 +178,113 @@ BFContext<T>::~BFContext() {
   if (ring) cudaFreeHost(ring);
 }
 
+namespace {
+constexpr size_t kRingBytes = size_t(128) << 20;
+}
+
+template <typename T>
+void BFContext<T>::sync() {
+  if (cap_mode == 2) {   // not allowed while capturing
+    cap_bad = true;
+    return;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  MF_CUDA(cudaStreamSynchronize(st));
+  t_wait += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+template <typename T>
+void BFContext<T>::flush() {
+  if (!pend || cap_mode == 2) return;
+  MF_CUDA(cudaMemcpyAsync(dring.as<char>() + pend_begin, ring + pend_begin, ring_off - pend_begin,
+                          cudaMemcpyHostToDevice, st));
+  ++n_copies;
+  pend = false;
+}
+
+template <typename T>
+const void* BFContext<T>::upload(const void* src, size_t bytes) {
+  if (cap_mode == 2) {
+    const size_t o = (cap_off + 15) & ~size_t(15);
+    if (o + bytes > cap_cap) {
+      cap_bad = true;
+      return cap_dev;
+    }
+    if (bytes) std::memcpy(cap_host + o, src, bytes);
+    cap_off = o + bytes;
+    return cap_dev + o;
+  }
+  if (cap_mode == 1) cap_off = ((cap_off + 15) & ~size_t(15)) + bytes;
+  if (!ring) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&ring), kRingBytes, cudaHostAllocDefault) != cudaSuccess)
+      throw CudaError("cudaHostAlloc of the staging ring failed");
+    dring.alloc(kRingBytes);
+    ring_cap = kRingBytes;
+  }
+  if (bytes == 0) return dring.p;
+  if (bytes > ring_cap / 4) {   // large: a scratch copy of its own
+    void* d = scratch.take(bytes);
+    flush();
+    MF_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st));
+    sync();
+    ++n_copies;
+    return d;
+  }
+  size_t o = (ring_off + 15) & ~size_t(15);
+  if (o + bytes > ring_cap) {   // wrap: once the stream drains, nothing reads the ring any more
+    flush();
+    sync();
+    o = 0;
+  }
+  std::memcpy(ring + o, src, bytes);
+  if (!pend) {
+    pend_begin = o;
+    pend = true;
+  }
+  ring_off = o + bytes;
+  return dring.as<char>() + o;
+}
+
+template <typename T>
+bool BFContext<T>::capture_end() {
+  cap_mode = 0;
+  if (cap_bad) return false;
+  MF_CUDA(cudaMemcpyAsync(cap_dev, cap_host, cap_off, cudaMemcpyHostToDevice, st));
+  MF_CUDA(cudaStreamSynchronize(st));
+  return true;
+}
+
 template <typename T>
 void BFContext<T>::h2d(void* dst, const void* src, size_t bytes) {
+  flush();
   if (bytes == 0) return;
-  if (!ring) {
-    ring_cap = size_t(128) << 20;
-    if (cudaHostAlloc(reinterpret_cast<void**>(&ring), ring_cap, cudaHostAllocDefault) != cudaSuccess) {
-      ring = nullptr;
-      ring_cap = 0;
+  if (cap_mode == 2) {   // a memcpy node from the persistent blob
+    const size_t o = (cap_off + 15) & ~size_t(15);
+    if (o + bytes > cap_cap) {
+      cap_bad = true;
+      return;
     }
+    std::memcpy(cap_host + o, src, bytes);
+    cap_off = o + bytes;
+    MF_CUDA(cudaMemcpyAsync(dst, cap_host + o, bytes, cudaMemcpyHostToDevice, st));
+    return;
   }
-  if (!ring || bytes > ring_cap / 4) {
+  if (cap_mode == 1) cap_off = ((cap_off + 15) & ~size_t(15)) + bytes;
+  if (!ring) upload(nullptr, 0);
+  if (bytes > ring_cap / 4) {
     MF_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
-    MF_CUDA(cudaStreamSynchronize(st));
+    sync();
+    ++n_copies;
     return;
   }
   size_t o = (ring_off + 255) & ~size_t(255);
   if (o + bytes > ring_cap) {          // wrap: every earlier copy out of the ring has completed after this
-    MF_CUDA(cudaStreamSynchronize(st));
+    sync();
     o = 0;
   }
   std::memcpy(ring + o, src, bytes);
   MF_CUDA(cudaMemcpyAsync(dst, ring + o, bytes, cudaMemcpyHostToDevice, st));
+  ++n_copies;
   ring_off = o + bytes;
 }
 
@@ -206,7 +292,7 @@ template <typename T>
 void BFContext<T>::check_status() {
   int32_t v = 0;
   MF_CUDA(cudaMemcpyAsync(&v, status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  MF_CUDA(cudaStreamSynchronize(st));
+  sync();
   if (v != 0) throw SingularError("singular block in a compressed front (zero pivot or indefinite normal equations)");
 }
 
@@ -223,16 +309,18 @@ void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
       for (int j = 0; j < (d.n + GEMM_TILE - 1) / GEMM_TILE; ++j) tl.push_back({idx, i, j, 0});
   }
   if (tl.empty()) return;
-  auto* dd = scratch.takeT<GemmDesc<T>>(D.size());
-  auto* dt = scratch.takeT<GemmTile>(tl.size());
-  h2d(dd, D.data(), D.size() * sizeof(GemmDesc<T>));
-  h2d(dt, tl.data(), tl.size() * sizeof(GemmTile));
+  const GemmDesc<T>* dd = static_cast<const GemmDesc<T>*>(upload(D.data(), D.size() * sizeof(GemmDesc<T>)));
+  const GemmTile* dt = stage(tl.data(), tl.size());
   launch_gemm<T>(dd, dt, (int)tl.size(), st);
 }
 
 template <typename T>
 void BFContext<T>::zero(Blk<T>& b) {
   if (b.rows <= 0 || b.cols <= 0) return;
+  if ((int64_t)b.rows * b.ld == b.plane) {   // the two planes are adjacent
+    MF_CUDA(cudaMemsetAsync(b.p, 0, sizeof(T) * 2 * (size_t)b.plane, st));
+    return;
+  }
   MF_CUDA(cudaMemsetAsync(b.p, 0, sizeof(T) * (size_t)b.rows * b.ld, st));
   MF_CUDA(cudaMemsetAsync(b.p + b.plane, 0, sizeof(T) * (size_t)b.rows * b.ld, st));
 }
@@ -242,16 +330,13 @@ static void run_blk2(BFContext<T>& cx, std::vector<Blk2Job<T>>& jobs) {
   if (jobs.empty()) return;
   int64_t mx = 0;
   for (auto& j : jobs) mx = std::max<int64_t>(mx, (int64_t)j.rows * j.cols);
-  auto* dj = cx.scratch.template takeT<Blk2Job<T>>(jobs.size());
-  cx.h2d(dj, jobs.data(), jobs.size() * sizeof(Blk2Job<T>));
+  const Blk2Job<T>* dj = cx.stage(jobs.data(), jobs.size());
   launch_blk2<T>(dj, (int)jobs.size(), mx, cx.st);
 }
 
 template <typename T>
 static const int32_t* dev_idx(BFContext<T>& cx, const IdxVec& v) {
-  auto* d = cx.scratch.template takeT<int32_t>(std::max<size_t>(v.size(), 1));
-  if (!v.empty()) cx.h2d(d, v.data(), v.size() * 4);
-  return d;
+  return static_cast<const int32_t*>(cx.upload(v.data(), v.size() * 4));
 }
 
 template <typename T>
@@ -310,8 +395,7 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
   }
   MF_CUDA(cudaMemsetAsync(drk, 0, nj * 4, st));
   if (!jobs.empty()) {
-    auto* dj = scratch.takeT<IdJob<T>>(jobs.size());
-    h2d(dj, jobs.data(), jobs.size() * sizeof(IdJob<T>));
+    const IdJob<T>* dj = stage(jobs.data(), jobs.size());
     if (launch_row_id<T>(dj, (int)jobs.size(), max_m, max_n, (T)tol, max_rank, st) != 0)
       throw std::runtime_error("ID block too large for the row-ID kernel (" + std::to_string(max_m) + " x " +
                                std::to_string(max_n) + ")");
@@ -320,7 +404,7 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
   std::vector<int32_t> hr(nj), hs(sktot);
   MF_CUDA(cudaMemcpyAsync(hr.data(), drk, nj * 4, cudaMemcpyDeviceToHost, st));
   MF_CUDA(cudaMemcpyAsync(hs.data(), dsk, sktot * 4, cudaMemcpyDeviceToHost, st));
-  MF_CUDA(cudaStreamSynchronize(st));
+  sync();
   for (size_t q = 0; q < nj; ++q) {
     int r = hr[q];
     Us[q].cols = r;
@@ -680,7 +764,7 @@ void BFContext<T>::entry_eval_batch(const DExtract<T>& ext, std::vector<BFProble
     }
     ext(all, blocks);
   }
-  MF_CUDA(cudaStreamSynchronize(st));
+  sync();
   scratch.release(mk);
 }
 
@@ -730,8 +814,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::random_matvec(const DOp<T>& op, const Tree
     if (!sg.empty()) {
       int mx = 0;
       for (auto& s : sg) mx = std::max<int>(mx, (int)((s.b - s.a) * s.w));
-      auto* dg = scratch.takeT<SketchGroup>(sg.size());
-      h2d(dg, sg.data(), sg.size() * sizeof(SketchGroup));
+      const SketchGroup* dg = stage(sg.data(), sg.size());
       launch_sketch<T>(dg, (int)sg.size(), mx, Om.p, Om.plane, (int)Om.ld, st);
     }
     return Om;
@@ -751,8 +834,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::random_matvec(const DOp<T>& op, const Tree
     if (gj.empty()) return;
     int64_t mx = 0;
     for (auto& g : gj) mx = std::max<int64_t>(mx, (int64_t)g.nrows * g.ncols);
-    auto* d = scratch.takeT<GatherJob<T>>(gj.size());
-    h2d(d, gj.data(), gj.size() * sizeof(GatherJob<T>));
+    const GatherJob<T>* d = stage(gj.data(), gj.size());
     launch_gather_rows<T>(d, (int)gj.size(), mx, st);
   };
   for (int l = L; l >= lc; --l) {                         // left half: sketches of K(X, S_nu)
@@ -880,7 +962,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::random_matvec(const DOp<T>& op, const Tree
     run_gathers(gj);
     run_lstsq(lj);
   }
-  MF_CUDA(cudaStreamSynchronize(st));
+  sync();
   scratch.release(mk);
   return bf;
 }
@@ -912,7 +994,6 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
   auto& centre1 = EP.centre1;
   auto& centre2 = EP.centre2;
   auto& scratch = cx.scratch;
-  auto zero = [&](Blk<T>& b) { cx.zero(b); };
   for (size_t q = 0; q < lst.size(); ++q) {
     const IdxVec& X0 = lst[q].first;
     const IdxVec& Y0 = lst[q].second;
@@ -950,13 +1031,12 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
       if (r == 0) continue;
       IdxVec rows;
       for (int t = Xp[L][i].p0; t < Xp[L][i].p1; ++t) rows.push_back((*Xptr)[t] - (int32_t)bf.rt[L][i].a);
-      zero(e);
       Blk2Job<T> j{};
       j.src = bf.U[L][i].p; j.splane = bf.U[L][i].plane; j.sld = bf.U[L][i].ld;
       j.dst = e.p; j.dplane = e.plane; j.dld = e.ld; j.rows = nr; j.cols = r; j.alpha = T(1);
       j.ridx = dev_idx(cx, rows);
-      j.cidx = dev_idx(cx, range_vec(0, r));
-      j.mode = 1;
+      j.cidx = nullptr;
+      j.mode = 4;
       gather0.push_back(j);
     }
     for (int l = L - 1; l >= lc; --l)
@@ -997,13 +1077,12 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
       if (c == 0) continue;
       IdxVec rows;
       for (int t = Yp[L][jj].p0; t < Yp[L][jj].p1; ++t) rows.push_back(Y[t] - (int32_t)bf.ct[L][jj].a);
-      zero(f);
       Blk2Job<T> j{};
       j.src = bf.V[0][jj].p; j.splane = bf.V[0][jj].plane; j.sld = bf.V[0][jj].ld;
       j.dst = f.p; j.dplane = f.plane; j.dld = f.ld; j.rows = nr; j.cols = c; j.alpha = T(1);
       j.ridx = dev_idx(cx, rows);
-      j.cidx = dev_idx(cx, range_vec(0, c));
-      j.mode = 1;
+      j.cidx = nullptr;
+      j.mode = 4;
       gather0.push_back(j);
     }
     for (int l = 1; l <= lc; ++l)
@@ -1071,8 +1150,7 @@ static void extract_run(BFContext<T>& cx, ExtractPlan<T>& EP) {
   if (!EP.pj.empty()) {
     int64_t mx = 0;
     for (auto& p : EP.pj) mx = std::max<int64_t>(mx, (int64_t)p.nr * p.nc);
-    auto* d = cx.scratch.template takeT<PlaceJob<T>>(EP.pj.size());
-    cx.h2d(d, EP.pj.data(), EP.pj.size() * sizeof(PlaceJob<T>));
+    const PlaceJob<T>* d = cx.stage(EP.pj.data(), EP.pj.size());
     launch_place<T>(d, (int)EP.pj.size(), mx, cx.st);
   }
 }
@@ -1290,6 +1368,7 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
   };
   std::vector<Req> reqs;
   std::map<const DBF<T>*, size_t> req_of;
+  std::vector<std::pair<char*, size_t>> zspans;   // accumulation targets, zeroed in as few memsets as possible
   for (size_t q = 0; q < lst.size(); ++q) {
     const IdxVec& X = lst[q].first;
     const IdxVec& Y = lst[q].second;
@@ -1304,11 +1383,10 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
         if (Y[b] >= r.a && Y[b] < r.b) { py.push_back((int32_t)b); ry.push_back(Y[b] - (int32_t)r.a); }
       if (px.empty() || py.empty()) continue;
       Blk<T> t = new_blk<T>(scratch, (int)px.size(), (int)py.size());
-      zero(t);
       Blk2Job<T> j{};
       j.src = H.D[li].p; j.splane = H.D[li].plane; j.sld = H.D[li].ld;
       j.dst = t.p; j.dplane = t.plane; j.dld = t.ld; j.rows = t.rows; j.cols = t.cols; j.alpha = T(1);
-      j.ridx = dev_idx(*this, rx); j.cidx = dev_idx(*this, ry); j.mode = 1;
+      j.ridx = dev_idx(*this, rx); j.cidx = dev_idx(*this, ry); j.mode = 4;
       gj.push_back(j);
       PlaceJob<T> pl;
       pl.src = t.p; pl.splane = t.plane; pl.sld = t.ld;
@@ -1337,7 +1415,7 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
         Req& R = reqs[it->second];
         R.lst.push_back({rx, ry});
         Blk<T> t = new_blk<T>(scratch, (int)rx.size(), (int)ry.size());
-        zero(t);
+        zspans.push_back({reinterpret_cast<char*>(t.p), (size_t)2 * t.plane * sizeof(T)});
         R.tmp.push_back(t);
         PlaceJob<T> pl;
         pl.src = t.p; pl.splane = t.plane; pl.sld = t.ld;
@@ -1345,6 +1423,17 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
         pl.dst = dst[q].p; pl.dplane = dst[q].plane; pl.dld = dst[q].ld; pl.sign = sign;
         pj.push_back(pl);
       }
+  }
+  for (size_t a = 0; a < zspans.size();) {   // merge adjacent spans (consecutive scratch allocations)
+    char* p0 = zspans[a].first;
+    char* p1 = p0 + zspans[a].second;
+    size_t b = a + 1;
+    while (b < zspans.size() && zspans[b].first >= p1 && zspans[b].first - p1 < 256) {
+      p1 = zspans[b].first + zspans[b].second;
+      ++b;
+    }
+    MF_CUDA(cudaMemsetAsync(p0, 0, (size_t)(p1 - p0), st));
+    a = b;
   }
   run_blk2(*this, gj);
   std::vector<const DBF<T>*> bfs;
@@ -1359,8 +1448,7 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
   if (!pj.empty()) {
     int64_t mx = 0;
     for (auto& p : pj) mx = std::max<int64_t>(mx, (int64_t)p.nr * p.nc);
-    auto* d = scratch.takeT<PlaceJob<T>>(pj.size());
-    h2d(d, pj.data(), pj.size() * sizeof(PlaceJob<T>));
+    const PlaceJob<T>* d = stage(pj.data(), pj.size());
     launch_place<T>(d, (int)pj.size(), mx, st);
   }
 }
@@ -1445,8 +1533,7 @@ static void small_inverse(BFContext<T>& cx, const std::vector<Blk<T>>& A, std::v
   const bool in_smem = small_inverse_smem_bytes(mx, sizeof(double)) <= kSmallInvSmemCap;
   if (!in_smem)
     for (auto& j : jobs) j.W = cx.scratch.template takeT<double>(4 * (size_t)j.n * j.n);
-  auto* d = cx.scratch.template takeT<InvJob<T>>(jobs.size());
-  cx.h2d(d, jobs.data(), jobs.size() * sizeof(InvJob<T>));
+  const InvJob<T>* d = cx.stage(jobs.data(), jobs.size());
   if (launch_small_inverse<T>(d, (int)jobs.size(), mx, in_smem, cx.status.template as<int32_t>(), cx.st) != 0)
     throw std::runtime_error("block too large for the small dense inverse (" + std::to_string(mx) + ")");
 }
@@ -1476,7 +1563,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::bf_smw(const DBF<T>& K, const BFParams& P,
       std::vector<T> eye(2 * (size_t)G.plane, T(0));
       for (int a = 0; a < c; ++a) eye[(size_t)a * G.ld + a] = T(1);
       h2d(G.p, eye.data(), eye.size() * sizeof(T));
-      MF_CUDA(cudaStreamSynchronize(st));
+      sync();
     }
     g = {gdesc<T>(c, c, r, 0, 0, T(1), T(1), VU, B, G)};
     gemm(g);
@@ -1484,7 +1571,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::bf_smw(const DBF<T>& K, const BFParams& P,
     small_inverse(*this, A1, X1);
     g = {gdesc<T>(r, c, c, 0, 0, T(-1), T(0), B, Gi, Bn)};
     gemm(g);
-    MF_CUDA(cudaStreamSynchronize(st));
+    sync();
     scratch.release(mk);
     return out;
   }
@@ -1501,7 +1588,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::bf_smw(const DBF<T>& K, const BFParams& P,
       std::vector<T> eye(2 * (size_t)G.plane, T(0));
       for (int a = 0; a < rs; ++a) eye[(size_t)a * G.ld + a] = T(1);
       h2d(G.p, eye.data(), eye.size() * sizeof(T));
-      MF_CUDA(cudaStreamSynchronize(st));
+      sync();
     }
     for (int j = 0; j < 2; ++j) {
       // column block j of Mbar Ubar:  R_j B_j (V_j^T U_j)  into G[:, off_j : off_j + r_j]
@@ -1531,7 +1618,7 @@ std::unique_ptr<DBF<T>> BFContext<T>::bf_smw(const DBF<T>& K, const BFParams& P,
       }
       out->U[0][j] = Rn;
     }
-    MF_CUDA(cudaStreamSynchronize(st));
+    sync();
     scratch.release(mk);
     return out;
   }
@@ -1760,8 +1847,7 @@ void BFContext<T>::run_lstsq(std::vector<LstsqJob<T>>& lj) {
   const bool in_smem = lstsq_smem_bytes<T>(mc, mr, mw, true) <= kLstsqSmemCap;
   if (!in_smem)
     for (auto& j : lj) j.W = scratch.takeT<T>((size_t)lstsq_work_elems(j.c, j.r, j.w));
-  auto* d = scratch.takeT<LstsqJob<T>>(lj.size());
-  h2d(d, lj.data(), lj.size() * sizeof(LstsqJob<T>));
+  const LstsqJob<T>* d = stage(lj.data(), lj.size());
   if (launch_lstsq<T>(d, (int)lj.size(), mc, mr, mw, in_smem, status.as<int32_t>(), st) != 0)
     throw std::runtime_error("centre block too large for the least-squares kernel");
 }
@@ -1789,8 +1875,7 @@ Blk<T> BFContext<T>::make_sketch(int rows, const std::vector<Range>& groups, int
   if (!sg.empty()) {
     int mx = 0;
     for (auto& g : sg) mx = std::max<int>(mx, (int)((g.b - g.a) * g.w));
-    auto* dg = scratch.takeT<SketchGroup>(sg.size());
-    h2d(dg, sg.data(), sg.size() * sizeof(SketchGroup));
+    const SketchGroup* dg = stage(sg.data(), sg.size());
     launch_sketch<T>(dg, (int)sg.size(), mx, Om.p, Om.plane, (int)Om.ld, st);
   }
   return Om;
@@ -1855,8 +1940,7 @@ void BFContext<T>::random_matvec_batch(const DOpB<T>& op, std::vector<RMProblem<
     if (gj.empty()) return;
     int64_t mx = 0;
     for (auto& g : gj) mx = std::max<int64_t>(mx, (int64_t)g.nrows * g.ncols);
-    auto* d = scratch.takeT<GatherJob<T>>(gj.size());
-    h2d(d, gj.data(), gj.size() * sizeof(GatherJob<T>));
+    const GatherJob<T>* d = stage(gj.data(), gj.size());
     launch_gather_rows<T>(d, (int)gj.size(), mx, st);
   };
   for (int side = 0; side < 2; ++side) {
@@ -1969,7 +2053,7 @@ void BFContext<T>::random_matvec_batch(const DOpB<T>& op, std::vector<RMProblem<
   }
   run_gathers(gj);
   run_lstsq(lj);
-  MF_CUDA(cudaStreamSynchronize(st));
+  sync();
   scratch.release(mk);
 }
 

@@ -49,6 +49,7 @@ class Arena {
   size_t used() const { return off_; }
   size_t peak() const { return peak_; }
   size_t capacity() const { return mem_.bytes; }
+  char* base() const { return static_cast<char*>(mem_.p); }
 
  private:
   DevMem mem_;
@@ -211,8 +212,16 @@ class BFContext {
   BFContext(cudaStream_t st, size_t persist_bytes, size_t scratch_bytes);
   ~BFContext();
   cudaStream_t st;
-  char* ring = nullptr;
-  size_t ring_cap = 0, ring_off = 0;
+  char* ring = nullptr;             // pinned host staging ring
+  DevMem dring;                     // its device mirror (targets of upload())
+  size_t ring_cap = 0, ring_off = 0, pend_begin = 0;
+  bool pend = false;
+  int64_t n_copies = 0;             // host -> device copies issued
+  char* cap_host = nullptr;         // capture blob (pinned host) and its device twin
+  char* cap_dev = nullptr;
+  size_t cap_cap = 0, cap_off = 0;
+  bool cap_bad = false;
+  double t_wait = 0;                // seconds the host spent waiting for the stream
   Arena persist, scratch;
   DevMem status;
   double flops = 0;
@@ -223,8 +232,35 @@ class BFContext {
   // Asynchronous host -> device copy of small host data through a pinned staging ring (the
   // host data may be reused as soon as the call returns).
   void h2d(void* dst, const void* src, size_t bytes);
+  // Small host arrays read by this context's kernels (index lists) are staged in the ring:
+  // upload() copies the bytes there and returns their device address in the mirror; the
+  // staged bytes go to the device in one cudaMemcpyAsync per run, issued by flush().  h2d()
+  // flushes first, and every launch is preceded by the h2d of its job table, so a kernel
+  // always finds the index lists its jobs point to.
+  const void* upload(const void* src, size_t bytes);
+  void flush();
+  // upload + flush: a job table that the next launch reads
+  template <typename U>
+  const U* stage(const U* src, size_t n) {
+    const U* d = static_cast<const U*>(upload(src, n * sizeof(U)));
+    flush();
+    return d;
+  }
+  // ---- CUDA-graph capture of a fixed launch sequence (the compressed solve)
+  // count_begin/count_end measure the staged bytes of one eager run of the sequence;
+  // capture_begin redirects staging into a persistent pinned blob (host) whose device
+  // twin the captured kernels read, and capture_end copies the blob to the device
+  // once.  A stream synchronize or an overflow while capturing marks the capture bad.
+  void count_begin() { cap_mode = 1; cap_off = 0; }
+  size_t count_end() { cap_mode = 0; return cap_off; }
+  void capture_begin(char* host_blob, char* dev_blob, size_t cap) {
+    cap_mode = 2; cap_host = host_blob; cap_dev = dev_blob; cap_cap = cap; cap_off = 0; cap_bad = false;
+  }
+  bool capture_end();               // after cudaStreamEndCapture; false if the capture is unusable
+  int cap_mode = 0;                 // 0 eager, 1 counting, 2 capturing
+  void sync();                      // stream synchronize, timed into t_wait
   void gemm(std::vector<GemmDesc<T>>& descs);             // one launch for all descs
-  void zero(Blk<T>& b);
+  void zero(Blk<T>& b);                                   // b: a whole block from new_blk
   // row IDs of the given matrices (device); results on host (ranks, skeletons) and U in persist
   // centre blocks by least squares, one launch for all jobs (work from scratch when shared memory is short)
   void run_lstsq(std::vector<LstsqJob<T>>& lj);

@@ -297,10 +297,15 @@ __global__ void k_blk2(const Blk2Job<T>* jobs) {
       const int64_t so = (int64_t)r * j.sld + c, dof = (int64_t)c * j.dld + r;
       j.dst[dof] = j.src[so];
       j.dst[dof + j.dplane] = j.src[so + j.splane];
-    } else if (j.mode == 1) {
-      const int64_t so = (int64_t)j.ridx[r] * j.sld + j.cidx[c], dof = (int64_t)r * j.dld + c;
-      j.dst[dof] += j.alpha * j.src[so];
-      j.dst[dof + j.dplane] += j.alpha * j.src[so + j.splane];
+    } else if (j.mode == 1 || j.mode == 4) {
+      const int64_t so = (int64_t)j.ridx[r] * j.sld + (j.cidx ? j.cidx[c] : c), dof = (int64_t)r * j.dld + c;
+      if (j.mode == 1) {
+        j.dst[dof] += j.alpha * j.src[so];
+        j.dst[dof + j.dplane] += j.alpha * j.src[so + j.splane];
+      } else {
+        j.dst[dof] = j.alpha * j.src[so];
+        j.dst[dof + j.dplane] = j.alpha * j.src[so + j.splane];
+      }
     } else if (j.mode == 2) {
       const int64_t so = (int64_t)r * j.sld + c, dof = (int64_t)r * j.dld + c;
       j.dst[dof] += j.alpha * j.src[so];

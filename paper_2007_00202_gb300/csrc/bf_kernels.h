@@ -105,7 +105,8 @@ constexpr size_t kSmallInvSmemCap = 200 * 1024;
 
 // Block-to-block operations on planar row-major blocks:
 //   mode 0: dst = src^T (plain transpose), dst is cols x rows
-//   mode 1: dst[a][b] += alpha * src[ridx[a]][cidx[b]]   (gather of a sub-block)
+//   mode 1: dst[a][b] += alpha * src[ridx[a]][cidx[b]]   (gather of a sub-block; cidx NULL: b)
+//   mode 4: dst[a][b]  = alpha * src[ridx[a]][cidx[b]]   (the same, assigning)
 //   mode 2: dst += alpha * src
 //   mode 3: dst = src
 template <typename T>

@@ -1,6 +1,8 @@
 // Compressed fronts (Alg. 5) on the GPU; see engine_comp.h.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <numeric>
 
 #include "engine_comp.h"
@@ -92,11 +94,8 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
         if (g[q].first.empty() || g[q].second.empty()) continue;
         FrontEntryJob<T> j;
         j.ctx = 0;
-        auto* dx = cx.scratch.template takeT<int32_t>(g[q].first.size());
-        auto* dy = cx.scratch.template takeT<int32_t>(g[q].second.size());
-        MF_CUDA(cudaMemcpyAsync(dx, g[q].first.data(), g[q].first.size() * 4, cudaMemcpyHostToDevice, st_));
-        MF_CUDA(cudaMemcpyAsync(dy, g[q].second.data(), g[q].second.size() * 4, cudaMemcpyHostToDevice, st_));
-        j.X = dx; j.Y = dy;
+        j.X = static_cast<const int32_t*>(cx.upload(g[q].first.data(), g[q].first.size() * 4));
+        j.Y = static_cast<const int32_t*>(cx.upload(g[q].second.data(), g[q].second.size() * 4));
         j.nx = (int)g[q].first.size(); j.ny = (int)g[q].second.size();
         j.dst = dst[q].p; j.dplane = dst[q].plane; j.dld = dst[q].ld;
         j.with_A = with_A ? 1 : 0;
@@ -105,8 +104,7 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
         mx = std::max<int64_t>(mx, (int64_t)j.nx * j.ny);
       }
       if (!jobs.empty()) {
-        auto* dj = cx.scratch.template takeT<FrontEntryJob<T>>(jobs.size());
-        MF_CUDA(cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(jobs[0]), cudaMemcpyHostToDevice, st_));
+        const FrontEntryJob<T>* dj = cx.stage(jobs.data(), jobs.size());
         launch_front_entries<T>(dj, (int)jobs.size(), mx, dctx, A_.rowptr.template as<int64_t>(),
                                 A_.col32.template as<int32_t>(), A_.vals.template as<double>(), st_);
       }
@@ -148,12 +146,34 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
   std::vector<IdxVec> nn21 = to_local(nb.nn21_ptr, nb.nn21, u, 0);   // I^u row -> I^s local
   std::vector<IdxVec> nn22 = to_local(nb.nn22_ptr, nb.nn22, u, s);
   Tree th = f.th_tree, t22 = f.f22_tree;
+  // optional phase trace (MF_TRACE=1): wall time and kernel launches per phase on stderr
+  const bool trace = getenv("MF_TRACE") && getenv("MF_TRACE")[0] == '1';
+  auto tp = std::chrono::steady_clock::now();
+  int64_t lp = launch_count();
+  int64_t idp = cx.n_id, cpp = cx.n_copies;
+  double wp = cx.t_wait;
+  auto phase = [&](const char* name) {
+    if (!trace) return;
+    cx.sync();
+    auto tn = std::chrono::steady_clock::now();
+    fprintf(stderr, "[mf] front %d (s=%d u=%d) %-10s %8.3f s (waiting %6.3f s) %7lld launches %6lld IDs %7lld copies\n",
+            fid, s, u, name, std::chrono::duration<double>(tn - tp).count(), cx.t_wait - wp,
+            (long long)(launch_count() - lp), (long long)(cx.n_id - idp), (long long)(cx.n_copies - cpp));
+    tp = tn;
+    lp = launch_count();
+    idp = cx.n_id;
+    cpp = cx.n_copies;
+    wp = cx.t_wait;
+  };
   cf.F11 = cx.hodbf_entry_eval(make_ext(0, 0, true, false), s, th, nn11, P);
+  phase("F11");
   cf.F11inv = cx.hodbf_invert(*cf.F11, P, (uint32_t)((seed * 7 + fid) & 0xFFFFF));
+  phase("F11inv");
   if (u > 0) {
     const int LH = (int)th.size() - 1, L22 = (int)t22.size() - 1, L = std::min(LH, L22);
     cf.F12 = cx.entry_eval(make_ext(0, s, true, false), s, u, th, t22, L, nn12, nn21, P);
     cf.F21 = cx.entry_eval(make_ext(s, 0, true, false), u, s, t22, th, L, nn21, nn12, P);
+    phase("F12,F21");
     const DBF<T>* F12p = cf.F12.get();
     const DBF<T>* F21p = cf.F21.get();
     const DHODBFInv<T>* Ip = cf.F11inv.get();
@@ -173,7 +193,9 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
     };
     auto S = cx.random_matvec(op, t22, t22, L22, P, (uint32_t)((seed * 13 + fid) & 0xFFFFF));
     Sptr = S.get();
+    phase("S");
     if (f.parent >= 0) cf.C = cx.hodbf_entry_eval(make_ext(s, s, false, true), u, t22, nn22, P);
+    phase("C");
     Sptr = nullptr;
     cf.max_rank = std::max({cf.F11->max_rank(), cf.F12->max_rank(), cf.F21->max_rank(), S->max_rank(),
                             cf.C ? cf.C->max_rank() : 0});
@@ -207,8 +229,7 @@ void CompressedPart<T>::densify_C(int fid, const FrontDev<T>& fd) {
   Blk<T> Cd;
   Cd.p = fd.C; Cd.rows = u; Cd.cols = u; Cd.ld = fd.lu; Cd.plane = fd.pl_uu;
   cx.hodbf_apply(*cf.C, I, Cd, false);
-  MF_CUDA(cudaStreamSynchronize(st_));
-  cx.scratch.release(mk);
+  cx.scratch.release(mk);   // stream order makes later reuse of the scratch safe
 }
 
 template <typename T>
@@ -224,11 +245,7 @@ void CompressedPart<T>::forward(int fid, Blk<T>& X) {
   j.src = w.p; j.splane = w.plane; j.sld = w.ld; j.dst = xs.p; j.dplane = xs.plane; j.dld = xs.ld;
   j.rows = s; j.cols = k; j.alpha = T(1); j.mode = 3;
   cp.push_back(j);
-  {
-    auto* d = cx.scratch.template takeT<Blk2Job<T>>(1);
-    MF_CUDA(cudaMemcpyAsync(d, cp.data(), sizeof(Blk2Job<T>), cudaMemcpyHostToDevice, st_));
-    launch_blk2<T>(d, 1, (int64_t)s * k, st_);
-  }
+  launch_blk2<T>(cx.stage(cp.data(), 1), 1, (int64_t)s * k, st_);
   if (u > 0) {
     Blk<T> t = new_blk<T>(cx.scratch, u, k);
     std::vector<const DBF<T>*> b{cf.F21.get()};
@@ -237,16 +254,13 @@ void CompressedPart<T>::forward(int fid, Blk<T>& X) {
     PlaceJob<T> pl;
     pl.src = t.p; pl.splane = t.plane; pl.sld = t.ld;
     IdxVec cols = iota_vec(k);
-    auto* dc = cx.scratch.template takeT<int32_t>(k);
-    MF_CUDA(cudaMemcpyAsync(dc, cols.data(), k * 4, cudaMemcpyHostToDevice, st_));
-    pl.rows = cf.d_upd32.template as<int32_t>(); pl.cols = dc; pl.nr = u; pl.nc = k;
+    pl.rows = cf.d_upd32.template as<int32_t>();
+    pl.cols = static_cast<const int32_t*>(cx.upload(cols.data(), (size_t)k * 4));
+    pl.nr = u; pl.nc = k;
     pl.dst = X.p; pl.dplane = X.plane; pl.dld = X.ld; pl.sign = T(-1);
-    auto* d = cx.scratch.template takeT<PlaceJob<T>>(1);
-    MF_CUDA(cudaMemcpyAsync(d, &pl, sizeof(pl), cudaMemcpyHostToDevice, st_));
-    launch_place<T>(d, 1, (int64_t)u * k, st_);
+    launch_place<T>(cx.stage(&pl, 1), 1, (int64_t)u * k, st_);
   }
-  MF_CUDA(cudaStreamSynchronize(st_));
-  cx.scratch.release(mk);
+  cx.scratch.release(mk);   // stream order makes later reuse of the scratch safe
 }
 
 template <typename T>
@@ -257,19 +271,11 @@ void CompressedPart<T>::backward(int fid, Blk<T>& X) {
   const size_t mk = cx.scratch.mark();
   Blk<T> xs = X.sub((int)cf.sep_begin, 0, s, k);
   Blk<T> g = new_blk<T>(cx.scratch, u, k);
-  cx.zero(g);
-  IdxVec cols = iota_vec(k);
-  auto* dc = cx.scratch.template takeT<int32_t>(k);
-  MF_CUDA(cudaMemcpyAsync(dc, cols.data(), k * 4, cudaMemcpyHostToDevice, st_));
   Blk2Job<T> j{};
   j.src = X.p; j.splane = X.plane; j.sld = X.ld; j.dst = g.p; j.dplane = g.plane; j.dld = g.ld;
-  j.rows = u; j.cols = k; j.alpha = T(1); j.mode = 1;
-  j.ridx = cf.d_upd32.template as<int32_t>(); j.cidx = dc;
-  {
-    auto* d = cx.scratch.template takeT<Blk2Job<T>>(1);
-    MF_CUDA(cudaMemcpyAsync(d, &j, sizeof(j), cudaMemcpyHostToDevice, st_));
-    launch_blk2<T>(d, 1, (int64_t)u * k, st_);
-  }
+  j.rows = u; j.cols = k; j.alpha = T(1); j.mode = 4;
+  j.ridx = cf.d_upd32.template as<int32_t>(); j.cidx = nullptr;
+  launch_blk2<T>(cx.stage(&j, 1), 1, (int64_t)u * k, st_);
   Blk<T> v = new_blk<T>(cx.scratch, s, k), z = new_blk<T>(cx.scratch, s, k);
   std::vector<const DBF<T>*> b{cf.F12.get()};
   std::vector<Blk<T>> gs{g}, vs{v};
@@ -278,13 +284,8 @@ void CompressedPart<T>::backward(int fid, Blk<T>& X) {
   Blk2Job<T> a{};
   a.src = z.p; a.splane = z.plane; a.sld = z.ld; a.dst = xs.p; a.dplane = xs.plane; a.dld = xs.ld;
   a.rows = s; a.cols = k; a.alpha = T(-1); a.mode = 2;
-  {
-    auto* d = cx.scratch.template takeT<Blk2Job<T>>(1);
-    MF_CUDA(cudaMemcpyAsync(d, &a, sizeof(a), cudaMemcpyHostToDevice, st_));
-    launch_blk2<T>(d, 1, (int64_t)s * k, st_);
-  }
-  MF_CUDA(cudaStreamSynchronize(st_));
-  cx.scratch.release(mk);
+  launch_blk2<T>(cx.stage(&a, 1), 1, (int64_t)s * k, st_);
+  cx.scratch.release(mk);   // stream order makes later reuse of the scratch safe
 }
 
 template class CompressedPart<float>;

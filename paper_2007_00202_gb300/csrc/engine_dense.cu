@@ -10,6 +10,7 @@
 // replayed by every factorization.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 
@@ -56,6 +57,7 @@ class DenseEngine : public EngineBase {
     P.knn = eo_.knn;
     comp_flops_ = 0;
     comp_seconds_ = 0;
+    for (auto& kv : sprog_) kv.second->drop_graph();   // compressed fronts move with every factorization
     if (comp_) {
       comp_->fronts.clear();
       comp_->cx.persist.release(0);
@@ -106,10 +108,25 @@ class DenseEngine : public EngineBase {
     const int64_t n = an_.n;
     T* X = sp.X.template as<T>();
     const int64_t xpl = n * nrhs;
+    static const bool trace = getenv("MF_TRACE") && getenv("MF_TRACE")[0] == '1';
+    std::chrono::steady_clock::time_point t0;
+    const int state0 = sp.state;
+    if (trace) {
+      MF_CUDA(cudaStreamSynchronize(st_));
+      t0 = std::chrono::steady_clock::now();
+    }
     launch_to_planar<T>(x, n, n, nrhs, nullptr, X, xpl, st_);
-    for (auto& op : sp.ops) op(st_);
+    run_solve_ops(sp);
     launch_from_planar<T>(X, xpl, n, nrhs, nullptr, y, n, st_);
     MF_CUDA(cudaGetLastError());
+    if (trace) {
+      auto t1 = std::chrono::steady_clock::now();
+      MF_CUDA(cudaStreamSynchronize(st_));
+      auto t2 = std::chrono::steady_clock::now();
+      fprintf(stderr, "[mf] precond nrhs %d state %d->%d  issue %.3f ms  total %.3f ms  (%d kernels)\n", nrhs, state0,
+              sp.state, std::chrono::duration<double, std::milli>(t1 - t0).count(),
+              std::chrono::duration<double, std::milli>(t2 - t0).count(), sp.glaunch);
+    }
   }
 
   double factor_flops() const override { return flops_ + comp_flops_; }
@@ -122,6 +139,23 @@ class DenseEngine : public EngineBase {
     DevMem X, tmp, ptrs, descs, tiles;
     std::vector<std::function<void(cudaStream_t)>> ops;
     int nlaunch = 0;
+    // CUDA graph of ops: state 0 = the next call runs eagerly and counts the staged bytes of
+    // the compressed fronts, 1 = the next call captures, 2 = replay, 3 = eager only
+    int state = 0;
+    cudaGraphExec_t exec = nullptr;
+    size_t blob = 0, blob_cap = 0, mark = 0;
+    int glaunch = 0;
+    char* hblob = nullptr;
+    DevMem dblob;
+    void drop_graph() {
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      state = 0;
+    }
+    ~SolveProg() {
+      drop_graph();
+      if (hblob) cudaFreeHost(hblob);
+    }
   };
 
   const Analysis& an_;
@@ -146,13 +180,99 @@ class DenseEngine : public EngineBase {
   double comp_flops_ = 0, comp_seconds_ = 0;
   int max_rank_ = 0;
   std::vector<cudaEvent_t> evs_;
+  cudaStream_t gs_ = nullptr;               // stream of the solve graphs (forked from and joined to st_)
+  cudaEvent_t gev_[2] = {nullptr, nullptr};
 
  public:
   ~DenseEngine() override {
     for (auto e : evs_) cudaEventDestroy(e);
+    sprog_.clear();
+    for (auto e : gev_)
+      if (e) cudaEventDestroy(e);
+    if (gs_) cudaStreamDestroy(gs_);
   }
 
  private:
+  // The solve program is the same launch sequence for every call with the same nrhs: the
+  // first call runs it eagerly (and sizes the job tables of the compressed fronts), the
+  // second captures it into a CUDA graph on gs_, later calls replay the graph.  A capture
+  // that fails (a synchronizing call inside, an error) leaves the program eager.
+  void run_solve_ops(SolveProg& sp) {
+    static const bool no_graph = getenv("MF_NO_GRAPH") && getenv("MF_NO_GRAPH")[0] == '1';
+    BFContext<T>* cx = comp_ ? &comp_->cx : nullptr;
+    auto eager = [&] {
+      for (auto& op : sp.ops) op(st_);
+    };
+    if (no_graph || sp.state == 3) return eager();
+    if (sp.state == 2 && cx && cx->scratch.mark() != sp.mark) sp.drop_graph();
+    if (sp.state == 2) {
+      MF_CUDA(cudaEventRecord(gev_[0], st_));
+      MF_CUDA(cudaStreamWaitEvent(gs_, gev_[0], 0));
+      MF_CUDA(cudaGraphLaunch(sp.exec, gs_));
+      count_launches(sp.glaunch);   // the kernel nodes the replay runs
+      MF_CUDA(cudaEventRecord(gev_[1], gs_));
+      MF_CUDA(cudaStreamWaitEvent(st_, gev_[1], 0));
+      return;
+    }
+    if (sp.state == 0) {
+      if (cx) cx->count_begin();
+      eager();
+      if (cx) sp.blob = cx->count_end();
+      sp.state = 1;
+      return;
+    }
+    // capture
+    if (!gs_) {
+      MF_CUDA(cudaStreamCreateWithFlags(&gs_, cudaStreamNonBlocking));
+      for (auto& e : gev_) MF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const size_t need = sp.blob + 4096;
+    if (cx && sp.blob_cap < need) {
+      if (sp.hblob) cudaFreeHost(sp.hblob);
+      sp.hblob = nullptr;
+      MF_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&sp.hblob), need, cudaHostAllocDefault));
+      sp.dblob.alloc(need);
+      sp.blob_cap = need;
+    }
+    if (cx) {
+      cx->flush();
+      sp.mark = cx->scratch.mark();
+      cx->st = gs_;
+      comp_->st_ = gs_;
+      cx->capture_begin(sp.hblob, sp.dblob.template as<char>(), sp.blob_cap);
+    }
+    cudaGraph_t g = nullptr;
+    const int64_t c0 = launch_count();
+    bool ok = cudaStreamBeginCapture(gs_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try {
+        for (auto& op : sp.ops) op(gs_);
+      } catch (...) {
+        ok = false;
+      }
+      if (cudaStreamEndCapture(gs_, &g) != cudaSuccess || !g) ok = false;
+    }
+    sp.glaunch = (int)(launch_count() - c0);
+    count_launches(-sp.glaunch);   // captured, not run
+    if (cx) {
+      cx->st = st_;
+      comp_->st_ = st_;
+      cx->scratch.release(sp.mark);
+      if (!cx->capture_end()) ok = false;   // copies the job tables to their device twin
+    }
+    if (ok && cudaGraphInstantiate(&sp.exec, g, 0) != cudaSuccess) {
+      sp.exec = nullptr;
+      ok = false;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();   // a failed capture leaves its error behind
+    if (!ok) {
+      sp.state = 3;
+      return eager();
+    }
+    sp.state = 2;
+    run_solve_ops(sp);
+  }
 
   const int32_t* flist(size_t lv) const { return flists_d_.template as<int32_t>() + level_off_[lv]; }
 

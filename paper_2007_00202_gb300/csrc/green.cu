@@ -171,11 +171,8 @@ int mf_green_build(int32_t nblk, const int32_t* m, double k, double spacing, dou
       for (size_t q = 0; q < lst.size(); ++q) {
         if (lst[q].first.empty() || lst[q].second.empty()) continue;
         mf::GreenJob<float> j;
-        auto* dx = cx->scratch.takeT<int32_t>(lst[q].first.size());
-        auto* dy = cx->scratch.takeT<int32_t>(lst[q].second.size());
-        MF_CUDA(cudaMemcpyAsync(dx, lst[q].first.data(), lst[q].first.size() * 4, cudaMemcpyHostToDevice, st));
-        MF_CUDA(cudaMemcpyAsync(dy, lst[q].second.data(), lst[q].second.size() * 4, cudaMemcpyHostToDevice, st));
-        j.X = dx; j.Y = dy;
+        j.X = static_cast<const int32_t*>(cx->upload(lst[q].first.data(), lst[q].first.size() * 4));
+        j.Y = static_cast<const int32_t*>(cx->upload(lst[q].second.data(), lst[q].second.size() * 4));
         j.nx = (int)lst[q].first.size(); j.ny = (int)lst[q].second.size();
         j.dst = dst[q].p; j.dplane = dst[q].plane; j.dld = dst[q].ld;
         jobs.push_back(j);
@@ -183,7 +180,7 @@ int mf_green_build(int32_t nblk, const int32_t* m, double k, double spacing, dou
       }
       if (jobs.empty()) return;
       auto* dj = cx->scratch.takeT<mf::GreenJob<float>>(jobs.size());
-      MF_CUDA(cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(jobs[0]), cudaMemcpyHostToDevice, st));
+      cx->h2d(dj, jobs.data(), jobs.size() * sizeof(jobs[0]));
       int bx = (int)std::min<int64_t>(512, (mx + 255) / 256);
       mf::count_launches(1);
       mf::k_green<float><<<dim3(bx, (unsigned)jobs.size()), 256, 0, st>>>(dj, dP, dQ, k);

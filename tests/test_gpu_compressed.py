@@ -66,3 +66,25 @@ def test_compressed_yee(g):
     x, info = h.mf_solve(b)
     A = p.to_scipy()
     assert np.max(np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)) <= 1e-8
+
+
+def test_solve_graph_replay_matches_eager(g):
+    # The solve program runs eagerly on its first call, is captured into a CUDA graph on the
+    # second and replayed afterwards: one preconditioner application (no refinement) must give
+    # the same x every time, and again after a refactorization drops the graph.  Sibling
+    # fronts add into their parents' right-hand sides with atomics, so sums may round in a
+    # different order from call to call (complex64: about 1e-6 relative here).
+    p = w.helmholtz7(16, 8)
+    b = w.rhs_gaussian(p, 3, 5)
+    h = g.analyze_problem(p, nmin_sep=64, leaf_size=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_NONE)
+    h.mf_factor(1e-4)
+    assert h.mf_stats()["ncompressed"] >= 3
+    xs = [h.mf_solve(b)[0] for _ in range(4)]
+    for x in xs[1:]:
+        assert np.linalg.norm(x - xs[0]) <= 1e-4 * np.linalg.norm(xs[0])
+    h.mf_factor(1e-4)
+    ys = [h.mf_solve(b)[0] for _ in range(3)]
+    for y in ys:
+        assert np.linalg.norm(y - xs[0]) <= 1e-4 * np.linalg.norm(xs[0])
+    A = p.to_scipy()
+    assert np.max(np.linalg.norm(A @ xs[0] - b, axis=0) / np.linalg.norm(b, axis=0)) <= 5e-2
