@@ -170,6 +170,22 @@ int mf_gemm_c64(int32_t engine, int32_t m, int32_t n, int32_t k, const float* A,
                 void* stream);
 
 /*
+ * Component entry point of the narrow GEMM kernel of the solve (Alg. 1, last line:
+ * the front products with the block of right-hand sides) and of the butterfly level
+ * products with blocks of vectors (Sec. 3).  One planar complex64 product on device
+ * memory:
+ *   C = alpha * op(A) * B + beta * C,  op(A) = A (trans_a = 0, A: m x k) or A^T
+ *   (trans_a = 1, A stored k x m), B: k x n, C: m x n, all row-major, n <= 64,
+ *   each matrix given by its real plane, leading dimension and imaginary-plane offset.
+ * ksplit: number of CTAs of a thread-block cluster sharing one 32-row tile's K range
+ * (1, 2, 4 or 8), 0 = the library's choice.  No alignment requirements.
+ * Runs on `stream` and waits for it.  Errors: MF_ERR_ARG, MF_ERR_CUDA.
+ */
+int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const float* A, int64_t lda, int64_t pla,
+                     const float* B, int64_t ldb, int64_t plb, float* C, int64_t ldc, int64_t plc, float alpha,
+                     float beta, int32_t ksplit, void* stream);
+
+/*
  * Component entry point of the batched row interpolative decomposition (Sec. 3):
  * for each of nmat complex64 matrices M_q (m x n), a column-pivoted Householder
  * QR of M_q^T truncated at the first k with |R_{k+1,k+1}| <= tol |R_11| (at most

@@ -299,19 +299,31 @@ void BFContext<T>::check_status() {
 template <typename T>
 void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
   std::vector<GemmDesc<T>> D;
-  std::vector<GemmTile> tl;
+  int maxn = 0, maxk = 1;
   for (auto& d : descs) {
     if (d.m <= 0 || d.n <= 0) continue;
-    int idx = (int)D.size();
     D.push_back(d);
     flops += 8.0 * d.m * d.n * d.k;
-    for (int i = 0; i < (d.m + GEMM_TILE - 1) / GEMM_TILE; ++i)
-      for (int j = 0; j < (d.n + GEMM_TILE - 1) / GEMM_TILE; ++j) tl.push_back({idx, i, j, 0});
+    maxn = std::max(maxn, (int)d.n);
+    maxk = std::max(maxk, (int)d.k);
   }
-  if (tl.empty()) return;
+  if (D.empty()) return;
+  // narrow products (blocks of vectors): 32-row tiles of the streaming kernel; else 64 x 64 tiles
+  const int nb = gemm_nrhs_width(maxn, sizeof(T));
+  const int tr = nb ? GEMM_NRHS_ROWS : GEMM_TILE;
+  std::vector<GemmTile> tl;
+  for (size_t idx = 0; idx < D.size(); ++idx) {
+    const auto& d = D[idx];
+    const int tn = nb ? 1 : (d.n + GEMM_TILE - 1) / GEMM_TILE;
+    for (int i = 0; i < (d.m + tr - 1) / tr; ++i)
+      for (int j = 0; j < tn; ++j) tl.push_back({(int)idx, i, j, 0});
+  }
   const GemmDesc<T>* dd = static_cast<const GemmDesc<T>*>(upload(D.data(), D.size() * sizeof(GemmDesc<T>)));
   const GemmTile* dt = stage(tl.data(), tl.size());
-  launch_gemm<T>(dd, dt, (int)tl.size(), st);
+  if (nb)
+    launch_gemm_nrhs<T>(dd, dt, (int)tl.size(), nb, gemm_nrhs_split((int)tl.size(), maxk), st);
+  else
+    launch_gemm<T>(dd, dt, (int)tl.size(), st);
 }
 
 template <typename T>

@@ -529,6 +529,35 @@ int mf_gemm_c64(int32_t engine, int32_t m, int32_t n, int32_t k, const float* A,
   });
 }
 
+int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const float* A, int64_t lda, int64_t pla,
+                     const float* B, int64_t ldb, int64_t plb, float* C, int64_t ldc, int64_t plc, float alpha,
+                     float beta, int32_t ksplit, void* stream) {
+  if (m <= 0 || n <= 0 || n > 64 || k <= 0 || !A || !B || !C || (trans_a != 0 && trans_a != 1) ||
+      lda < (trans_a ? m : k) || ldb < n || ldc < n)
+    return fail(nullptr, MF_ERR_ARG, "invalid narrow-GEMM arguments");
+  if (ksplit != 0 && ksplit != 1 && ksplit != 2 && ksplit != 4 && ksplit != 8)
+    return fail(nullptr, MF_ERR_ARG, "ksplit must be 0, 1, 2, 4 or 8");
+  return guarded(nullptr, [&]() -> int {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    mf::GemmDesc<float> d;
+    d.m = m; d.n = n; d.k = k; d.transA = trans_a; d.transB = 0; d.alpha = alpha; d.beta = beta;
+    d.A = {const_cast<float*>(A), pla, lda};
+    d.B = {const_cast<float*>(B), plb, ldb};
+    d.C = {C, plc, ldc};
+    std::vector<mf::GemmTile> tl;
+    for (int i = 0; i < (m + mf::GEMM_NRHS_ROWS - 1) / mf::GEMM_NRHS_ROWS; ++i) tl.push_back({0, i, 0, 0});
+    const int ks = ksplit ? ksplit : mf::gemm_nrhs_split((int)tl.size(), k);
+    DevMem dd, dt;
+    mf::upload(dd, std::vector<mf::GemmDesc<float>>{d}, st);
+    mf::upload(dt, tl, st);
+    mf::launch_gemm_nrhs<float>(dd.as<mf::GemmDesc<float>>(), dt.as<mf::GemmTile>(), (int)tl.size(),
+                                mf::gemm_nrhs_width(n, sizeof(float)), ks, st);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaStreamSynchronize(st));
+    return MF_OK;
+  });
+}
+
 int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol, int32_t max_rank, float* U,
                   int32_t* sk, int32_t* rank, void* stream) {
   if (nmat <= 0 || m <= 0 || n <= 0 || m > 2048 || n > 8192 || !M || !U || !sk || !rank || !(tol >= 0))

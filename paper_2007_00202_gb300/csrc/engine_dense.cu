@@ -283,13 +283,13 @@ class DenseEngine : public EngineBase {
     size_t nd;
   };
   GemmRef add_gemm(std::vector<GemmDesc<T>>& D, std::vector<GemmTile>& Tl, const std::vector<GemmDesc<T>>& batch,
-                   int tile = GEMM_TILE) {
+                   int tile = GEMM_TILE, bool row_tiles_only = false) {
     GemmRef r{D.size(), Tl.size(), 0, 0};
     for (auto& d : batch) {
       if (d.m <= 0 || d.n <= 0) continue;
       int idx = (int)(D.size() - r.d0);
       D.push_back(d);
-      int tm = (d.m + tile - 1) / tile, tn = (d.n + tile - 1) / tile;
+      int tm = (d.m + tile - 1) / tile, tn = row_tiles_only ? 1 : (d.n + tile - 1) / tile;
       for (int i = 0; i < tm; ++i)
         for (int j = 0; j < tn; ++j) Tl.push_back({idx, i, j, 0});
     }
@@ -644,7 +644,23 @@ class DenseEngine : public EngineBase {
     T* X = sp->X.template as<T>();
     const int64_t xpl = n * nrhs;
     SolveProg* spp = sp.get();
+    // narrow products (n = nrhs): 32-row tiles of the streaming kernel, K split over a cluster when
+    // a level has few row tiles; wider ones: the square-tile SIMT kernel
+    const int nb = gemm_nrhs_width(nrhs, sizeof(T));
     auto gemm_op = [&](const std::vector<GemmDesc<T>>& b) {
+      if (nb) {
+        GemmRef g = add_gemm(D, Tl, b, GEMM_NRHS_ROWS, true);
+        if (!g.nt) return;
+        int maxk = 1;
+        for (auto& x : b) maxk = std::max(maxk, (int)x.k);
+        const int ks = gemm_nrhs_split(g.nt, maxk);
+        sp->ops.push_back([spp, g, nb, ks](cudaStream_t st) {
+          launch_gemm_nrhs<T>(spp->descs.template as<GemmDesc<T>>() + g.d0, spp->tiles.template as<GemmTile>() + g.t0,
+                              g.nt, nb, ks, st);
+        });
+        sp->nlaunch++;
+        return;
+      }
       GemmRef g = add_gemm(D, Tl, b);
       if (g.nt) {
         sp->ops.push_back([spp, g](cudaStream_t st) {

@@ -97,6 +97,9 @@ SIGNATURES = {
                                         _P]),
     "mf_gemm_c64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int64, C.c_int64, _P, C.c_int64,
                               C.c_int64, _P, C.c_int64, C.c_int64, C.c_float, C.c_float, _P]),
+    "mf_gemm_nrhs_c64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int64, C.c_int64, _P,
+                                   C.c_int64, C.c_int64, _P, C.c_int64, C.c_int64, C.c_float, C.c_float, C.c_int32,
+                                   _P]),
     "mf_profile_read": (C.c_int, [_P, C.POINTER(mf_kernel_profile_t)]),
     "mf_analysis_sizes": (C.c_int, [_P, C.POINTER(mf_analysis_sizes_t)]),
     "mf_analysis_export": (C.c_int, [_P, _I64P, _I64P, _I64P, _I32P, _I64P, _I64P]),
@@ -273,6 +276,12 @@ def mf_gemm_c64(engine, m, n, k, A, lda, pla, B, ldb, plb, C_, ldc, plc, alpha, 
     """Component GEMM on device pointers (ints); see include/mf.h."""
     _check(lib().mf_gemm_c64(engine, m, n, k, C.c_void_p(A), lda, pla, C.c_void_p(B), ldb, plb, C.c_void_p(C_), ldc,
                              plc, alpha, beta, C.c_void_p(stream)))
+
+
+def mf_gemm_nrhs_c64(trans_a, m, n, k, A, lda, pla, B, ldb, plb, C_, ldc, plc, alpha, beta, ksplit=0, stream=0):
+    """Component narrow GEMM (solve / butterfly level products) on device pointers (ints); see include/mf.h."""
+    _check(lib().mf_gemm_nrhs_c64(trans_a, m, n, k, C.c_void_p(A), lda, pla, C.c_void_p(B), ldb, plb, C.c_void_p(C_),
+                                  ldc, plc, alpha, beta, ksplit, C.c_void_p(stream)))
 
 
 def mf_row_id_c64(nmat, m, n, M, tol, max_rank, U, sk, rank, stream=0):

@@ -48,3 +48,29 @@ def test_gemm_nt_against_fp64(tk, engine, m, n, k, beta):
     assert err < {0: 2e-5, 1: 4e-3, 2: 2e-5}[engine], err
     # the padding column of C (beyond n) is untouched
     assert float(dC[0, :, n:].abs().max()) == float(_planar(torch, C0, ldc)[0, :, n:].abs().max())
+
+
+@pytest.mark.parametrize("trans_a", [0, 1])
+@pytest.mark.parametrize("m,n,k,beta,ksplit", [(3072, 16, 3072, 0.0, 0), (40, 16, 2000, 1.0, 0), (70, 3, 33, 1.0, 0),
+                                               (1, 1, 1, 0.0, 1), (300, 64, 129, 1.0, 2), (129, 33, 500, 1.0, 8),
+                                               (64, 17, 100, 0.0, 4)])
+def test_gemm_nrhs_against_fp64(tk, trans_a, m, n, k, beta, ksplit):
+    # the solve's narrow products: C = -op(A) B + beta C, n <= 64, K split over a cluster
+    import paper_2007_00202_gb300.mf as mf
+    torch = tk
+    rng = np.random.default_rng(7 * m + n + k + trans_a)
+    A = rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))
+    B = rng.standard_normal((k, n)) + 1j * rng.standard_normal((k, n))
+    C0 = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+    As = A.T.copy() if trans_a else A            # stored k x m when transposed
+    lda = As.shape[1] + 1
+    ldb, ldc = n + 2, n + 1
+    dA, dB, dC = _planar(torch, As, lda), _planar(torch, B, ldb), _planar(torch, C0, ldc)
+    mf.mf_gemm_nrhs_c64(trans_a, m, n, k, dA.data_ptr(), lda, As.shape[0] * lda, dB.data_ptr(), ldb, k * ldb,
+                        dC.data_ptr(), ldc, m * ldc, -1.0, beta, ksplit, 0)
+    torch.cuda.synchronize()
+    out = dC[0, :, :n].double().cpu().numpy() + 1j * dC[1, :, :n].double().cpu().numpy()
+    ref = -(A @ B) + beta * C0
+    scale = np.sqrt(k) * np.abs(A).max() * np.abs(B).max()
+    assert np.abs(out - ref).max() / scale < 2e-5
+    assert float(dC[0, :, n:].abs().max()) == float(_planar(torch, C0, ldc)[0, :, n:].abs().max())
