@@ -175,7 +175,7 @@ int mf_gemm_c64(int32_t engine, int32_t m, int32_t n, int32_t k, const float* A,
  * products with blocks of vectors (Sec. 3).  One planar complex64 product on device
  * memory:
  *   C = alpha * op(A) * B + beta * C,  op(A) = A (trans_a = 0, A: m x k) or A^T
- *   (trans_a = 1, A stored k x m), B: k x n, C: m x n, all row-major, n <= 64,
+ *   (trans_a = 1, A stored k x m), B: k x n, C: m x n, all row-major, n <= 128,
  *   each matrix given by its real plane, leading dimension and imaginary-plane offset.
  * ksplit: number of CTAs of a thread-block cluster sharing one 32-row tile's K range
  * (1, 2, 4 or 8), 0 = the library's choice.  No alignment requirements.

@@ -308,13 +308,13 @@ void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
     maxk = std::max(maxk, (int)d.k);
   }
   if (D.empty()) return;
-  // narrow products (blocks of vectors): 32-row tiles of the streaming kernel; else 64 x 64 tiles
+  // narrow products (blocks of vectors, n <= 128): 32-row tiles of the streaming kernel; else 64 x 64 tiles
   const int nb = gemm_nrhs_width(maxn, sizeof(T));
   const int tr = nb ? GEMM_NRHS_ROWS : GEMM_TILE;
   std::vector<GemmTile> tl;
   for (size_t idx = 0; idx < D.size(); ++idx) {
     const auto& d = D[idx];
-    const int tn = nb ? 1 : (d.n + GEMM_TILE - 1) / GEMM_TILE;
+    const int tn = (d.n + (nb ? nb : GEMM_TILE) - 1) / (nb ? nb : GEMM_TILE);
     for (int i = 0; i < (d.m + tr - 1) / tr; ++i)
       for (int j = 0; j < tn; ++j) tl.push_back({(int)idx, i, j, 0});
   }
@@ -358,8 +358,10 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
   sk.assign(nj, {});
   Us.assign(nj, Blk<T>());
   if (!nj) return;
-  std::vector<IdJob<T>> jobs;
+  std::vector<IdJob<T>> jobs, sjobs;
   std::vector<size_t> which;
+  int smax_m = 1, smax_n = 1;
+  size_t sbytes = 0;
   int32_t* dsk = nullptr;
   int32_t* drk = scratch.takeT<int32_t>(nj);
   std::vector<int> kmaxv(nj, 0);
@@ -398,14 +400,30 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
     j.ldu = (int32_t)U.ld;
     j.sk = dsk + skoffv[q];
     j.rank = drk + q;
-    j.work = scratch.takeT<T>(2 * (size_t)m * n);
     j.wplane = (int64_t)m * n;
-    jobs.push_back(j);
+    const size_t sb = row_id_smem_bytes(m, n, sizeof(T), true);
+    if (sb <= kRowIdSmemCap) {   // QR work in shared memory
+      j.work = nullptr;
+      sjobs.push_back(j);
+      smax_m = std::max(smax_m, m);
+      smax_n = std::max(smax_n, n);
+      sbytes = std::max(sbytes, sb);
+    } else {
+      j.work = scratch.takeT<T>(2 * (size_t)m * n);
+      jobs.push_back(j);
+      max_m = std::max(max_m, m);
+      max_n = std::max(max_n, n);
+    }
     which.push_back(q);
-    max_m = std::max(max_m, m);
-    max_n = std::max(max_n, n);
   }
   MF_CUDA(cudaMemsetAsync(drk, 0, nj * 4, st));
+  // matrices whose QR work fits in shared memory, then the others (work in global memory)
+  if (!sjobs.empty()) {
+    const IdJob<T>* dj = stage(sjobs.data(), sjobs.size());
+    if (launch_row_id<T>(dj, (int)sjobs.size(), smax_m, smax_n, (T)tol, max_rank, st, true, sbytes) != 0)
+      throw std::runtime_error("ID block too large for the shared-memory row-ID kernel");
+    n_id += (int64_t)sjobs.size();
+  }
   if (!jobs.empty()) {
     const IdJob<T>* dj = stage(jobs.data(), jobs.size());
     if (launch_row_id<T>(dj, (int)jobs.size(), max_m, max_n, (T)tol, max_rank, st) != 0)

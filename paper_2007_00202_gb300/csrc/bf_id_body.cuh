@@ -1,6 +1,8 @@
 // Device body of the batched row interpolative decomposition (Sec. 3), shared
 // by the batched kernel and its fixed-scratch variant.  One CTA (256 threads)
-// per matrix; dynamic shared memory of sizeof(T) * (2 n + m) + 4 m bytes.
+// per matrix; dynamic shared memory of row_id_smem_bytes(m, n, work_in_smem):
+// the QR work matrix (2 m n values) sits there too when work_in_smem, else in
+// jb.work.
 //
 // Row ID of M (m x n): column-pivoted Householder QR of M^T, truncated at the
 // first k with |R_{k+1,k+1}| <= tol |R_11| (or k = kmax), then
@@ -14,10 +16,12 @@
 namespace mf {
 
 template <typename T>
-__device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t max_rank) {
+__device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t max_rank, bool work_in_smem) {
   const int m = jb.m, n = jb.n;
-  extern __shared__ unsigned char smraw[];
-  T* vr = reinterpret_cast<T*>(smraw);       // Householder vector, n entries (re, im)
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Wr = work_in_smem ? reinterpret_cast<T*>(smraw) : jb.work;
+  T* Wi = work_in_smem ? Wr + (int64_t)m * n : jb.work + jb.wplane;
+  T* vr = reinterpret_cast<T*>(smraw) + (work_in_smem ? 2 * (int64_t)m * n : 0);   // Householder vector (re, im)
   T* vi = vr + n;
   T* nrm = vi + n;                           // remaining squared norms, by position
   int* perm = reinterpret_cast<int*>(nrm + m);
@@ -26,8 +30,6 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
   __shared__ T sh_alpha_r, sh_alpha_i, sh_scale, sh_ref;
   __shared__ int sh_p, sh_stop;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  T* Wr = jb.work;
-  T* Wi = jb.work + jb.wplane;
   // copy M to the work matrix (ld = n) and compute the row norms
   for (int r = warp; r < m; r += nw) {
     const T* mr = jb.M + (int64_t)r * jb.ld;

@@ -15,22 +15,23 @@ namespace mf {
 // Batched row ID (Sec. 3), one CTA per matrix (body in bf_id_body.cuh).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_row_id(const IdJob<T>* jobs, T tol, int32_t max_rank) {
-  row_id_body<T>(jobs[blockIdx.x], tol, max_rank);
+__global__ void __launch_bounds__(256) k_row_id(const IdJob<T>* jobs, T tol, int32_t max_rank, int work_in_smem) {
+  row_id_body<T>(jobs[blockIdx.x], tol, max_rank, work_in_smem != 0);
 }
 
 template <typename T>
-int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st) {
+int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st,
+                  bool work_in_smem, size_t smem_bytes) {
   if (njobs <= 0) return 0;
-  size_t sm = sizeof(T) * (2 * (size_t)max_n + max_m) + sizeof(int) * (size_t)max_m;
-  if (sm > 200 * 1024) return -1;
+  const size_t sm = smem_bytes ? smem_bytes : row_id_smem_bytes(max_m, max_n, sizeof(T), work_in_smem);
+  if (sm > kRowIdSmemCap) return -1;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_row_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_row_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
     attr = true;
   }
   count_launches(1);
-  k_row_id<T><<<njobs, 256, sm, st>>>(d_jobs, tol, max_rank);
+  k_row_id<T><<<njobs, 256, sm, st>>>(d_jobs, tol, max_rank, work_in_smem ? 1 : 0);
   return 0;
 }
 
@@ -504,7 +505,7 @@ int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int max_r, int
 }
 
 #define MF_BF_INST(T)                                                                                            \
-  template int launch_row_id<T>(const IdJob<T>*, int, int, int, T, int, cudaStream_t);                          \
+  template int launch_row_id<T>(const IdJob<T>*, int, int, int, T, int, cudaStream_t, bool, size_t);                          \
   template void launch_sketch<T>(const SketchGroup*, int, int, T*, int64_t, int, cudaStream_t);                 \
   template void launch_gather_rows<T>(const GatherJob<T>*, int, int64_t, cudaStream_t);                         \
   template void launch_front_entries<T>(const FrontEntryJob<T>*, int, int64_t, const FrontCtx<T>*, const int64_t*, \

@@ -157,8 +157,17 @@ template <typename T>
 int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int max_r, int max_w, bool work_in_smem,
                  int32_t* status, cudaStream_t st);
 
+// Dynamic shared memory of one row-ID CTA (m x n matrix); the work matrix adds 2 m n values.
+// launch_row_id takes the largest per-job figure (smem_bytes), or computes it from max_m, max_n.
+inline size_t row_id_smem_bytes(int m, int n, size_t elem, bool work_in_smem) {
+  size_t b = elem * (2 * (size_t)n + m) + sizeof(int) * (size_t)m;
+  if (work_in_smem) b += elem * 2 * (size_t)m * n;
+  return b;
+}
+constexpr size_t kRowIdSmemCap = 200 * 1024;
 template <typename T>
-int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st);
+int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st,
+                  bool work_in_smem = false, size_t smem_bytes = 0);
 template <typename T>
 void launch_sketch(const SketchGroup* d_groups, int ngroups, int max_elems, T* out, int64_t plane, int ld,
                    cudaStream_t st);

@@ -532,7 +532,7 @@ int mf_gemm_c64(int32_t engine, int32_t m, int32_t n, int32_t k, const float* A,
 int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const float* A, int64_t lda, int64_t pla,
                      const float* B, int64_t ldb, int64_t plb, float* C, int64_t ldc, int64_t plc, float alpha,
                      float beta, int32_t ksplit, void* stream) {
-  if (m <= 0 || n <= 0 || n > 64 || k <= 0 || !A || !B || !C || (trans_a != 0 && trans_a != 1) ||
+  if (m <= 0 || n <= 0 || n > 128 || k <= 0 || !A || !B || !C || (trans_a != 0 && trans_a != 1) ||
       lda < (trans_a ? m : k) || ldb < n || ldc < n)
     return fail(nullptr, MF_ERR_ARG, "invalid narrow-GEMM arguments");
   if (ksplit != 0 && ksplit != 1 && ksplit != 2 && ksplit != 4 && ksplit != 8)
@@ -545,13 +545,14 @@ int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const flo
     d.B = {const_cast<float*>(B), plb, ldb};
     d.C = {C, plc, ldc};
     std::vector<mf::GemmTile> tl;
-    for (int i = 0; i < (m + mf::GEMM_NRHS_ROWS - 1) / mf::GEMM_NRHS_ROWS; ++i) tl.push_back({0, i, 0, 0});
+    const int nb = mf::gemm_nrhs_width(n, sizeof(float));
+    for (int i = 0; i < (m + mf::GEMM_NRHS_ROWS - 1) / mf::GEMM_NRHS_ROWS; ++i)
+      for (int j = 0; j < (n + nb - 1) / nb; ++j) tl.push_back({0, i, j, 0});
     const int ks = ksplit ? ksplit : mf::gemm_nrhs_split((int)tl.size(), k);
     DevMem dd, dt;
     mf::upload(dd, std::vector<mf::GemmDesc<float>>{d}, st);
     mf::upload(dt, tl, st);
-    mf::launch_gemm_nrhs<float>(dd.as<mf::GemmDesc<float>>(), dt.as<mf::GemmTile>(), (int)tl.size(),
-                                mf::gemm_nrhs_width(n, sizeof(float)), ks, st);
+    mf::launch_gemm_nrhs<float>(dd.as<mf::GemmDesc<float>>(), dt.as<mf::GemmTile>(), (int)tl.size(), nb, ks, st);
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaStreamSynchronize(st));
     return MF_OK;

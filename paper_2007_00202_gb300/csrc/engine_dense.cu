@@ -283,13 +283,14 @@ class DenseEngine : public EngineBase {
     size_t nd;
   };
   GemmRef add_gemm(std::vector<GemmDesc<T>>& D, std::vector<GemmTile>& Tl, const std::vector<GemmDesc<T>>& batch,
-                   int tile = GEMM_TILE, bool row_tiles_only = false) {
+                   int tile = GEMM_TILE, int col_tile = 0) {
     GemmRef r{D.size(), Tl.size(), 0, 0};
     for (auto& d : batch) {
       if (d.m <= 0 || d.n <= 0) continue;
       int idx = (int)(D.size() - r.d0);
       D.push_back(d);
-      int tm = (d.m + tile - 1) / tile, tn = row_tiles_only ? 1 : (d.n + tile - 1) / tile;
+      const int ct = col_tile ? col_tile : tile;
+      int tm = (d.m + tile - 1) / tile, tn = (d.n + ct - 1) / ct;
       for (int i = 0; i < tm; ++i)
         for (int j = 0; j < tn; ++j) Tl.push_back({idx, i, j, 0});
     }
@@ -649,7 +650,7 @@ class DenseEngine : public EngineBase {
     const int nb = gemm_nrhs_width(nrhs, sizeof(T));
     auto gemm_op = [&](const std::vector<GemmDesc<T>>& b) {
       if (nb) {
-        GemmRef g = add_gemm(D, Tl, b, GEMM_NRHS_ROWS, true);
+        GemmRef g = add_gemm(D, Tl, b, GEMM_NRHS_ROWS, nb);
         if (!g.nt) return;
         int maxk = 1;
         for (auto& x : b) maxk = std::max(maxk, (int)x.k);

@@ -1,10 +1,10 @@
 // Batched planar complex GEMM for narrow products, C = alpha op(A) B + beta C with
-// n <= NB (NB = 16, 32, or 64 for complex64): the solve's front products (n = number of right-hand
+// n <= 128, in column tiles of NB = 16, 32 (or 64 for complex64): the solve's front products (n = number of right-hand
 // sides, Alg. 1's last line) and the butterfly level products with blocks of vectors
 // (Sec. 3).  These stream op(A) once and are bound by HBM (or, for n >= 16, by the
 // FP32 FMA rate), not by a square tile's reuse.
 //
-// One CTA (4 warps) owns 32 rows of C and all of its <= NB columns.  K advances in
+// One CTA (4 warps) owns 32 rows and NB columns of C (tile {desc, tm, tn}).  K advances in
 // tiles of 32: the A tile (32 x 32) and the B tile (32 x NB) are staged in shared
 // memory (register double buffering: the next tile's loads are in flight while the
 // current one is multiplied); each warp takes 8 of the tile's k, lane = row, with the
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict
   const GemmTile t = tiles[blockIdx.x];
   const GemmDesc<T> d = descs[t.desc];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = t.tm * NR_BM;
+  const int m0 = t.tm * NR_BM, n0 = t.tn * NB;
   const int nkt = (d.k + NR_BK - 1) / NR_BK;
   const int ks = gridDim.y, kr = blockIdx.y;
   const int kt0 = (int)((int64_t)nkt * kr / ks), kt1 = (int)((int64_t)nkt * (kr + 1) / ks);
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict
     }
 #pragma unroll
     for (int e = 0; e < BE; ++e) {
-      const int nn = b_nn + b_dn * e, gk = k0 + b_kk + b_dk * e;
+      const int nn = n0 + b_nn + b_dn * e, gk = k0 + b_kk + b_dk * e;
       T vr = T(0), vi = T(0);
       if (nn < d.n && gk < d.k) {
         const int64_t off = d.transB == 0 ? (int64_t)gk * d.B.ld + nn : (int64_t)nn * d.B.ld + gk;
@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict
   for (int e = tid; e < NB * NR_BM; e += 128) {
     const int j = e / NR_BM, r = e % NR_BM;
     const int gm = m0 + r;
-    if (gm >= d.m || j >= d.n) continue;
-    const int64_t off = (int64_t)gm * d.C.ld + j;
+    if (gm >= d.m || n0 + j >= d.n) continue;
+    const int64_t off = (int64_t)gm * d.C.ld + n0 + j;
     T vr = d.alpha * part[j * NR_BM + r], vi = d.alpha * part[(NB + j) * NR_BM + r];
     if (d.beta != T(0)) {
       vr += d.beta * Cr[off];
@@ -198,7 +198,8 @@ int gemm_nrhs_width(int max_n, size_t elem) {
   if (max_n <= 16) return 16;
   if (max_n <= 32) return 32;
   if (max_n <= 64 && elem == 4) return 64;
-  return 0;
+  if (max_n > 128) return 0;
+  return (max_n + 15) / 16 * 16 < (max_n + 31) / 32 * 32 ? 16 : 32;   // column tiles of 16 or 32
 }
 
 int gemm_nrhs_split(int ntiles, int max_k) {

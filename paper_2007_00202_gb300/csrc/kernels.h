@@ -17,14 +17,14 @@ void launch_gemm(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles,
 // Tile size of the SIMT GEMM (both dimensions).
 constexpr int GEMM_TILE = 64;
 
-// Narrow planar complex GEMM (n <= 64) over a tile list of 32-row tiles {desc, tm, 0}:
-// nb = gemm_nrhs_width(max n) selects the column capacity, ksplit the number of CTAs of
-// a thread-block cluster that share one tile's K range (gemm_nrhs_split).
+// Narrow planar complex GEMM (n <= 128) over a tile list of tiles {desc, tm, tn} of 32 rows
+// and nb columns: nb = gemm_nrhs_width(max n) (a desc has ceil(n / nb) column tiles), ksplit
+// the number of CTAs of a thread-block cluster that share one tile's K range (gemm_nrhs_split).
 template <typename T>
 void launch_gemm_nrhs(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, int nb, int ksplit,
                       cudaStream_t st);
 constexpr int GEMM_NRHS_ROWS = 32;
-int gemm_nrhs_width(int max_n, size_t elem);   // 16, 32, 64 (complex64 only), else 0
+int gemm_nrhs_width(int max_n, size_t elem);   // 16, 32, 64 (complex64 only); 0 when max_n > 128
 int gemm_nrhs_split(int ntiles, int max_k);
 
 // tcgen05 (kind::tf32) planar complex GEMM, "NT" form only (transA = 0, transB = 1),

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_row_id_fixed_scratch(const float* M, in
   jb.rank = rank + q;
   jb.work = scratch + (size_t)2 * m * n * q;
   jb.wplane = (int64_t)m * n;
-  row_id_body<float>(jb, tol, max_rank);
+  row_id_body<float>(jb, tol, max_rank, false);
 }
 
 constexpr int kMaxDevices = 64;

@@ -53,9 +53,10 @@ def test_gemm_nt_against_fp64(tk, engine, m, n, k, beta):
 @pytest.mark.parametrize("trans_a", [0, 1])
 @pytest.mark.parametrize("m,n,k,beta,ksplit", [(3072, 16, 3072, 0.0, 0), (40, 16, 2000, 1.0, 0), (70, 3, 33, 1.0, 0),
                                                (1, 1, 1, 0.0, 1), (300, 64, 129, 1.0, 2), (129, 33, 500, 1.0, 8),
-                                               (64, 17, 100, 0.0, 4)])
+                                               (64, 17, 100, 0.0, 4), (200, 72, 300, 1.0, 0),
+                                               (33, 128, 64, 0.0, 2)])
 def test_gemm_nrhs_against_fp64(tk, trans_a, m, n, k, beta, ksplit):
-    # the solve's narrow products: C = -op(A) B + beta C, n <= 64, K split over a cluster
+    # the solve's narrow products: C = -op(A) B + beta C, n <= 128 (column tiles), K split over a cluster
     import paper_2007_00202_gb300.mf as mf
     torch = tk
     rng = np.random.default_rng(7 * m + n + k + trans_a)
