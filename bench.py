@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--nmin", type=int, default=1024, help="separators >= nmin are HOD-BF compressed")
+    ap.add_argument("--no-dense", action="store_true", help="skip the all-dense complex64 comparison step")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -126,25 +128,92 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(seconds_cap=30.0):
-    """The FP64 oracle (dense multifrontal + solve, 16 RHS) on a bounded sample: the same
-    Helmholtz operator at 32^3, timed on the host cores."""
+# nominal FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz maximum SM clock
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM traffic of the narrow GEMM per algorithmic byte, from the ncu capture summarised in
+# profiles/k_gemm_nrhs_4096x16x4096.md (one streaming launch, 136 MB of A: read once), valid
+# while the kernel source hashes to NARROW_SRC_SHA1; scaled to the bench's launches by their
+# algorithmic bytes
+NARROW_TRAFFIC_PER_ALG_BYTE = 1.0205
+NARROW_SRC_SHA1 = "b2cc7b13d8b837d9cef7d5caf01cd6a54a08d785"
+
+
+def _src_sha1(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2007_00202_gb300", "csrc", name)
+    try:
+        return hashlib.sha1(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+
+
+def roofline(prof, peaks):
+    """Roofline of the dominant kernel, the narrow GEMM (k_gemm_nrhs), from the CUDA-event
+    profile of the timed steps: algorithmic flops and bytes over the summed launch time.
+    Its arithmetic intensity (about 4 n flop per byte for n right-hand sides) is above the
+    FP32-ALU / HBM ridge, so the ALU ceiling binds; the HBM fraction is reported beside it."""
+    if not prof or prof["ms"] <= 0:
+        return None
+    sec = prof["ms"] / 1e3
+    tflops = prof["flops"] / sec / 1e12
+    gbs = prof["bytes"] / sec / 1e9
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    ai = prof["flops"] / max(prof["bytes"], 1.0)
+    traffic = None
+    if NARROW_TRAFFIC_PER_ALG_BYTE is not None and _src_sha1("gemm_nrhs.cu") == NARROW_SRC_SHA1:
+        traffic = NARROW_TRAFFIC_PER_ALG_BYTE * prof["bytes"] / max(prof["launches"], 1)
+    alu_bound = ai * hbm / 1e3 > FP32_ALU_TFLOPS
+    r = {"kernel": "k_gemm_nrhs (narrow planar complex GEMM: solve front products, butterfly level products)",
+         "launches": prof["launches"], "ms_per_launch": prof["ms"] / max(prof["launches"], 1),
+         "flop_per_byte": ai, "traffic": traffic, "traffic_unit": "bytes per launch",
+         "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm,
+         "peak_source": "alu: nominal FP32 SIMT peak 152 SM x 128 lanes x 2 x 2.07 GHz; "
+                        "hbm: MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if alu_bound:
+        r.update({"bound": "alu", "achieved": tflops, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                  "frac": tflops / FP32_ALU_TFLOPS})
+    else:
+        r.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm})
+    return r
+
+
+def roofline_front(prof, peaks):
+    """The dense fronts' Schur-update GEMMs of the factorization (tcgen05, split TF32: three
+    passes per product) against the TF32 tensor peak, 999 TFLOP/s measured with cuBLAS on this
+    pool (bf16 measured peak x 1/2, the nominal TF32:bf16 ratio, gives 950)."""
+    if not prof or prof["ms"] <= 0:
+        return None
+    sec = prof["ms"] / 1e3
+    alg = prof["flops"] / sec / 1e12
+    peak = 999.0
+    return {"kernel": "k_gemm_tc<1> (tcgen05 kind::tf32, split precision) + SIMT trailing updates",
+            "bound": "tensor", "achieved": alg, "achieved_tensor_passes": 3 * alg, "peak": peak,
+            "unit": "TFLOP/s", "frac": alg / peak, "frac_tensor_passes": 3 * alg / peak,
+            "launches": prof["launches"], "traffic": None,
+            "peak_source": "TF32 cuBLAS 999 TFLOP/s measured on this pool (profiles/peaks_probe.md)"}
+
+
+def cpu_baseline():
+    """The FP64 oracle on a bounded sample of the same workload: the same Helmholtz
+    operator (ppw 10) at 16^3, separators >= 128 HOD-BF compressed at tol 1e-4 with
+    rank cap 64, factor + GMRES(30) solve of 16 RHS to 1e-8, timed on the host cores."""
     import numpy as np
     import workloads as w
     from oracle.analysis import analyze
-    from oracle import dense_mf as dm
-    p = w.helmholtz7(32, 10)
+    from oracle import compressed_mf as cm, gmres as gm
+    p = w.helmholtz7(16, 10)
     b = w.rhs_gaussian(p, 16, 7)
+    A = p.to_scipy()
     t0 = time.perf_counter()
-    an = analyze(p, 64, 10 ** 9)
-    fac, _ = dm.multifrontal_factor(p, an)
-    x = dm.solve(p, an, fac, b)
+    an = analyze(p, 64, 128, 64)
+    fac, st = cm.compressed_factor(p, an, 1e-4, max_rank=64)
+    X, its, res = gm.gmres(A, b, cm.preconditioner(an, fac), rtol=1e-8)
     dt = time.perf_counter() - t0
-    res = float(np.max(np.linalg.norm(p.to_scipy() @ x - b, axis=0) / np.linalg.norm(b, axis=0)))
     cores = len(os.sched_getaffinity(0))
     return {"value": 16 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle, exact multifrontal factor + solve of helmholtz7 32^3 (N={p.n}), 16 RHS, "
-                      f"{dt:.1f} s, residual {res:.1e}"}
+            "sample": f"FP64 oracle: HOD-BF multifrontal factor (tol 1e-4, rank <= 64, separators >= 128) + "
+                      f"GMRES(30) of 16 RHS to 1e-8 on helmholtz7 16^3 (N={p.n}); {dt:.1f} s, "
+                      f"{max(its)} iterations, residual {max(res):.1e}"}
 
 
 def run_reference(args, rank, world):
@@ -159,7 +228,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 16 / v * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": "helmholtz7 32^3 sample of the 64^3 workload (FP64 CPU oracle)", "nrhs": 16},
+            "config": {"workload": "helmholtz7 16^3 sample of the 64^3 workload (FP64 CPU oracle, HOD-BF tol 1e-4)",
+                       "nrhs": 16},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -187,17 +257,17 @@ def main():
     nrhs = args.nrhs
     b = w.rhs_gaussian(p, nrhs, 7)
     stream = torch.cuda.current_stream()
-    # complex64 factors, FP64 GMRES(30); HOD-BF fronts are not in this build's GPU path yet,
-    # so every front is dense (nmin_sep above the largest separator)
-    nmin = 10 ** 9
-    h = g.analyze_problem(p, nmin_sep=nmin, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
+    # complex64 factors, separators >= 1024 in HOD-BF at tol 1e-4 (rank <= 64), FP64 GMRES(30) to 1e-8
+    nmin = args.nmin
+    tol = 1e-4
+    h = g.analyze_problem(p, nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
                           stream=stream.cuda_stream)
     bd = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()     # N x nrhs column-major, resident
     xd = torch.empty_like(bd)
     A = p.to_scipy()
 
     def step():
-        h.mf_factor(1e-4)
+        h.mf_factor(tol)
         return h.mf_solve_device(nrhs, bd.data_ptr(), xd.data_ptr())
 
     for _ in range(args.warmup):
@@ -209,14 +279,17 @@ def main():
     c0 = g.lib().mf_launch_counter()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
+        torch.cuda.profiler.start()   # under `ncu --profile-from-start off`: the timed steps only
         e0.record(stream)
         for _ in range(args.steps):
             info = step()
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     launches = g.lib().mf_launch_counter() - c0
     ms = e0.elapsed_time(e1) / args.steps
-    prof = h.mf_profile_read()
+    prof = h.mf_profile_read(g.MF_PROF_NARROW_GEMM)
+    prof_front = h.mf_profile_read(g.MF_PROF_FRONT_GEMM)
     h.mf_profile(False)
     barrier(world)
     ms_max = allmax(ms, world)
@@ -227,19 +300,23 @@ def main():
     # factor-only timing (one extra untimed pass, for the factor-seconds part of the metric)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h.mf_factor(1e-4)
+    h.mf_factor(tol)
     torch.cuda.synchronize()
     factor_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    h.mf_solve_device(nrhs, bd.data_ptr(), xd.data_ptr())
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
 
     # e2e: the public host-buffer call (H2D of b and D2H of x inside the timed region)
     for _ in range(1):
-        h.mf_factor(1e-4)
+        h.mf_factor(tol)
         h.mf_solve(b)
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        h.mf_factor(1e-4)
+        h.mf_factor(tol)
         xe, _ = h.mf_solve(b)
     torch.cuda.synchronize()
     e2e_ms = allmax((time.perf_counter() - t0) / args.steps * 1e3, world)
@@ -247,31 +324,45 @@ def main():
     line = None
     if rank == 0:
         peaks = measured_peaks()
-        # roofline of the dominant kernel: the batched complex GEMM (FP32 SIMT), ALU-bound
-        # nominal FP32 peak = 152 SMs x 128 lanes x 2 flop x 2.07 GHz
-        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
-        achieved = prof["flops"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] > 0 else 0.0
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "c64", "data": "synthetic",
                 "config": {"workload": f"helmholtz7 {n}^3 (N={p.n}), ppw 10, 16 Gaussian RHS seed 7, complex64 "
-                                       f"factors, FP64 GMRES(30) to 1e-8; all fronts dense on the GPU",
+                                       f"factors, separators >= {nmin} HOD-BF at tol 1e-4 (rank <= 64), "
+                                       f"FP64 GMRES(30) to 1e-8",
+                           "compressed_fronts": st["ncompressed"], "max_rank": st["max_rank"],
                            "nrhs": nrhs, "nmin_sep": nmin, "l2": "inputs larger than L2 (factors "
                            f"{st['factor_bytes'] / 1e9:.1f} GB)", "parallelism": "replicas" if world > 1 else "1gpu"},
-                "factor_s": factor_s, "solve_iters": int(info.iters), "max_rel_residual_host_check": res,
-                "gpu_launches": int(launches // max(args.steps, 1)) * args.steps,
-                "roofline": {"kernel": "k_gemm<float> (batched planar complex GEMM, SIMT FP32)", "bound": "alu",
-                             "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                             "frac": achieved / fp32_peak if fp32_peak else None, "traffic": None,
-                             "peak_source": "nominal FP32 SIMT peak 152 SM x 128 lanes x 2 x 2.07 GHz"},
+                "factor_s": factor_s, "solve_s": solve_s, "solve_iters": int(info.iters),
+                "max_rel_residual_host_check": res,
+                "gpu_launches": int(launches),
+                "roofline": roofline(prof, peaks),
+                "roofline_front_gemm": roofline_front(prof_front, peaks),
                 "e2e": {"value": world * nrhs / (e2e_ms / 1e3), "unit": UNIT,
                         "h2d_bytes_per_step": int(16 * p.n * nrhs), "d2h_bytes_per_step": int(16 * p.n * nrhs)}}
         c = clk.summary()
         if c:
             line["clocks"] = c
+    # all-dense complex64 path (same solver without compression), one step
+    if rank == 0 and not args.no_dense:
+        hd = g.analyze_problem(p, nmin_sep=10 ** 9, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
+                               stream=stream.cuda_stream)
+        hd.mf_factor(tol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hd.mf_factor(tol)
+        torch.cuda.synchronize()
+        fd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        infod = hd.mf_solve_device(nrhs, bd.data_ptr(), xd.data_ptr())
+        torch.cuda.synchronize()
+        sd = time.perf_counter() - t0
+        line["dense_c64_path"] = {"factor_s": fd, "solve_s": sd, "solves_per_s": nrhs / (fd + sd),
+                                  "gmres_iters": int(infod.iters), "max_rel_residual": infod.max_rel_residual}
+        del hd
     # FP64 GPU path (same code in complex128), one step, for the mixed-vs-FP64 comparison
     if rank == 0 and not args.no_fp64:
-        h64 = g.analyze_problem(p, nmin_sep=nmin, precision=g.MF_PREC_C128, refine=g.MF_REFINE_IR,
+        h64 = g.analyze_problem(p, nmin_sep=10 ** 9, precision=g.MF_PREC_C128, refine=g.MF_REFINE_IR,
                                 stream=stream.cuda_stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -282,9 +373,25 @@ def main():
         info64 = h64.mf_solve_device(nrhs, bd.data_ptr(), xd.data_ptr())
         torch.cuda.synchronize()
         s64 = time.perf_counter() - t0
-        line["fp64_path"] = {"factor_s": f64, "solve_s": s64, "solves_per_s": nrhs / (f64 + s64),
+        line["fp64_path"] = {"variant": "exact (all-dense) multifrontal in complex128 + iterative refinement",
+                             "factor_s": f64, "solve_s": s64, "solves_per_s": nrhs / (f64 + s64),
                              "refinement_steps": int(info64.iters), "max_rel_residual": info64.max_rel_residual}
         del h64
+        # FP64 butterfly variant: the compressed path in complex128 + GMRES
+        hb = g.analyze_problem(p, nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C128, refine=g.MF_REFINE_GMRES,
+                               stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hb.mf_factor(tol)
+        torch.cuda.synchronize()
+        fb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        infob = hb.mf_solve_device(nrhs, bd.data_ptr(), xd.data_ptr())
+        torch.cuda.synchronize()
+        sb = time.perf_counter() - t0
+        line["fp64_butterfly_path"] = {"factor_s": fb, "solve_s": sb, "solves_per_s": nrhs / (fb + sb),
+                                       "gmres_iters": int(infob.iters), "max_rel_residual": infob.max_rel_residual}
+        del hb
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -139,18 +139,26 @@ int mf_stats(const mf_handle* h, mf_stats_t* out);
 /* Message of the last failure on h (h == NULL: of the calling thread). Never NULL. */
 const char* mf_last_error(const mf_handle* h);
 
-/* Event timing of the dominant kernel of mf_factor (the batched front GEMM).
- * mf_profile(h, 1) enables it and clears the counters; every following
- * mf_factor records CUDA events around each of those launches on the handle's
- * stream.  mf_profile_read returns the accumulated launches, device time and
- * algorithmic flops (8 m n k per complex product). */
+/* CUDA-event timing of two kernel families, for roofline figures.
+ * mf_profile(h, 1) enables it and clears the counters (0 disables it); while it is
+ * on, every launch of the family gets a start and a stop event on the stream it
+ * runs on (inside the solve's CUDA graphs as graph nodes):
+ *   MF_PROF_NARROW_GEMM: the narrow GEMM (n <= 128: the solve's front products
+ *     with the right-hand sides and the butterfly level products) in mf_factor
+ *     and mf_solve*;
+ *   MF_PROF_FRONT_GEMM: the dense fronts' Schur-update GEMMs in mf_factor.
+ * mf_profile_read returns for one family the timed launches, their summed device
+ * time, algorithmic flops (8 m n k per complex product) and algorithmic bytes
+ * (A and B read once, C written, and read when beta != 0; planar complex). */
+enum { MF_PROF_NARROW_GEMM = 0, MF_PROF_FRONT_GEMM = 1 };
 typedef struct {
   int64_t launches;
   double ms;
   double flops;
+  double bytes;
 } mf_kernel_profile_t;
 int mf_profile(mf_handle* h, int32_t enable);
-int mf_profile_read(const mf_handle* h, mf_kernel_profile_t* out);
+int mf_profile_read(mf_handle* h, int32_t kernel, mf_kernel_profile_t* out);
 
 /*
  * Component entry point of the front-update GEMM kernels (the Schur update
@@ -197,7 +205,8 @@ int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const flo
  *   U     out, nmat blocks of 2 m kmax floats (real then imaginary m x kmax row-major;
  *         columns >= rank_q are unspecified)
  *   sk    out, nmat x kmax int32 (first rank_q entries valid), rank out, nmat int32.
- * Scratch of 2 m n floats per matrix is allocated by the call.  Runs on `stream`
+ * The QR work matrix (2 m n floats per matrix) lives in shared memory when it fits
+ * (2 m n + 2 n + 2 m floats <= 200 KiB), else in scratch allocated by the call.  Runs on `stream`
  * and waits for it.  Errors: MF_ERR_ARG (sizes: n <= 8192, m <= 2048), MF_ERR_OOM, MF_ERR_CUDA.
  */
 int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol, int32_t max_rank, float* U,

@@ -320,10 +320,21 @@ void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
   }
   const GemmDesc<T>* dd = static_cast<const GemmDesc<T>*>(upload(D.data(), D.size() * sizeof(GemmDesc<T>)));
   const GemmTile* dt = stage(tl.data(), tl.size());
-  if (nb)
-    launch_gemm_nrhs<T>(dd, dt, (int)tl.size(), nb, gemm_nrhs_split((int)tl.size(), maxk), st);
-  else
+  if (nb) {
+    auto go = [&] { launch_gemm_nrhs<T>(dd, dt, (int)tl.size(), nb, gemm_nrhs_split((int)tl.size(), maxk), st); };
+    if (prof && prof->on) {
+      double fl = 0, by = 0;
+      for (auto& d : D) {
+        fl += 8.0 * d.m * d.n * d.k;
+        by += gemm_bytes(d);
+      }
+      prof->time(st, fl, by, go);
+    } else {
+      go();
+    }
+  } else {
     launch_gemm<T>(dd, dt, (int)tl.size(), st);
+  }
 }
 
 template <typename T>

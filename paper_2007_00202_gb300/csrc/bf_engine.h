@@ -222,6 +222,7 @@ class BFContext {
   size_t cap_cap = 0, cap_off = 0;
   bool cap_bad = false;
   double t_wait = 0;                // seconds the host spent waiting for the stream
+  LaunchProfiler* prof = nullptr;   // event timing of the narrow GEMM launches (when on)
   Arena persist, scratch;
   DevMem status;
   double flops = 0;

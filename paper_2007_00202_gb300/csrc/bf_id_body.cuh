@@ -8,8 +8,8 @@
 // first k with |R_{k+1,k+1}| <= tol |R_11| (or k = kmax), then
 // U = P [I; (R11^-1 R12)^T].  The columns of M^T are the rows of M, which are
 // contiguous: every reflection updates each remaining row with one dot product
-// and one axpy (a warp per row), and the remaining row norms are recomputed in
-// the same pass.  Pivot: largest remaining norm, lowest position on ties.
+// and one axpy (a group of 4 to 32 lanes per row, sized to the row length), and
+// the remaining row norms are recomputed in the same pass.  Pivot: largest remaining norm, lowest position on ties.
 #pragma once
 #include "bf_kernels.h"
 
@@ -30,6 +30,9 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
   __shared__ T sh_alpha_r, sh_alpha_i, sh_scale, sh_ref;
   __shared__ int sh_p, sh_stop;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  int G = 32;   // lanes per row in the reflection updates: about 12 or more columns per lane
+  while (G > 4 && (G >> 1) * 12 >= n) G >>= 1;
+  const int gid = tid / G, glane = tid % G, ngrp = (int)blockDim.x / G;
   // copy M to the work matrix (ld = n) and compute the row norms
   for (int r = warp; r < m; r += nw) {
     const T* mr = jb.M + (int64_t)r * jb.ld;
@@ -111,34 +114,39 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
       xr[c] = c == k ? sh_alpha_r : T(0);
       xi[c] = c == k ? sh_alpha_i : T(0);
     }
-    // apply H to the remaining rows, recompute their norms beyond coordinate k
+    // apply H to the remaining rows, recompute their norms beyond coordinate k: groups of G
+    // lanes per row (G sized to the row length), all groups of a warp in lockstep
     const T sc = sh_scale;
-    for (int q = k + 1 + warp; q < m; q += nw) {
-      T* yr = Wr + (int64_t)perm[q] * n;
-      T* yi = Wi + (int64_t)perm[q] * n;
+    for (int base = k + 1; base < m; base += ngrp) {
+      const int q = base + gid;
+      const bool act = q < m;
+      T* yr = Wr + (int64_t)(act ? perm[q] : 0) * n;
+      T* yi = Wi + (int64_t)(act ? perm[q] : 0) * n;
       T dr = 0, di = 0;   // v^H y
-      for (int c = k + lane; c < n; c += 32) {
-        T a = vr[c], b = vi[c], p = yr[c], r = yi[c];
-        dr += a * p + b * r;
-        di += a * r - b * p;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
+      if (act)
+        for (int c = k + glane; c < n; c += G) {
+          T a = vr[c], b = vi[c], p = yr[c], r = yi[c];
+          dr += a * p + b * r;
+          di += a * r - b * p;
+        }
+      for (int o = G >> 1; o > 0; o >>= 1) {
         dr += __shfl_xor_sync(0xffffffffu, dr, o);
         di += __shfl_xor_sync(0xffffffffu, di, o);
       }
       dr *= sc;
       di *= sc;
       T s = 0;
-      for (int c = k + lane; c < n; c += 32) {
-        T a = vr[c], b = vi[c];
-        T p = yr[c] - (a * dr - b * di);
-        T r = yi[c] - (a * di + b * dr);
-        yr[c] = p;
-        yi[c] = r;
-        if (c > k) s += p * p + r * r;
-      }
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) nrm[q] = s;
+      if (act)
+        for (int c = k + glane; c < n; c += G) {
+          T a = vr[c], b = vi[c];
+          T p = yr[c] - (a * dr - b * di);
+          T r = yi[c] - (a * di + b * dr);
+          yr[c] = p;
+          yi[c] = r;
+          if (c > k) s += p * p + r * r;
+        }
+      for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (act && glane == 0) nrm[q] = s;
     }
     __syncthreads();
     rank = k + 1;
@@ -158,19 +166,18 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
     Ur[(int64_t)perm[b] * ldu + c] = b == c ? T(1) : T(0);
     Ui[(int64_t)perm[b] * ldu + c] = T(0);
   }
-  // non-pivot rows: back substitution with R11 (R11[a][b] = work[perm[b]][a], a <= b)
+  // non-pivot rows: back substitution with R11 (R11[a][b] = work[perm[b]][a], a <= b), in place
+  // in the row's first r work entries (its R12 column), then copied out to U
   for (int j = r + tid; j < m; j += blockDim.x) {
     const int q = perm[j];
-    const T* yr = Wr + (int64_t)q * n;
-    const T* yi = Wi + (int64_t)q * n;
-    T* ur = Ur + (int64_t)q * ldu;
-    T* ui = Ui + (int64_t)q * ldu;
+    T* yr = Wr + (int64_t)q * n;
+    T* yi = Wi + (int64_t)q * n;
     for (int b = r - 1; b >= 0; --b) {
       T accr = yr[b], acci = yi[b];
       for (int c = b + 1; c < r; ++c) {
         const int pc = perm[c];
         T Rr = Wr[(int64_t)pc * n + b], Ri = Wi[(int64_t)pc * n + b];
-        T tr = ur[c], ti = ui[c];
+        T tr = yr[c], ti = yi[c];
         accr -= Rr * tr - Ri * ti;
         acci -= Rr * ti + Ri * tr;
       }
@@ -178,9 +185,15 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
       T dr = Wr[(int64_t)pb * n + b], di = Wi[(int64_t)pb * n + b];
       T den = dr * dr + di * di;
       if (den == T(0)) den = T(1);
-      ur[b] = (accr * dr + acci * di) / den;
-      ui[b] = (acci * dr - accr * di) / den;
+      yr[b] = (accr * dr + acci * di) / den;
+      yi[b] = (acci * dr - accr * di) / den;
     }
+  }
+  __syncthreads();
+  for (int e = tid; e < (m - r) * r; e += blockDim.x) {
+    const int q = perm[r + e / r], c = e % r;
+    Ur[(int64_t)q * ldu + c] = Wr[(int64_t)q * n + c];
+    Ui[(int64_t)q * ldu + c] = Wi[(int64_t)q * n + c];
   }
 }
 

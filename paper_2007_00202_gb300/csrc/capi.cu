@@ -385,7 +385,7 @@ int mf_factor(mf_handle* h, double tol) {
       eo.scratch_bytes = any_comp ? std::max<size_t>(size_t(4) << 30, comp_n * 10000 * el) : 0;
       h->eng = h->opt.precision == MF_PREC_C128 ? mf::make_engine_c128(h->an, h->A, h->stream, eo)
                                                : mf::make_engine_c64(h->an, h->A, h->stream, eo);
-      h->eng->profiling = h->profile;
+      h->eng->set_profiling(h->profile);
     }
     h->factored = false;
     h->eng->factor(tol);
@@ -475,22 +475,27 @@ int mf_stats(const mf_handle* h, mf_stats_t* out) {
 int mf_profile(mf_handle* h, int32_t enable) {
   if (!h) return fail(nullptr, MF_ERR_ARG, "handle is NULL");
   h->profile = enable != 0;
-  if (h->eng) {
-    h->eng->profiling = h->profile;
-    h->eng->prof = mf::EngineBase::Profile();
-  }
+  if (h->eng) return guarded(h, [&]() -> int {
+    h->eng->set_profiling(h->profile);
+    return MF_OK;
+  });
   return MF_OK;
 }
 
-int mf_profile_read(const mf_handle* h, mf_kernel_profile_t* out) {
-  if (!h || !out) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "NULL argument");
+int mf_profile_read(mf_handle* h, int32_t kernel, mf_kernel_profile_t* out) {
+  if (!h || !out) return fail(h, MF_ERR_ARG, "NULL argument");
+  if (kernel != MF_PROF_NARROW_GEMM && kernel != MF_PROF_FRONT_GEMM) return fail(h, MF_ERR_ARG, "unknown kernel");
   std::memset(out, 0, sizeof(*out));
-  if (h->eng) {
-    out->launches = h->eng->prof.launches;
-    out->ms = h->eng->prof.ms;
-    out->flops = h->eng->prof.flops;
-  }
-  return MF_OK;
+  if (!h->eng) return MF_OK;
+  return guarded(h, [&]() -> int {
+    mf::LaunchProfiler& p = h->eng->prof[kernel];
+    p.collect();
+    out->launches = p.launches;
+    out->ms = p.ms;
+    out->flops = p.flops;
+    out->bytes = p.bytes;
+    return MF_OK;
+  });
 }
 
 int mf_gemm_c64(int32_t engine, int32_t m, int32_t n, int32_t k, const float* A, int64_t lda, int64_t pla,
@@ -568,7 +573,8 @@ int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol
     int kmax = std::min(m, n);
     if (max_rank > 0) kmax = std::min(kmax, (int)max_rank);
     DevMem work, jobs;
-    work.alloc(sizeof(float) * 2 * (size_t)m * n * nmat);
+    const bool in_smem = mf::row_id_smem_bytes(m, n, sizeof(float), true) <= mf::kRowIdSmemCap;
+    if (!in_smem) work.alloc(sizeof(float) * 2 * (size_t)m * n * nmat);
     std::vector<mf::IdJob<float>> jb(nmat);
     for (int q = 0; q < nmat; ++q) {
       auto& j = jb[q];
@@ -582,11 +588,11 @@ int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol
       j.ldu = kmax;
       j.sk = sk + (size_t)kmax * q;
       j.rank = rank + q;
-      j.work = work.as<float>() + (size_t)2 * m * n * q;
+      j.work = in_smem ? nullptr : work.as<float>() + (size_t)2 * m * n * q;
       j.wplane = (int64_t)m * n;
     }
     mf::upload(jobs, jb, st);
-    if (mf::launch_row_id<float>(jobs.as<mf::IdJob<float>>(), nmat, m, n, (float)tol, max_rank, st) != 0)
+    if (mf::launch_row_id<float>(jobs.as<mf::IdJob<float>>(), nmat, m, n, (float)tol, max_rank, st, in_smem) != 0)
       return fail(nullptr, MF_ERR_ARG, "matrix too large for the row-ID kernel");
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaStreamSynchronize(st));

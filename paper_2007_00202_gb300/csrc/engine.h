@@ -76,6 +76,94 @@ struct DeviceMatrix {
   DevMem rowptr, col64, col32, vals;   // vals: interleaved complex128
 };
 
+// CUDA-event timing of the launches of one kernel family: a start and a stop event
+// around every launch; collect() reads the finished pairs and adds them up.  Inside a
+// CUDA graph capture the events come from the graph's own list (capture_into), and
+// every replay of the graph hands that list back through replayed().
+struct LaunchProfiler {
+  struct Rec {
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  bool on = false;
+  std::vector<Rec>* capture_into = nullptr;
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  int64_t launches = 0, recorded = 0;
+  double ms = 0, flops = 0, bytes = 0;
+
+  LaunchProfiler() = default;
+  LaunchProfiler(const LaunchProfiler&) = delete;
+  LaunchProfiler& operator=(const LaunchProfiler&) = delete;
+  ~LaunchProfiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+  static cudaEvent_t make_event() {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) throw CudaError("cudaEventCreate failed");
+    return e;
+  }
+  template <class F>
+  void time(cudaStream_t st, double fl, double by, F&& launch) {
+    if (!on) {
+      launch();
+      return;
+    }
+    Rec r;
+    if (capture_into) {   // events of the graph: created by reserve_graph before the capture
+      const size_t i = capture_into->size();
+      if (i >= graph_reserve.size()) {   // not reserved: leave this launch untimed
+        launch();
+        return;
+      }
+      r = graph_reserve[i];
+    } else {
+      while (pool.size() < pool_used + 2) pool.push_back(make_event());
+      r.a = pool[pool_used++];
+      r.b = pool[pool_used++];
+    }
+    r.flops = fl;
+    r.bytes = by;
+    // inside a capture an event becomes a record node of the graph only as an "external" record
+    const unsigned fl_rec = capture_into ? cudaEventRecordExternal : cudaEventRecordDefault;
+    cudaEventRecordWithFlags(r.a, st, fl_rec);
+    launch();
+    cudaEventRecordWithFlags(r.b, st, fl_rec);
+    ++recorded;
+    if (capture_into) capture_into->push_back(r);
+    else pending.push_back(r);
+  }
+  // n event pairs for a graph about to be captured (owned by the caller afterwards)
+  std::vector<Rec> graph_reserve;
+  void reserve_graph(size_t n) {
+    graph_reserve.clear();
+    for (size_t i = 0; i < n; ++i) graph_reserve.push_back(Rec{make_event(), make_event(), 0, 0});
+  }
+  void replayed(const std::vector<Rec>& recs) {
+    if (on) pending.insert(pending.end(), recs.begin(), recs.end());
+  }
+  void collect() {
+    for (auto& r : pending) {
+      float t = 0;
+      if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        ms += t;
+        flops += r.flops;
+        bytes += r.bytes;
+        ++launches;
+      }
+    }
+    pending.clear();
+    pool_used = 0;
+  }
+  void enable(bool v) {
+    collect();
+    on = v;
+    launches = 0;
+    ms = flops = bytes = 0;
+  }
+};
+
 class EngineBase {
  public:
   virtual ~EngineBase() = default;
@@ -89,13 +177,13 @@ class EngineBase {
   virtual int launches_solve(int nrhs) = 0;
   virtual int max_rank() const { return 0; }
   virtual double compressed_seconds() const { return 0; }
-  // Event timing of the dominant kernel (the batched front GEMM) inside factor().
-  struct Profile {
-    int64_t launches = 0;
-    double ms = 0, flops = 0;
-  };
-  bool profiling = false;
-  Profile prof;
+  // Event timing of two kernel families (see mf_profile in mf.h):
+  // prof[0] the narrow GEMM (k_gemm_nrhs) in factor() and apply_precond(), prof[1] the
+  // factor's dense front GEMMs (Schur updates).
+  LaunchProfiler prof[2];
+  virtual void set_profiling(bool on) {
+    for (auto& p : prof) p.enable(on);
+  }
 };
 
 // Parameters of the compressed fronts (Alg. 2-5).

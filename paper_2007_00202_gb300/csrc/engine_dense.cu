@@ -40,16 +40,6 @@ class DenseEngine : public EngineBase {
     const int64_t c0 = launch_count();
     MF_CUDA(cudaMemsetAsync(arena_.p, 0, zero_bytes_, st_));
     MF_CUDA(cudaMemsetAsync(status_.p, 0, sizeof(int32_t), st_));
-    size_t ng = 0;
-    if (profiling) {
-      for (size_t i = 0; i < fops_.size(); ++i) ng += gemm_flops_[i] > 0 ? 1 : 0;
-      while (evs_.size() < 2 * ng) {
-        cudaEvent_t e;
-        MF_CUDA(cudaEventCreate(&e));
-        evs_.push_back(e);
-      }
-    }
-    size_t k = 0;
     BFParams P;
     P.tol = tol > 0 ? tol : 1e-12;
     P.max_rank = eo_.max_rank;
@@ -57,6 +47,7 @@ class DenseEngine : public EngineBase {
     P.knn = eo_.knn;
     comp_flops_ = 0;
     comp_seconds_ = 0;
+    prof[0].collect();   // pending records may name the events of the graphs dropped next
     for (auto& kv : sprog_) kv.second->drop_graph();   // compressed fronts move with every factorization
     if (comp_) {
       comp_->fronts.clear();
@@ -66,10 +57,8 @@ class DenseEngine : public EngineBase {
     }
     for (size_t lv = 0; lv < levels_.size(); ++lv) {
       for (size_t i = lvl_begin_[lv]; i < lvl_begin_[lv + 1]; ++i) {
-        bool timed = profiling && gemm_flops_[i] > 0;
-        if (timed) MF_CUDA(cudaEventRecord(evs_[2 * k], st_));
-        fops_[i](st_);
-        if (timed) { MF_CUDA(cudaEventRecord(evs_[2 * k + 1], st_)); ++k; }
+        if (gemm_flops_[i] > 0) prof[1].time(st_, gemm_flops_[i], gemm_bytes_[i], [&] { fops_[i](st_); });
+        else fops_[i](st_);
       }
       for (int32_t fid : comp_levels_[lv]) {
         auto t0 = std::chrono::steady_clock::now();
@@ -83,22 +72,11 @@ class DenseEngine : public EngineBase {
     if (comp_) comp_flops_ = comp_->cx.flops;
     MF_CUDA(cudaGetLastError());
     nlaunch_factor_ = (int)(launch_count() - c0);
-    if (profiling) {
-      MF_CUDA(cudaStreamSynchronize(st_));
-      k = 0;
-      for (size_t i = 0; i < fops_.size(); ++i) {
-        if (gemm_flops_[i] <= 0) continue;
-        float ms = 0;
-        MF_CUDA(cudaEventElapsedTime(&ms, evs_[2 * k], evs_[2 * k + 1]));
-        prof.ms += ms;
-        prof.flops += gemm_flops_[i];
-        prof.launches += 1;
-        ++k;
-      }
-    }
     int32_t stat = 0;
     MF_CUDA(cudaMemcpyAsync(&stat, status_.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     MF_CUDA(cudaStreamSynchronize(st_));
+    prof[0].collect();
+    prof[1].collect();
     if (stat == 2) throw CudaError("a bounded wait in the tensor-core GEMM expired (MF_ERR_TIMEOUT)");
     if (stat != DEV_OK) throw SingularError("zero pivot in a dense front");
   }
@@ -145,12 +123,19 @@ class DenseEngine : public EngineBase {
     cudaGraphExec_t exec = nullptr;
     size_t blob = 0, blob_cap = 0, mark = 0;
     int glaunch = 0;
+    int64_t nrec = 0;                                  // timed launches of one run (profiling)
+    std::vector<LaunchProfiler::Rec> prof_recs;        // event pairs recorded by the graph
     char* hblob = nullptr;
     DevMem dblob;
     void drop_graph() {
       if (exec) cudaGraphExecDestroy(exec);
       exec = nullptr;
       state = 0;
+      for (auto& r : prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+      }
+      prof_recs.clear();
     }
     ~SolveProg() {
       drop_graph();
@@ -173,19 +158,18 @@ class DenseEngine : public EngineBase {
   int nlaunch_factor_ = 0;
   std::map<int, std::unique_ptr<SolveProg>> sprog_;
   std::vector<double> gemm_flops_;          // per factor op: algorithmic flops if it is a GEMM launch, else 0
+  std::vector<double> gemm_bytes_;          // and its algorithmic bytes
   EngineOptions eo_;
   std::vector<std::vector<int32_t>> comp_levels_;   // compressed fronts per level
   std::vector<size_t> lvl_begin_;           // factor ops of level lv: [lvl_begin_[lv], lvl_begin_[lv+1])
   std::unique_ptr<CompressedPart<T>> comp_;
   double comp_flops_ = 0, comp_seconds_ = 0;
   int max_rank_ = 0;
-  std::vector<cudaEvent_t> evs_;
   cudaStream_t gs_ = nullptr;               // stream of the solve graphs (forked from and joined to st_)
   cudaEvent_t gev_[2] = {nullptr, nullptr};
 
  public:
   ~DenseEngine() override {
-    for (auto e : evs_) cudaEventDestroy(e);
     sprog_.clear();
     for (auto e : gev_)
       if (e) cudaEventDestroy(e);
@@ -193,6 +177,12 @@ class DenseEngine : public EngineBase {
   }
 
  private:
+  void set_profiling(bool on) override {
+    prof[0].collect();
+    for (auto& kv : sprog_) kv.second->drop_graph();   // recaptured with (or without) timing events
+    EngineBase::set_profiling(on);
+  }
+
   // The solve program is the same launch sequence for every call with the same nrhs: the
   // first call runs it eagerly (and sizes the job tables of the compressed fronts), the
   // second captures it into a CUDA graph on gs_, later calls replay the graph.  A capture
@@ -206,17 +196,21 @@ class DenseEngine : public EngineBase {
     if (no_graph || sp.state == 3) return eager();
     if (sp.state == 2 && cx && cx->scratch.mark() != sp.mark) sp.drop_graph();
     if (sp.state == 2) {
+      prof[0].collect();   // the previous replay's events are recorded again by this one
       MF_CUDA(cudaEventRecord(gev_[0], st_));
       MF_CUDA(cudaStreamWaitEvent(gs_, gev_[0], 0));
       MF_CUDA(cudaGraphLaunch(sp.exec, gs_));
       count_launches(sp.glaunch);   // the kernel nodes the replay runs
       MF_CUDA(cudaEventRecord(gev_[1], gs_));
       MF_CUDA(cudaStreamWaitEvent(st_, gev_[1], 0));
+      prof[0].replayed(sp.prof_recs);
       return;
     }
     if (sp.state == 0) {
       if (cx) cx->count_begin();
+      const int64_t r0 = prof[0].recorded;
       eager();
+      sp.nrec = prof[0].recorded - r0;
       if (cx) sp.blob = cx->count_end();
       sp.state = 1;
       return;
@@ -242,6 +236,11 @@ class DenseEngine : public EngineBase {
       cx->capture_begin(sp.hblob, sp.dblob.template as<char>(), sp.blob_cap);
     }
     cudaGraph_t g = nullptr;
+    if (prof[0].on) {
+      prof[0].collect();
+      prof[0].reserve_graph((size_t)sp.nrec);
+      prof[0].capture_into = &sp.prof_recs;
+    }
     const int64_t c0 = launch_count();
     bool ok = cudaStreamBeginCapture(gs_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
@@ -254,6 +253,14 @@ class DenseEngine : public EngineBase {
     }
     sp.glaunch = (int)(launch_count() - c0);
     count_launches(-sp.glaunch);   // captured, not run
+    if (prof[0].capture_into) {    // reserved event pairs the capture did not use
+      for (size_t i = sp.prof_recs.size(); i < prof[0].graph_reserve.size(); ++i) {
+        cudaEventDestroy(prof[0].graph_reserve[i].a);
+        cudaEventDestroy(prof[0].graph_reserve[i].b);
+      }
+      prof[0].graph_reserve.clear();
+      prof[0].capture_into = nullptr;
+    }
     if (cx) {
       cx->st = st_;
       comp_->st_ = st_;
@@ -310,15 +317,16 @@ class DenseEngine : public EngineBase {
     GemmRef g = add_gemm(D, Tl, b, tc ? gemm_tc_tile() : GEMM_TILE);
     if (!g.nt) return;
     if (tc)
-      push_op([this, g](cudaStream_t st) { launch_nt(g, st); }, ref_flops(D, g));
+      push_op([this, g](cudaStream_t st) { launch_nt(g, st); }, ref_flops(D, g), ref_bytes(D, g));
     else
       push_op([this, g](cudaStream_t st) {
         launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt, st);
-      }, ref_flops(D, g));
+      }, ref_flops(D, g), ref_bytes(D, g));
   }
   void launch_nt(const GemmRef& g, cudaStream_t st);
 
-  void push_op(std::function<void(cudaStream_t)> fn, double fl = 0) {
+  void push_op(std::function<void(cudaStream_t)> fn, double fl = 0, double by = 0) {
+    gemm_bytes_.push_back(by);
     fops_.push_back(std::move(fn));
     gemm_flops_.push_back(fl);
   }
@@ -327,6 +335,11 @@ class DenseEngine : public EngineBase {
     double f = 0;
     for (size_t i = g.d0; i < g.d0 + g.nd; ++i) f += 8.0 * D[i].m * D[i].n * D[i].k;
     return f;
+  }
+  double ref_bytes(const std::vector<GemmDesc<T>>& D, const GemmRef& g) const {
+    double b = 0;
+    for (size_t i = g.d0; i < g.d0 + g.nd; ++i) b += gemm_bytes(D[i]);
+    return b;
   }
 
   static GemmDesc<T> gd(int m, int n, int k, int ta, int tb, T alpha, T beta, PMat<T> a, PMat<T> b, PMat<T> c) {
@@ -417,7 +430,10 @@ class DenseEngine : public EngineBase {
       if (f.compressed) { comp_levels_[depth - 1 - f.level].push_back((int32_t)f.id); any_comp = true; }
       else levels_[depth - 1 - f.level].push_back((int32_t)f.id);
     }
-    if (any_comp) comp_ = std::make_unique<CompressedPart<T>>(an_, A_, st_, eo_.persist_bytes, eo_.scratch_bytes);
+    if (any_comp) {
+      comp_ = std::make_unique<CompressedPart<T>>(an_, A_, st_, eo_.persist_bytes, eo_.scratch_bytes);
+      comp_->cx.prof = &prof[0];
+    }
     std::vector<int32_t> all;
     for (auto& lv : levels_) {
       level_off_.push_back(all.size());
@@ -527,7 +543,7 @@ class DenseEngine : public EngineBase {
         if (g.nt) {
           push_op([this, g](cudaStream_t st) {
             launch_gemm<T>(descs_d_.template as<GemmDesc<T>>() + g.d0, tiles_d_.template as<GemmTile>() + g.t0, g.nt, st);
-          }, ref_flops(D, g));
+          }, ref_flops(D, g), ref_bytes(D, g));
           nlaunch_factor_++;
         }
       }
@@ -655,9 +671,12 @@ class DenseEngine : public EngineBase {
         int maxk = 1;
         for (auto& x : b) maxk = std::max(maxk, (int)x.k);
         const int ks = gemm_nrhs_split(g.nt, maxk);
-        sp->ops.push_back([spp, g, nb, ks](cudaStream_t st) {
-          launch_gemm_nrhs<T>(spp->descs.template as<GemmDesc<T>>() + g.d0, spp->tiles.template as<GemmTile>() + g.t0,
-                              g.nt, nb, ks, st);
+        const double fl = ref_flops(D, g), by = ref_bytes(D, g);
+        sp->ops.push_back([this, spp, g, nb, ks, fl, by](cudaStream_t st) {
+          prof[0].time(st, fl, by, [&] {
+            launch_gemm_nrhs<T>(spp->descs.template as<GemmDesc<T>>() + g.d0,
+                                spp->tiles.template as<GemmTile>() + g.t0, g.nt, nb, ks, st);
+          });
         });
         sp->nlaunch++;
         return;

@@ -24,6 +24,11 @@ template <typename T>
 void launch_gemm_nrhs(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, int nb, int ksplit,
                       cudaStream_t st);
 constexpr int GEMM_NRHS_ROWS = 32;
+// Algorithmic bytes of one product: A and B read once, C written (and read when beta != 0).
+template <typename T>
+inline double gemm_bytes(const GemmDesc<T>& d) {
+  return 2.0 * sizeof(T) * ((double)d.m * d.k + (double)d.k * d.n + (double)d.m * d.n * (d.beta != T(0) ? 2 : 1));
+}
 int gemm_nrhs_width(int max_n, size_t elem);   // 16, 32, 64 (complex64 only); 0 when max_n > 128
 int gemm_nrhs_split(int ntiles, int max_k);
 

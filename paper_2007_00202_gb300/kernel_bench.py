@@ -1,0 +1,168 @@
+"""Microbenchmarks of the library's hot kernels through their C-ABI component entry points,
+and single-phase runs of the 64^3 workload for profilers.
+
+    python -m paper_2007_00202_gb300.kernel_bench [narrow|front|rowid|factor|solve] [--reps R] [--grid G]
+
+narrow: the narrow GEMM of the solve (mf_gemm_nrhs_c64), C = -A B + C with A 4096 x 4096,
+        B 4096 x 16 (complex64): one launch streams 128 MiB of A (larger than L2).
+front:  the split-TF32 tcgen05 front GEMM (mf_gemm_c64 engine 2), 4096 x 4096 x 4096.
+rowid:  the batched row ID (mf_row_id_c64) of 256 matrices of 128 x 72 (the randomized
+        construction's sketch blocks).
+factor: the compressed complex64 factorization of the bench workload (helmholtz7 G^3, ppw 10,
+        separators >= 1024 HOD-BF at tol 1e-4, rank <= 64), once to warm up, then once between
+        cudaProfilerStart/Stop (for `ncu --profile-from-start off`).
+solve:  after that factorization, one preconditioner application to 16 right-hand sides
+        (no refinement) between cudaProfilerStart/Stop, after three warm-up solves.
+Prints one JSON line per item: device time per call (CUDA events, after warm-up; the
+component entry points include their own synchronisation) and the achieved rate against the
+peaks used by bench.py.
+"""
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def _time(torch, fn, reps):
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def narrow(torch, mf, reps, m=4096, k=4096, n=16):
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn(2, m, k, device="cuda", generator=g)
+    B = torch.randn(2, k, n, device="cuda", generator=g)
+    C = torch.randn(2, m, n, device="cuda", generator=g)
+    st = torch.cuda.current_stream().cuda_stream
+
+    def run():
+        mf.mf_gemm_nrhs_c64(0, m, n, k, A.data_ptr(), k, m * k, B.data_ptr(), n, k * n, C.data_ptr(), n, m * n,
+                            -1.0, 1.0, 0, st)
+    ms = _time(torch, run, reps)
+    flops = 8.0 * m * n * k
+    by = 8.0 * (m * k + k * n + 2 * m * n)
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    return {"kernel": "k_gemm_nrhs", "shape": [m, n, k], "ms": ms, "tflops": flops / ms / 1e9,
+            "alu_frac": flops / ms / 1e9 / FP32_ALU_TFLOPS, "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm,
+            "alg_bytes": by}
+
+
+def front(torch, mf, reps, m=4096, n=4096, k=4096):
+    g = torch.Generator(device="cuda").manual_seed(2)
+    A = torch.randn(2, m, k, device="cuda", generator=g)
+    B = torch.randn(2, n, k, device="cuda", generator=g)
+    C = torch.zeros(2, m, n, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+
+    def run():
+        mf.mf_gemm_c64(2, m, n, k, A.data_ptr(), k, m * k, B.data_ptr(), k, n * k, C.data_ptr(), n, m * n,
+                       -1.0, 0.0, st)
+    ms = _time(torch, run, reps)
+    flops = 8.0 * m * n * k
+    return {"kernel": "k_gemm_tc<1> (split TF32, 3 passes)", "shape": [m, n, k], "ms": ms,
+            "tflops": flops / ms / 1e9, "tensor_tflops": 3 * flops / ms / 1e9,
+            "tf32_frac": 3 * flops / ms / 1e9 / 999.0}
+
+
+def rowid(torch, mf, reps, nmat=256, m=128, n=72):
+    g = torch.Generator(device="cuda").manual_seed(3)
+    M = torch.randn(nmat, 2, m, n, device="cuda", generator=g)
+    kmax = min(m, n)
+    U = torch.zeros(nmat, 2, m, kmax, device="cuda")
+    sk = torch.zeros(nmat, kmax, dtype=torch.int32, device="cuda")
+    rk = torch.zeros(nmat, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+
+    def run():
+        mf.mf_row_id_c64(nmat, m, n, M.data_ptr(), 1e-4, 64, U.data_ptr(), sk.data_ptr(), rk.data_ptr(), st)
+    ms = _time(torch, run, reps)
+    return {"kernel": "k_row_id", "shape": [nmat, m, n], "ms": ms, "us_per_matrix": ms * 1e3 / nmat}
+
+
+def _workload(torch, grid):
+    import workloads as w
+    import paper_2007_00202_gb300 as g
+    p = w.helmholtz7(grid, 10)
+    h = g.analyze_problem(p, nmin_sep=1024, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_NONE)
+    return g, p, h
+
+
+def factor(torch, mf, reps, grid=64):
+    import time
+    g, p, h = _workload(torch, grid)
+    h.mf_factor(1e-4)
+    torch.cuda.synchronize()
+    c0 = g.lib().mf_launch_counter()
+    torch.cuda.profiler.start()
+    t0 = time.perf_counter()
+    h.mf_factor(1e-4)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
+    return {"item": "compressed factorization", "grid": grid, "s": dt, "launches": g.lib().mf_launch_counter() - c0}
+
+
+def solve(torch, mf, reps, grid=64):
+    import time
+    import workloads as w
+    g, p, h = _workload(torch, grid)
+    h.mf_factor(1e-4)
+    b = w.rhs_gaussian(p, 16, 7)
+    bd = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()
+    xd = torch.empty_like(bd)
+    for _ in range(3):
+        h.mf_solve_device(16, bd.data_ptr(), xd.data_ptr(), allow_no_convergence=True)
+    torch.cuda.synchronize()
+    c0 = g.lib().mf_launch_counter()
+    torch.cuda.profiler.start()
+    t0 = time.perf_counter()
+    h.mf_solve_device(16, bd.data_ptr(), xd.data_ptr(), allow_no_convergence=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
+    return {"item": "preconditioner application, 16 RHS", "grid": grid, "ms": dt * 1e3,
+            "launches": g.lib().mf_launch_counter() - c0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", nargs="*", default=["narrow", "front", "rowid"])
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--grid", type=int, default=64)
+    args = ap.parse_args()
+    import torch
+    from paper_2007_00202_gb300 import build, mf
+    build.build()
+    for w in args.which:
+        if w in ("factor", "solve"):
+            r = {"factor": factor, "solve": solve}[w](torch, mf, args.reps, args.grid)
+        else:
+            r = {"narrow": narrow, "front": front, "rowid": rowid}[w](torch, mf, args.reps)
+        print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

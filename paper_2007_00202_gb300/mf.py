@@ -21,6 +21,7 @@ ERRORS = {-1: "MF_ERR_ARG", -2: "MF_ERR_STATE", -3: "MF_ERR_UNSUPPORTED", -4: "M
 MF_LATTICE_NODE, MF_LATTICE_EDGE = 0, 1
 MF_PREC_C64, MF_PREC_C128 = 0, 1
 MF_REFINE_NONE, MF_REFINE_GMRES, MF_REFINE_IR = 0, 1, 2
+MF_PROF_NARROW_GEMM, MF_PROF_FRONT_GEMM = 0, 1
 MF_OPTIONS_V1 = 1
 
 
@@ -50,7 +51,7 @@ class mf_stats_t(C.Structure):
 
 
 class mf_kernel_profile_t(C.Structure):
-    _fields_ = [("launches", C.c_int64), ("ms", C.c_double), ("flops", C.c_double)]
+    _fields_ = [("launches", C.c_int64), ("ms", C.c_double), ("flops", C.c_double), ("bytes", C.c_double)]
 
 
 class mf_request_info(C.Structure):
@@ -100,7 +101,7 @@ SIGNATURES = {
     "mf_gemm_nrhs_c64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int64, C.c_int64, _P,
                                    C.c_int64, C.c_int64, _P, C.c_int64, C.c_int64, C.c_float, C.c_float, C.c_int32,
                                    _P]),
-    "mf_profile_read": (C.c_int, [_P, C.POINTER(mf_kernel_profile_t)]),
+    "mf_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(mf_kernel_profile_t)]),
     "mf_analysis_sizes": (C.c_int, [_P, C.POINTER(mf_analysis_sizes_t)]),
     "mf_analysis_export": (C.c_int, [_P, _I64P, _I64P, _I64P, _I32P, _I64P, _I64P]),
     "mf_front_trees": (C.c_int, [_P, C.c_int64, _I64P, _I64P]),
@@ -196,10 +197,11 @@ class Handle:
     def mf_profile(self, enable: bool):
         _check(lib().mf_profile(self.ptr, 1 if enable else 0), self.ptr)
 
-    def mf_profile_read(self) -> dict:
+    def mf_profile_read(self, kernel: int = 0) -> dict:
+        """kernel: MF_PROF_NARROW_GEMM (0) or MF_PROF_FRONT_GEMM (1); see include/mf.h."""
         p = mf_kernel_profile_t()
-        _check(lib().mf_profile_read(self.ptr, C.byref(p)), self.ptr)
-        return dict(launches=p.launches, ms=p.ms, flops=p.flops)
+        _check(lib().mf_profile_read(self.ptr, kernel, C.byref(p)), self.ptr)
+        return dict(launches=p.launches, ms=p.ms, flops=p.flops, bytes=p.bytes)
 
     # ---------------- inspection (host only) ----------------
     def mf_analysis_export(self) -> dict:

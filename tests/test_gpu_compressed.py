@@ -88,3 +88,24 @@ def test_solve_graph_replay_matches_eager(g):
         assert np.linalg.norm(y - xs[0]) <= 1e-4 * np.linalg.norm(xs[0])
     A = p.to_scipy()
     assert np.max(np.linalg.norm(A @ xs[0] - b, axis=0) / np.linalg.norm(b, axis=0)) <= 5e-2
+
+
+def test_profile_counters(g):
+    # event timing of the narrow GEMM (factor and graph-replayed solve) and of the front GEMMs
+    p = w.helmholtz7(16, 8)
+    b = w.rhs_gaussian(p, 4, 7)
+    h = g.analyze_problem(p, nmin_sep=64, leaf_size=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES)
+    h.mf_factor(1e-4)
+    h.mf_profile(True)
+    h.mf_factor(1e-4)
+    x, info = h.mf_solve(b)
+    x2, info2 = h.mf_solve(b)
+    nar = h.mf_profile_read(g.MF_PROF_NARROW_GEMM)
+    fr = h.mf_profile_read(g.MF_PROF_FRONT_GEMM)
+    h.mf_profile(False)
+    assert nar["launches"] > 100 and nar["ms"] > 0 and nar["flops"] > 0 and nar["bytes"] > 0
+    assert fr["launches"] > 0 and fr["ms"] > 0 and fr["flops"] > 0
+    A = p.to_scipy()
+    for xx in (x, x2):
+        assert np.max(np.linalg.norm(A @ xx - b, axis=0) / np.linalg.norm(b, axis=0)) <= 1e-8
+    assert h.mf_profile_read(g.MF_PROF_NARROW_GEMM)["launches"] == 0

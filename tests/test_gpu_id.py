@@ -57,7 +57,8 @@ def run_gpu_id(torch, mats, tol, max_rank=0, fn=None):
 
 
 @pytest.mark.parametrize("m,n,kind,tol", [(64, 640, "lowrank", 1e-5), (40, 300, "decay", 1e-3),
-                                          (128, 1000, "decay", 1e-4), (7, 5, "decay", 1e-2)])
+                                          (128, 1000, "decay", 1e-4), (7, 5, "decay", 1e-2),
+                                          (128, 72, "decay", 1e-4)])
 def test_row_id_matches_oracle(tk, m, n, kind, tol):
     rng = np.random.default_rng(m * n)
     mats = _mats(rng, 12, m, n, kind)
