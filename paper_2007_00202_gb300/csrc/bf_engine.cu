@@ -204,6 +204,7 @@ void BFContext<T>::flush() {
 
 template <typename T>
 const void* BFContext<T>::upload(const void* src, size_t bytes) {
+  HostTimer ht_(t_host + H_UPLOAD);
   if (cap_mode == 2) {
     const size_t o = (cap_off + 15) & ~size_t(15);
     if (o + bytes > cap_cap) {
@@ -298,6 +299,7 @@ void BFContext<T>::check_status() {
 
 template <typename T>
 void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
+  HostTimer ht_(t_host + H_GEMM);
   std::vector<GemmDesc<T>> D;
   int maxn = 0, maxk = 1;
   for (auto& d : descs) {
@@ -350,6 +352,7 @@ void BFContext<T>::zero(Blk<T>& b) {
 
 template <typename T>
 static void run_blk2(BFContext<T>& cx, std::vector<Blk2Job<T>>& jobs) {
+  typename BFContext<T>::HostTimer ht_(cx.t_host + BFContext<T>::H_BLK2);
   if (jobs.empty()) return;
   int64_t mx = 0;
   for (auto& j : jobs) mx = std::max<int64_t>(mx, (int64_t)j.rows * j.cols);
@@ -365,6 +368,7 @@ static const int32_t* dev_idx(BFContext<T>& cx, const IdxVec& v) {
 template <typename T>
 void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_rank, std::vector<IdxVec>& sk,
                            std::vector<Blk<T>>& Us) {
+  HostTimer ht_(t_host + H_ROWID);
   const size_t nj = Ms.size();
   sk.assign(nj, {});
   Us.assign(nj, Blk<T>());
@@ -461,6 +465,7 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
 template <typename T>
 void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vector<Blk<T>>& X, std::vector<Blk<T>>& Y,
                          bool transpose, bool accumulate) {
+  HostTimer ht_(t_host + H_APPLY);
   const size_t nb = bfs.size();
   if (!nb) return;
   std::map<int, std::vector<GemmDesc<T>>> stages;   // stage index -> descs
@@ -723,13 +728,17 @@ void BFContext<T>::entry_eval_batch(const DExtract<T>& ext, std::vector<BFProble
                             : cat(bf.Osk[l + 1][bf.pidx(l + 1, 2 * i, j / 2)],
                                   bf.Osk[l + 1][bf.pidx(l + 1, 2 * i + 1, j / 2)]);
           const Range c = bf.ct[L - l][j];
+          HostTimer tp_(t_host + H_PROXY);
           loc[q].push_back({X, proxies(X, c.a, c.b, probs[q].nn_r, P.alpha, P.knn)});
         }
       shifted(loc[q], probs[q], all);
     }
     std::vector<Blk<T>> blocks(all.size());
     for (size_t t = 0; t < all.size(); ++t) blocks[t] = new_blk<T>(scratch, (int)all[t].first.size(), (int)all[t].second.size());
-    ext(all, blocks);
+    {
+      HostTimer te_(t_host + H_EXT);
+      ext(all, blocks);
+    }
     std::vector<IdxVec> sk;
     std::vector<Blk<T>> Us;
     row_ids(blocks, P.tol, P.max_rank, sk, Us);
@@ -756,6 +765,7 @@ void BFContext<T>::entry_eval_batch(const DExtract<T>& ext, std::vector<BFProble
                             : cat(bf.Ssk[l - 1][bf.pidx(l - 1, i / 2, 2 * j)],
                                   bf.Ssk[l - 1][bf.pidx(l - 1, i / 2, 2 * j + 1)]);
           const Range r = bf.rt[l][i];
+          HostTimer tp_(t_host + H_PROXY);
           loc[q].push_back({proxies(Y, r.a, r.b, probs[q].nn_c, P.alpha, P.knn), Y});
         }
       shifted(loc[q], probs[q], all);
@@ -765,7 +775,10 @@ void BFContext<T>::entry_eval_batch(const DExtract<T>& ext, std::vector<BFProble
       blocks[t] = new_blk<T>(scratch, (int)all[t].first.size(), (int)all[t].second.size());
       tblocks[t] = new_blk<T>(scratch, (int)all[t].second.size(), (int)all[t].first.size());
     }
-    ext(all, blocks);
+    {
+      HostTimer te_(t_host + H_EXT);
+      ext(all, blocks);
+    }
     std::vector<Blk2Job<T>> tj;
     for (size_t t = 0; t < all.size(); ++t) {
       Blk2Job<T> jb{};
@@ -803,7 +816,10 @@ void BFContext<T>::entry_eval_batch(const DExtract<T>& ext, std::vector<BFProble
         blocks.push_back(bf.B[p]);
       }
     }
-    ext(all, blocks);
+    {
+      HostTimer te_(t_host + H_EXT);
+      ext(all, blocks);
+    }
   }
   sync();
   scratch.release(mk);
@@ -1024,6 +1040,7 @@ struct ExtractPlan {
 template <typename T>
 static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vector<std::pair<IdxVec, IdxVec>>& lst,
                             std::vector<Blk<T>>& dst, T sign, ExtractPlan<T>& EP) {
+  typename BFContext<T>::HostTimer ht_(cx.t_host + BFContext<T>::H_EXTRACT);
   const int L = bf.L, lc = bf.lc;
   struct Part {
     int p0, p1;   // positions [p0, p1) in the sorted list
@@ -1397,6 +1414,7 @@ void BFContext<T>::hodbf_apply(const DHODBF<T>& H, const Blk<T>& X, Blk<T>& Y, b
 template <typename T>
 void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair<IdxVec, IdxVec>>& lst,
                                  std::vector<Blk<T>>& dst, T sign) {
+  HostTimer ht_(t_host + H_HEXTRACT);
   const int LH = H.LH;
   std::vector<Blk2Job<T>> gj;
   std::vector<PlaceJob<T>> pj;
@@ -1896,6 +1914,7 @@ void BFContext<T>::run_lstsq(std::vector<LstsqJob<T>>& lj) {
 template <typename T>
 Blk<T> BFContext<T>::make_sketch(int rows, const std::vector<Range>& groups, int q, int level, int side, uint32_t key,
                                  std::vector<std::pair<int, int>>& cols) {
+  HostTimer ht_(t_host + H_SKETCH);
   cols.clear();
   int tot = 0;
   std::vector<SketchGroup> sg;
@@ -1954,6 +1973,7 @@ void BFContext<T>::axpy_b(const std::vector<Blk<T>>& x, std::vector<Blk<T>>& y, 
 template <typename T>
 void BFContext<T>::random_matvec_batch(const DOpB<T>& op, std::vector<RMProblem<T>>& probs, int L,
                                        const BFParams& P) {
+  HostTimer ht_(t_host + H_RMV);
   const size_t nq = probs.size();
   if (!nq) return;
   const int lc = L / 2;

@@ -14,6 +14,7 @@
 #include <cstdint>
 #include <functional>
 #include <memory>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -223,6 +224,15 @@ class BFContext {
   bool cap_bad = false;
   double t_wait = 0;                // seconds the host spent waiting for the stream
   LaunchProfiler* prof = nullptr;   // event timing of the narrow GEMM launches (when on)
+  // host seconds spent inside the main routines (inclusive; read by the MF_TRACE=1 phase trace)
+  enum { H_GEMM, H_ROWID, H_APPLY, H_EXTRACT, H_PROXY, H_RMV, H_BLK2, H_SKETCH, H_UPLOAD, H_HEXTRACT, H_EXT, H_N };
+  double t_host[H_N] = {};
+  struct HostTimer {
+    double* acc;
+    std::chrono::steady_clock::time_point t0;
+    explicit HostTimer(double* a) : acc(a), t0(std::chrono::steady_clock::now()) {}
+    ~HostTimer() { *acc += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+  };
   Arena persist, scratch;
   DevMem status;
   double flops = 0;

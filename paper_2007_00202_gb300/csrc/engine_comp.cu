@@ -152,18 +152,26 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
   int64_t lp = launch_count();
   int64_t idp = cx.n_id, cpp = cx.n_copies;
   double wp = cx.t_wait;
+  std::vector<double> hp(cx.t_host, cx.t_host + BFContext<T>::H_N);
   auto phase = [&](const char* name) {
     if (!trace) return;
     cx.sync();
     auto tn = std::chrono::steady_clock::now();
-    fprintf(stderr, "[mf] front %d (s=%d u=%d) %-10s %8.3f s (waiting %6.3f s) %7lld launches %6lld IDs %7lld copies\n",
+    static const char* hn[] = {"gemm", "rowid", "apply", "extract", "proxy", "rmv", "blk2", "sketch", "upload",
+                               "hextract", "ext"};
+    char hb[512];
+    int o = 0;
+    for (int c = 0; c < BFContext<T>::H_N; ++c)
+      o += snprintf(hb + o, sizeof(hb) - o, " %s %.3f", hn[c], cx.t_host[c] - hp[c]);
+    fprintf(stderr, "[mf] front %d (s=%d u=%d) %-10s %8.3f s (waiting %6.3f s) %7lld launches %6lld IDs %7lld copies |%s\n",
             fid, s, u, name, std::chrono::duration<double>(tn - tp).count(), cx.t_wait - wp,
-            (long long)(launch_count() - lp), (long long)(cx.n_id - idp), (long long)(cx.n_copies - cpp));
+            (long long)(launch_count() - lp), (long long)(cx.n_id - idp), (long long)(cx.n_copies - cpp), hb);
     tp = tn;
     lp = launch_count();
     idp = cx.n_id;
     cpp = cx.n_copies;
     wp = cx.t_wait;
+    hp.assign(cx.t_host, cx.t_host + BFContext<T>::H_N);
   };
   cf.F11 = cx.hodbf_entry_eval(make_ext(0, 0, true, false), s, th, nn11, P);
   phase("F11");

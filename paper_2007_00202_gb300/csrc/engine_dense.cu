@@ -38,6 +38,7 @@ class DenseEngine : public EngineBase {
 
   void factor(double tol) override {
     const int64_t c0 = launch_count();
+    const auto tf0 = std::chrono::steady_clock::now();
     MF_CUDA(cudaMemsetAsync(arena_.p, 0, zero_bytes_, st_));
     MF_CUDA(cudaMemsetAsync(status_.p, 0, sizeof(int32_t), st_));
     BFParams P;
@@ -70,6 +71,11 @@ class DenseEngine : public EngineBase {
       }
     }
     if (comp_) comp_flops_ = comp_->cx.flops;
+    if (getenv("MF_TRACE") && getenv("MF_TRACE")[0] == '1') {
+      MF_CUDA(cudaStreamSynchronize(st_));
+      fprintf(stderr, "[mf] factor: %.3f s, compressed fronts %.3f s (host-issued, synchronised per phase)\n",
+              std::chrono::duration<double>(std::chrono::steady_clock::now() - tf0).count(), comp_seconds_);
+    }
     MF_CUDA(cudaGetLastError());
     nlaunch_factor_ = (int)(launch_count() - c0);
     int32_t stat = 0;
