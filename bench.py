@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-dense", action="store_true", help="skip the all-dense complex64 comparison step")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) measurement")
     return ap.parse_args()
 
 
@@ -195,13 +196,13 @@ def roofline_front(prof, peaks):
 
 def cpu_baseline():
     """The FP64 oracle on a bounded sample of the same workload: the same Helmholtz
-    operator (ppw 10) at 16^3, separators >= 128 HOD-BF compressed at tol 1e-4 with
+    operator (ppw 10) at 20^3, separators >= 128 HOD-BF compressed at tol 1e-4 with
     rank cap 64, factor + GMRES(30) solve of 16 RHS to 1e-8, timed on the host cores."""
     import numpy as np
     import workloads as w
     from oracle.analysis import analyze
     from oracle import compressed_mf as cm, gmres as gm
-    p = w.helmholtz7(16, 10)
+    p = w.helmholtz7(20, 10)
     b = w.rhs_gaussian(p, 16, 7)
     A = p.to_scipy()
     t0 = time.perf_counter()
@@ -212,8 +213,60 @@ def cpu_baseline():
     cores = len(os.sched_getaffinity(0))
     return {"value": 16 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle: HOD-BF multifrontal factor (tol 1e-4, rank <= 64, separators >= 128) + "
-                      f"GMRES(30) of 16 RHS to 1e-8 on helmholtz7 16^3 (N={p.n}); {dt:.1f} s, "
+                      f"GMRES(30) of 16 RHS to 1e-8 on helmholtz7 20^3 (N={p.n}); {dt:.1f} s, "
                       f"{max(its)} iterations, residual {max(res):.1e}"}
+
+
+def serving(g, w, torch):
+    """Continuous batching over resident factorizations (the serving workload, bounded): the
+    helmholtz7 32^3 and 64^3 problems (complex64, separators >= 1024 HOD-BF at tol 1e-4, rank
+    <= 64) factored and kept on the device, each on its own stream; 60 requests with Poisson
+    arrivals (mean gap 100 ms, seed 5), each 1-16 complex Gaussian right-hand sides for a problem
+    drawn uniformly; solved to 1e-8 by GMRES in the batches the server forms.  Latency is
+    arrival to completion."""
+    import numpy as np
+    probs = [w.helmholtz7(32, 10), w.helmholtz7(64, 10)]
+    streams = [torch.cuda.Stream() for _ in probs]
+    hs = []
+    for p, st in zip(probs, streams):
+        h = g.analyze_problem(p, nmin_sep=1024, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
+                              stream=st.cuda_stream)
+        h.mf_factor(1e-4)
+        hs.append(h)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    pools = [np.asfortranarray(w.complex_gaussian(rng, p.n, 16)) for p in probs]
+    nreq = 60
+    gaps = rng.exponential(0.1, nreq)
+    which = rng.integers(0, len(probs), nreq)
+    widths = rng.integers(1, 17, nreq)
+    srv = g.Server(hs, max_batch_rhs=256, mem_budget_bytes=96 << 30)
+    ids, t0 = [], time.perf_counter()
+    t = t0
+    for k in range(nreq):
+        t += gaps[k]
+        while time.perf_counter() < t:
+            time.sleep(max(0.0, min(1e-3, t - time.perf_counter())))
+        ids.append((srv.submit(int(which[k]), pools[which[k]][:, :widths[k]]), int(which[k]), int(widths[k])))
+    lat, batches, worst = [], [], 0.0
+    checked = set()
+    for rid, pi, k in ids:
+        x, info = srv.wait(rid)
+        lat.append((info["t_done"] - info["t_arrival"]) * 1e3)
+        batches.append(info["batch_rhs"])
+        if pi not in checked:
+            A = probs[pi].to_scipy()
+            bb = pools[pi][:, :k]
+            worst = max(worst, float(np.max(np.linalg.norm(A @ x - bb, axis=0) / np.linalg.norm(bb, axis=0))))
+            checked.add(pi)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat.sort()
+    return {"workload": "helmholtz7 32^3 + 64^3 resident, complex64 HOD-BF tol 1e-4; 60 Poisson requests "
+                        "(mean gap 100 ms, seed 5) of 1-16 RHS each, GMRES to 1e-8",
+            "requests": nreq, "rhs": int(widths.sum()), "p50_ms": lat[len(lat) // 2],
+            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "solves_per_s": float(widths.sum()) / wall,
+            "mean_batch_rhs": float(np.mean(batches)), "max_rel_residual_checked": worst}
 
 
 def run_reference(args, rank, world):
@@ -228,7 +281,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 16 / v * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": "helmholtz7 16^3 sample of the 64^3 workload (FP64 CPU oracle, HOD-BF tol 1e-4)",
+            "config": {"workload": "helmholtz7 20^3 sample of the 64^3 workload (FP64 CPU oracle, HOD-BF tol 1e-4)",
                        "nrhs": 16},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -392,6 +445,8 @@ def main():
         line["fp64_butterfly_path"] = {"factor_s": fb, "solve_s": sb, "solves_per_s": nrhs / (fb + sb),
                                        "gmres_iters": int(infob.iters), "max_rel_residual": infob.max_rel_residual}
         del hb
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving(g, w, torch)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

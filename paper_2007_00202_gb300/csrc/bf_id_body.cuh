@@ -1,6 +1,6 @@
 // Device body of the batched row interpolative decomposition (Sec. 3), shared
-// by the batched kernel and its fixed-scratch variant.  One CTA (256 threads)
-// per matrix; dynamic shared memory of row_id_smem_bytes(m, n, work_in_smem):
+// by the batched kernel and its fixed-scratch variant.  One CTA (256 threads, or
+// 1024 for matrices whose work stays in global memory) per matrix; dynamic shared memory of row_id_smem_bytes(m, n, work_in_smem):
 // the QR work matrix (2 m n values) sits there too when work_in_smem, else in
 // jb.work.
 //
@@ -25,8 +25,8 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
   T* vi = vr + n;
   T* nrm = vi + n;                           // remaining squared norms, by position
   int* perm = reinterpret_cast<int*>(nrm + m);
-  __shared__ T red_v[8];
-  __shared__ int red_i[8];
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
   __shared__ T sh_alpha_r, sh_alpha_i, sh_scale, sh_ref;
   __shared__ int sh_p, sh_stop;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -84,18 +84,13 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
     const int pr = perm[k];
     T* xr = Wr + (int64_t)pr * n;
     T* xi = Wi + (int64_t)pr * n;
-    T s2 = 0;
     for (int c = k + tid; c < n; c += blockDim.x) {
-      T a = xr[c], b = xi[c];
-      vr[c] = a; vi[c] = b;
-      s2 += a * a + b * b;
+      vr[c] = xr[c];
+      vi[c] = xi[c];
     }
-    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    if (lane == 0) red_v[warp] = s2;
     __syncthreads();
     if (tid == 0) {
-      T tot = 0;
-      for (int w = 0; w < nw; ++w) tot += red_v[w];
+      const T tot = nrm[k];   // the pivot row's squared norm over coordinates k.. (independent of blockDim)
       T nx = sqrt(tot);
       T x0r = vr[k], x0i = vi[k];
       T ax0 = sqrt(x0r * x0r + x0i * x0i);
@@ -124,6 +119,7 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
       T* yi = Wi + (int64_t)(act ? perm[q] : 0) * n;
       T dr = 0, di = 0;   // v^H y
       if (act)
+#pragma unroll 4
         for (int c = k + glane; c < n; c += G) {
           T a = vr[c], b = vi[c], p = yr[c], r = yi[c];
           dr += a * p + b * r;
@@ -137,6 +133,7 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
       di *= sc;
       T s = 0;
       if (act)
+#pragma unroll 4
         for (int c = k + glane; c < n; c += G) {
           T a = vr[c], b = vi[c];
           T p = yr[c] - (a * dr - b * di);

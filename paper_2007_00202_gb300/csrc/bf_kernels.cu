@@ -14,8 +14,8 @@ namespace mf {
 // ---------------------------------------------------------------------------
 // Batched row ID (Sec. 3), one CTA per matrix (body in bf_id_body.cuh).
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_row_id(const IdJob<T>* jobs, T tol, int32_t max_rank, int work_in_smem) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_row_id(const IdJob<T>* jobs, T tol, int32_t max_rank, int work_in_smem) {
   row_id_body<T>(jobs[blockIdx.x], tol, max_rank, work_in_smem != 0);
 }
 
@@ -27,11 +27,14 @@ int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol
   if (sm > kRowIdSmemCap) return -1;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_row_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
+    cudaFuncSetAttribute(k_row_id<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
+    cudaFuncSetAttribute(k_row_id<T, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
     attr = true;
   }
   count_launches(1);
-  k_row_id<T><<<njobs, 256, sm, st>>>(d_jobs, tol, max_rank, work_in_smem ? 1 : 0);
+  // matrices in global memory are the large ones (few per launch): a 1024-thread CTA each
+  if (work_in_smem) k_row_id<T, 256><<<njobs, 256, sm, st>>>(d_jobs, tol, max_rank, 1);
+  else k_row_id<T, 1024><<<njobs, 1024, sm, st>>>(d_jobs, tol, max_rank, 0);
   return 0;
 }
 

@@ -656,43 +656,45 @@ void launch_gather_upd(const FrontDev<T>* d_fronts, const int32_t* d_flist, int 
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_to_planar(const double* src, int64_t ld, int64_t n, int nrhs, const int64_t* perm, T* dst,
-                            int64_t pl) {
+                            int64_t pl, int pld) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * nrhs) return;
   int64_t i = e / nrhs;
   int c = (int)(e % nrhs);
   int64_t o = perm ? perm[i] : i;
-  dst[e] = (T)src[2 * (o + c * ld)];
-  dst[e + pl] = (T)src[2 * (o + c * ld) + 1];
+  dst[i * pld + c] = (T)src[2 * (o + c * ld)];
+  dst[i * pld + c + pl] = (T)src[2 * (o + c * ld) + 1];
 }
 
 template <typename T>
 __global__ void k_from_planar(const T* src, int64_t pl, int64_t n, int nrhs, const int64_t* perm, double* dst,
-                              int64_t ld) {
+                              int64_t ld, int pld) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * nrhs) return;
   int64_t i = e / nrhs;
   int c = (int)(e % nrhs);
   int64_t o = perm ? perm[i] : i;
-  dst[2 * (o + c * ld)] = (double)src[e];
-  dst[2 * (o + c * ld) + 1] = (double)src[e + pl];
+  dst[2 * (o + c * ld)] = (double)src[i * pld + c];
+  dst[2 * (o + c * ld) + 1] = (double)src[i * pld + c + pl];
 }
 
 template <typename T>
 void launch_to_planar(const double* src, int64_t ld, int64_t n, int nrhs, const int64_t* perm, T* dst, int64_t pl,
-                      cudaStream_t st) {
+                      cudaStream_t st, int pld) {
+  if (pld <= 0) pld = nrhs;
   int64_t tot = n * nrhs;
   if (tot <= 0) return;
   g_launches++;
-  k_to_planar<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, ld, n, nrhs, perm, dst, pl);
+  k_to_planar<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, ld, n, nrhs, perm, dst, pl, pld);
 }
 template <typename T>
 void launch_from_planar(const T* src, int64_t pl, int64_t n, int nrhs, const int64_t* perm, double* dst, int64_t ld,
-                        cudaStream_t st) {
+                        cudaStream_t st, int pld) {
+  if (pld <= 0) pld = nrhs;
   int64_t tot = n * nrhs;
   if (tot <= 0) return;
   g_launches++;
-  k_from_planar<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, pl, n, nrhs, perm, dst, ld);
+  k_from_planar<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, pl, n, nrhs, perm, dst, ld, pld);
 }
 
 // ---------------------------------------------------------------------------
@@ -871,9 +873,9 @@ void launch_colnorm2(int64_t n, int nrhs, const double* X, int64_t ldx, double* 
   template void launch_gather_upd<T>(const FrontDev<T>*, const int32_t*, int, int, const T*, int64_t, int,        \
                                      T* const*, cudaStream_t);                                                    \
   template void launch_to_planar<T>(const double*, int64_t, int64_t, int, const int64_t*, T*, int64_t,            \
-                                    cudaStream_t);                                                                \
+                                    cudaStream_t, int);                                                           \
   template void launch_from_planar<T>(const T*, int64_t, int64_t, int, const int64_t*, double*, int64_t,          \
-                                      cudaStream_t);
+                                      cudaStream_t, int);
 
 MF_INST(float)
 MF_INST(double)

@@ -87,11 +87,20 @@ class DenseEngine : public EngineBase {
     if (stat != DEV_OK) throw SingularError("zero pivot in a dense front");
   }
 
+  // Solve programs exist for column counts 16, 32, 64, ...: a call with nrhs columns runs the
+  // smallest one that holds them (the extra columns stay zero; columns never mix).
+  static int nrhs_bucket(int nrhs) {
+    int nb = 16;
+    while (nb < nrhs) nb *= 2;
+    return nb;
+  }
+
   void apply_precond(const double* x, double* y, int nrhs) override {
-    SolveProg& sp = solve_prog(nrhs);
+    const int nb = nrhs_bucket(nrhs);
+    SolveProg& sp = solve_prog(nb);
     const int64_t n = an_.n;
     T* X = sp.X.template as<T>();
-    const int64_t xpl = n * nrhs;
+    const int64_t xpl = n * nb;
     static const bool trace = getenv("MF_TRACE") && getenv("MF_TRACE")[0] == '1';
     std::chrono::steady_clock::time_point t0;
     const int state0 = sp.state;
@@ -99,9 +108,9 @@ class DenseEngine : public EngineBase {
       MF_CUDA(cudaStreamSynchronize(st_));
       t0 = std::chrono::steady_clock::now();
     }
-    launch_to_planar<T>(x, n, n, nrhs, nullptr, X, xpl, st_);
+    launch_to_planar<T>(x, n, n, nrhs, nullptr, X, xpl, st_, nb);
     run_solve_ops(sp);
-    launch_from_planar<T>(X, xpl, n, nrhs, nullptr, y, n, st_);
+    launch_from_planar<T>(X, xpl, n, nrhs, nullptr, y, n, st_, nb);
     MF_CUDA(cudaGetLastError());
     if (trace) {
       auto t1 = std::chrono::steady_clock::now();
@@ -116,7 +125,7 @@ class DenseEngine : public EngineBase {
   double factor_flops() const override { return flops_ + comp_flops_; }
   double factor_bytes() const override { return factor_bytes_; }
   int launches_factor() const override { return nlaunch_factor_; }
-  int launches_solve(int nrhs) override { return solve_prog(nrhs).nlaunch + 2; }
+  int launches_solve(int nrhs) override { return solve_prog(nrhs_bucket(nrhs)).nlaunch + 2; }
 
  private:
   struct SolveProg {
@@ -638,6 +647,7 @@ class DenseEngine : public EngineBase {
     const auto& F = an_.fronts;
     const int64_t n = an_.n;
     sp->X.alloc(sizeof(T) * 2 * n * nrhs);
+    MF_CUDA(cudaMemsetAsync(sp->X.p, 0, sizeof(T) * 2 * n * nrhs, st_));   // padding columns stay zero
     // per-front temps ta (s x nrhs), tb (s x nrhs), tu (u x nrhs)
     std::vector<size_t> ta(F.size()), tb(F.size()), tu(F.size());
     size_t off = 0;

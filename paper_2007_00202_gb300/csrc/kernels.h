@@ -89,10 +89,10 @@ void launch_gather_sep(const FrontDev<T>* d_fronts, const int32_t* d_flist, int 
 // and planar T (row-major N x nrhs, new numbering).
 template <typename T>
 void launch_to_planar(const double* src, int64_t ld, int64_t n, int nrhs, const int64_t* perm, T* dst, int64_t pl,
-                      cudaStream_t st);
+                      cudaStream_t st, int pld = 0);   // planar rows of pld >= nrhs values (0: nrhs)
 template <typename T>
 void launch_from_planar(const T* src, int64_t pl, int64_t n, int nrhs, const int64_t* perm, double* dst, int64_t ld,
-                        cudaStream_t st);
+                        cudaStream_t st, int pld = 0);
 
 // FP64 sparse residual and Krylov helpers (interleaved complex128, column-major n x nrhs).
 void launch_spmv_residual(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
