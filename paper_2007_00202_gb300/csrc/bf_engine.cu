@@ -3,6 +3,7 @@
 // and solve is a batched device launch on the context's stream.
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -1077,7 +1078,8 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
     for (int l = 0; l <= L; ++l) { Xp[l] = parts(bf.rt, l, X); Yp[l] = parts(bf.ct, l, Y); }
     auto nonempty = [](const Part& p) { return p.p1 > p.p0; };
     // E^l blocks, l = L .. lc : rows = positions of X in O_i, cols = r(l,i,j)
-    std::vector<std::map<int, Blk<T>>> E(L + 1), F(L + 1);
+    std::vector<std::vector<Blk<T>>> E(L + 1, std::vector<Blk<T>>((size_t)1 << L)),
+        F(L + 1, std::vector<Blk<T>>((size_t)1 << L));   // p == nullptr: absent
     const IdxVec* Xptr = &X;
     for (int i = 0; i < (1 << L); ++i) {
       if (!nonempty(Xp[L][i]) || !nonempty(Yp[0][0])) continue;
@@ -1113,13 +1115,13 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
             const int ci = 2 * i + t;
             if (!nonempty(Xp[l + 1][ci])) continue;
             const int cp = bf.pidx(l + 1, ci, jj / 2);
-            auto it = E[l + 1].find(cp);
+            const Blk<T>& ec = E[l + 1][cp];
             const int nrc = Xp[l + 1][ci].p1 - Xp[l + 1][ci].p0;
             const int rc = bf.rr(l + 1, ci, jj / 2);
             const Blk<T>& R = bf.U[l][p];
             const int off = Xp[l + 1][ci].p0 - Xp[l][i].p0;
-            if (it == E[l + 1].end()) continue;
-            Estage[L - 1 - l].push_back(gdesc<T>(nrc, r, rc, 0, 0, T(1), T(0), it->second,
+            if (!ec.p) continue;
+            Estage[L - 1 - l].push_back(gdesc<T>(nrc, r, rc, 0, 0, T(1), T(0), ec,
                                          R.sub(t == 0 ? 0 : r1, 0, rc, R.cols), e.sub(off, 0, nrc, r)));
             (void)roff;
           }
@@ -1158,13 +1160,13 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
             const int cj = 2 * jj + t;
             if (!nonempty(Yp[L - l + 1][cj])) continue;
             const int cp = bf.pidx(l - 1, i / 2, cj);
-            auto it = F[l - 1].find(cp);
-            if (it == F[l - 1].end()) continue;
+            const Blk<T>& fc = F[l - 1][cp];
+            if (!fc.p) continue;
             const int nrc = Yp[L - l + 1][cj].p1 - Yp[L - l + 1][cj].p0;
             const int cc = bf.rc(l - 1, i / 2, cj);
             const Blk<T>& W = bf.V[l][p];
             const int off = Yp[L - l + 1][cj].p0 - Yp[L - l][jj].p0;
-            Fstage[l - 1].push_back(gdesc<T>(nrc, c, cc, 0, 0, T(1), T(0), it->second,
+            Fstage[l - 1].push_back(gdesc<T>(nrc, c, cc, 0, 0, T(1), T(0), fc,
                                          W.sub(t == 0 ? 0 : c1, 0, cc, W.cols), f.sub(off, 0, nrc, c)));
           }
         }
@@ -1173,16 +1175,16 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
       for (int jj = 0; jj < (1 << (L - lc)); ++jj) {
         if (!nonempty(Xp[lc][i]) || !nonempty(Yp[L - lc][jj])) continue;
         const int p = bf.pidx(lc, i, jj);
-        auto ie = E[lc].find(p);
-        auto iff = F[lc].find(p);
-        if (ie == E[lc].end() || iff == F[lc].end()) continue;
+        const Blk<T>& ie = E[lc][p];
+        const Blk<T>& iff = F[lc][p];
+        if (!ie.p || !iff.p) continue;
         const int r = bf.rr(lc, i, jj), c = bf.rc(lc, i, jj);
         const int nx = Xp[lc][i].p1 - Xp[lc][i].p0, ny = Yp[L - lc][jj].p1 - Yp[L - lc][jj].p0;
         Blk<T> tmp = new_blk<T>(scratch, nx, std::max(c, 1));
         Blk<T> out = new_blk<T>(scratch, nx, ny);
         if (r == 0 || c == 0) continue;
-        centre1.push_back(gdesc<T>(nx, c, r, 0, 0, T(1), T(0), ie->second, bf.B[p], tmp));
-        centre2.push_back(gdesc<T>(nx, ny, c, 0, 1, T(1), T(0), tmp, iff->second, out));
+        centre1.push_back(gdesc<T>(nx, c, r, 0, 0, T(1), T(0), ie, bf.B[p], tmp));
+        centre2.push_back(gdesc<T>(nx, ny, c, 0, 1, T(1), T(0), tmp, iff, out));
         IdxVec rows, cols;
         for (int t = Xp[lc][i].p0; t < Xp[lc][i].p1; ++t) rows.push_back(xo[t]);
         for (int t = Yp[L - lc][jj].p0; t < Yp[L - lc][jj].p1; ++t) cols.push_back(yo[t]);
@@ -1428,19 +1430,35 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
   std::vector<Req> reqs;
   std::map<const DBF<T>*, size_t> req_of;
   std::vector<std::pair<char*, size_t>> zspans;   // accumulation targets, zeroed in as few memsets as possible
+  // each list item's indices sorted once (value, position): the part inside a tree range is a slice
+  std::vector<std::pair<int32_t, int32_t>> xs, ys;
+  auto sorted_of = [](const IdxVec& v, std::vector<std::pair<int32_t, int32_t>>& out) {
+    out.resize(v.size());
+    for (size_t a = 0; a < v.size(); ++a) out[a] = {v[a], (int32_t)a};
+    std::sort(out.begin(), out.end());
+  };
+  auto slice = [](const std::vector<std::pair<int32_t, int32_t>>& v, Range r, IdxVec& pos, IdxVec& loc) {
+    pos.clear();
+    loc.clear();
+    auto lo = std::lower_bound(v.begin(), v.end(), std::make_pair((int32_t)r.a, INT32_MIN));
+    auto hi = std::lower_bound(lo, v.end(), std::make_pair((int32_t)r.b, INT32_MIN));
+    for (auto it = lo; it != hi; ++it) {
+      pos.push_back(it->second);
+      loc.push_back(it->first - (int32_t)r.a);
+    }
+    return lo != hi;
+  };
   for (size_t q = 0; q < lst.size(); ++q) {
     const IdxVec& X = lst[q].first;
     const IdxVec& Y = lst[q].second;
     if (X.empty() || Y.empty()) continue;
+    sorted_of(X, xs);
+    sorted_of(Y, ys);
     // leaves
     for (size_t li = 0; li < H.tree[LH].size(); ++li) {
       const Range r = H.tree[LH][li];
       IdxVec px, py, rx, ry;
-      for (size_t a = 0; a < X.size(); ++a)
-        if (X[a] >= r.a && X[a] < r.b) { px.push_back((int32_t)a); rx.push_back(X[a] - (int32_t)r.a); }
-      for (size_t b = 0; b < Y.size(); ++b)
-        if (Y[b] >= r.a && Y[b] < r.b) { py.push_back((int32_t)b); ry.push_back(Y[b] - (int32_t)r.a); }
-      if (px.empty() || py.empty()) continue;
+      if (!slice(xs, r, px, rx) || !slice(ys, r, py, ry)) continue;
       Blk<T> t = new_blk<T>(scratch, (int)px.size(), (int)py.size());
       Blk2Job<T> j{};
       j.src = H.D[li].p; j.splane = H.D[li].plane; j.sld = H.D[li].ld;
@@ -1458,12 +1476,7 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
       for (int i = 0; i < (1 << l); ++i) {
         const Range rr = H.tree[l][i], cr = H.tree[l][i ^ 1];
         IdxVec px, py, rx, ry;
-        for (size_t a = 0; a < X.size(); ++a)
-          if (X[a] >= rr.a && X[a] < rr.b) { px.push_back((int32_t)a); rx.push_back(X[a] - (int32_t)rr.a); }
-        if (px.empty()) continue;
-        for (size_t b = 0; b < Y.size(); ++b)
-          if (Y[b] >= cr.a && Y[b] < cr.b) { py.push_back((int32_t)b); ry.push_back(Y[b] - (int32_t)cr.a); }
-        if (py.empty()) continue;
+        if (!slice(xs, rr, px, rx) || !slice(ys, cr, py, ry)) continue;
         const DBF<T>* bf = H.off[l][i].get();
         auto it = req_of.find(bf);
         if (it == req_of.end()) {
