@@ -842,187 +842,15 @@ std::unique_ptr<DBF<T>> BFContext<T>::entry_eval(const DExtract<T>& ext, int m, 
 template <typename T>
 std::unique_ptr<DBF<T>> BFContext<T>::random_matvec(const DOp<T>& op, const Tree& rt, const Tree& ct, int L,
                                                      const BFParams& P, uint32_t key) {
-  const int m = op.rows, n = op.cols;
-  auto bf = std::make_unique<DBF<T>>();
-  bf->init(m, n, rt, ct, L);
-  const int lc = bf->lc;
-  const int q0 = (P.max_rank > 0 ? P.max_rank : P.q_start) + P.p;
-  const size_t mk = scratch.mark();
-  Blk<T> cOm, cY;
-  std::vector<std::pair<int, int>> ccols;
-  auto sketch = [&](int rows, const std::vector<Range>& groups, int q, int level, int side,
-                    std::vector<std::pair<int, int>>& cols) -> Blk<T> {
-    cols.clear();
-    int tot = 0;
-    std::vector<SketchGroup> sg;
-    for (size_t g = 0; g < groups.size(); ++g) {
-      int size = (int)(groups[g].b - groups[g].a);
-      int w = size <= q ? size : q;
-      cols.push_back({tot, tot + w});
-      SketchGroup s;
-      s.a = groups[g].a; s.b = groups[g].b; s.c0 = tot; s.w = w;
-      s.key = (int32_t)((key * 1000003u + (uint32_t)level * 7919u + (uint32_t)side * 104729u + (uint32_t)g) & 0xFFFFFF);
-      s.identity = (w == size) ? 1 : 0;
-      if (w > 0) sg.push_back(s);
-      tot += w;
-    }
-    Blk<T> Om = new_blk<T>(scratch, rows, std::max(tot, 1));
-    Om.cols = tot;
-    zero(Om);
-    if (!sg.empty()) {
-      int mx = 0;
-      for (auto& s : sg) mx = std::max<int>(mx, (int)((s.b - s.a) * s.w));
-      const SketchGroup* dg = stage(sg.data(), sg.size());
-      launch_sketch<T>(dg, (int)sg.size(), mx, Om.p, Om.plane, (int)Om.ld, st);
-    }
-    return Om;
-  };
-  auto gather = [&](const Blk<T>& Y, const IdxVec& rows, std::pair<int, int> cols) -> std::pair<Blk<T>, GatherJob<T>> {
-    Blk<T> M = new_blk<T>(scratch, (int)rows.size(), cols.second - cols.first);
-    GatherJob<T> g;
-    g.src = Y.p; g.splane = Y.plane; g.sld = Y.ld;
-    g.rows = dev_idx(*this, rows);
-    g.c0 = cols.first;
-    g.nrows = (int)rows.size();
-    g.ncols = cols.second - cols.first;
-    g.dst = M.p; g.dplane = M.plane; g.dld = M.ld;
-    return {M, g};
-  };
-  auto run_gathers = [&](std::vector<GatherJob<T>>& gj) {
-    if (gj.empty()) return;
-    int64_t mx = 0;
-    for (auto& g : gj) mx = std::max<int64_t>(mx, (int64_t)g.nrows * g.ncols);
-    const GatherJob<T>* d = stage(gj.data(), gj.size());
-    launch_gather_rows<T>(d, (int)gj.size(), mx, st);
-  };
-  for (int l = L; l >= lc; --l) {                         // left half: sketches of K(X, S_nu)
-    const auto& groups = bf->ct[L - l];
-    int q = q0;
-    for (;;) {
-      std::vector<std::pair<int, int>> cols;
-      Blk<T> Om = sketch(n, groups, q, l, 0, cols);
-      Blk<T> Y = new_blk<T>(scratch, m, std::max(Om.cols, 1));
-      Y.cols = Om.cols;
-      if (Om.cols > 0) op.apply(Om, Y, false);
-      std::vector<Blk<T>> Ms;
-      std::vector<GatherJob<T>> gj;
-      std::vector<IdxVec> Xs;
-      for (int i = 0; i < (1 << l); ++i)
-        for (int j = 0; j < (1 << (L - l)); ++j) {
-          IdxVec X = l == L ? range_vec(bf->rt[L][i].a, bf->rt[L][i].b)
-                            : cat(bf->Osk[l + 1][bf->pidx(l + 1, 2 * i, j / 2)],
-                                  bf->Osk[l + 1][bf->pidx(l + 1, 2 * i + 1, j / 2)]);
-          auto pr = gather(Y, X, cols[j]);
-          Ms.push_back(pr.first);
-          if (pr.second.nrows && pr.second.ncols) gj.push_back(pr.second);
-          Xs.push_back(X);
-        }
-      run_gathers(gj);
-      std::vector<IdxVec> sk;
-      std::vector<Blk<T>> Us;
-      row_ids(Ms, P.tol, P.max_rank, sk, Us);
-      bool grow = false;
-      if (P.max_rank <= 0)
-        for (size_t p = 0; p < Ms.size(); ++p) {
-          int j = (int)(p % (1 << (L - l)));
-          int w = cols[j].second - cols[j].first, size = (int)(groups[j].b - groups[j].a);
-          if (w < size && (int)sk[p].size() > w - P.p) grow = true;
-        }
-      if (grow && q < 4096) {
-        q *= 2;
-        continue;
-      }
-      for (size_t p = 0; p < Ms.size(); ++p) {
-        bf->U[l][p] = Us[p];
-        IdxVec o;
-        for (int32_t s : sk[p]) o.push_back(Xs[p][s]);
-        bf->Osk[l][p] = o;
-      }
-      if (l == lc) { cOm = Om; cY = Y; ccols = cols; }
-      break;
-    }
-  }
-  const size_t mk2 = scratch.mark();
-  for (int l = 0; l <= lc; ++l) {                         // right half: sketches of K(O_tau, Y)^T
-    const auto& groups = bf->rt[l];
-    int q = q0;
-    for (;;) {
-      std::vector<std::pair<int, int>> cols;
-      Blk<T> Ps = sketch(m, groups, q, l, 1, cols);
-      Blk<T> Z = new_blk<T>(scratch, n, std::max(Ps.cols, 1));
-      Z.cols = Ps.cols;
-      if (Ps.cols > 0) op.apply(Ps, Z, true);
-      std::vector<Blk<T>> Ms;
-      std::vector<GatherJob<T>> gj;
-      std::vector<IdxVec> Ys;
-      for (int i = 0; i < (1 << l); ++i)
-        for (int j = 0; j < (1 << (L - l)); ++j) {
-          IdxVec Yc = l == 0 ? range_vec(bf->ct[L][j].a, bf->ct[L][j].b)
-                             : cat(bf->Ssk[l - 1][bf->pidx(l - 1, i / 2, 2 * j)],
-                                   bf->Ssk[l - 1][bf->pidx(l - 1, i / 2, 2 * j + 1)]);
-          auto pr = gather(Z, Yc, cols[i]);
-          Ms.push_back(pr.first);
-          if (pr.second.nrows && pr.second.ncols) gj.push_back(pr.second);
-          Ys.push_back(Yc);
-        }
-      run_gathers(gj);
-      std::vector<IdxVec> sk;
-      std::vector<Blk<T>> Vs;
-      row_ids(Ms, P.tol, P.max_rank, sk, Vs);
-      bool grow = false;
-      if (P.max_rank <= 0)
-        for (size_t p = 0; p < Ms.size(); ++p) {
-          int i = (int)(p / (1 << (L - l)));
-          int w = cols[i].second - cols[i].first, size = (int)(groups[i].b - groups[i].a);
-          if (w < size && (int)sk[p].size() > w - P.p) grow = true;
-        }
-      if (grow && q < 4096) {
-        q *= 2;
-        continue;
-      }
-      for (size_t p = 0; p < Ms.size(); ++p) {
-        bf->V[l][p] = Vs[p];
-        IdxVec o;
-        for (int32_t s : sk[p]) o.push_back(Ys[p][s]);
-        bf->Ssk[l][p] = o;
-      }
-      break;
-    }
-    scratch.release(mk2);
-  }
-  // centre: B (V^T Omega_nu) = Y(Obar, cols(nu)) in the least-squares sense
-  {
-    std::vector<Blk<T>> xs;
-    right_transform(*bf, cOm, xs);
-    std::vector<LstsqJob<T>> lj;
-    std::vector<GatherJob<T>> gj;
-    std::vector<Blk<T>> Yr(xs.size());
-    for (int i = 0; i < (1 << lc); ++i)
-      for (int j = 0; j < (1 << (L - lc)); ++j) {
-        const int p = bf->pidx(lc, i, j);
-        const int r = bf->rr(lc, i, j), c = bf->rc(lc, i, j);
-        Blk<T> Bm = new_blk<T>(persist, r, c);
-        bf->B[p] = Bm;
-        if (r == 0 || c == 0) continue;
-        auto pr = gather(cY, bf->Osk[lc][p], ccols[j]);
-        Yr[p] = pr.first;
-        gj.push_back(pr.second);
-        LstsqJob<T> L1;
-        Blk<T> Tm = xs[p];
-        L1.Tm = Tm.p + ccols[j].first; L1.tplane = Tm.plane; L1.tld = Tm.ld;
-        L1.Y = Yr[p].p; L1.yplane = Yr[p].plane; L1.yld = Yr[p].ld;
-        L1.B = Bm.p; L1.bplane = Bm.plane; L1.bld = Bm.ld;
-        L1.c = c; L1.r = r; L1.w = ccols[j].second - ccols[j].first;
-        L1.W = nullptr;
-        lj.push_back(L1);
-        flops += 8.0 * ((double)c * c * L1.w + (double)r * c * L1.w);
-      }
-    run_gathers(gj);
-    run_lstsq(lj);
-  }
-  sync();
-  scratch.release(mk);
-  return bf;
+  std::vector<RMProblem<T>> pr(1);
+  pr[0].m = op.rows;
+  pr[0].n = op.cols;
+  pr[0].rt = rt;
+  pr[0].ct = ct;
+  pr[0].key = key;
+  DOpB<T> opb = [&op](const std::vector<Blk<T>>& X, std::vector<Blk<T>>& Y, bool tr) { op.apply(X[0], Y[0], tr); };
+  random_matvec_batch(opb, pr, L, P);
+  return std::move(pr[0].out);
 }
 
 // ---------------------------------------------------------------------------
@@ -1955,6 +1783,45 @@ Blk<T> BFContext<T>::make_sketch(int rows, const std::vector<Range>& groups, int
 }
 
 template <typename T>
+Blk<T> BFContext<T>::make_sketch_levels(int rows, const std::vector<std::pair<const std::vector<Range>*, int>>& lv,
+                                        int q, int side, uint32_t key,
+                                        std::vector<std::vector<std::pair<int, int>>>& cols, std::vector<int>& base) {
+  HostTimer ht_(t_host + H_SKETCH);
+  cols.assign(lv.size(), {});
+  base.assign(lv.size(), 0);
+  int tot = 0;
+  std::vector<SketchGroup> sg;
+  for (size_t k = 0; k < lv.size(); ++k) {
+    const std::vector<Range>& groups = *lv[k].first;
+    const int level = lv[k].second;
+    base[k] = tot;
+    int tl = 0;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      int size = (int)(groups[g].b - groups[g].a);
+      int w = size <= q ? size : q;
+      cols[k].push_back({tl, tl + w});
+      SketchGroup sgr;
+      sgr.a = groups[g].a; sgr.b = groups[g].b; sgr.c0 = tot + tl; sgr.w = w;
+      sgr.key = (int32_t)((key * 1000003u + (uint32_t)level * 7919u + (uint32_t)side * 104729u + (uint32_t)g) & 0xFFFFFF);
+      sgr.identity = (w == size) ? 1 : 0;
+      if (w > 0) sg.push_back(sgr);
+      tl += w;
+    }
+    tot += tl;
+  }
+  Blk<T> Om = new_blk<T>(scratch, rows, std::max(tot, 1));
+  Om.cols = tot;
+  zero(Om);
+  if (!sg.empty()) {
+    int mx = 0;
+    for (auto& g : sg) mx = std::max<int>(mx, (int)((g.b - g.a) * g.w));
+    const SketchGroup* dg = stage(sg.data(), sg.size());
+    launch_sketch<T>(dg, (int)sg.size(), mx, Om.p, Om.plane, (int)Om.ld, st);
+  }
+  return Om;
+}
+
+template <typename T>
 std::vector<Blk<T>> BFContext<T>::copy_b(const std::vector<Blk<T>>& x) {
   std::vector<Blk<T>> out(x.size());
   std::vector<Blk2Job<T>> jobs;
@@ -2017,22 +1884,53 @@ void BFContext<T>::random_matvec_batch(const DOpB<T>& op, std::vector<RMProblem<
     const GatherJob<T>* d = stage(gj.data(), gj.size());
     launch_gather_rows<T>(d, (int)gj.size(), mx, st);
   };
+  // With a rank cap the sketch widths are fixed and no sketch depends on an earlier level's
+  // IDs, so all levels of one side go through the operator in one application (fused);
+  // without a cap the width may grow per level and each level applies the operator itself.
+  const bool fused = P.max_rank > 0;
   for (int side = 0; side < 2; ++side) {
     const int lfirst = side == 0 ? L : 0, llast = lc, step = side == 0 ? -1 : 1;
+    std::vector<Blk<T>> OmAll(nq), YAll(nq);
+    std::vector<std::vector<std::vector<std::pair<int, int>>>> lcols(nq);
+    std::vector<std::vector<int>> lbase(nq);
+    if (fused) {
+      for (size_t t = 0; t < nq; ++t) {
+        DBF<T>& bf = *probs[t].out;
+        std::vector<std::pair<const std::vector<Range>*, int>> lv;
+        for (int l = lfirst;; l += step) {
+          lv.push_back({side == 0 ? &bf.ct[L - l] : &bf.rt[l], l});
+          if (l == llast) break;
+        }
+        OmAll[t] = make_sketch_levels(side == 0 ? bf.n : bf.m, lv, q0, side, probs[t].key, lcols[t], lbase[t]);
+        YAll[t] = new_blk<T>(scratch, side == 0 ? bf.m : bf.n, std::max(OmAll[t].cols, 1));
+        YAll[t].cols = OmAll[t].cols;
+      }
+      op(OmAll, YAll, side == 1);
+    }
     for (int l = lfirst;; l += step) {
       int q = q0;
       const size_t mkl = scratch.mark();
+      const int li = side == 0 ? lfirst - l : l - lfirst;   // position of l in the fused sketch
       for (;;) {
         std::vector<Blk<T>> Om(nq), Yb(nq);
         std::vector<std::vector<std::pair<int, int>>> cols(nq);
-        for (size_t t = 0; t < nq; ++t) {
-          DBF<T>& bf = *probs[t].out;
-          const auto& groups = side == 0 ? bf.ct[L - l] : bf.rt[l];
-          Om[t] = make_sketch(side == 0 ? bf.n : bf.m, groups, q, l, side, probs[t].key, cols[t]);
-          Yb[t] = new_blk<T>(scratch, side == 0 ? bf.m : bf.n, std::max(Om[t].cols, 1));
-          Yb[t].cols = Om[t].cols;
+        if (fused) {
+          for (size_t t = 0; t < nq; ++t) {
+            const int w = li + 1 < (int)lbase[t].size() ? lbase[t][li + 1] - lbase[t][li] : OmAll[t].cols - lbase[t][li];
+            Om[t] = OmAll[t].sub(0, lbase[t][li], OmAll[t].rows, w);
+            Yb[t] = YAll[t].sub(0, lbase[t][li], YAll[t].rows, w);
+            cols[t] = lcols[t][li];
+          }
+        } else {
+          for (size_t t = 0; t < nq; ++t) {
+            DBF<T>& bf = *probs[t].out;
+            const auto& groups = side == 0 ? bf.ct[L - l] : bf.rt[l];
+            Om[t] = make_sketch(side == 0 ? bf.n : bf.m, groups, q, l, side, probs[t].key, cols[t]);
+            Yb[t] = new_blk<T>(scratch, side == 0 ? bf.m : bf.n, std::max(Om[t].cols, 1));
+            Yb[t].cols = Om[t].cols;
+          }
+          op(Om, Yb, side == 1);
         }
-        op(Om, Yb, side == 1);
         std::vector<Blk<T>> Ms;
         std::vector<GatherJob<T>> gj;
         std::vector<IdxVec> sets;

@@ -310,6 +310,11 @@ class BFContext {
   // ---- batched forms (all problems of one call in lockstep)
   Blk<T> make_sketch(int rows, const std::vector<Range>& groups, int q, int level, int side, uint32_t key,
                      std::vector<std::pair<int, int>>& cols);
+  // the sketches of several levels side by side in one block: level k's columns start at base[k],
+  // its groups' column ranges (relative to base[k]) in cols[k]; one launch
+  Blk<T> make_sketch_levels(int rows, const std::vector<std::pair<const std::vector<Range>*, int>>& lv, int q,
+                            int side, uint32_t key, std::vector<std::vector<std::pair<int, int>>>& cols,
+                            std::vector<int>& base);
   void random_matvec_batch(const DOpB<T>& op, std::vector<RMProblem<T>>& probs, int L, const BFParams& P);
   void inv_apply_b(const DHODBFInv<T>& Hi, int l0, const std::vector<int>& i0s, const std::vector<Blk<T>>& X,
                    std::vector<Blk<T>>& Y, bool transpose);

@@ -41,7 +41,8 @@ int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol
 // ---------------------------------------------------------------------------
 // Counter-based complex Gaussian sketches: splitmix64 (Steele, Lea, Flood 2014)
 // on the counter (key << 40) ^ (col << 24) ^ row, hashed twice (2c, 2c + 1) to
-// two 53-bit uniforms in (0, 1), Box-Muller, scaled by 1/sqrt(2).
+// two uniforms in (0, 1) (24-bit for complex64, 53-bit for complex128), Box-Muller,
+// scaled by 1/sqrt(2).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t smix(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
@@ -66,12 +67,22 @@ __global__ void k_sketch(const SketchGroup* groups, int ngroups, T* out, int64_t
     } else {
       uint64_t c = ((uint64_t)(g.key & 0xFFFFFF) << 40) ^ ((uint64_t)(col & 0xFFFF) << 24) ^ (uint64_t)row;
       uint64_t h1 = smix(c * 2ull), h2 = smix(c * 2ull + 1ull);
-      double u1 = ((double)(h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-      double u2 = ((double)(h2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-      double rad = sqrt(-2.0 * log(u1));
-      double ang = 6.283185307179586476925286766559 * u2;
-      re = (T)(rad * cos(ang) * 0.70710678118654752440);
-      im = (T)(rad * sin(ang) * 0.70710678118654752440);
+      if constexpr (sizeof(T) == 4) {   // 24-bit uniforms and single-precision Box-Muller (FP64 is slow here)
+        float u1 = ((float)(h1 >> 40) + 0.5f) * (1.0f / 16777216.0f);
+        float u2 = ((float)(h2 >> 40) + 0.5f) * (1.0f / 16777216.0f);
+        float rad = sqrtf(-2.0f * logf(u1)) * 0.70710678f;
+        float s, co;
+        sincospif(2.0f * u2, &s, &co);
+        re = (T)(rad * co);
+        im = (T)(rad * s);
+      } else {
+        double u1 = ((double)(h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        double u2 = ((double)(h2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        double rad = sqrt(-2.0 * log(u1));
+        double ang = 6.283185307179586476925286766559 * u2;
+        re = (T)(rad * cos(ang) * 0.70710678118654752440);
+        im = (T)(rad * sin(ang) * 0.70710678118654752440);
+      }
     }
     const int64_t off = row * ld + g.c0 + col;
     out[off] = re;
