@@ -1016,7 +1016,7 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
         IdxVec rows, cols;
         for (int t = Xp[lc][i].p0; t < Xp[lc][i].p1; ++t) rows.push_back(xo[t]);
         for (int t = Yp[L - lc][jj].p0; t < Yp[L - lc][jj].p1; ++t) cols.push_back(yo[t]);
-        PlaceJob<T> pl;
+        PlaceJob<T> pl{};
         pl.src = out.p; pl.splane = out.plane; pl.sld = out.ld;
         pl.rows = dev_idx(cx, rows);
         pl.cols = dev_idx(cx, cols);
@@ -1293,7 +1293,7 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
       j.dst = t.p; j.dplane = t.plane; j.dld = t.ld; j.rows = t.rows; j.cols = t.cols; j.alpha = T(1);
       j.ridx = dev_idx(*this, rx); j.cidx = dev_idx(*this, ry); j.mode = 4;
       gj.push_back(j);
-      PlaceJob<T> pl;
+      PlaceJob<T> pl{};
       pl.src = t.p; pl.splane = t.plane; pl.sld = t.ld;
       pl.rows = dev_idx(*this, px); pl.cols = dev_idx(*this, py); pl.nr = t.rows; pl.nc = t.cols;
       pl.dst = dst[q].p; pl.dplane = dst[q].plane; pl.dld = dst[q].ld; pl.sign = sign;
@@ -1317,7 +1317,7 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
         Blk<T> t = new_blk<T>(scratch, (int)rx.size(), (int)ry.size());
         zspans.push_back({reinterpret_cast<char*>(t.p), (size_t)2 * t.plane * sizeof(T)});
         R.tmp.push_back(t);
-        PlaceJob<T> pl;
+        PlaceJob<T> pl{};
         pl.src = t.p; pl.splane = t.plane; pl.sld = t.ld;
         pl.rows = dev_idx(*this, px); pl.cols = dev_idx(*this, py); pl.nr = t.rows; pl.nc = t.cols;
         pl.dst = dst[q].p; pl.dplane = dst[q].plane; pl.dld = dst[q].ld; pl.sign = sign;
@@ -1413,6 +1413,76 @@ void BFContext<T>::inv_apply(const DHODBFInv<T>& Hi, const Blk<T>& X, Blk<T>& Y,
     run_blk2(*this, bj);
   }
   (void)mk;   // Z stays reserved until the caller releases its scratch mark
+}
+
+template <typename T>
+void BFContext<T>::inv_apply_multi(const std::vector<const DHODBFInv<T>*>& His, const std::vector<Blk<T>>& X,
+                                   std::vector<Blk<T>>& Y, bool transpose) {
+  // several full inverses in lockstep: one launch per step for all of them.  Without transpose
+  // inverse q applies its level LH_q - 1 - d at step d (deepest first); with transpose the
+  // levels run top-down and an inverse with fewer levels starts maxLH - LH_q steps later.
+  const size_t nq = His.size();
+  if (!nq) return;
+  int maxLH = 0;
+  for (auto* h : His) maxLH = std::max(maxLH, h->LH);
+  std::vector<Blk<T>> Z(nq);
+  for (size_t q = 0; q < nq; ++q) Z[q] = new_blk<T>(scratch, X[q].rows, X[q].cols);
+  auto leaves = [&](const std::vector<Blk<T>>& src, std::vector<Blk<T>>& out) {
+    std::vector<GemmDesc<T>> g;
+    for (size_t q = 0; q < nq; ++q) {
+      const DHODBFInv<T>& Hi = *His[q];
+      const int k = X[q].cols;
+      for (size_t li = 0; li < Hi.tree[Hi.LH].size(); ++li) {
+        const Range r = Hi.tree[Hi.LH][li];
+        const int nr = (int)(r.b - r.a);
+        if (nr == 0) continue;
+        g.push_back(gdesc<T>(nr, k, nr, transpose ? 1 : 0, 0, T(1), T(0), Hi.Dinv[li],
+                             src[q].sub((int)r.a, 0, nr, k), out[q].sub((int)r.a, 0, nr, k)));
+      }
+    }
+    gemm(g);
+  };
+  auto copies = [&](const std::vector<Blk<T>>& src, std::vector<Blk<T>>& dst) {
+    std::vector<Blk2Job<T>> cj;
+    for (size_t q = 0; q < nq; ++q) {
+      Blk2Job<T> j{};
+      j.src = src[q].p; j.splane = src[q].plane; j.sld = src[q].ld;
+      j.dst = dst[q].p; j.dplane = dst[q].plane; j.dld = dst[q].ld;
+      j.rows = src[q].rows; j.cols = src[q].cols; j.alpha = T(1); j.mode = 3;
+      if (j.rows && j.cols) cj.push_back(j);
+    }
+    run_blk2(*this, cj);
+  };
+  auto step = [&](int d) {
+    std::vector<const DBF<T>*> bfs;
+    std::vector<Blk<T>> xs, zs, ys, zz;
+    for (size_t q = 0; q < nq; ++q) {
+      const DHODBFInv<T>& Hi = *His[q];
+      const int l = transpose ? d - (maxLH - Hi.LH) : Hi.LH - 1 - d;
+      if (l < 0 || l >= Hi.LH) continue;
+      const int k = X[q].cols;
+      for (int i = 0; i < (1 << l); ++i) {
+        const Range r = Hi.tree[l][i];
+        bfs.push_back(Hi.M[l][i].get());
+        xs.push_back(Y[q].sub((int)r.a, 0, (int)(r.b - r.a), k));
+        zs.push_back(Z[q].sub((int)r.a, 0, (int)(r.b - r.a), k));
+      }
+      ys.push_back(Y[q]);
+      zz.push_back(Z[q]);
+    }
+    if (bfs.empty()) return;
+    apply(bfs, xs, zs, transpose, false);
+    axpy_b(zz, ys, T(1));
+  };
+  if (!transpose) {
+    leaves(X, Y);
+    for (int d = 0; d < maxLH; ++d) step(d);
+  } else {
+    copies(X, Y);
+    for (int d = 0; d < maxLH; ++d) step(d);
+    leaves(Y, Z);
+    copies(Z, Y);
+  }
 }
 
 template <typename T>

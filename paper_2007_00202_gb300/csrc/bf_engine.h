@@ -303,6 +303,9 @@ class BFContext {
                      T sign);
   std::unique_ptr<DHODBFInv<T>> hodbf_invert(const DHODBF<T>& H, const BFParams& P, uint32_t key);
   void inv_apply(const DHODBFInv<T>& Hi, const Blk<T>& X, Blk<T>& Y, bool transpose, int l0 = 0, int i0 = 0);
+  // Y_q = H_q^-1 X_q (or H_q^-T X_q) for several full inverses at once, in lockstep
+  void inv_apply_multi(const std::vector<const DHODBFInv<T>*>& His, const std::vector<Blk<T>>& X,
+                       std::vector<Blk<T>>& Y, bool transpose);
   std::unique_ptr<DBF<T>> bf_smw(const DBF<T>& K, const BFParams& P, uint32_t key);
   std::unique_ptr<DBF<T>> smw_assemble(int n, const Tree& tr, int L, const DBF<T>* K11, const DBF<T>& K12,
                                        const DBF<T>& K21, const DBF<T>* K22i, const BFParams& P, uint32_t key);

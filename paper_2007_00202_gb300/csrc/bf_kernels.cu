@@ -190,8 +190,13 @@ __global__ void k_place(const PlaceJob<T>* jobs) {
     const int a = (int)(e / j.nc), b = (int)(e % j.nc);
     const int64_t so = (int64_t)a * j.sld + b;
     const int64_t dof = (int64_t)j.rows[a] * j.dld + j.cols[b];
-    j.dst[dof] += j.sign * j.src[so];
-    j.dst[dof + j.dplane] += j.sign * j.src[so + j.splane];
+    if (j.atomic) {
+      atomicAdd(j.dst + dof, j.sign * j.src[so]);
+      atomicAdd(j.dst + dof + j.dplane, j.sign * j.src[so + j.splane]);
+    } else {
+      j.dst[dof] += j.sign * j.src[so];
+      j.dst[dof + j.dplane] += j.sign * j.src[so + j.splane];
+    }
   }
 }
 

@@ -87,6 +87,7 @@ struct PlaceJob {
   T* dst;
   int64_t dplane, dld;
   T sign;
+  int32_t atomic;      // 1: jobs of the launch may overlap in dst (atomic adds)
 };
 
 template <typename T>

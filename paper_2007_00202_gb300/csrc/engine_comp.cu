@@ -241,58 +241,106 @@ void CompressedPart<T>::densify_C(int fid, const FrontDev<T>& fd) {
 }
 
 template <typename T>
-void CompressedPart<T>::forward(int fid, Blk<T>& X) {
-  CompFront<T>& cf = *fronts.at(fid);
-  const int s = cf.s, u = cf.u, k = X.cols;
+void CompressedPart<T>::forward(const std::vector<int>& fids, Blk<T>& X) {
+  // all compressed fronts of one level at once: w_f = F11_f^-1 x_s(f), x_s(f) = w_f, x_u(f) -= F21_f w_f
+  const int k = X.cols;
   const size_t mk = cx.scratch.mark();
-  Blk<T> xs = X.sub((int)cf.sep_begin, 0, s, k);
-  Blk<T> w = new_blk<T>(cx.scratch, s, k);
-  cx.inv_apply(*cf.F11inv, xs, w, false, 0, 0);
+  std::vector<const DHODBFInv<T>*> inv;
+  std::vector<Blk<T>> xs, ws;
+  std::vector<CompFront<T>*> cfs;
+  for (int fid : fids) {
+    CompFront<T>& cf = *fronts.at(fid);
+    cfs.push_back(&cf);
+    inv.push_back(cf.F11inv.get());
+    xs.push_back(X.sub((int)cf.sep_begin, 0, cf.s, k));
+    ws.push_back(new_blk<T>(cx.scratch, cf.s, k));
+  }
+  cx.inv_apply_multi(inv, xs, ws, false);
   std::vector<Blk2Job<T>> cp;
-  Blk2Job<T> j{};
-  j.src = w.p; j.splane = w.plane; j.sld = w.ld; j.dst = xs.p; j.dplane = xs.plane; j.dld = xs.ld;
-  j.rows = s; j.cols = k; j.alpha = T(1); j.mode = 3;
-  cp.push_back(j);
-  launch_blk2<T>(cx.stage(cp.data(), 1), 1, (int64_t)s * k, st_);
-  if (u > 0) {
-    Blk<T> t = new_blk<T>(cx.scratch, u, k);
-    std::vector<const DBF<T>*> b{cf.F21.get()};
-    std::vector<Blk<T>> xsv{w}, ys{t};
-    cx.apply(b, xsv, ys, false, false);
-    PlaceJob<T> pl;
-    pl.src = t.p; pl.splane = t.plane; pl.sld = t.ld;
+  for (size_t q = 0; q < cfs.size(); ++q) {
+    Blk2Job<T> j{};
+    j.src = ws[q].p; j.splane = ws[q].plane; j.sld = ws[q].ld; j.dst = xs[q].p; j.dplane = xs[q].plane;
+    j.dld = xs[q].ld; j.rows = cfs[q]->s; j.cols = k; j.alpha = T(1); j.mode = 3;
+    cp.push_back(j);
+  }
+  int64_t mx = 0;
+  for (auto& j : cp) mx = std::max<int64_t>(mx, (int64_t)j.rows * j.cols);
+  launch_blk2<T>(cx.stage(cp.data(), cp.size()), (int)cp.size(), mx, st_);
+  std::vector<const DBF<T>*> b;
+  std::vector<Blk<T>> wu, ts;
+  std::vector<size_t> which;
+  for (size_t q = 0; q < cfs.size(); ++q) {
+    if (cfs[q]->u == 0) continue;
+    b.push_back(cfs[q]->F21.get());
+    wu.push_back(ws[q]);
+    ts.push_back(new_blk<T>(cx.scratch, cfs[q]->u, k));
+    which.push_back(q);
+  }
+  if (!b.empty()) {
+    cx.apply(b, wu, ts, false, false);
     IdxVec cols = iota_vec(k);
-    pl.rows = cf.d_upd32.template as<int32_t>();
-    pl.cols = static_cast<const int32_t*>(cx.upload(cols.data(), (size_t)k * 4));
-    pl.nr = u; pl.nc = k;
-    pl.dst = X.p; pl.dplane = X.plane; pl.dld = X.ld; pl.sign = T(-1);
-    launch_place<T>(cx.stage(&pl, 1), 1, (int64_t)u * k, st_);
+    const int32_t* dc = static_cast<const int32_t*>(cx.upload(cols.data(), (size_t)k * 4));
+    std::vector<PlaceJob<T>> pls;
+    int64_t mxp = 0;
+    for (size_t t = 0; t < b.size(); ++t) {
+      const CompFront<T>& cf = *cfs[which[t]];
+      PlaceJob<T> pl{};
+      pl.src = ts[t].p; pl.splane = ts[t].plane; pl.sld = ts[t].ld;
+      pl.rows = cf.d_upd32.template as<int32_t>(); pl.cols = dc; pl.nr = cf.u; pl.nc = k;
+      pl.dst = X.p; pl.dplane = X.plane; pl.dld = X.ld; pl.sign = T(-1);
+      pl.atomic = b.size() > 1 ? 1 : 0;   // sibling fronts share update rows
+      pls.push_back(pl);
+      mxp = std::max<int64_t>(mxp, (int64_t)cf.u * k);
+    }
+    launch_place<T>(cx.stage(pls.data(), pls.size()), (int)pls.size(), mxp, st_);
   }
   cx.scratch.release(mk);   // stream order makes later reuse of the scratch safe
 }
 
 template <typename T>
-void CompressedPart<T>::backward(int fid, Blk<T>& X) {
-  CompFront<T>& cf = *fronts.at(fid);
-  const int s = cf.s, u = cf.u, k = X.cols;
-  if (u == 0) return;
+void CompressedPart<T>::backward(const std::vector<int>& fids, Blk<T>& X) {
+  // all compressed fronts of one level at once: x_s(f) -= F11_f^-1 F12_f x_u(f)
+  const int k = X.cols;
   const size_t mk = cx.scratch.mark();
-  Blk<T> xs = X.sub((int)cf.sep_begin, 0, s, k);
-  Blk<T> g = new_blk<T>(cx.scratch, u, k);
-  Blk2Job<T> j{};
-  j.src = X.p; j.splane = X.plane; j.sld = X.ld; j.dst = g.p; j.dplane = g.plane; j.dld = g.ld;
-  j.rows = u; j.cols = k; j.alpha = T(1); j.mode = 4;
-  j.ridx = cf.d_upd32.template as<int32_t>(); j.cidx = nullptr;
-  launch_blk2<T>(cx.stage(&j, 1), 1, (int64_t)u * k, st_);
-  Blk<T> v = new_blk<T>(cx.scratch, s, k), z = new_blk<T>(cx.scratch, s, k);
-  std::vector<const DBF<T>*> b{cf.F12.get()};
-  std::vector<Blk<T>> gs{g}, vs{v};
+  std::vector<CompFront<T>*> cfs;
+  for (int fid : fids) {
+    CompFront<T>& cf = *fronts.at(fid);
+    if (cf.u > 0) cfs.push_back(&cf);
+  }
+  if (cfs.empty()) return;
+  std::vector<Blk<T>> gs, vs, zs, xs;
+  std::vector<Blk2Job<T>> gj;
+  std::vector<const DBF<T>*> b;
+  std::vector<const DHODBFInv<T>*> inv;
+  int64_t mx = 0;
+  for (CompFront<T>* cf : cfs) {
+    Blk<T> g = new_blk<T>(cx.scratch, cf->u, k);
+    Blk2Job<T> j{};
+    j.src = X.p; j.splane = X.plane; j.sld = X.ld; j.dst = g.p; j.dplane = g.plane; j.dld = g.ld;
+    j.rows = cf->u; j.cols = k; j.alpha = T(1); j.mode = 4;
+    j.ridx = cf->d_upd32.template as<int32_t>(); j.cidx = nullptr;
+    gj.push_back(j);
+    mx = std::max<int64_t>(mx, (int64_t)cf->u * k);
+    gs.push_back(g);
+    vs.push_back(new_blk<T>(cx.scratch, cf->s, k));
+    zs.push_back(new_blk<T>(cx.scratch, cf->s, k));
+    xs.push_back(X.sub((int)cf->sep_begin, 0, cf->s, k));
+    b.push_back(cf->F12.get());
+    inv.push_back(cf->F11inv.get());
+  }
+  launch_blk2<T>(cx.stage(gj.data(), gj.size()), (int)gj.size(), mx, st_);
   cx.apply(b, gs, vs, false, false);
-  cx.inv_apply(*cf.F11inv, v, z, false, 0, 0);
-  Blk2Job<T> a{};
-  a.src = z.p; a.splane = z.plane; a.sld = z.ld; a.dst = xs.p; a.dplane = xs.plane; a.dld = xs.ld;
-  a.rows = s; a.cols = k; a.alpha = T(-1); a.mode = 2;
-  launch_blk2<T>(cx.stage(&a, 1), 1, (int64_t)s * k, st_);
+  cx.inv_apply_multi(inv, vs, zs, false);
+  std::vector<Blk2Job<T>> aj;
+  int64_t mxa = 0;
+  for (size_t q = 0; q < cfs.size(); ++q) {
+    Blk2Job<T> a{};
+    a.src = zs[q].p; a.splane = zs[q].plane; a.sld = zs[q].ld; a.dst = xs[q].p; a.dplane = xs[q].plane;
+    a.dld = xs[q].ld; a.rows = cfs[q]->s; a.cols = k; a.alpha = T(-1); a.mode = 2;
+    aj.push_back(a);
+    mxa = std::max<int64_t>(mxa, (int64_t)cfs[q]->s * k);
+  }
+  launch_blk2<T>(cx.stage(aj.data(), aj.size()), (int)aj.size(), mxa, st_);
   cx.scratch.release(mk);   // stream order makes later reuse of the scratch safe
 }
 

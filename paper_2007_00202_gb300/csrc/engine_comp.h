@@ -42,9 +42,11 @@ class CompressedPart {
   void factor_front(int fid, const std::vector<FrontDev<T>>& fr, const BFParams& P, uint64_t seed);
   // Expand C of a compressed front into the dense buffer of its (dense) parent's extend-add.
   void densify_C(int fid, const FrontDev<T>& f);
-  // Solve steps on X (N x k, planar row-major, new numbering)
-  void forward(int fid, Blk<T>& X);
-  void backward(int fid, Blk<T>& X);
+  // Solve steps on X (N x k, planar row-major, new numbering) for all compressed fronts of one
+  // tree level at once (they touch disjoint separator rows; the update rows they write are
+  // combined by the scatter-add of the forward step)
+  void forward(const std::vector<int>& fids, Blk<T>& X);
+  void backward(const std::vector<int>& fids, Blk<T>& X);
 
   const Analysis& an_;
   const DeviceMatrix& A_;

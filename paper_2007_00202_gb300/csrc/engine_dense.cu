@@ -706,14 +706,14 @@ class DenseEngine : public EngineBase {
       }
     };
     auto comp_op = [&](size_t lv, bool fwd) {
-      for (int32_t fid : comp_levels_[lv]) {
-        sp->ops.push_back([this, fid, fwd, X, n, nrhs](cudaStream_t) {
-          Blk<T> Xb;
-          Xb.p = X; Xb.rows = (int)n; Xb.cols = nrhs; Xb.ld = nrhs; Xb.plane = n * nrhs;
-          if (fwd) comp_->forward(fid, Xb);
-          else comp_->backward(fid, Xb);
-        });
-      }
+      if (comp_levels_[lv].empty()) return;
+      std::vector<int> fids(comp_levels_[lv].begin(), comp_levels_[lv].end());
+      sp->ops.push_back([this, fids, fwd, X, n, nrhs](cudaStream_t) {
+        Blk<T> Xb;
+        Xb.p = X; Xb.rows = (int)n; Xb.cols = nrhs; Xb.ld = nrhs; Xb.plane = n * nrhs;
+        if (fwd) comp_->forward(fids, Xb);
+        else comp_->backward(fids, Xb);
+      });
     };
     // forward: leaves -> root
     for (size_t lv = 0; lv < levels_.size(); ++lv) {
