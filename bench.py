@@ -129,6 +129,9 @@ def measured_peaks():
         return {}
 
 
+# event timing of one launch (and one solve-graph replay) in PROFILE_PERIOD during the timed steps:
+# the per-launch average comes from that sample, and the timing costs little of the step
+PROFILE_PERIOD = 8
 # nominal FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz maximum SM clock
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM traffic of the narrow GEMM per algorithmic byte, from the ncu capture summarised in
@@ -165,7 +168,7 @@ def roofline(prof, peaks):
         traffic = NARROW_TRAFFIC_PER_ALG_BYTE * prof["bytes"] / max(prof["launches"], 1)
     alu_bound = ai * hbm / 1e3 > FP32_ALU_TFLOPS
     r = {"kernel": "k_gemm_nrhs (narrow planar complex GEMM: solve front products, butterfly level products)",
-         "launches": prof["launches"], "ms_per_launch": prof["ms"] / max(prof["launches"], 1),
+         "launches_timed": prof["launches"], "sample": f"one launch / graph replay in {PROFILE_PERIOD}", "ms_per_launch": prof["ms"] / max(prof["launches"], 1),
          "flop_per_byte": ai, "traffic": traffic, "traffic_unit": "bytes per launch",
          "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm,
          "peak_source": "alu: nominal FP32 SIMT peak 152 SM x 128 lanes x 2 x 2.07 GHz; "
@@ -326,7 +329,7 @@ def main():
     for _ in range(args.warmup):
         info = step()
     torch.cuda.synchronize()
-    h.mf_profile(True)
+    h.mf_profile(True, period=PROFILE_PERIOD)
     barrier(world)
     torch.cuda.synchronize()
     c0 = g.lib().mf_launch_counter()

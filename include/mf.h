@@ -139,10 +139,11 @@ int mf_stats(const mf_handle* h, mf_stats_t* out);
 /* Message of the last failure on h (h == NULL: of the calling thread). Never NULL. */
 const char* mf_last_error(const mf_handle* h);
 
-/* CUDA-event timing of two kernel families, for roofline figures.
- * mf_profile(h, 1) enables it and clears the counters (0 disables it); while it is
- * on, every launch of the family gets a start and a stop event on the stream it
- * runs on (inside the solve's CUDA graphs as graph nodes):
+/* CUDA-event timing of two kernel families, for roofline figures (sampled).
+ * mf_profile(h, N) with N > 0 enables it and clears the counters (0 disables it);
+ * while it is on, one launch in N of each family gets a start and a stop event on
+ * the stream it runs on, and one replay in N of each solve graph runs a copy of
+ * the graph with those events as graph nodes (N = 1: every launch):
  *   MF_PROF_NARROW_GEMM: the narrow GEMM (n <= 128: the solve's front products
  *     with the right-hand sides and the butterfly level products) in mf_factor
  *     and mf_solve*;

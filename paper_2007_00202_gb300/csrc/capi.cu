@@ -33,7 +33,7 @@ struct mf_handle {
   bool on_device = false;
   std::unique_ptr<mf::EngineBase> eng;
   bool factored = false;
-  bool profile = false;
+  int profile = 0;   // profiling period (0: off)
   double factor_seconds = 0;
   // solve work (FP64, new numbering)
   DevMem wb, wx, wr, wz, wV, wH, wsc, wy;
@@ -474,7 +474,8 @@ int mf_stats(const mf_handle* h, mf_stats_t* out) {
 
 int mf_profile(mf_handle* h, int32_t enable) {
   if (!h) return fail(nullptr, MF_ERR_ARG, "handle is NULL");
-  h->profile = enable != 0;
+  if (enable < 0) return fail(h, MF_ERR_ARG, "enable must be >= 0");
+  h->profile = enable;
   if (h->eng) return guarded(h, [&]() -> int {
     h->eng->set_profiling(h->profile);
     return MF_OK;

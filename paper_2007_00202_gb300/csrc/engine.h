@@ -86,6 +86,8 @@ struct LaunchProfiler {
     double flops, bytes;
   };
   bool on = false;
+  int every = 1;                    // time one eager launch (and one graph replay) in `every`
+  int64_t calls = 0;
   std::vector<Rec>* capture_into = nullptr;
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
@@ -106,7 +108,7 @@ struct LaunchProfiler {
   }
   template <class F>
   void time(cudaStream_t st, double fl, double by, F&& launch) {
-    if (!on) {
+    if (!on || (!capture_into && (calls++ % every) != 0)) {
       launch();
       return;
     }
@@ -156,9 +158,11 @@ struct LaunchProfiler {
     pending.clear();
     pool_used = 0;
   }
-  void enable(bool v) {
+  void enable(int period) {   // 0: off; N > 0: time one launch in N
     collect();
-    on = v;
+    on = period > 0;
+    every = period > 0 ? period : 1;
+    calls = 0;
     launches = 0;
     ms = flops = bytes = 0;
   }
@@ -181,8 +185,8 @@ class EngineBase {
   // prof[0] the narrow GEMM (k_gemm_nrhs) in factor() and apply_precond(), prof[1] the
   // factor's dense front GEMMs (Schur updates).
   LaunchProfiler prof[2];
-  virtual void set_profiling(bool on) {
-    for (auto& p : prof) p.enable(on);
+  virtual void set_profiling(int period) {
+    for (auto& p : prof) p.enable(period);
   }
 };
 

@@ -136,6 +136,8 @@ class DenseEngine : public EngineBase {
     // the compressed fronts, 1 = the next call captures, 2 = replay, 3 = eager only
     int state = 0;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec_prof = nullptr;   // the same program with timing events (profiling)
+    int64_t nrep = 0;
     size_t blob = 0, blob_cap = 0, mark = 0;
     int glaunch = 0;
     int64_t nrec = 0;                                  // timed launches of one run (profiling)
@@ -144,8 +146,10 @@ class DenseEngine : public EngineBase {
     DevMem dblob;
     void drop_graph() {
       if (exec) cudaGraphExecDestroy(exec);
-      exec = nullptr;
+      if (exec_prof) cudaGraphExecDestroy(exec_prof);
+      exec = exec_prof = nullptr;
       state = 0;
+      nrep = 0;
       for (auto& r : prof_recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -192,10 +196,10 @@ class DenseEngine : public EngineBase {
   }
 
  private:
-  void set_profiling(bool on) override {
+  void set_profiling(int period) override {
     prof[0].collect();
     for (auto& kv : sprog_) kv.second->drop_graph();   // recaptured with (or without) timing events
-    EngineBase::set_profiling(on);
+    EngineBase::set_profiling(period);
   }
 
   // The solve program is the same launch sequence for every call with the same nrhs: the
@@ -211,21 +215,23 @@ class DenseEngine : public EngineBase {
     if (no_graph || sp.state == 3) return eager();
     if (sp.state == 2 && cx && cx->scratch.mark() != sp.mark) sp.drop_graph();
     if (sp.state == 2) {
-      prof[0].collect();   // the previous replay's events are recorded again by this one
+      // with profiling on, one replay in prof[0].every runs the copy with timing events
+      const bool timed = prof[0].on && sp.exec_prof && (sp.nrep++ % prof[0].every) == 0;
+      if (timed) prof[0].collect();   // the previous timed replay's events are recorded again
       MF_CUDA(cudaEventRecord(gev_[0], st_));
       MF_CUDA(cudaStreamWaitEvent(gs_, gev_[0], 0));
-      MF_CUDA(cudaGraphLaunch(sp.exec, gs_));
+      MF_CUDA(cudaGraphLaunch(timed ? sp.exec_prof : sp.exec, gs_));
       count_launches(sp.glaunch);   // the kernel nodes the replay runs
       MF_CUDA(cudaEventRecord(gev_[1], gs_));
       MF_CUDA(cudaStreamWaitEvent(st_, gev_[1], 0));
-      prof[0].replayed(sp.prof_recs);
+      if (timed) prof[0].replayed(sp.prof_recs);
       return;
     }
     if (sp.state == 0) {
       if (cx) cx->count_begin();
-      const int64_t r0 = prof[0].recorded;
+      const int64_t r0 = prof[0].calls;
       eager();
-      sp.nrec = prof[0].recorded - r0;
+      sp.nrec = prof[0].calls - r0;   // narrow-GEMM launches of one run (event pairs a timed graph needs)
       if (cx) sp.blob = cx->count_end();
       sp.state = 1;
       return;
@@ -246,52 +252,63 @@ class DenseEngine : public EngineBase {
     if (cx) {
       cx->flush();
       sp.mark = cx->scratch.mark();
-      cx->st = gs_;
-      comp_->st_ = gs_;
-      cx->capture_begin(sp.hblob, sp.dblob.template as<char>(), sp.blob_cap);
     }
-    cudaGraph_t g = nullptr;
-    if (prof[0].on) {
-      prof[0].collect();
-      prof[0].reserve_graph((size_t)sp.nrec);
-      prof[0].capture_into = &sp.prof_recs;
-    }
-    const int64_t c0 = launch_count();
-    bool ok = cudaStreamBeginCapture(gs_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    if (ok) {
-      try {
-        for (auto& op : sp.ops) op(gs_);
-      } catch (...) {
-        ok = false;
+    // one capture of the program; with_events: the copy with timing events for profiled replays
+    auto capture = [&](bool with_events) -> cudaGraphExec_t {
+      if (cx) {
+        cx->st = gs_;
+        comp_->st_ = gs_;
+        cx->capture_begin(sp.hblob, sp.dblob.template as<char>(), sp.blob_cap);
       }
-      if (cudaStreamEndCapture(gs_, &g) != cudaSuccess || !g) ok = false;
-    }
-    sp.glaunch = (int)(launch_count() - c0);
-    count_launches(-sp.glaunch);   // captured, not run
-    if (prof[0].capture_into) {    // reserved event pairs the capture did not use
-      for (size_t i = sp.prof_recs.size(); i < prof[0].graph_reserve.size(); ++i) {
-        cudaEventDestroy(prof[0].graph_reserve[i].a);
-        cudaEventDestroy(prof[0].graph_reserve[i].b);
+      const bool prof_on = prof[0].on;
+      if (with_events) {
+        prof[0].collect();
+        prof[0].reserve_graph((size_t)sp.nrec);
+        sp.prof_recs.clear();
+        prof[0].capture_into = &sp.prof_recs;
+      } else {
+        prof[0].on = false;
       }
-      prof[0].graph_reserve.clear();
-      prof[0].capture_into = nullptr;
-    }
-    if (cx) {
-      cx->st = st_;
-      comp_->st_ = st_;
-      cx->scratch.release(sp.mark);
-      if (!cx->capture_end()) ok = false;   // copies the job tables to their device twin
-    }
-    if (ok && cudaGraphInstantiate(&sp.exec, g, 0) != cudaSuccess) {
-      sp.exec = nullptr;
-      ok = false;
-    }
-    if (g) cudaGraphDestroy(g);
-    cudaGetLastError();   // a failed capture leaves its error behind
-    if (!ok) {
+      cudaGraph_t g = nullptr;
+      const int64_t c0 = launch_count();
+      bool ok = cudaStreamBeginCapture(gs_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        try {
+          for (auto& op : sp.ops) op(gs_);
+        } catch (...) {
+          ok = false;
+        }
+        if (cudaStreamEndCapture(gs_, &g) != cudaSuccess || !g) ok = false;
+      }
+      sp.glaunch = (int)(launch_count() - c0);
+      count_launches(-sp.glaunch);   // captured, not run
+      prof[0].on = prof_on;
+      if (with_events) {             // reserved event pairs the capture did not use
+        for (size_t i = sp.prof_recs.size(); i < prof[0].graph_reserve.size(); ++i) {
+          cudaEventDestroy(prof[0].graph_reserve[i].a);
+          cudaEventDestroy(prof[0].graph_reserve[i].b);
+        }
+        prof[0].graph_reserve.clear();
+        prof[0].capture_into = nullptr;
+      }
+      if (cx) {
+        cx->st = st_;
+        comp_->st_ = st_;
+        cx->scratch.release(sp.mark);
+        if (!cx->capture_end()) ok = false;   // copies the job tables to their device twin
+      }
+      cudaGraphExec_t ex = nullptr;
+      if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();   // a failed capture leaves its error behind
+      return ex;
+    };
+    sp.exec = capture(false);
+    if (!sp.exec) {
       sp.state = 3;
       return eager();
     }
+    if (prof[0].on) sp.exec_prof = capture(true);   // without it, replays are simply not timed
     sp.state = 2;
     run_solve_ops(sp);
   }

@@ -194,8 +194,9 @@ class Handle:
         _check(lib().mf_stats(self.ptr, C.byref(s)), self.ptr)
         return {k: getattr(s, k) for k, _ in s._fields_}
 
-    def mf_profile(self, enable: bool):
-        _check(lib().mf_profile(self.ptr, 1 if enable else 0), self.ptr)
+    def mf_profile(self, enable, period: int = 1):
+        """enable: False stops; True times one launch (and one graph replay) in `period`."""
+        _check(lib().mf_profile(self.ptr, int(period) if enable else 0), self.ptr)
 
     def mf_profile_read(self, kernel: int = 0) -> dict:
         """kernel: MF_PROF_NARROW_GEMM (0) or MF_PROF_FRONT_GEMM (1); see include/mf.h."""
