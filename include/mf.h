@@ -206,7 +206,8 @@ int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const flo
  *   U     out, nmat blocks of 2 m kmax floats (real then imaginary m x kmax row-major;
  *         columns >= rank_q are unspecified)
  *   sk    out, nmat x kmax int32 (first rank_q entries valid), rank out, nmat int32.
- * The QR work matrix (2 m n floats per matrix) lives in shared memory when it fits
+ * Matrices with m, n <= 128 keep their rows in registers (1024 threads each); otherwise
+ * the QR work matrix (2 m n floats per matrix) lives in shared memory when it fits
  * (2 m n + 2 n + 2 m floats <= 200 KiB), else in scratch allocated by the call.  Runs on `stream`
  * and waits for it.  Errors: MF_ERR_ARG (sizes: n <= 8192, m <= 2048), MF_ERR_OOM, MF_ERR_CUDA.
  */

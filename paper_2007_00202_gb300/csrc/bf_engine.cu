@@ -374,9 +374,9 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
   sk.assign(nj, {});
   Us.assign(nj, Blk<T>());
   if (!nj) return;
-  std::vector<IdJob<T>> jobs, sjobs;
+  std::vector<IdJob<T>> jobs, sjobs, rjobs;
   std::vector<size_t> which;
-  int smax_m = 1, smax_n = 1;
+  int smax_m = 1, smax_n = 1, rmax_m = 1, rmax_n = 1;
   size_t sbytes = 0;
   int32_t* dsk = nullptr;
   int32_t* drk = scratch.takeT<int32_t>(nj);
@@ -418,7 +418,12 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
     j.rank = drk + q;
     j.wplane = (int64_t)m * n;
     const size_t sb = row_id_smem_bytes(m, n, sizeof(T), true);
-    if (sb <= kRowIdSmemCap) {   // QR work in shared memory
+    if (sizeof(T) == 4 && m <= 128 && n <= 128) {   // rows in registers
+      j.work = nullptr;
+      rjobs.push_back(j);
+      rmax_m = std::max(rmax_m, m);
+      rmax_n = std::max(rmax_n, n);
+    } else if (sb <= kRowIdSmemCap) {   // QR work in shared memory
       j.work = nullptr;
       sjobs.push_back(j);
       smax_m = std::max(smax_m, m);
@@ -433,7 +438,14 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
     which.push_back(q);
   }
   MF_CUDA(cudaMemsetAsync(drk, 0, nj * 4, st));
-  // matrices whose QR work fits in shared memory, then the others (work in global memory)
+  // small matrices with their rows in registers, matrices whose QR work fits in shared memory,
+  // then the others (work in global memory)
+  if (!rjobs.empty()) {
+    const IdJob<T>* dj = stage(rjobs.data(), rjobs.size());
+    if (launch_row_id_reg<T>(dj, (int)rjobs.size(), rmax_m, rmax_n, (T)tol, max_rank, st) != 0)
+      throw std::runtime_error("ID block too large for the register row-ID kernel");
+    n_id += (int64_t)rjobs.size();
+  }
   if (!sjobs.empty()) {
     const IdJob<T>* dj = stage(sjobs.data(), sjobs.size());
     if (launch_row_id<T>(dj, (int)sjobs.size(), smax_m, smax_n, (T)tol, max_rank, st, true, sbytes) != 0)

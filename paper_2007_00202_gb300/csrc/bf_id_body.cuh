@@ -196,3 +196,193 @@ __device__ __forceinline__ void row_id_body(const IdJob<T>& jb, T tol, int32_t m
 
 
 }  // namespace mf
+
+namespace mf {
+
+// Register-resident variant for m <= 128 rows of n <= 8 RC columns (the randomized
+// construction's sketch blocks): 1024 threads, 8 lanes per row, each lane keeping its RC
+// columns (c = lane8 + 8 j) of the row in registers for the whole factorization.  A step
+// costs two barriers: the pivot row's owners publish it in shared memory, every thread
+// derives the reflection from it, updates its own columns, and the lanes of a row reduce
+// the dot product and the new norm with shuffles; each warp leaves its largest norm for the
+// next step's pivot.  The final rows go to shared memory for the back substitution.
+// Same result contract as row_id_body; pivot: largest remaining norm, lowest row on ties.
+template <typename T, int RC>
+__device__ __forceinline__ void row_id_body_reg(const IdJob<T>& jb, T tol, int32_t max_rank) {
+  constexpr int LPR = 8;
+  const int m = jb.m, n = jb.n;
+  const int kw = m < n ? m : n;   // columns kept for the back substitution (>= any rank)
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* pr = reinterpret_cast<T*>(smraw);   // pivot row (n values, re / im)
+  T* pi = pr + n;
+  T* Wr = pi + n;                         // m x kw, after the factorization
+  T* Wi = Wr + (int64_t)m * kw;
+  int* piv = reinterpret_cast<int*>(Wi + (int64_t)m * kw);
+  __shared__ T wbest_v[2][32];
+  __shared__ int wbest_i[2][32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row = tid / LPR, l8 = tid % LPR;
+  const bool mine = row < m;
+  auto better = [](T v, int i, T ov, int oi) { return ov > v || (ov == v && oi < i); };
+  T yr[RC], yi[RC];
+  bool done = !mine;
+  {
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < RC; ++j) {
+      const int c = l8 + LPR * j;
+      T a = 0, b = 0;
+      if (mine && c < n) {
+        a = jb.M[(int64_t)row * jb.ld + c];
+        b = jb.M[(int64_t)row * jb.ld + c + jb.plane];
+      }
+      yr[j] = a;
+      yi[j] = b;
+      s += a * a + b * b;
+    }
+    for (int o = LPR >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    T bv = mine ? s : T(-1);
+    int bi = mine ? row : m;
+    for (int o = 16; o >= LPR; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (better(bv, bi, ov, oi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { wbest_v[0][warp] = bv; wbest_i[0][warp] = bi; }
+  }
+  int kmax = kw;
+  if (max_rank > 0 && max_rank < kmax) kmax = max_rank;
+  __syncthreads();
+  int rank = 0;
+  T ref = T(0);
+  const int nw = blockDim.x >> 5;
+  for (int k = 0; k < kmax; ++k) {
+    const int cb = k & 1, nb = cb ^ 1;
+    T best = lane < nw ? wbest_v[cb][lane] : T(-1);   // the warps' candidates, reduced in every warp
+    int q = lane < nw ? wbest_i[cb][lane] : m;
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, q, o);
+      if (better(best, q, ov, oi)) { best = ov; q = oi; }
+    }
+    if (q >= m) break;
+    const T nu = sqrt(best > T(0) ? best : T(0));
+    if (k == 0) ref = nu;
+    if (ref == T(0) || nu <= tol * ref) break;
+    if (tid == 0) piv[k] = q;
+    if (row == q) {   // publish the pivot row's coordinates k.. and take its place in R
+#pragma unroll
+      for (int j = 0; j < RC; ++j) {
+        const int c = l8 + LPR * j;
+        if (c >= k && c < n) { pr[c] = yr[j]; pi[c] = yi[j]; }
+      }
+    }
+    __syncthreads();
+    const T x0r = pr[k], x0i = pi[k];
+    const T ax0 = sqrt(x0r * x0r + x0i * x0i);
+    const T phr = ax0 > T(0) ? x0r / ax0 : T(1), phi = ax0 > T(0) ? x0i / ax0 : T(0);
+    const T alr = -phr * nu, ali = -phi * nu;
+    const T v0r = x0r - alr, v0i = x0i - ali;
+    const T vv = best - (x0r * x0r + x0i * x0i) + v0r * v0r + v0i * v0i;
+    const T sc = vv > T(0) ? T(2) / vv : T(0);
+    if (row == q) {
+      done = true;
+#pragma unroll
+      for (int j = 0; j < RC; ++j) {
+        const int c = l8 + LPR * j;
+        if (c >= k) { yr[j] = c == k ? alr : T(0); yi[j] = c == k ? ali : T(0); }
+      }
+    }
+    T dr = 0, di = 0;   // v^H y over this lane's columns
+    if (!done) {
+#pragma unroll
+      for (int j = 0; j < RC; ++j) {
+        const int c = l8 + LPR * j;
+        if (c >= k && c < n) {
+          const T a = c == k ? v0r : pr[c], b = c == k ? v0i : pi[c];
+          dr += a * yr[j] + b * yi[j];
+          di += a * yi[j] - b * yr[j];
+        }
+      }
+    }
+    for (int o = LPR >> 1; o > 0; o >>= 1) {
+      dr += __shfl_xor_sync(0xffffffffu, dr, o);
+      di += __shfl_xor_sync(0xffffffffu, di, o);
+    }
+    dr *= sc;
+    di *= sc;
+    T s = 0;
+    if (!done) {
+#pragma unroll
+      for (int j = 0; j < RC; ++j) {
+        const int c = l8 + LPR * j;
+        if (c >= k && c < n) {
+          const T a = c == k ? v0r : pr[c], b = c == k ? v0i : pi[c];
+          yr[j] -= a * dr - b * di;
+          yi[j] -= a * di + b * dr;
+          if (c > k) s += yr[j] * yr[j] + yi[j] * yi[j];
+        }
+      }
+    }
+    for (int o = LPR >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    T bv = done ? T(-1) : s;
+    int bi = done ? m : row;
+    for (int o = 16; o >= LPR; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (better(bv, bi, ov, oi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { wbest_v[nb][warp] = bv; wbest_i[nb][warp] = bi; }
+    rank = k + 1;
+    __syncthreads();
+  }
+  // rows to shared memory (first kw columns: R of the pivots, R12 of the others)
+  if (mine) {
+#pragma unroll
+    for (int j = 0; j < RC; ++j) {
+      const int c = l8 + LPR * j;
+      if (c < kw) { Wr[(int64_t)row * kw + c] = yr[j]; Wi[(int64_t)row * kw + c] = yi[j]; }
+    }
+  }
+  __syncthreads();
+  const int r = rank;
+  if (tid == 0) *jb.rank = r;
+  for (int b = tid; b < r; b += blockDim.x) jb.sk[b] = piv[b];
+  const int ldu = jb.ldu;
+  T* Ur = jb.U;
+  T* Ui = jb.U + jb.uplane;
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    int b = e / r, c = e % r;
+    Ur[(int64_t)piv[b] * ldu + c] = b == c ? T(1) : T(0);
+    Ui[(int64_t)piv[b] * ldu + c] = T(0);
+  }
+  // non-pivot rows (the row's own lanes know whether it is done): back substitution in place
+  if (mine && !done && l8 == 0) {
+    T* wr = Wr + (int64_t)row * kw;
+    T* wi = Wi + (int64_t)row * kw;
+    for (int b = r - 1; b >= 0; --b) {
+      T accr = wr[b], acci = wi[b];
+      for (int c = b + 1; c < r; ++c) {
+        const int pc = piv[c];
+        T Rr = Wr[(int64_t)pc * kw + b], Ri = Wi[(int64_t)pc * kw + b];
+        accr -= Rr * wr[c] - Ri * wi[c];
+        acci -= Rr * wi[c] + Ri * wr[c];
+      }
+      const int pb = piv[b];
+      T dr2 = Wr[(int64_t)pb * kw + b], di2 = Wi[(int64_t)pb * kw + b];
+      T den = dr2 * dr2 + di2 * di2;
+      if (den == T(0)) den = T(1);
+      wr[b] = (accr * dr2 + acci * di2) / den;
+      wi[b] = (acci * dr2 - accr * di2) / den;
+    }
+  }
+  __syncthreads();
+  // copy the non-pivot rows' coefficients out (the lanes of a row, columns strided)
+  if (mine && !done)
+    for (int c = l8; c < r; c += LPR) {
+      Ur[(int64_t)row * ldu + c] = Wr[(int64_t)row * kw + c];
+      Ui[(int64_t)row * ldu + c] = Wi[(int64_t)row * kw + c];
+    }
+}
+
+}  // namespace mf

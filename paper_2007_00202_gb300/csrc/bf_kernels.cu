@@ -19,6 +19,29 @@ __global__ void __launch_bounds__(NT) k_row_id(const IdJob<T>* jobs, T tol, int3
   row_id_body<T>(jobs[blockIdx.x], tol, max_rank, work_in_smem != 0);
 }
 
+template <typename T, int RC>
+__global__ void __launch_bounds__(1024, 1) k_row_id_reg(const IdJob<T>* jobs, T tol, int32_t max_rank) {
+  row_id_body_reg<T, RC>(jobs[blockIdx.x], tol, max_rank);
+}
+
+template <typename T>
+int launch_row_id_reg(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank,
+                      cudaStream_t st) {
+  if (njobs <= 0) return 0;
+  if (max_m > 128 || max_n > 128) return -1;
+  const size_t sm = row_id_reg_smem_bytes(max_m, max_n, sizeof(T));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_row_id_reg<T, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
+    cudaFuncSetAttribute(k_row_id_reg<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
+    attr = true;
+  }
+  count_launches(1);
+  if (max_n <= 80) k_row_id_reg<T, 10><<<njobs, 1024, sm, st>>>(d_jobs, tol, max_rank);
+  else k_row_id_reg<T, 16><<<njobs, 1024, sm, st>>>(d_jobs, tol, max_rank);
+  return 0;
+}
+
 template <typename T>
 int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st,
                   bool work_in_smem, size_t smem_bytes) {
@@ -524,7 +547,8 @@ int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int max_r, int
 }
 
 #define MF_BF_INST(T)                                                                                            \
-  template int launch_row_id<T>(const IdJob<T>*, int, int, int, T, int, cudaStream_t, bool, size_t);                          \
+  template int launch_row_id<T>(const IdJob<T>*, int, int, int, T, int, cudaStream_t, bool, size_t);          \
+  template int launch_row_id_reg<T>(const IdJob<T>*, int, int, int, T, int, cudaStream_t);                          \
   template void launch_sketch<T>(const SketchGroup*, int, int, T*, int64_t, int, cudaStream_t);                 \
   template void launch_gather_rows<T>(const GatherJob<T>*, int, int64_t, cudaStream_t);                         \
   template void launch_front_entries<T>(const FrontEntryJob<T>*, int, int64_t, const FrontCtx<T>*, const int64_t*, \

@@ -166,6 +166,14 @@ inline size_t row_id_smem_bytes(int m, int n, size_t elem, bool work_in_smem) {
   return b;
 }
 constexpr size_t kRowIdSmemCap = 200 * 1024;
+// Register-resident row ID for m <= 128 and n <= 128 (1024 threads, rows in registers): its
+// dynamic shared memory (pivot row, the rows' first min(m, n) columns, the pivots).
+inline size_t row_id_reg_smem_bytes(int m, int n, size_t elem) {
+  const int kw = m < n ? m : n;
+  return elem * (2 * (size_t)n + 2 * (size_t)m * kw) + sizeof(int) * (size_t)m + 16;
+}
+template <typename T>
+int launch_row_id_reg(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st);
 template <typename T>
 int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol, int max_rank, cudaStream_t st,
                   bool work_in_smem = false, size_t smem_bytes = 0);

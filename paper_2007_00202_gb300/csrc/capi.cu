@@ -574,7 +574,7 @@ int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol
     int kmax = std::min(m, n);
     if (max_rank > 0) kmax = std::min(kmax, (int)max_rank);
     DevMem work, jobs;
-    const bool in_smem = mf::row_id_smem_bytes(m, n, sizeof(float), true) <= mf::kRowIdSmemCap;
+    const bool in_smem = (m <= 128 && n <= 128) || mf::row_id_smem_bytes(m, n, sizeof(float), true) <= mf::kRowIdSmemCap;
     if (!in_smem) work.alloc(sizeof(float) * 2 * (size_t)m * n * nmat);
     std::vector<mf::IdJob<float>> jb(nmat);
     for (int q = 0; q < nmat; ++q) {
@@ -593,7 +593,10 @@ int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol
       j.wplane = (int64_t)m * n;
     }
     mf::upload(jobs, jb, st);
-    if (mf::launch_row_id<float>(jobs.as<mf::IdJob<float>>(), nmat, m, n, (float)tol, max_rank, st, in_smem) != 0)
+    if (m <= 128 && n <= 128) {   // the solver's register-resident kernel for small blocks
+      if (mf::launch_row_id_reg<float>(jobs.as<mf::IdJob<float>>(), nmat, m, n, (float)tol, max_rank, st) != 0)
+        return fail(nullptr, MF_ERR_ARG, "matrix too large for the row-ID kernel");
+    } else if (mf::launch_row_id<float>(jobs.as<mf::IdJob<float>>(), nmat, m, n, (float)tol, max_rank, st, in_smem) != 0)
       return fail(nullptr, MF_ERR_ARG, "matrix too large for the row-ID kernel");
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaStreamSynchronize(st));
