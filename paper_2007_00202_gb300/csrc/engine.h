@@ -7,6 +7,7 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -106,9 +107,12 @@ struct LaunchProfiler {
     if (cudaEventCreate(&e) != cudaSuccess) throw CudaError("cudaEventCreate failed");
     return e;
   }
+  std::mutex mu;   // two host threads may launch timed kernels (fronts of one level)
   template <class F>
   void time(cudaStream_t st, double fl, double by, F&& launch) {
+    std::unique_lock<std::mutex> lk(mu);
     if (!on || (!capture_into && (calls++ % every) != 0)) {
+      lk.unlock();
       launch();
       return;
     }
@@ -116,6 +120,7 @@ struct LaunchProfiler {
     if (capture_into) {   // events of the graph: created by reserve_graph before the capture
       const size_t i = capture_into->size();
       if (i >= graph_reserve.size()) {   // not reserved: leave this launch untimed
+        lk.unlock();
         launch();
         return;
       }
@@ -127,14 +132,16 @@ struct LaunchProfiler {
     }
     r.flops = fl;
     r.bytes = by;
+    std::vector<Rec>* into = capture_into ? capture_into : &pending;
+    lk.unlock();
     // inside a capture an event becomes a record node of the graph only as an "external" record
-    const unsigned fl_rec = capture_into ? cudaEventRecordExternal : cudaEventRecordDefault;
+    const unsigned fl_rec = into != &pending ? cudaEventRecordExternal : cudaEventRecordDefault;
     cudaEventRecordWithFlags(r.a, st, fl_rec);
     launch();
     cudaEventRecordWithFlags(r.b, st, fl_rec);
+    lk.lock();
     ++recorded;
-    if (capture_into) capture_into->push_back(r);
-    else pending.push_back(r);
+    into->push_back(r);
   }
   // n event pairs for a graph about to be captured (owned by the caller afterwards)
   std::vector<Rec> graph_reserve;
@@ -143,9 +150,11 @@ struct LaunchProfiler {
     for (size_t i = 0; i < n; ++i) graph_reserve.push_back(Rec{make_event(), make_event(), 0, 0});
   }
   void replayed(const std::vector<Rec>& recs) {
+    std::lock_guard<std::mutex> lk(mu);
     if (on) pending.insert(pending.end(), recs.begin(), recs.end());
   }
   void collect() {
+    std::lock_guard<std::mutex> lk(mu);
     for (auto& r : pending) {
       float t = 0;
       if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
@@ -160,6 +169,7 @@ struct LaunchProfiler {
   }
   void enable(int period) {   // 0: off; N > 0: time one launch in N
     collect();
+    std::lock_guard<std::mutex> lk(mu);
     on = period > 0;
     every = period > 0 ? period : 1;
     calls = 0;

@@ -20,7 +20,18 @@ IdxVec iota_vec(int n) {
 }  // namespace
 
 template <typename T>
-void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr, const BFParams& P, uint64_t seed) {
+void CompressedPart<T>::ensure_second() {
+  if (cx2) return;
+  MF_CUDA(cudaStreamCreateWithFlags(&st2_, cudaStreamNonBlocking));
+  cx2 = std::make_unique<BFContext<T>>(st2_, persist_bytes_, scratch_bytes_);
+  cx2->prof = cx.prof;
+}
+
+template <typename T>
+void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr, const BFParams& P, uint64_t seed,
+                                     int w) {
+  BFContext<T>& cx = ctx(w);          // this front's execution context and stream
+  const cudaStream_t st_ = stream(w);
   auto t0 = std::chrono::steady_clock::now();
   const FrontInfo& f = an_.fronts[fid];
   const int s = (int)f.s(), u = (int)f.u();
@@ -41,6 +52,7 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
   struct Kid {
     int id;
     bool compressed;
+    const CompFront<T>* cf = nullptr;   // a compressed child's factors (built at a lower level)
     std::vector<int32_t> inv;
     DevMem d_inv;
   };
@@ -49,6 +61,10 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
     Kid k;
     k.id = (int)c;
     k.compressed = an_.fronts[c].compressed;
+    if (k.compressed) {
+      std::lock_guard<std::mutex> lk(fronts_mu_);
+      k.cf = fronts.at(k.id).get();
+    }
     k.inv.assign(s + u, -1);
     const auto& cu = an_.fronts[c].upd;
     for (size_t i = 0; i < cu.size(); ++i) {
@@ -117,7 +133,7 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
           for (int32_t y : g[q].second) m[q].second.push_back(y >= 0 && y < s + u ? k.inv[y] : -1);
           any = true;
         }
-        if (any) cx.hodbf_extract(*fronts.at(k.id)->C, m, dst, T(1));
+        if (any) cx.hodbf_extract(*k.cf->C, m, dst, T(1));
       }
       if (minus_S && Sptr) {
         std::vector<std::pair<IdxVec, IdxVec>> m(g);
@@ -188,7 +204,9 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
     DOp<T> op;
     op.rows = u;
     op.cols = u;
-    op.apply = [this, F12p, F21p, Ip, s, u](const Blk<T>& X, Blk<T>& Y, bool tr) {
+    BFContext<T>* cxp = &cx;
+    op.apply = [cxp, F12p, F21p, Ip, s](const Blk<T>& X, Blk<T>& Y, bool tr) {
+      BFContext<T>& cx = *cxp;
       const int k = X.cols;
       Blk<T> a = new_blk<T>(cx.scratch, s, k), b = new_blk<T>(cx.scratch, s, k);
       std::vector<Blk<T>> xs{X}, as{a};
@@ -216,12 +234,20 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
   MF_CUDA(cudaStreamSynchronize(st_));
   cx.check_status();
   cf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  std::lock_guard<std::mutex> lk(fronts_mu_);
   fronts[fid] = std::move(cfp);
 }
 
 template <typename T>
-void CompressedPart<T>::densify_C(int fid, const FrontDev<T>& fd) {
-  CompFront<T>& cf = *fronts.at(fid);
+void CompressedPart<T>::densify_C(int fid, const FrontDev<T>& fd, int w) {
+  BFContext<T>& cx = ctx(w);
+  const cudaStream_t st_ = stream(w);
+  CompFront<T>* cfp;
+  {
+    std::lock_guard<std::mutex> lk(fronts_mu_);
+    cfp = fronts.at(fid).get();
+  }
+  CompFront<T>& cf = *cfp;
   if (!cf.C || cf.u == 0) return;
   const int u = cf.u;
   const size_t mk = cx.scratch.mark();

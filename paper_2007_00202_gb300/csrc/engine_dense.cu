@@ -13,6 +13,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
+#include <thread>
 
 #include "engine.h"
 #include "engine_comp.h"
@@ -52,25 +54,64 @@ class DenseEngine : public EngineBase {
     for (auto& kv : sprog_) kv.second->drop_graph();   // compressed fronts move with every factorization
     if (comp_) {
       comp_->fronts.clear();
-      comp_->cx.persist.release(0);
-      comp_->cx.scratch.release(0);
-      comp_->cx.flops = 0;
+      for (int w = 0; w < (comp_->cx2 ? 2 : 1); ++w) {
+        comp_->ctx(w).persist.release(0);
+        comp_->ctx(w).scratch.release(0);
+        comp_->ctx(w).flops = 0;
+      }
     }
+    static const bool serial = getenv("MF_SERIAL_FRONTS") && getenv("MF_SERIAL_FRONTS")[0] == '1';
     for (size_t lv = 0; lv < levels_.size(); ++lv) {
       for (size_t i = lvl_begin_[lv]; i < lvl_begin_[lv + 1]; ++i) {
         if (gemm_flops_[i] > 0) prof[1].time(st_, gemm_flops_[i], gemm_bytes_[i], [&] { fops_[i](st_); });
         else fops_[i](st_);
       }
-      for (int32_t fid : comp_levels_[lv]) {
-        auto t0 = std::chrono::steady_clock::now();
-        comp_->factor_front(fid, fr_, P, eo_.seed);
-        const auto& F = an_.fronts;
-        if (F[fid].parent >= 0 && !F[F[fid].parent].compressed) comp_->densify_C(fid, fr_[fid]);
-        max_rank_ = std::max(max_rank_, comp_->fronts.at(fid)->max_rank);
-        comp_seconds_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      const auto& lvl = comp_levels_[lv];
+      if (lvl.empty()) continue;
+      auto t0 = std::chrono::steady_clock::now();
+      const auto& F = an_.fronts;
+      // front list[i] with execution context w; densify on the same context
+      auto run = [&](const std::vector<int32_t>& list, size_t i0, size_t step, int w) {
+        for (size_t i = i0; i < list.size(); i += step) {
+          const int fid = list[i];
+          comp_->factor_front(fid, fr_, P, eo_.seed, w);
+          if (F[fid].parent >= 0 && !F[F[fid].parent].compressed) comp_->densify_C(fid, fr_[fid], w);
+        }
+      };
+      if (lvl.size() == 1 || serial) {
+        run(lvl, 0, 1, 0);
+      } else {
+        // the fronts of one level are independent: two host threads build them, each with its own
+        // stream and arenas, so one thread's host work overlaps the other's GPU work
+        comp_->ensure_second();
+        MF_CUDA(cudaEventRecord(lev_ev_[0], st_));                  // children and dense fronts below
+        MF_CUDA(cudaStreamWaitEvent(comp_->stream(1), lev_ev_[0], 0));
+        int dev = 0;
+        MF_CUDA(cudaGetDevice(&dev));
+        std::exception_ptr err;
+        std::thread th([&, dev] {
+          try {
+            MF_CUDA(cudaSetDevice(dev));
+            run(lvl, 1, 2, 1);
+            MF_CUDA(cudaStreamSynchronize(comp_->stream(1)));
+          } catch (...) {
+            err = std::current_exception();
+          }
+        });
+        std::exception_ptr err0;
+        try {
+          run(lvl, 0, 2, 0);
+        } catch (...) {
+          err0 = std::current_exception();
+        }
+        th.join();
+        if (err0) std::rethrow_exception(err0);
+        if (err) std::rethrow_exception(err);
       }
+      for (int32_t fid : lvl) max_rank_ = std::max(max_rank_, comp_->fronts.at(fid)->max_rank);
+      comp_seconds_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
-    if (comp_) comp_flops_ = comp_->cx.flops;
+    if (comp_) comp_flops_ = comp_->cx.flops + (comp_->cx2 ? comp_->cx2->flops : 0.0);
     if (getenv("MF_TRACE") && getenv("MF_TRACE")[0] == '1') {
       MF_CUDA(cudaStreamSynchronize(st_));
       fprintf(stderr, "[mf] factor: %.3f s, compressed fronts %.3f s (host-issued, synchronised per phase)\n",
@@ -185,6 +226,7 @@ class DenseEngine : public EngineBase {
   double comp_flops_ = 0, comp_seconds_ = 0;
   int max_rank_ = 0;
   cudaStream_t gs_ = nullptr;               // stream of the solve graphs (forked from and joined to st_)
+  cudaEvent_t lev_ev_[1] = {nullptr};       // the engine stream's progress before a level's compressed fronts
   cudaEvent_t gev_[2] = {nullptr, nullptr};
 
  public:
@@ -192,6 +234,7 @@ class DenseEngine : public EngineBase {
     sprog_.clear();
     for (auto e : gev_)
       if (e) cudaEventDestroy(e);
+    if (lev_ev_[0]) cudaEventDestroy(lev_ev_[0]);
     if (gs_) cudaStreamDestroy(gs_);
   }
 
@@ -465,6 +508,7 @@ class DenseEngine : public EngineBase {
     if (any_comp) {
       comp_ = std::make_unique<CompressedPart<T>>(an_, A_, st_, eo_.persist_bytes, eo_.scratch_bytes);
       comp_->cx.prof = &prof[0];
+      MF_CUDA(cudaEventCreateWithFlags(&lev_ev_[0], cudaEventDisableTiming));
     }
     std::vector<int32_t> all;
     for (auto& lv : levels_) {
