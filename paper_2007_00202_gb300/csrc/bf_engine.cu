@@ -83,6 +83,21 @@ GemmDesc<T> gdesc(int m, int n, int k, int ta, int tb, T alpha, T beta, const Bl
   return d;
 }
 
+// C = alpha (op(A1) op(B1) + op(A2) op(B2)) + beta C as one two-term product (k1 + k2 reduction
+// indices; narrow kernel only)
+template <typename T>
+GemmDesc<T> gdesc2(int m, int n, int k1, int k2, int ta, int tb, T alpha, T beta, const Blk<T>& A1, const Blk<T>& B1,
+                   const Blk<T>& A2, const Blk<T>& B2, const Blk<T>& C) {
+  if (k1 == 0) return gdesc<T>(m, n, k2, ta, tb, alpha, beta, A2, B2, C);
+  GemmDesc<T> d = gdesc<T>(m, n, k1 + k2, ta, tb, alpha, beta, A1, B1, C);
+  if (k2 > 0) {
+    d.k1 = k1;
+    d.A2 = A2.pm();
+    d.B2 = B2.pm();
+  }
+  return d;
+}
+
 }  // namespace
 
 Tree subtree(const Tree& t, int l0, int i0, int depth);
@@ -482,6 +497,10 @@ void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vecto
   const size_t nb = bfs.size();
   if (!nb) return;
   std::map<int, std::vector<GemmDesc<T>>> stages;   // stage index -> descs
+  // narrow products (n <= 128): the two halves of a pulled level go into one two-term product
+  int maxcols = 0;
+  for (size_t q = 0; q < nb; ++q) maxcols = std::max(maxcols, (int)X[q].cols);
+  const bool two = gemm_nrhs_width(maxcols, sizeof(T)) != 0;
   const T one = T(1), zero = T(0), beta_out = accumulate ? T(1) : T(0);
   for (size_t q = 0; q < nb; ++q) {
     const DBF<T>& bf = *bfs[q];
@@ -557,20 +576,36 @@ void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vecto
         for (int i = 0; i < (1 << (l + 1)); ++i)
           for (int j = 0; j < (1 << (L - l - 1)); ++j) rk.push_back(bf.rr(l + 1, i, j));
         vec_buf(rk, nxt);
-        for (int t = 0; t < 2; ++t) {
+        if (two) {
           for (int i2 = 0; i2 < (1 << (l + 1)); ++i2)
             for (int j2 = 0; j2 < (1 << (L - l - 1)); ++j2) {
-              const int i = i2 / 2, nu = 2 * j2 + t;
-              const int p = bf.pidx(l, i, nu);
+              const int i = i2 / 2, p0 = bf.pidx(l, i, 2 * j2), p1 = bf.pidx(l, i, 2 * j2 + 1);
               const int r1 = bf.rr(l + 1, 2 * i, j2);
               const int rows0 = (i2 % 2 == 0) ? 0 : r1;
               const int nrow = bf.rr(l + 1, i2, j2);
-              const Blk<T>& R = bf.U[l][p];
-              stages[stg + t].push_back(gdesc<T>(nrow, k, bf.rr(l, i, nu), 0, 0, one, t == 0 ? zero : one,
-                                                 R.sub(rows0, 0, nrow, R.cols), ys[p], nxt[bf.pidx(l + 1, i2, j2)]));
+              const Blk<T>& R0 = bf.U[l][p0];
+              const Blk<T>& R1 = bf.U[l][p1];
+              stages[stg].push_back(gdesc2<T>(nrow, k, bf.rr(l, i, 2 * j2), bf.rr(l, i, 2 * j2 + 1), 0, 0, one, zero,
+                                              R0.sub(rows0, 0, nrow, R0.cols), ys[p0], R1.sub(rows0, 0, nrow, R1.cols),
+                                              ys[p1], nxt[bf.pidx(l + 1, i2, j2)]));
             }
+          stg += 1;
+        } else {
+          for (int t = 0; t < 2; ++t) {
+            for (int i2 = 0; i2 < (1 << (l + 1)); ++i2)
+              for (int j2 = 0; j2 < (1 << (L - l - 1)); ++j2) {
+                const int i = i2 / 2, nu = 2 * j2 + t;
+                const int p = bf.pidx(l, i, nu);
+                const int r1 = bf.rr(l + 1, 2 * i, j2);
+                const int rows0 = (i2 % 2 == 0) ? 0 : r1;
+                const int nrow = bf.rr(l + 1, i2, j2);
+                const Blk<T>& R = bf.U[l][p];
+                stages[stg + t].push_back(gdesc<T>(nrow, k, bf.rr(l, i, nu), 0, 0, one, t == 0 ? zero : one,
+                                                   R.sub(rows0, 0, nrow, R.cols), ys[p], nxt[bf.pidx(l + 1, i2, j2)]));
+              }
+          }
+          stg += 2;
         }
-        stg += 2;
         ys.swap(nxt);
       }
       for (int i = 0; i < (1 << L); ++i) {
@@ -599,20 +634,33 @@ void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vecto
         for (int i = 0; i < (1 << l); ++i)
           for (int j = 0; j < (1 << (L - l)); ++j) rk.push_back(bf.rr(l, i, j));
         vec_buf(rk, nxt);
-        for (int t = 0; t < 2; ++t) {
+        if (two) {
           for (int i = 0; i < (1 << l); ++i)
             for (int j = 0; j < (1 << (L - l)); ++j) {
               const int p = bf.pidx(l, i, j);
-              const int r1 = bf.rr(l + 1, 2 * i, j / 2);
-              const int rows0 = t == 0 ? 0 : r1;
-              const int nrow = bf.rr(l + 1, 2 * i + t, j / 2);
+              const int r1 = bf.rr(l + 1, 2 * i, j / 2), r2 = bf.rr(l + 1, 2 * i + 1, j / 2);
               const Blk<T>& R = bf.U[l][p];
-              stages[stg + t].push_back(gdesc<T>(bf.rr(l, i, j), k, nrow, 1, 0, one, t == 0 ? zero : one,
-                                                 R.sub(rows0, 0, nrow, R.cols), cur[bf.pidx(l + 1, 2 * i + t, j / 2)],
-                                                 nxt[p]));
+              stages[stg].push_back(gdesc2<T>(bf.rr(l, i, j), k, r1, r2, 1, 0, one, zero, R.sub(0, 0, r1, R.cols),
+                                              cur[bf.pidx(l + 1, 2 * i, j / 2)], R.sub(r1, 0, r2, R.cols),
+                                              cur[bf.pidx(l + 1, 2 * i + 1, j / 2)], nxt[p]));
             }
+          stg += 1;
+        } else {
+          for (int t = 0; t < 2; ++t) {
+            for (int i = 0; i < (1 << l); ++i)
+              for (int j = 0; j < (1 << (L - l)); ++j) {
+                const int p = bf.pidx(l, i, j);
+                const int r1 = bf.rr(l + 1, 2 * i, j / 2);
+                const int rows0 = t == 0 ? 0 : r1;
+                const int nrow = bf.rr(l + 1, 2 * i + t, j / 2);
+                const Blk<T>& R = bf.U[l][p];
+                stages[stg + t].push_back(gdesc<T>(bf.rr(l, i, j), k, nrow, 1, 0, one, t == 0 ? zero : one,
+                                                   R.sub(rows0, 0, nrow, R.cols), cur[bf.pidx(l + 1, 2 * i + t, j / 2)],
+                                                   nxt[p]));
+              }
+          }
+          stg += 2;
         }
-        stg += 2;
         cur.swap(nxt);
       }
       std::vector<Blk<T>> ys;
@@ -634,20 +682,36 @@ void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vecto
         for (int i = 0; i < (1 << (l - 1)); ++i)
           for (int j = 0; j < (1 << (L - l + 1)); ++j) rk.push_back(bf.rc(l - 1, i, j));
         vec_buf(rk, nxt);
-        for (int t = 0; t < 2; ++t) {
+        if (two) {
           for (int i2 = 0; i2 < (1 << (l - 1)); ++i2)
             for (int j2 = 0; j2 < (1 << (L - l + 1)); ++j2) {
-              const int i = 2 * i2 + t, j = j2 / 2;
-              const int p = bf.pidx(l, i, j);
+              const int j = j2 / 2, p0 = bf.pidx(l, 2 * i2, j), p1 = bf.pidx(l, 2 * i2 + 1, j);
               const int c1 = bf.rc(l - 1, i2, 2 * j);
               const int rows0 = (j2 % 2 == 0) ? 0 : c1;
               const int nrow = bf.rc(l - 1, i2, j2);
-              const Blk<T>& W = bf.V[l][p];
-              stages[stg + t].push_back(gdesc<T>(nrow, k, bf.rc(l, i, j), 0, 0, one, t == 0 ? zero : one,
-                                                 W.sub(rows0, 0, nrow, W.cols), ys[p], nxt[bf.pidx(l - 1, i2, j2)]));
+              const Blk<T>& W0 = bf.V[l][p0];
+              const Blk<T>& W1 = bf.V[l][p1];
+              stages[stg].push_back(gdesc2<T>(nrow, k, bf.rc(l, 2 * i2, j), bf.rc(l, 2 * i2 + 1, j), 0, 0, one, zero,
+                                              W0.sub(rows0, 0, nrow, W0.cols), ys[p0], W1.sub(rows0, 0, nrow, W1.cols),
+                                              ys[p1], nxt[bf.pidx(l - 1, i2, j2)]));
             }
+          stg += 1;
+        } else {
+          for (int t = 0; t < 2; ++t) {
+            for (int i2 = 0; i2 < (1 << (l - 1)); ++i2)
+              for (int j2 = 0; j2 < (1 << (L - l + 1)); ++j2) {
+                const int i = 2 * i2 + t, j = j2 / 2;
+                const int p = bf.pidx(l, i, j);
+                const int c1 = bf.rc(l - 1, i2, 2 * j);
+                const int rows0 = (j2 % 2 == 0) ? 0 : c1;
+                const int nrow = bf.rc(l - 1, i2, j2);
+                const Blk<T>& W = bf.V[l][p];
+                stages[stg + t].push_back(gdesc<T>(nrow, k, bf.rc(l, i, j), 0, 0, one, t == 0 ? zero : one,
+                                                   W.sub(rows0, 0, nrow, W.cols), ys[p], nxt[bf.pidx(l - 1, i2, j2)]));
+              }
+          }
+          stg += 2;
         }
-        stg += 2;
         ys.swap(nxt);
       }
       for (int j = 0; j < (1 << L); ++j) {

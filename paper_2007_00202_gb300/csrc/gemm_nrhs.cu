@@ -47,10 +47,7 @@ __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict
   const int nkt = (d.k + NR_BK - 1) / NR_BK;
   const int ks = gridDim.y, kr = blockIdx.y;
   const int kt0 = (int)((int64_t)nkt * kr / ks), kt1 = (int)((int64_t)nkt * (kr + 1) / ks);
-  const T* Ar = d.A.re;
-  const T* Ai = d.A.re + d.A.plane;
-  const T* Br = d.B.re;
-  const T* Bi = d.B.re + d.B.plane;
+  const int k1 = d.k1 > 0 ? d.k1 : d.k;   // reduction indices of the first term
   // this thread's A elements: (mm, kk) = (tid / 32 + 4 e, tid % 32) for transA = 0 (k-contiguous
   // rows), (tid % 32, tid / 32 + 4 e) for transA = 1 (m-contiguous rows of the stored A)
   const int a_fast = tid & 31, a_slow = tid >> 5;
@@ -66,9 +63,11 @@ __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict
       const int gm = m0 + a_mm + a_dm * e, gk = k0 + a_kk + a_dk * e;
       T vr = T(0), vi = T(0);
       if (gm < d.m && gk < d.k) {
-        const int64_t off = d.transA == 0 ? (int64_t)gm * d.A.ld + gk : (int64_t)gk * d.A.ld + gm;
-        vr = Ar[off];
-        vi = Ai[off];
+        const PMat<T>& A = gk < k1 ? d.A : d.A2;
+        const int kk2 = gk < k1 ? gk : gk - k1;
+        const int64_t off = d.transA == 0 ? (int64_t)gm * A.ld + kk2 : (int64_t)kk2 * A.ld + gm;
+        vr = A.re[off];
+        vi = A.re[off + A.plane];
       }
       ra[0][e] = vr;
       ra[1][e] = vi;
@@ -78,9 +77,11 @@ __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict
       const int nn = n0 + b_nn + b_dn * e, gk = k0 + b_kk + b_dk * e;
       T vr = T(0), vi = T(0);
       if (nn < d.n && gk < d.k) {
-        const int64_t off = d.transB == 0 ? (int64_t)gk * d.B.ld + nn : (int64_t)nn * d.B.ld + gk;
-        vr = Br[off];
-        vi = Bi[off];
+        const PMat<T>& B = gk < k1 ? d.B : d.B2;
+        const int kk2 = gk < k1 ? gk : gk - k1;
+        const int64_t off = d.transB == 0 ? (int64_t)kk2 * B.ld + nn : (int64_t)nn * B.ld + kk2;
+        vr = B.re[off];
+        vi = B.re[off + B.plane];
       }
       rb[0][e] = vr;
       rb[1][e] = vi;

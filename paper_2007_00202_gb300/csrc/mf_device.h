@@ -17,12 +17,17 @@ struct PMat {
 // One batched GEMM problem: C = alpha * op(A) op(B) + beta * C  (complex, planar).
 // transA = 0: A is M x K row-major (K contiguous); 1: A stored K x M row-major.
 // transB = 0: B is K x N row-major (N contiguous); 1: B stored N x K row-major.
+// Optional second term (the narrow kernel k_gemm_nrhs only): with k1 > 0 the first k1
+// reduction indices use (A, B) and the remaining k - k1 use (A2, B2) with the same
+// transposes, i.e. C = alpha (op(A) op(B) + op(A2) op(B2)) + beta C.
 template <typename T>
 struct GemmDesc {
   int32_t m, n, k;
   int32_t transA, transB;
   T alpha, beta;       // real scalars
   PMat<T> A, B, C;
+  int32_t k1 = 0;
+  PMat<T> A2{}, B2{};
 };
 
 // A tile of a batched GEMM: problem index and tile coordinates.
