@@ -318,8 +318,10 @@ void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
   HostTimer ht_(t_host + H_GEMM);
   std::vector<GemmDesc<T>> D;
   int maxn = 0, maxk = 1;
+  bool two = false;
   for (auto& d : descs) {
     if (d.m <= 0 || d.n <= 0) continue;
+    two = two || d.k1 > 0;
     D.push_back(d);
     flops += 8.0 * d.m * d.n * d.k;
     maxn = std::max(maxn, (int)d.n);
@@ -339,7 +341,7 @@ void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
   const GemmDesc<T>* dd = static_cast<const GemmDesc<T>*>(upload(D.data(), D.size() * sizeof(GemmDesc<T>)));
   const GemmTile* dt = stage(tl.data(), tl.size());
   if (nb) {
-    auto go = [&] { launch_gemm_nrhs<T>(dd, dt, (int)tl.size(), nb, gemm_nrhs_split((int)tl.size(), maxk), st); };
+    auto go = [&] { launch_gemm_nrhs<T>(dd, dt, (int)tl.size(), nb, gemm_nrhs_split((int)tl.size(), maxk), st, two); };
     if (prof && prof->on) {
       double fl = 0, by = 0;
       for (auto& d : D) {

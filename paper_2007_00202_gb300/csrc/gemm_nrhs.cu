@@ -32,7 +32,7 @@ struct NrSmem {
   T br[NR_BK][NB], bi[NR_BK][NB];                 // B tile
 };
 
-template <typename T, int NB>
+template <typename T, int NB, bool TWO>
 __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict__ descs,
                                                    const GemmTile* __restrict__ tiles) {
   constexpr int AE = NR_BM * NR_BK / 128;   // A elements per thread and plane (8)
@@ -63,11 +63,13 @@ __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict
       const int gm = m0 + a_mm + a_dm * e, gk = k0 + a_kk + a_dk * e;
       T vr = T(0), vi = T(0);
       if (gm < d.m && gk < d.k) {
-        const PMat<T>& A = gk < k1 ? d.A : d.A2;
-        const int kk2 = gk < k1 ? gk : gk - k1;
-        const int64_t off = d.transA == 0 ? (int64_t)gm * A.ld + kk2 : (int64_t)kk2 * A.ld + gm;
-        vr = A.re[off];
-        vi = A.re[off + A.plane];
+        const bool s2 = TWO && gk >= k1;   // second term of a two-term product
+        const T* a = s2 ? d.A2.re : d.A.re;
+        const int64_t apl = s2 ? d.A2.plane : d.A.plane, ald = s2 ? d.A2.ld : d.A.ld;
+        const int kk2 = s2 ? gk - k1 : gk;
+        const int64_t off = d.transA == 0 ? (int64_t)gm * ald + kk2 : (int64_t)kk2 * ald + gm;
+        vr = a[off];
+        vi = a[off + apl];
       }
       ra[0][e] = vr;
       ra[1][e] = vi;
@@ -77,11 +79,13 @@ __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict
       const int nn = n0 + b_nn + b_dn * e, gk = k0 + b_kk + b_dk * e;
       T vr = T(0), vi = T(0);
       if (nn < d.n && gk < d.k) {
-        const PMat<T>& B = gk < k1 ? d.B : d.B2;
-        const int kk2 = gk < k1 ? gk : gk - k1;
-        const int64_t off = d.transB == 0 ? (int64_t)kk2 * B.ld + nn : (int64_t)nn * B.ld + kk2;
-        vr = B.re[off];
-        vi = B.re[off + B.plane];
+        const bool s2 = TWO && gk >= k1;
+        const T* b = s2 ? d.B2.re : d.B.re;
+        const int64_t bpl = s2 ? d.B2.plane : d.B.plane, bld = s2 ? d.B2.ld : d.B.ld;
+        const int kk2 = s2 ? gk - k1 : gk;
+        const int64_t off = d.transB == 0 ? (int64_t)kk2 * bld + nn : (int64_t)nn * bld + kk2;
+        vr = b[off];
+        vi = b[off + bpl];
       }
       rb[0][e] = vr;
       rb[1][e] = vi;
@@ -168,14 +172,14 @@ __global__ void __launch_bounds__(128) k_gemm_nrhs(const GemmDesc<T>* __restrict
   }
 }
 
-template <typename T, int NB>
+template <typename T, int NB, bool TWO>
 void launch_nb(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, int ksplit, cudaStream_t st) {
   const size_t red = (size_t)(NR_WARPS + 1) * 2 * NB * NR_BM * sizeof(T);
   const size_t smem = sizeof(NrSmem<T, NB>) > red ? sizeof(NrSmem<T, NB>) : red;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gemm_nrhs<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_gemm_nrhs<T, NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+    cudaFuncSetAttribute(k_gemm_nrhs<T, NB, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_gemm_nrhs<T, NB, TWO>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -190,7 +194,13 @@ void launch_nb(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, i
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = ksplit > 1 ? 1 : 0;
-  cudaLaunchKernelEx(&cfg, k_gemm_nrhs<T, NB>, d_desc, d_tiles);
+  cudaLaunchKernelEx(&cfg, k_gemm_nrhs<T, NB, TWO>, d_desc, d_tiles);
+}
+
+template <typename T, int NB>
+void launch_nb2(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, int ksplit, bool two, cudaStream_t st) {
+  if (two) launch_nb<T, NB, true>(d_desc, d_tiles, ntiles, ksplit, st);
+  else launch_nb<T, NB, false>(d_desc, d_tiles, ntiles, ksplit, st);
 }
 
 }  // namespace
@@ -211,16 +221,16 @@ int gemm_nrhs_split(int ntiles, int max_k) {
 
 template <typename T>
 void launch_gemm_nrhs(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, int nb, int ksplit,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool two) {
   if (ntiles <= 0) return;
   if (ksplit < 1) ksplit = 1;
   count_launches(1);
-  if (nb <= 16) launch_nb<T, 16>(d_desc, d_tiles, ntiles, ksplit, st);
-  else if (nb <= 32 || sizeof(T) != 4) launch_nb<T, 32>(d_desc, d_tiles, ntiles, ksplit, st);
-  else launch_nb<T, (sizeof(T) == 4 ? 64 : 32)>(d_desc, d_tiles, ntiles, ksplit, st);
+  if (nb <= 16) launch_nb2<T, 16>(d_desc, d_tiles, ntiles, ksplit, two, st);
+  else if (nb <= 32 || sizeof(T) != 4) launch_nb2<T, 32>(d_desc, d_tiles, ntiles, ksplit, two, st);
+  else launch_nb2<T, (sizeof(T) == 4 ? 64 : 32)>(d_desc, d_tiles, ntiles, ksplit, two, st);
 }
 
-template void launch_gemm_nrhs<float>(const GemmDesc<float>*, const GemmTile*, int, int, int, cudaStream_t);
-template void launch_gemm_nrhs<double>(const GemmDesc<double>*, const GemmTile*, int, int, int, cudaStream_t);
+template void launch_gemm_nrhs<float>(const GemmDesc<float>*, const GemmTile*, int, int, int, cudaStream_t, bool);
+template void launch_gemm_nrhs<double>(const GemmDesc<double>*, const GemmTile*, int, int, int, cudaStream_t, bool);
 
 }  // namespace mf

@@ -22,7 +22,7 @@ constexpr int GEMM_TILE = 64;
 // the number of CTAs of a thread-block cluster that share one tile's K range (gemm_nrhs_split).
 template <typename T>
 void launch_gemm_nrhs(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, int nb, int ksplit,
-                      cudaStream_t st);
+                      cudaStream_t st, bool two_term = false);   // two_term: some descs have k1 > 0
 constexpr int GEMM_NRHS_ROWS = 32;
 // Algorithmic bytes of one product: A and B read once, C written (and read when beta != 0).
 template <typename T>
