@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) measurement")
+    ap.add_argument("--no-bfapply", action="store_true", help="skip the batched butterfly-apply measurement")
     return ap.parse_args()
 
 
@@ -278,6 +279,55 @@ def serving(g, w, torch):
             "mean_batch_rhs": float(np.mean(batches)), "max_rel_residual_checked": worst}
 
 
+def butterfly_apply(g, w, torch, peaks, nrhs=64):
+    """The batched butterfly-apply workload: 200 compressed blocks of the Helmholtz Green's function
+    between two parallel m x m point planes one spacing apart (m = rint(16 * 8^u), u ~ U(0,1),
+    seed 3; k = pi/4; ID tolerance 1e-4, leaf 64), built on the GPU and applied to 64 complex
+    Gaussian vectors per block (all blocks and levels in stage-merged launches).  Bytes =
+    stored factor entries x 8 + input and output vectors; error against the dense FP64 product
+    on three blocks of at most 48 x 48 points."""
+    import numpy as np
+    import paper_2007_00202_gb300.mf as mf
+    ms = w.butterfly_bench_sizes(200, 3)
+    S = mf.GreenSet([int(m) for m in ms], math.pi / 4, 1.0, 1e-4, leaf=64,
+                    stream=torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(8)
+    X = w.complex_gaussian(rng, S.rows, nrhs)
+    dX = torch.from_numpy(np.concatenate([X.real.ravel(), X.imag.ravel()]).astype(np.float32)).cuda()
+    dY = torch.zeros_like(dX)
+    for _ in range(3):
+        S.apply(nrhs, dX.data_ptr(), dY.data_ptr())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        S.apply(nrhs, dX.data_ptr(), dY.data_ptr())
+    e1.record()
+    torch.cuda.synchronize()
+    ms_apply = e0.elapsed_time(e1) / reps
+    Yg = dY.cpu().numpy().astype(np.float64)
+    Yg = (Yg[:S.rows * nrhs] + 1j * Yg[S.rows * nrhs:]).reshape(S.rows, nrhs)
+    P, Q = S.points()
+    offs = np.concatenate([[0], np.cumsum(ms.astype(np.int64) ** 2)])
+    err = 0.0
+    small = [int(b) for b in np.argsort(ms) if ms[b] <= 48]   # dense K of at most 2304^2 entries
+    for b in [small[0], small[len(small) // 2], small[-1]]:
+        a, e = int(offs[b]), int(offs[b + 1])
+        K = w.green_entries(P[a:e], Q[a:e], math.pi / 4, np.arange(e - a), np.arange(e - a))
+        ref = K @ X[a:e]
+        err = max(err, float(np.linalg.norm(Yg[a:e] - ref) / np.linalg.norm(ref)))
+    alg_bytes = 8.0 * S.storage + 2.0 * 8.0 * S.rows * nrhs
+    flops = 8.0 * S.storage * nrhs
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    gbs = alg_bytes / (ms_apply / 1e3) / 1e9
+    return {"workload": f"200 Green's-function blocks (m = rint(16*8^u), seed 3), tol 1e-4, {nrhs} vectors each",
+            "rows": S.rows, "stored_entries": S.storage, "max_rank": S.max_rank, "build_s": S.build_seconds,
+            "apply_ms": ms_apply, "alg_gbs": gbs, "hbm_frac": gbs / hbm,
+            "tflops": flops / (ms_apply / 1e3) / 1e12, "alu_frac": flops / (ms_apply / 1e3) / 1e12 / FP32_ALU_TFLOPS,
+            "max_rel_err_vs_dense_fp64": err}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -456,6 +506,8 @@ def main():
         del hb
     if rank == 0 and not args.no_serving:
         line["serving"] = serving(g, w, torch)
+    if rank == 0 and not args.no_bfapply:
+        line["butterfly_apply"] = butterfly_apply(g, w, torch, measured_peaks())
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -295,7 +295,10 @@ int mf_green_points(const mf_bfset* s, double* P, double* Q);
 /*
  * y_b = H_b x_b for every block (the butterfly apply of Sec. 3.1, level by level).
  * x, y: device, planar complex64 rows x nrhs row-major (real plane, then the
- * imaginary plane at offset rows * nrhs).  Waits for the set's stream.
+ * imaginary plane at offset rows * nrhs).  Waits for the set's stream.  The launch
+ * sequence for one (nrhs, x, y) runs eagerly on its first call, is captured into a
+ * CUDA graph on the second and replayed by later calls (x and y must stay allocated
+ * while the set uses them).
  */
 int mf_green_apply(mf_bfset* s, int32_t nrhs, const float* x, float* y);
 void mf_green_destroy(mf_bfset* s);

@@ -381,8 +381,10 @@ int mf_factor(mf_handle* h, double tol) {
         if (f.compressed) { any_comp = true; comp_n += (size_t)(f.s() + f.u()); }
       // arenas for the compressed fronts, sized from their dimensions (generous: 280 GB devices)
       size_t el = h->opt.precision == MF_PREC_C128 ? 16 : 8;
+      // without a rank cap the sketch widths may double several times: give the work arena room
+      const size_t per = h->opt.max_rank > 0 ? 10000 : 40000;
       eo.persist_bytes = any_comp ? std::max<size_t>(size_t(8) << 30, comp_n * 20000 * el) : 0;
-      eo.scratch_bytes = any_comp ? std::max<size_t>(size_t(4) << 30, comp_n * 10000 * el) : 0;
+      eo.scratch_bytes = any_comp ? std::max<size_t>(size_t(4) << 30, comp_n * per * el) : 0;
       h->eng = h->opt.precision == MF_PREC_C128 ? mf::make_engine_c128(h->an, h->A, h->stream, eo)
                                                : mf::make_engine_c64(h->an, h->A, h->stream, eo);
       h->eng->set_profiling(h->profile);

@@ -86,8 +86,35 @@ void cluster2d(const std::vector<std::array<int64_t, 2>>& pts, int64_t leaf, std
 }  // namespace
 }  // namespace mf
 
+// The apply for one (nrhs, x, y): eager on its first call (sizing the job tables), captured into a
+// CUDA graph on a private stream on the second, replayed afterwards (state 3: eager only).
+struct GreenPlan {
+  int32_t nrhs = 0;
+  const float* x = nullptr;
+  float* y = nullptr;
+  int state = 0;
+  size_t blob = 0, mark = 0;
+  char* hblob = nullptr;
+  mf::DevMem dblob;
+  cudaGraphExec_t exec = nullptr;
+  int glaunch = 0;
+  ~GreenPlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (hblob) cudaFreeHost(hblob);
+  }
+};
+
 struct mf_bfset {
+  ~mf_bfset() {
+    plans.clear();
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+    if (gs) cudaStreamDestroy(gs);
+  }
   cudaStream_t st = nullptr;
+  cudaStream_t gs = nullptr;          // stream of the apply graphs (forked from and joined to st)
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<std::unique_ptr<GreenPlan>> plans;
   std::unique_ptr<mf::BFContext<float>> cx;
   std::vector<std::unique_ptr<mf::DHODBF<float>>> H;
   std::vector<int64_t> off;
@@ -226,47 +253,114 @@ int mf_green_apply(mf_bfset* s, int32_t nrhs, const float* x, float* y) {
   if (!s || nrhs <= 0 || !x || !y) return MF_ERR_ARG;
   try {
     auto& cx = *s->cx;
-    const size_t mk = cx.scratch.mark();
-    Blk<float> X, Y;
-    X.p = const_cast<float*>(x); X.rows = (int)s->rows; X.cols = nrhs; X.ld = nrhs; X.plane = s->rows * nrhs;
-    Y = X;
-    Y.p = y;
     // leaves of every block in one launch, then each HOD-BF level of every block in one stage-merged apply
-    std::vector<mf::GemmDesc<float>> g;
-    int maxLH = 0;
-    for (size_t b = 0; b < s->H.size(); ++b) {
-      const auto& H = *s->H[b];
-      maxLH = std::max(maxLH, H.LH);
-      for (size_t q = 0; q < H.D.size(); ++q) {
-        const mf::Range r = H.tree[H.LH][q];
-        const int nr = (int)(r.b - r.a);
-        mf::GemmDesc<float> d;
-        d.m = nr; d.n = nrhs; d.k = nr; d.transA = 0; d.transB = 0; d.alpha = 1.f; d.beta = 0.f;
-        d.A = H.D[q].pm();
-        d.B = X.sub((int)(s->off[b] + r.a), 0, nr, nrhs).pm();
-        d.C = Y.sub((int)(s->off[b] + r.a), 0, nr, nrhs).pm();
-        g.push_back(d);
-      }
-    }
-    cx.gemm(g);
-    for (int l = 1; l <= maxLH; ++l) {
-      std::vector<const mf::DBF<float>*> bfs;
-      std::vector<Blk<float>> xs, ys;
+    auto body = [&]() {
+      const size_t mk = cx.scratch.mark();
+      Blk<float> X, Y;
+      X.p = const_cast<float*>(x); X.rows = (int)s->rows; X.cols = nrhs; X.ld = nrhs; X.plane = s->rows * nrhs;
+      Y = X;
+      Y.p = y;
+      std::vector<mf::GemmDesc<float>> g;
+      int maxLH = 0;
       for (size_t b = 0; b < s->H.size(); ++b) {
         const auto& H = *s->H[b];
-        if (l > H.LH) continue;
-        for (int i = 0; i < (1 << l); ++i) {
-          const mf::Range rr = H.tree[l][i], cr = H.tree[l][i ^ 1];
-          bfs.push_back(H.off[l][i].get());
-          xs.push_back(X.sub((int)(s->off[b] + cr.a), 0, (int)(cr.b - cr.a), nrhs));
-          ys.push_back(Y.sub((int)(s->off[b] + rr.a), 0, (int)(rr.b - rr.a), nrhs));
+        maxLH = std::max(maxLH, H.LH);
+        for (size_t q = 0; q < H.D.size(); ++q) {
+          const mf::Range r = H.tree[H.LH][q];
+          const int nr = (int)(r.b - r.a);
+          mf::GemmDesc<float> d;
+          d.m = nr; d.n = nrhs; d.k = nr; d.transA = 0; d.transB = 0; d.alpha = 1.f; d.beta = 0.f;
+          d.A = H.D[q].pm();
+          d.B = X.sub((int)(s->off[b] + r.a), 0, nr, nrhs).pm();
+          d.C = Y.sub((int)(s->off[b] + r.a), 0, nr, nrhs).pm();
+          g.push_back(d);
         }
       }
-      cx.apply(bfs, xs, ys, false, true);
+      cx.gemm(g);
+      for (int l = 1; l <= maxLH; ++l) {
+        std::vector<const mf::DBF<float>*> bfs;
+        std::vector<Blk<float>> xs, ys;
+        for (size_t b = 0; b < s->H.size(); ++b) {
+          const auto& H = *s->H[b];
+          if (l > H.LH) continue;
+          for (int i = 0; i < (1 << l); ++i) {
+            const mf::Range rr = H.tree[l][i], cr = H.tree[l][i ^ 1];
+            bfs.push_back(H.off[l][i].get());
+            xs.push_back(X.sub((int)(s->off[b] + cr.a), 0, (int)(cr.b - cr.a), nrhs));
+            ys.push_back(Y.sub((int)(s->off[b] + rr.a), 0, (int)(rr.b - rr.a), nrhs));
+          }
+        }
+        cx.apply(bfs, xs, ys, false, true);
+      }
+      cx.scratch.release(mk);   // stream order makes later reuse of the scratch safe
+    };
+    GreenPlan* pl = nullptr;
+    for (auto& p : s->plans)
+      if (p->nrhs == nrhs && p->x == x && p->y == y) pl = p.get();
+    if (!pl) {
+      s->plans.push_back(std::make_unique<GreenPlan>());
+      pl = s->plans.back().get();
+      pl->nrhs = nrhs;
+      pl->x = x;
+      pl->y = y;
+    }
+    if (pl->state == 2 && cx.scratch.mark() != pl->mark) pl->state = 3;   // scratch moved under the graph
+    if (pl->state == 0 || pl->state == 3) {
+      if (pl->state == 0) cx.count_begin();
+      body();
+      if (pl->state == 0) {
+        pl->blob = cx.count_end();
+        pl->state = 1;
+      }
+    } else {
+      if (pl->state == 1) {   // capture on the private stream
+        if (!s->gs) {
+          MF_CUDA(cudaStreamCreateWithFlags(&s->gs, cudaStreamNonBlocking));
+          for (auto& e : s->ev) MF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        const size_t cap = pl->blob + 4096;
+        MF_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&pl->hblob), cap, cudaHostAllocDefault));
+        pl->dblob.alloc(cap);
+        cx.flush();
+        pl->mark = cx.scratch.mark();
+        cx.st = s->gs;
+        cx.capture_begin(pl->hblob, pl->dblob.as<char>(), cap);
+        cudaGraph_t gr = nullptr;
+        const int64_t c0 = mf::launch_count();
+        bool ok = cudaStreamBeginCapture(s->gs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          try {
+            body();
+          } catch (...) {
+            ok = false;
+          }
+          if (cudaStreamEndCapture(s->gs, &gr) != cudaSuccess || !gr) ok = false;
+        }
+        pl->glaunch = (int)(mf::launch_count() - c0);
+        mf::count_launches(-pl->glaunch);   // captured, not run
+        cx.st = s->st;
+        cx.scratch.release(pl->mark);
+        if (!cx.capture_end()) ok = false;
+        if (ok && cudaGraphInstantiate(&pl->exec, gr, 0) != cudaSuccess) {
+          pl->exec = nullptr;
+          ok = false;
+        }
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        pl->state = ok ? 2 : 3;
+        if (!ok) body();
+      }
+      if (pl->state == 2) {
+        MF_CUDA(cudaEventRecord(s->ev[0], s->st));
+        MF_CUDA(cudaStreamWaitEvent(s->gs, s->ev[0], 0));
+        MF_CUDA(cudaGraphLaunch(pl->exec, s->gs));
+        mf::count_launches(pl->glaunch);
+        MF_CUDA(cudaEventRecord(s->ev[1], s->gs));
+        MF_CUDA(cudaStreamWaitEvent(s->st, s->ev[1], 0));
+      }
     }
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaStreamSynchronize(s->st));
-    cx.scratch.release(mk);
   } catch (const std::exception&) {
     return MF_ERR_CUDA;
   }

@@ -41,6 +41,12 @@ def test_green_hodbf_apply_matches_dense(tk, tol):
     dY = torch.zeros_like(dX)
     S.apply(nrhs, dX.data_ptr(), dY.data_ptr())
     torch.cuda.synchronize()
+    Y1 = dY.cpu().numpy()
+    for _ in range(3):                       # captured on the second call, replayed on the third and fourth
+        dY.zero_()
+        S.apply(nrhs, dX.data_ptr(), dY.data_ptr())
+    torch.cuda.synchronize()
+    assert np.array_equal(dY.cpu().numpy(), Y1)
     Yg = dY.cpu().numpy().astype(np.float64)
     Yg = (Yg[:S.rows * nrhs] + 1j * Yg[S.rows * nrhs:]).reshape(S.rows, nrhs)
     off = 0

@@ -109,3 +109,32 @@ def test_profile_counters(g):
     for xx in (x, x2):
         assert np.max(np.linalg.norm(A @ xx - b, axis=0) / np.linalg.norm(b, axis=0)) <= 1e-8
     assert h.mf_profile_read(g.MF_PROF_NARROW_GEMM)["launches"] == 0
+
+
+def test_full_size_64cube_helmholtz_to_1e8(g):
+    # the bench configuration at full size (64^3, complex64 HOD-BF tol 1e-4, rank <= 64, separators
+    # >= 1024, 16 Gaussian RHS seed 7): the true FP64 residual reaches 1e-8 on every column
+    p = w.helmholtz7(64, 10)
+    b = w.rhs_gaussian(p, 16, 7)
+    h = g.analyze_problem(p, nmin_sep=1024, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES)
+    h.mf_factor(1e-4)
+    st = h.mf_stats()
+    assert st["ncompressed"] == 5 and st["max_rank"] <= 64
+    x, info = h.mf_solve(b)
+    A = p.to_scipy()
+    res = np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)
+    assert info.converged == 1 and res.max() <= 1e-8
+
+
+def test_full_size_yee48_maxwell_to_1e8(g):
+    # the Maxwell configuration at full size: Yee curl-curl on 48^3 cells (PEC), complex64 HOD-BF at
+    # tol 1e-4 on separators >= 1024, 32 edge dipoles (seed 11), GMRES to 1e-8
+    p = w.yee_maxwell(48, 10)
+    b = w.rhs_dipoles(p, 32, 11)
+    h = g.analyze_problem(p, nmin_sep=1024, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES)
+    h.mf_factor(1e-4)
+    assert h.mf_stats()["ncompressed"] >= 1
+    x, info = h.mf_solve(b)
+    A = p.to_scipy()
+    res = np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)
+    assert info.converged == 1 and res.max() <= 1e-8
