@@ -29,7 +29,7 @@ template <typename T>
 inline double gemm_bytes(const GemmDesc<T>& d) {
   return 2.0 * sizeof(T) * ((double)d.m * d.k + (double)d.k * d.n + (double)d.m * d.n * (d.beta != T(0) ? 2 : 1));
 }
-int gemm_nrhs_width(int max_n, size_t elem);   // 16, 32, 64 (complex64 only); 0 when max_n > 128
+int gemm_nrhs_width(int max_n, size_t elem);   // 16 or 32 (column tile); 0 when max_n > 128
 int gemm_nrhs_split(int ntiles, int max_k);
 
 // tcgen05 (kind::tf32) planar complex GEMM, "NT" form only (transA = 0, transB = 1),
