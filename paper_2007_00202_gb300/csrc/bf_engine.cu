@@ -341,7 +341,7 @@ void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
   const GemmDesc<T>* dd = static_cast<const GemmDesc<T>*>(upload(D.data(), D.size() * sizeof(GemmDesc<T>)));
   const GemmTile* dt = stage(tl.data(), tl.size());
   if (nb) {
-    auto go = [&] { launch_gemm_nrhs<T>(dd, dt, (int)tl.size(), nb, gemm_nrhs_split((int)tl.size(), maxk), st, two); };
+    auto go = [&] { launch_gemm_nrhs<T>(dd, dt, (int)tl.size(), nb, gemm_nrhs_split((int)tl.size(), maxk), maxk, st, two); };
     if (prof && prof->on) {
       double fl = 0, by = 0;
       for (auto& d : D) {

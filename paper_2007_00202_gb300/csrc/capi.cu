@@ -560,7 +560,7 @@ int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const flo
     DevMem dd, dt;
     mf::upload(dd, std::vector<mf::GemmDesc<float>>{d}, st);
     mf::upload(dt, tl, st);
-    mf::launch_gemm_nrhs<float>(dd.as<mf::GemmDesc<float>>(), dt.as<mf::GemmTile>(), (int)tl.size(), nb, ks, st);
+    mf::launch_gemm_nrhs<float>(dd.as<mf::GemmDesc<float>>(), dt.as<mf::GemmTile>(), (int)tl.size(), nb, ks, k, st);
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaStreamSynchronize(st));
     return MF_OK;

@@ -749,10 +749,10 @@ class DenseEngine : public EngineBase {
         for (auto& x : b) maxk = std::max(maxk, (int)x.k);
         const int ks = gemm_nrhs_split(g.nt, maxk);
         const double fl = ref_flops(D, g), by = ref_bytes(D, g);
-        sp->ops.push_back([this, spp, g, nb, ks, fl, by](cudaStream_t st) {
+        sp->ops.push_back([this, spp, g, nb, ks, maxk, fl, by](cudaStream_t st) {
           prof[0].time(st, fl, by, [&] {
             launch_gemm_nrhs<T>(spp->descs.template as<GemmDesc<T>>() + g.d0,
-                                spp->tiles.template as<GemmTile>() + g.t0, g.nt, nb, ks, st);
+                                spp->tiles.template as<GemmTile>() + g.t0, g.nt, nb, ks, maxk, st);
           });
         });
         sp->nlaunch++;

@@ -19,9 +19,11 @@ constexpr int GEMM_TILE = 64;
 
 // Narrow planar complex GEMM (n <= 128) over a tile list of tiles {desc, tm, tn} of 32 rows
 // and nb columns: nb = gemm_nrhs_width(max n) (a desc has ceil(n / nb) column tiles), ksplit
-// the number of CTAs of a thread-block cluster that share one tile's K range (gemm_nrhs_split).
+// the number of CTAs of a thread-block cluster that share one tile's K range (gemm_nrhs_split),
+// max_k the largest k of the descs (sizes the pipeline's shared memory; a smaller value only
+// shortens the pipeline).
 template <typename T>
-void launch_gemm_nrhs(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, int nb, int ksplit,
+void launch_gemm_nrhs(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, int nb, int ksplit, int max_k,
                       cudaStream_t st, bool two_term = false);   // two_term: some descs have k1 > 0
 constexpr int GEMM_NRHS_ROWS = 32;
 // Algorithmic bytes of one product: A and B read once, C written (and read when beta != 0).
