@@ -2,6 +2,8 @@
 // index sets, ranks and skeletons are host data; every product, ID, gather
 // and solve is a batched device launch on the context's stream.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <chrono>
 #include <climits>
 #include <cstring>
@@ -455,6 +457,14 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
     which.push_back(q);
   }
   MF_CUDA(cudaMemsetAsync(drk, 0, nj * 4, st));
+  // MF_TRACE=2: one line per call with the three kernels' job counts, largest shapes and GPU time
+  static const bool id_trace = getenv("MF_TRACE") && getenv("MF_TRACE")[0] == '2';
+  cudaEvent_t ie0 = nullptr, ie1 = nullptr;
+  if (id_trace && cap_mode != 2) {
+    MF_CUDA(cudaEventCreate(&ie0));
+    MF_CUDA(cudaEventCreate(&ie1));
+    MF_CUDA(cudaEventRecord(ie0, st));
+  }
   // small matrices with their rows in registers, matrices whose QR work fits in shared memory,
   // then the others (work in global memory)
   if (!rjobs.empty()) {
@@ -477,9 +487,18 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
     n_id += (int64_t)jobs.size();
   }
   std::vector<int32_t> hr(nj), hs(sktot);
+  if (ie0) MF_CUDA(cudaEventRecord(ie1, st));
   MF_CUDA(cudaMemcpyAsync(hr.data(), drk, nj * 4, cudaMemcpyDeviceToHost, st));
   MF_CUDA(cudaMemcpyAsync(hs.data(), dsk, sktot * 4, cudaMemcpyDeviceToHost, st));
   sync();
+  if (ie0) {
+    float ms = 0;
+    MF_CUDA(cudaEventElapsedTime(&ms, ie0, ie1));
+    fprintf(stderr, "[id] reg %zu (%dx%d) smem %zu (%dx%d) global %zu (%dx%d) max_rank %d  %.3f ms\n", rjobs.size(),
+            rmax_m, rmax_n, sjobs.size(), smax_m, smax_n, jobs.size(), max_m, max_n, max_rank, ms);
+    cudaEventDestroy(ie0);
+    cudaEventDestroy(ie1);
+  }
   for (size_t q = 0; q < nj; ++q) {
     int r = hr[q];
     Us[q].cols = r;

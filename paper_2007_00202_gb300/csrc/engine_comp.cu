@@ -1,9 +1,11 @@
 // Compressed fronts (Alg. 5) on the GPU; see engine_comp.h.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <numeric>
+#include <thread>
 
 #include "engine_comp.h"
 
@@ -27,6 +29,81 @@ void CompressedPart<T>::ensure_second() {
   cx2->prof = cx.prof;
 }
 
+namespace {
+
+// position of a global index in front f: I^s -> [0, s), I^u -> s + index, else -1
+int32_t front_position(const FrontInfo& f, int64_t g) {
+  if (g >= f.sep_begin && g < f.sep_end) return (int32_t)(g - f.sep_begin);
+  auto it = std::lower_bound(f.upd.begin(), f.upd.end(), g);
+  if (it == f.upd.end() || *it != g) return -1;
+  return (int32_t)(f.s() + (it - f.upd.begin()));
+}
+
+template <typename Neigh>
+void compute_neighbours(const Analysis& an, const FrontInfo& f, int knn, Neigh& out) {
+  FrontNeighbours nb;
+  front_neighbours(an, f, knn, nb);
+  const int s = (int)f.s(), u = (int)f.u();
+  auto to_local = [&](const std::vector<int64_t>& ptr, const std::vector<int64_t>& idx, int rows, int base) {
+    std::vector<IdxVec> o(rows);
+    for (int r = 0; r < rows; ++r)
+      for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) {
+        int32_t p = front_position(f, idx[k]);
+        if (p >= 0) o[r].push_back(p - base);
+      }
+    return o;
+  };
+  out.nn11 = to_local(nb.nn11_ptr, nb.nn11, s, 0);
+  out.nn12 = to_local(nb.nn12_ptr, nb.nn12, s, s);   // I^s row -> I^u local
+  out.nn21 = to_local(nb.nn21_ptr, nb.nn21, u, 0);   // I^u row -> I^s local
+  out.nn22 = to_local(nb.nn22_ptr, nb.nn22, u, s);
+}
+
+}  // namespace
+
+template <typename T>
+void CompressedPart<T>::prepare_neighbours(int knn) {
+  std::vector<int> fids;
+  for (const auto& f : an_.fronts)
+    if (f.compressed) fids.push_back((int)f.id);
+  std::vector<std::unique_ptr<Neigh>> res(fids.size());
+  std::atomic<size_t> next{0};
+  auto work = [&] {
+    for (size_t i; (i = next.fetch_add(1)) < fids.size();) {
+      res[i] = std::make_unique<Neigh>();
+      compute_neighbours(an_, an_.fronts[fids[i]], knn, *res[i]);
+    }
+  };
+  const size_t nt = std::min<size_t>(fids.size(), std::max(1u, std::min(8u, std::thread::hardware_concurrency())));
+  std::vector<std::thread> th;
+  for (size_t t = 1; t < nt; ++t) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  std::lock_guard<std::mutex> lk(neigh_mu_);
+  neigh_.clear();
+  for (size_t i = 0; i < fids.size(); ++i) neigh_[fids[i]] = std::move(res[i]);
+  neigh_knn_ = knn;
+}
+
+template <typename T>
+const typename CompressedPart<T>::Neigh& CompressedPart<T>::neighbours(int fid, int knn) {
+  {
+    std::lock_guard<std::mutex> lk(neigh_mu_);
+    if (neigh_knn_ != knn) {
+      neigh_.clear();
+      neigh_knn_ = knn;
+    }
+    auto it = neigh_.find(fid);
+    if (it != neigh_.end()) return *it->second;
+  }
+  auto n = std::make_unique<Neigh>();
+  compute_neighbours(an_, an_.fronts[fid], knn, *n);
+  std::lock_guard<std::mutex> lk(neigh_mu_);
+  auto& slot = neigh_[fid];
+  if (!slot) slot = std::move(n);
+  return *slot;
+}
+
 template <typename T>
 void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr, const BFParams& P, uint64_t seed,
                                      int w) {
@@ -42,12 +119,7 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
   cf.u = u;
   cf.sep_begin = f.sep_begin;
   // position of each global index in this front: I^s -> [0, s), I^u -> s + index
-  auto front_pos = [&](int64_t g) -> int32_t {
-    if (g >= f.sep_begin && g < f.sep_end) return (int32_t)(g - f.sep_begin);
-    auto it = std::lower_bound(f.upd.begin(), f.upd.end(), g);
-    if (it == f.upd.end() || *it != g) return -1;
-    return (int32_t)(s + (it - f.upd.begin()));
-  };
+  auto front_pos = [&](int64_t g) -> int32_t { return front_position(f, g); };
   // children: inverse relative maps (front position -> child position, -1 if absent)
   struct Kid {
     int id;
@@ -145,22 +217,12 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
       }
     };
   };
-  // neighbour lists in front positions
-  FrontNeighbours nb;
-  front_neighbours(an_, f, P.knn, nb);
-  auto to_local = [&](const std::vector<int64_t>& ptr, const std::vector<int64_t>& idx, int rows, int base) {
-    std::vector<IdxVec> out(rows);
-    for (int r = 0; r < rows; ++r)
-      for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) {
-        int32_t p = front_pos(idx[k]);
-        if (p >= 0) out[r].push_back(p - base);
-      }
-    return out;
-  };
-  std::vector<IdxVec> nn11 = to_local(nb.nn11_ptr, nb.nn11, s, 0);
-  std::vector<IdxVec> nn12 = to_local(nb.nn12_ptr, nb.nn12, s, s);   // I^s row -> I^u local
-  std::vector<IdxVec> nn21 = to_local(nb.nn21_ptr, nb.nn21, u, 0);   // I^u row -> I^s local
-  std::vector<IdxVec> nn22 = to_local(nb.nn22_ptr, nb.nn22, u, s);
+  // neighbour lists in front positions (symbolic: computed once per analysis)
+  const Neigh& ng = neighbours(fid, P.knn);
+  const std::vector<IdxVec>& nn11 = ng.nn11;
+  const std::vector<IdxVec>& nn12 = ng.nn12;
+  const std::vector<IdxVec>& nn21 = ng.nn21;
+  const std::vector<IdxVec>& nn22 = ng.nn22;
   Tree th = f.th_tree, t22 = f.f22_tree;
   // optional phase trace (MF_TRACE=1): wall time and kernel launches per phase on stderr
   const bool trace = getenv("MF_TRACE") && getenv("MF_TRACE")[0] == '1';

@@ -59,6 +59,17 @@ class CompressedPart {
   void forward(const std::vector<int>& fids, Blk<T>& X);
   void backward(const std::vector<int>& fids, Blk<T>& X);
 
+  // Neighbour lists of a compressed front in front positions (the proxy candidates of Sec. 5.2):
+  // nn11 (I^s -> I^s), nn12 (I^s -> I^u, local), nn21 (I^u -> I^s), nn22 (I^u -> I^u, local).
+  // They depend on the graph and the trees only, so they are computed once per analysis.
+  struct Neigh {
+    std::vector<IdxVec> nn11, nn12, nn21, nn22;
+  };
+  // computes the lists of every compressed front (several host threads); factor_front computes a
+  // missing entry itself
+  void prepare_neighbours(int knn);
+  const Neigh& neighbours(int fid, int knn);
+
   const Analysis& an_;
   const DeviceMatrix& A_;
   cudaStream_t st_;
@@ -68,6 +79,9 @@ class CompressedPart {
   size_t persist_bytes_, scratch_bytes_;
   std::mutex fronts_mu_;   // guards fronts while two contexts build fronts of one level
   std::map<int, std::unique_ptr<CompFront<T>>> fronts;
+  std::mutex neigh_mu_;
+  std::map<int, std::unique_ptr<Neigh>> neigh_;   // per front, for neigh_knn_
+  int neigh_knn_ = -1;
 };
 
 }  // namespace mf

@@ -507,6 +507,7 @@ class DenseEngine : public EngineBase {
     }
     if (any_comp) {
       comp_ = std::make_unique<CompressedPart<T>>(an_, A_, st_, eo_.persist_bytes, eo_.scratch_bytes);
+      comp_->prepare_neighbours(eo_.knn);   // symbolic proxy candidates, part of the analysis
       comp_->cx.prof = &prof[0];
       MF_CUDA(cudaEventCreateWithFlags(&lev_ev_[0], cudaEventDisableTiming));
     }
