@@ -19,6 +19,13 @@ __global__ void __launch_bounds__(NT) k_row_id(const IdJob<T>* jobs, T tol, int3
   row_id_body<T>(jobs[blockIdx.x], tol, max_rank, work_in_smem != 0);
 }
 
+// the large matrices (QR work in global memory): a cluster of kIdCluster CTAs per matrix
+constexpr int kIdCluster = 8;
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) k_row_id_cluster(const IdJob<T>* jobs, T tol, int32_t max_rank) {
+  row_id_body_cluster<T, kIdCluster>(jobs[blockIdx.x / kIdCluster], tol, max_rank);
+}
+
 template <typename T, int RC>
 __global__ void __launch_bounds__(1024, 1) k_row_id_reg(const IdJob<T>* jobs, T tol, int32_t max_rank) {
   row_id_body_reg<T, RC>(jobs[blockIdx.x], tol, max_rank);
@@ -51,13 +58,35 @@ int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_row_id<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
-    cudaFuncSetAttribute(k_row_id<T, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
     attr = true;
   }
   count_launches(1);
-  // matrices in global memory are the large ones (few per launch): a 1024-thread CTA each
-  if (work_in_smem) k_row_id<T, 256><<<njobs, 256, sm, st>>>(d_jobs, tol, max_rank, 1);
-  else k_row_id<T, 1024><<<njobs, 1024, sm, st>>>(d_jobs, tol, max_rank, 0);
+  if (work_in_smem) {
+    k_row_id<T, 256><<<njobs, 256, sm, st>>>(d_jobs, tol, max_rank, 1);
+    return 0;
+  }
+  // matrices in global memory are the large ones (few per launch): a cluster of kIdCluster
+  // 1024-thread CTAs each, every CTA updating its share of the rows
+  static bool cattr = false;
+  if (!cattr) {
+    cudaFuncSetAttribute(k_row_id_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
+    cattr = true;
+  }
+  const size_t csm = row_id_cluster_smem_bytes(max_m, max_n, sizeof(T));
+  if (csm > kRowIdSmemCap) return -1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)njobs * kIdCluster, 1, 1);
+  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.dynamicSmemBytes = csm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kIdCluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_row_id_cluster<T>, d_jobs, tol, (int32_t)max_rank);
   return 0;
 }
 

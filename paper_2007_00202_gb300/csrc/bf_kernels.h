@@ -166,6 +166,11 @@ inline size_t row_id_smem_bytes(int m, int n, size_t elem, bool work_in_smem) {
   return b;
 }
 constexpr size_t kRowIdSmemCap = 200 * 1024;
+// Cluster row ID (the work matrix in global memory, shared by the CTAs of a cluster): per CTA the
+// Householder vector, the norms and the position order.
+inline size_t row_id_cluster_smem_bytes(int m, int n, size_t elem) {
+  return elem * (2 * (size_t)n + m) + 2 * sizeof(int) * (size_t)m;
+}
 // Register-resident row ID for m <= 128 and n <= 128 (1024 threads, rows in registers): its
 // dynamic shared memory (pivot row, the rows' first min(m, n) columns, the pivots).
 inline size_t row_id_reg_smem_bytes(int m, int n, size_t elem) {

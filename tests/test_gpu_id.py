@@ -56,9 +56,12 @@ def run_gpu_id(torch, mats, tol, max_rank=0, fn=None):
     return res
 
 
+# shapes cover the three kernels: rows in registers (m, n <= 128), QR work in shared memory, and
+# the thread-block-cluster kernel for work in global memory (incl. fewer rows than cluster CTAs)
 @pytest.mark.parametrize("m,n,kind,tol", [(64, 640, "lowrank", 1e-5), (40, 300, "decay", 1e-3),
                                           (128, 1000, "decay", 1e-4), (7, 5, "decay", 1e-2),
-                                          (128, 72, "decay", 1e-4)])
+                                          (128, 72, "decay", 1e-4), (256, 1024, "decay", 1e-4),
+                                          (200, 333, "lowrank", 1e-5), (5, 6000, "lowrank", 1e-5)])
 def test_row_id_matches_oracle(tk, m, n, kind, tol):
     rng = np.random.default_rng(m * n)
     mats = _mats(rng, 12, m, n, kind)

@@ -65,6 +65,20 @@ def test_noalloc_row_id_matches_allocating_call_twice_in_a_row(tk):
             assert err <= 1e-3
 
 
+def test_cluster_row_id_equals_the_single_cta_body(tk):
+    # large blocks: the allocating call runs one thread-block cluster per matrix, the
+    # allocation-free one a single CTA with the same per-row arithmetic; skeletons agree exactly
+    import paper_2007_00202_gb300.mf as mf
+    rng = np.random.default_rng(77)
+    for m, n in ((256, 1024), (13, 4000)):
+        mats = _batch(rng, 3, m, n)
+        ref = _run(tk, mf.mf_row_id_c64, mats, 1e-4, max_rank=64)
+        got = _run(tk, mf.mf_row_id_c64_noalloc, mats, 1e-4, max_rank=64)
+        for (Ur, skr), (Ug, skg) in zip(ref, got):
+            assert np.array_equal(skg, skr)
+            assert np.array_equal(Ug, Ur)
+
+
 def test_noalloc_rejects_batches_beyond_the_fixed_scratch(tk):
     import paper_2007_00202_gb300.mf as mf
     with pytest.raises(mf.MfError) as e:
