@@ -194,6 +194,11 @@ BFContext<T>::BFContext(cudaStream_t s, size_t pb, size_t sb) : st(s) {
 template <typename T>
 BFContext<T>::~BFContext() {
   if (ring) cudaFreeHost(ring);
+  for (int i = 0; i < 2; ++i) {
+    if (side[i]) cudaStreamDestroy(side[i]);
+    if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+  }
+  if (ev_fork) cudaEventDestroy(ev_fork);
 }
 
 namespace {
@@ -466,26 +471,45 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
     MF_CUDA(cudaEventRecord(ie0, st));
   }
   // small matrices with their rows in registers, matrices whose QR work fits in shared memory,
-  // then the others (work in global memory)
-  if (!rjobs.empty()) {
-    const IdJob<T>* dj = stage(rjobs.data(), rjobs.size());
-    if (launch_row_id_reg<T>(dj, (int)rjobs.size(), rmax_m, rmax_n, (T)tol, max_rank, st) != 0)
+  // and the others (work in global memory, a thread-block cluster each): three independent
+  // kernels, run side by side on forked streams when more than one kind is present
+  const IdJob<T>* drj = rjobs.empty() ? nullptr : stage(rjobs.data(), rjobs.size());
+  const IdJob<T>* dsj = sjobs.empty() ? nullptr : stage(sjobs.data(), sjobs.size());
+  const IdJob<T>* dgj = jobs.empty() ? nullptr : stage(jobs.data(), jobs.size());
+  const int kinds = (drj ? 1 : 0) + (dsj ? 1 : 0) + (dgj ? 1 : 0);
+  const bool fork = kinds > 1 && cap_mode != 2;
+  if (fork) {
+    if (!ev_fork) {
+      MF_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+      for (int i = 0; i < 2; ++i) {
+        MF_CUDA(cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking));
+        MF_CUDA(cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming));
+      }
+    }
+    MF_CUDA(cudaEventRecord(ev_fork, st));
+    for (int i = 0; i < 2; ++i) MF_CUDA(cudaStreamWaitEvent(side[i], ev_fork, 0));
+  }
+  if (drj) {
+    if (launch_row_id_reg<T>(drj, (int)rjobs.size(), rmax_m, rmax_n, (T)tol, max_rank, fork ? side[0] : st) != 0)
       throw std::runtime_error("ID block too large for the register row-ID kernel");
     n_id += (int64_t)rjobs.size();
   }
-  if (!sjobs.empty()) {
-    const IdJob<T>* dj = stage(sjobs.data(), sjobs.size());
-    if (launch_row_id<T>(dj, (int)sjobs.size(), smax_m, smax_n, (T)tol, max_rank, st, true, sbytes) != 0)
-      throw std::runtime_error("ID block too large for the shared-memory row-ID kernel");
-    n_id += (int64_t)sjobs.size();
-  }
-  if (!jobs.empty()) {
-    const IdJob<T>* dj = stage(jobs.data(), jobs.size());
-    if (launch_row_id<T>(dj, (int)jobs.size(), max_m, max_n, (T)tol, max_rank, st) != 0)
+  if (dgj) {
+    if (launch_row_id<T>(dgj, (int)jobs.size(), max_m, max_n, (T)tol, max_rank, fork ? side[1] : st) != 0)
       throw std::runtime_error("ID block too large for the row-ID kernel (" + std::to_string(max_m) + " x " +
                                std::to_string(max_n) + ")");
     n_id += (int64_t)jobs.size();
   }
+  if (dsj) {
+    if (launch_row_id<T>(dsj, (int)sjobs.size(), smax_m, smax_n, (T)tol, max_rank, st, true, sbytes) != 0)
+      throw std::runtime_error("ID block too large for the shared-memory row-ID kernel");
+    n_id += (int64_t)sjobs.size();
+  }
+  if (fork)
+    for (int i = 0; i < 2; ++i) {
+      MF_CUDA(cudaEventRecord(ev_join[i], side[i]));
+      MF_CUDA(cudaStreamWaitEvent(st, ev_join[i], 0));
+    }
   std::vector<int32_t> hr(nj), hs(sktot);
   if (ie0) MF_CUDA(cudaEventRecord(ie1, st));
   MF_CUDA(cudaMemcpyAsync(hr.data(), drk, nj * 4, cudaMemcpyDeviceToHost, st));

@@ -213,6 +213,8 @@ class BFContext {
   BFContext(cudaStream_t st, size_t persist_bytes, size_t scratch_bytes);
   ~BFContext();
   cudaStream_t st;
+  cudaStream_t side[2] = {nullptr, nullptr};            // forked streams of row_ids (created on first use)
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   char* ring = nullptr;             // pinned host staging ring
   DevMem dring;                     // its device mirror (targets of upload())
   size_t ring_cap = 0, ring_off = 0, pend_begin = 0;

@@ -58,11 +58,14 @@ int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_row_id<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
+    cudaFuncSetAttribute(k_row_id<T, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
     attr = true;
   }
   count_launches(1);
   if (work_in_smem) {
-    k_row_id<T, 256><<<njobs, 256, sm, st>>>(d_jobs, tol, max_rank, 1);
+    // large shared-memory work (one or two CTAs per SM): four times the threads per matrix
+    if (sm > 64 * 1024) k_row_id<T, 1024><<<njobs, 1024, sm, st>>>(d_jobs, tol, max_rank, 1);
+    else k_row_id<T, 256><<<njobs, 256, sm, st>>>(d_jobs, tol, max_rank, 1);
     return 0;
   }
   // matrices in global memory are the large ones (few per launch): a cluster of kIdCluster
