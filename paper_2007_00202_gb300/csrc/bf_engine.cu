@@ -1623,7 +1623,7 @@ static void small_inverse(BFContext<T>& cx, const std::vector<Blk<T>>& A, std::v
   if (jobs.empty()) return;
   const bool in_smem = small_inverse_smem_bytes(mx, sizeof(double)) <= kSmallInvSmemCap;
   if (!in_smem)
-    for (auto& j : jobs) j.W = cx.scratch.template takeT<double>(4 * (size_t)j.n * j.n);
+    for (auto& j : jobs) j.W = cx.scratch.template takeT<double>(2 * (size_t)j.n * j.n);
   const InvJob<T>* d = cx.stage(jobs.data(), jobs.size());
   if (launch_small_inverse<T>(d, (int)jobs.size(), mx, in_smem, cx.status.template as<int32_t>(), cx.st) != 0)
     throw std::runtime_error("block too large for the small dense inverse (" + std::to_string(mx) + ")");

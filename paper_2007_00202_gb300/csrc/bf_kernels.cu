@@ -270,79 +270,100 @@ void launch_place(const PlaceJob<T>* d_jobs, int njobs, int64_t max_elems, cudaS
 // inverses (Alg. 4, "directly compute D_tau^-1").
 template <typename T>
 __global__ void __launch_bounds__(256) k_small_inverse(const InvJob<T>* jobs, int work_in_smem, int32_t* status) {
+  // In-place complex Gauss-Jordan with partial pivoting (largest modulus, lowest row on ties), in
+  // FP64 whatever the storage precision.  Step k: swap rows k and p, scale row k by 1 / a_kk
+  // (a_kk <- 1 / a_kk), eliminate column k from the other rows (a_ik <- -a_ik / a_kk); the row
+  // interchanges are undone at the end as column interchanges in reverse order.
   const InvJob<T> j = jobs[blockIdx.x];
-  using R = double;   // arithmetic in FP64 whatever the storage precision
+  using R = double;
   const int n = j.n;
   extern __shared__ __align__(16) unsigned char smraw[];
-  R* Ar = work_in_smem ? reinterpret_cast<R*>(smraw) : j.W;   // n x 2n augmented [A | I]
-  R* Ai = Ar + n * 2 * n;
-  __shared__ int piv;
-  const int w = 2 * n;
-  for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
-    int r = e / w, c = e % w;
-    if (c < n) {
-      Ar[e] = (R)j.A[(int64_t)r * j.lda + c];
-      Ai[e] = (R)j.A[(int64_t)r * j.lda + c + j.aplane];
-    } else {
-      Ar[e] = (c - n == r) ? R(1) : R(0);
-      Ai[e] = R(0);
-    }
+  R* colr = reinterpret_cast<R*>(smraw);   // column k before the step (re, im)
+  R* coli = colr + n;
+  R* rowr = coli + n;                      // row k after scaling (re, im)
+  R* rowi = rowr + n;
+  int* piv = reinterpret_cast<int*>(rowi + n);
+  R* Ar = work_in_smem ? reinterpret_cast<R*>(smraw + small_inverse_vec_bytes(n)) : j.W;   // n x n
+  R* Ai = Ar + (int64_t)n * n;
+  __shared__ int sp;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    Ar[e] = (R)j.A[(int64_t)r * j.lda + c];
+    Ai[e] = (R)j.A[(int64_t)r * j.lda + c + j.aplane];
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x < 32) {   // pivot: largest modulus in column k at or below the diagonal, lowest row on ties
+    if (tid < 32) {
       R best = R(-1);
       int bi = n;
-      for (int r = k + threadIdx.x; r < n; r += 32) {
-        R m2 = Ar[r * w + k] * Ar[r * w + k] + Ai[r * w + k] * Ai[r * w + k];
+      for (int r = k + tid; r < n; r += 32) {
+        const R m2 = Ar[r * n + k] * Ar[r * n + k] + Ai[r * n + k] * Ai[r * n + k];
         if (m2 > best) { best = m2; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        R ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (threadIdx.x == 0) {
-        piv = bi < n ? bi : k;
+      if (tid == 0) {
+        sp = bi < n ? bi : k;
+        piv[k] = sp;
         if (!(best > R(0)) && status) atomicExch(status, (int32_t)DEV_ZERO_PIVOT);
       }
     }
     __syncthreads();
-    const int p = piv;
+    const int p = sp;
     if (p != k)
-      for (int c = threadIdx.x; c < w; c += blockDim.x) {
-        R t = Ar[k * w + c]; Ar[k * w + c] = Ar[p * w + c]; Ar[p * w + c] = t;
-        t = Ai[k * w + c]; Ai[k * w + c] = Ai[p * w + c]; Ai[p * w + c] = t;
+      for (int c = tid; c < n; c += blockDim.x) {
+        R t = Ar[k * n + c]; Ar[k * n + c] = Ar[p * n + c]; Ar[p * n + c] = t;
+        t = Ai[k * n + c]; Ai[k * n + c] = Ai[p * n + c]; Ai[p * n + c] = t;
       }
     __syncthreads();
-    R dr = Ar[k * w + k], di = Ai[k * w + k];
+    R dr = Ar[k * n + k], di = Ai[k * n + k];
     R den = dr * dr + di * di;
     if (den == R(0)) { dr = R(1); di = R(0); den = R(1); }
-    const R ir = dr / den, ii = -di / den;
-    __syncthreads();
-    for (int c = threadIdx.x; c < w; c += blockDim.x) {
-      R a = Ar[k * w + c], b = Ai[k * w + c];
-      Ar[k * w + c] = a * ir - b * ii;
-      Ai[k * w + c] = a * ii + b * ir;
+    const R ir = dr / den, ii = -di / den;   // 1 / a_kk
+    for (int e = tid; e < n; e += blockDim.x) {
+      colr[e] = Ar[e * n + k];
+      coli[e] = Ai[e * n + k];
+      const R a = Ar[k * n + e], b = Ai[k * n + e];
+      rowr[e] = e == k ? ir : a * ir - b * ii;
+      rowi[e] = e == k ? ii : a * ii + b * ir;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
-      int r = e / w, c = e % w;
-      if (r == k || c == k) continue;
-      R fr = Ar[r * w + k], fi = Ai[r * w + k];
-      R a = Ar[k * w + c], b = Ai[k * w + c];
-      Ar[e] -= fr * a - fi * b;
-      Ai[e] -= fr * b + fi * a;
+    for (int r = ty; r < n; r += 16) {
+      const R fr = colr[r], fi = coli[r];
+      for (int c = tx; c < n; c += 16) {
+        const int e = r * n + c;
+        if (r == k) {
+          Ar[e] = rowr[c];
+          Ai[e] = rowi[c];
+        } else if (c == k) {
+          Ar[e] = -(fr * ir - fi * ii);
+          Ai[e] = -(fr * ii + fi * ir);
+        } else {
+          const R a = rowr[c], b = rowi[c];
+          Ar[e] -= fr * a - fi * b;
+          Ai[e] -= fr * b + fi * a;
+        }
+      }
     }
-    __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x)
-      if (r != k) { Ar[r * w + k] = R(0); Ai[r * w + k] = R(0); }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int r = e / n, c = e % n;
-    j.X[(int64_t)r * j.ldx + c] = (T)Ar[r * w + n + c];
-    j.X[(int64_t)r * j.ldx + c + j.xplane] = (T)Ai[r * w + n + c];
+  // undo the row interchanges: column interchanges in reverse order, each thread on its rows
+  for (int r = tid; r < n; r += blockDim.x)
+    for (int k = n - 1; k >= 0; --k) {
+      const int q = piv[k];
+      if (q == k) continue;
+      R t = Ar[r * n + k]; Ar[r * n + k] = Ar[r * n + q]; Ar[r * n + q] = t;
+      t = Ai[r * n + k]; Ai[r * n + k] = Ai[r * n + q]; Ai[r * n + q] = t;
+    }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    j.X[(int64_t)r * j.ldx + c] = (T)Ar[e];
+    j.X[(int64_t)r * j.ldx + c + j.xplane] = (T)Ai[e];
   }
 }
 
@@ -350,7 +371,8 @@ template <typename T>
 int launch_small_inverse(const InvJob<T>* d_jobs, int njobs, int max_n, bool work_in_smem, int32_t* status,
                          cudaStream_t st) {
   if (njobs <= 0) return 0;
-  const size_t smem = work_in_smem ? small_inverse_smem_bytes(max_n, sizeof(double)) : 0;
+  // the step vectors always sit in shared memory; the work matrix too when work_in_smem
+  const size_t smem = work_in_smem ? small_inverse_smem_bytes(max_n, sizeof(double)) : small_inverse_vec_bytes(max_n);
   if (smem > kSmallInvSmemCap) return -1;
   static bool attr = false;
   if (!attr) {

@@ -97,11 +97,19 @@ struct InvJob {
   int32_t n;
   T* X;
   int64_t xplane, ldx;
-  double* W;           // work of 4 n^2 doubles (augmented [A | I], real and imaginary planes) when not in shared memory
+  double* W;           // work of 2 n^2 doubles (real and imaginary planes) when not in shared memory
 };
 // Gauss-Jordan elimination with partial pivoting in FP64 (stored in T); the
 // augmented matrix sits in shared memory when the launch's largest job fits.
-inline size_t small_inverse_smem_bytes(int max_n, size_t elem) { return 4 * (size_t)max_n * max_n * elem; }
+// per-step vectors (column and row k, re / im, in FP64) and the pivots, 16-byte aligned
+__host__ __device__ inline size_t small_inverse_vec_bytes(int n) {
+  return ((4 * sizeof(double) + sizeof(int)) * (size_t)n + 15) / 16 * 16;
+}
+// dynamic shared memory of the small inverse with its n x n FP64 work in shared memory (elem:
+// the work's element size, sizeof(double))
+inline size_t small_inverse_smem_bytes(int max_n, size_t elem) {
+  return small_inverse_vec_bytes(max_n) + 2 * (size_t)max_n * max_n * elem;
+}
 constexpr size_t kSmallInvSmemCap = 200 * 1024;
 
 // Block-to-block operations on planar row-major blocks:

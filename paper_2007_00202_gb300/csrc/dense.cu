@@ -36,37 +36,53 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc<T>* __restrict__ de
   const T* Ai = d.A.re + d.A.plane;
   const T* Br = d.B.re;
   const T* Bi = d.B.re + d.B.plane;
-  for (int k0 = 0; k0 < d.k; k0 += BK) {
+  // the next k tile is read into registers while the current one is multiplied
+  T par[4], pai[4], pbr[4], pbi[4];
+  auto load = [&](int k0) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      int idx = tid + e * 256;
+      const int idx = tid + e * 256;
       int mm, kk;
       if (d.transA == 0) { mm = idx / BK; kk = idx % BK; }
       else { kk = idx / BM; mm = idx % BM; }
       int gm = m0 + mm, gk = k0 + kk;
-      T vr = T(0), vi = T(0);
+      par[e] = pai[e] = T(0);
       if (gm < d.m && gk < d.k) {
-        int64_t off = d.transA == 0 ? (int64_t)gm * d.A.ld + gk : (int64_t)gk * d.A.ld + gm;
-        vr = Ar[off];
-        vi = Ai[off];
+        const int64_t off = d.transA == 0 ? (int64_t)gm * d.A.ld + gk : (int64_t)gk * d.A.ld + gm;
+        par[e] = Ar[off];
+        pai[e] = Ai[off];
       }
-      As[0][kk][mm] = vr;
-      As[1][kk][mm] = vi;
       int nn;
       if (d.transB == 0) { kk = idx / BN; nn = idx % BN; }
       else { nn = idx / BK; kk = idx % BK; }
-      int gn = n0 + nn;
+      const int gn = n0 + nn;
       gk = k0 + kk;
-      vr = T(0); vi = T(0);
+      pbr[e] = pbi[e] = T(0);
       if (gn < d.n && gk < d.k) {
-        int64_t off = d.transB == 0 ? (int64_t)gk * d.B.ld + gn : (int64_t)gn * d.B.ld + gk;
-        vr = Br[off];
-        vi = Bi[off];
+        const int64_t off = d.transB == 0 ? (int64_t)gk * d.B.ld + gn : (int64_t)gn * d.B.ld + gk;
+        pbr[e] = Br[off];
+        pbi[e] = Bi[off];
       }
-      Bs[0][kk][nn] = vr;
-      Bs[1][kk][nn] = vi;
+    }
+  };
+  if (d.k > 0) load(0);
+  for (int k0 = 0; k0 < d.k; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = tid + e * 256;
+      int mm, kk;
+      if (d.transA == 0) { mm = idx / BK; kk = idx % BK; }
+      else { kk = idx / BM; mm = idx % BM; }
+      As[0][kk][mm] = par[e];
+      As[1][kk][mm] = pai[e];
+      int nn;
+      if (d.transB == 0) { kk = idx / BN; nn = idx % BN; }
+      else { nn = idx / BK; kk = idx % BK; }
+      Bs[0][kk][nn] = pbr[e];
+      Bs[1][kk][nn] = pbi[e];
     }
     __syncthreads();
+    if (k0 + BK < d.k) load(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       T ar[4], ai[4], br[4], bi[4];
