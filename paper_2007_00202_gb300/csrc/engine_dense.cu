@@ -62,11 +62,22 @@ class DenseEngine : public EngineBase {
     }
     static const bool serial = getenv("MF_SERIAL_FRONTS") && getenv("MF_SERIAL_FRONTS")[0] == '1';
     for (size_t lv = 0; lv < levels_.size(); ++lv) {
-      for (size_t i = lvl_begin_[lv]; i < lvl_begin_[lv + 1]; ++i) {
-        if (gemm_flops_[i] > 0) prof[1].time(st_, gemm_flops_[i], gemm_bytes_[i], [&] { fops_[i](st_); });
-        else fops_[i](st_);
-      }
       const auto& lvl = comp_levels_[lv];
+      // the dense fronts of a level with compressed fronts run on their own stream: neither
+      // depends on the other (both read only lower levels), and the compressed fronts' host-driven
+      // construction would otherwise start behind the dense fronts' LU
+      const bool side = !lvl.empty() && lvl_begin_[lv + 1] > lvl_begin_[lv] && !serial;
+      cudaStream_t dst = st_;
+      if (side) {
+        MF_CUDA(cudaEventRecord(lev_ev_[1], st_));
+        MF_CUDA(cudaStreamWaitEvent(ds_, lev_ev_[1], 0));
+        dst = ds_;
+      }
+      for (size_t i = lvl_begin_[lv]; i < lvl_begin_[lv + 1]; ++i) {
+        if (gemm_flops_[i] > 0) prof[1].time(dst, gemm_flops_[i], gemm_bytes_[i], [&] { fops_[i](dst); });
+        else fops_[i](dst);
+      }
+      if (side) MF_CUDA(cudaEventRecord(lev_ev_[2], ds_));
       if (lvl.empty()) continue;
       auto t0 = std::chrono::steady_clock::now();
       const auto& F = an_.fronts;
@@ -108,6 +119,7 @@ class DenseEngine : public EngineBase {
         if (err0) std::rethrow_exception(err0);
         if (err) std::rethrow_exception(err);
       }
+      if (side) MF_CUDA(cudaStreamWaitEvent(st_, lev_ev_[2], 0));   // the next level needs both
       for (int32_t fid : lvl) max_rank_ = std::max(max_rank_, comp_->fronts.at(fid)->max_rank);
       comp_seconds_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
@@ -226,7 +238,10 @@ class DenseEngine : public EngineBase {
   double comp_flops_ = 0, comp_seconds_ = 0;
   int max_rank_ = 0;
   cudaStream_t gs_ = nullptr;               // stream of the solve graphs (forked from and joined to st_)
-  cudaEvent_t lev_ev_[1] = {nullptr};       // the engine stream's progress before a level's compressed fronts
+  // the engine stream's progress before a level's compressed fronts [0] and dense fronts [1]; the
+  // dense fronts' completion on ds_ [2]
+  cudaEvent_t lev_ev_[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t ds_ = nullptr;               // dense fronts of the levels that also hold compressed fronts
   cudaEvent_t gev_[2] = {nullptr, nullptr};
 
  public:
@@ -234,7 +249,9 @@ class DenseEngine : public EngineBase {
     sprog_.clear();
     for (auto e : gev_)
       if (e) cudaEventDestroy(e);
-    if (lev_ev_[0]) cudaEventDestroy(lev_ev_[0]);
+    for (auto e : lev_ev_)
+      if (e) cudaEventDestroy(e);
+    if (ds_) cudaStreamDestroy(ds_);
     if (gs_) cudaStreamDestroy(gs_);
   }
 
@@ -509,7 +526,8 @@ class DenseEngine : public EngineBase {
       comp_ = std::make_unique<CompressedPart<T>>(an_, A_, st_, eo_.persist_bytes, eo_.scratch_bytes);
       comp_->prepare_neighbours(eo_.knn);   // symbolic proxy candidates, part of the analysis
       comp_->cx.prof = &prof[0];
-      MF_CUDA(cudaEventCreateWithFlags(&lev_ev_[0], cudaEventDisableTiming));
+      for (auto& e : lev_ev_) MF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      MF_CUDA(cudaStreamCreateWithFlags(&ds_, cudaStreamNonBlocking));
     }
     std::vector<int32_t> all;
     for (auto& lv : levels_) {
