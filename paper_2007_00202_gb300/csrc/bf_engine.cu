@@ -1002,19 +1002,26 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
   auto& centre1 = EP.centre1;
   auto& centre2 = EP.centre2;
   auto& scratch = cx.scratch;
+  // E^l / F^l blocks of one list item, flat [l][p] (p < 2^L), reset after each item
+  std::vector<Blk<T>> Ebuf(((size_t)L + 1) << L), Fbuf(((size_t)L + 1) << L);
+  std::vector<size_t> touched;
+  std::vector<int> xo, yo;
+  IdxVec X, Y;
   for (size_t q = 0; q < lst.size(); ++q) {
     const IdxVec& X0 = lst[q].first;
     const IdxVec& Y0 = lst[q].second;
     if (X0.empty() || Y0.empty()) continue;
-    // sorted copies and their original positions
-    std::vector<int> xo(X0.size()), yo(Y0.size());
-    std::iota(xo.begin(), xo.end(), 0);
-    std::iota(yo.begin(), yo.end(), 0);
-    std::sort(xo.begin(), xo.end(), [&](int a, int b) { return X0[a] < X0[b]; });
-    std::sort(yo.begin(), yo.end(), [&](int a, int b) { return Y0[a] < Y0[b]; });
-    IdxVec X(X0.size()), Y(Y0.size());
-    for (size_t t = 0; t < xo.size(); ++t) X[t] = X0[xo[t]];
-    for (size_t t = 0; t < yo.size(); ++t) Y[t] = Y0[yo[t]];
+    // sorted copies and their original positions (lists that arrive sorted skip the sort)
+    auto sort_pos = [](const IdxVec& v, std::vector<int>& o, IdxVec& sorted) {
+      o.resize(v.size());
+      std::iota(o.begin(), o.end(), 0);
+      if (!std::is_sorted(v.begin(), v.end()))
+        std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return v[a] < v[b]; });
+      sorted.resize(v.size());
+      for (size_t t = 0; t < o.size(); ++t) sorted[t] = v[o[t]];
+    };
+    sort_pos(X0, xo, X);
+    sort_pos(Y0, yo, Y);
     auto parts = [&](const Tree& tr, int l, const IdxVec& v) {
       std::vector<Part> out(tr[l].size());
       for (size_t k = 0; k < tr[l].size(); ++k) {
@@ -1027,8 +1034,11 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
     for (int l = 0; l <= L; ++l) { Xp[l] = parts(bf.rt, l, X); Yp[l] = parts(bf.ct, l, Y); }
     auto nonempty = [](const Part& p) { return p.p1 > p.p0; };
     // E^l blocks, l = L .. lc : rows = positions of X in O_i, cols = r(l,i,j)
-    std::vector<std::vector<Blk<T>>> E(L + 1, std::vector<Blk<T>>((size_t)1 << L)),
-        F(L + 1, std::vector<Blk<T>>((size_t)1 << L));   // p == nullptr: absent
+    for (size_t t : touched) Ebuf[t] = Fbuf[t] = Blk<T>();   // p == nullptr: absent
+    touched.clear();
+    auto E = [&](int l, int p) -> Blk<T>& { return Ebuf[((size_t)l << L) + p]; };
+    auto F = [&](int l, int p) -> Blk<T>& { return Fbuf[((size_t)l << L) + p]; };
+    auto touch = [&](int l, int p) { touched.push_back(((size_t)l << L) + p); };
     const IdxVec* Xptr = &X;
     for (int i = 0; i < (1 << L); ++i) {
       if (!nonempty(Xp[L][i]) || !nonempty(Yp[0][0])) continue;
@@ -1036,7 +1046,8 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
       const int nr = Xp[L][i].p1 - Xp[L][i].p0;
       Blk<T> e = new_blk<T>(scratch, nr, std::max(r, 1));
       e.cols = r;
-      E[L][i] = e;
+      E(L, i) = e;
+      touch(L, i);
       if (r == 0) continue;
       IdxVec rows;
       for (int t = Xp[L][i].p0; t < Xp[L][i].p1; ++t) rows.push_back((*Xptr)[t] - (int32_t)bf.rt[L][i].a);
@@ -1057,14 +1068,15 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
           const int nr = Xp[l][i].p1 - Xp[l][i].p0;
           Blk<T> e = new_blk<T>(scratch, nr, std::max(r, 1));
           e.cols = r;
-          E[l][p] = e;
+          E(l, p) = e;
+          touch(l, p);
           const int r1 = bf.rr(l + 1, 2 * i, jj / 2);
           int roff = 0;
           for (int t = 0; t < 2; ++t) {
             const int ci = 2 * i + t;
             if (!nonempty(Xp[l + 1][ci])) continue;
             const int cp = bf.pidx(l + 1, ci, jj / 2);
-            const Blk<T>& ec = E[l + 1][cp];
+            const Blk<T>& ec = E(l + 1, cp);
             const int nrc = Xp[l + 1][ci].p1 - Xp[l + 1][ci].p0;
             const int rc = bf.rr(l + 1, ci, jj / 2);
             const Blk<T>& R = bf.U[l][p];
@@ -1082,7 +1094,8 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
       const int nr = Yp[L][jj].p1 - Yp[L][jj].p0;
       Blk<T> f = new_blk<T>(scratch, nr, std::max(c, 1));
       f.cols = c;
-      F[0][jj] = f;
+      F(0, jj) = f;
+      touch(0, jj);
       if (c == 0) continue;
       IdxVec rows;
       for (int t = Yp[L][jj].p0; t < Yp[L][jj].p1; ++t) rows.push_back(Y[t] - (int32_t)bf.ct[L][jj].a);
@@ -1103,13 +1116,14 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
           const int nr = Yp[L - l][jj].p1 - Yp[L - l][jj].p0;
           Blk<T> f = new_blk<T>(scratch, nr, std::max(c, 1));
           f.cols = c;
-          F[l][p] = f;
+          F(l, p) = f;
+          touch(l, p);
           const int c1 = bf.rc(l - 1, i / 2, 2 * jj);
           for (int t = 0; t < 2; ++t) {
             const int cj = 2 * jj + t;
             if (!nonempty(Yp[L - l + 1][cj])) continue;
             const int cp = bf.pidx(l - 1, i / 2, cj);
-            const Blk<T>& fc = F[l - 1][cp];
+            const Blk<T>& fc = F(l - 1, cp);
             if (!fc.p) continue;
             const int nrc = Yp[L - l + 1][cj].p1 - Yp[L - l + 1][cj].p0;
             const int cc = bf.rc(l - 1, i / 2, cj);
@@ -1124,8 +1138,8 @@ static void extract_collect(BFContext<T>& cx, const DBF<T>& bf, const std::vecto
       for (int jj = 0; jj < (1 << (L - lc)); ++jj) {
         if (!nonempty(Xp[lc][i]) || !nonempty(Yp[L - lc][jj])) continue;
         const int p = bf.pidx(lc, i, jj);
-        const Blk<T>& ie = E[lc][p];
-        const Blk<T>& iff = F[lc][p];
+        const Blk<T>& ie = E(lc, p);
+        const Blk<T>& iff = F(lc, p);
         if (!ie.p || !iff.p) continue;
         const int r = bf.rr(lc, i, jj), c = bf.rc(lc, i, jj);
         const int nx = Xp[lc][i].p1 - Xp[lc][i].p0, ny = Yp[L - lc][jj].p1 - Yp[L - lc][jj].p0;
@@ -1434,8 +1448,8 @@ void BFContext<T>::hodbf_extract(const DHODBF<T>& H, const std::vector<std::pair
           it = req_of.find(bf);
         }
         Req& R = reqs[it->second];
-        R.lst.push_back({rx, ry});
         Blk<T> t = new_blk<T>(scratch, (int)rx.size(), (int)ry.size());
+        R.lst.emplace_back(std::move(rx), std::move(ry));   // rx, ry are not used below
         zspans.push_back({reinterpret_cast<char*>(t.p), (size_t)2 * t.plane * sizeof(T)});
         R.tmp.push_back(t);
         PlaceJob<T> pl{};
