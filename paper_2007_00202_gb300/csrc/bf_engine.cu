@@ -27,14 +27,30 @@ inline uint64_t splitmix(uint64_t x) {
 
 // cnt indices of [a, b) uniformly without replacement: the cnt smallest hashes
 // h(c) = splitmix64(salt ^ (c * golden)), salt = (a << 32) | b, returned sorted.
+// The order of [a, b) by hash depends on (a, b) only; it is kept per thread (ranges recur for every
+// row block of a cluster-tree level) and every sample is a prefix of it.
 IdxVec uniform_sample(int64_t a, int64_t b, int64_t cnt) {
-  const uint64_t salt = ((uint64_t)(a & 0xFFFFFFFF) << 32) | (uint64_t)(b & 0xFFFFFFFF);
-  std::vector<std::pair<uint64_t, int32_t>> h;
-  h.reserve(b - a);
-  for (int64_t c = a; c < b; ++c) h.push_back({splitmix(salt ^ ((uint64_t)c * 0x9E3779B97F4A7C15ull)), (int32_t)c});
-  if (cnt < (int64_t)h.size()) std::partial_sort(h.begin(), h.begin() + cnt, h.end());
-  IdxVec out;
-  for (int64_t k = 0; k < cnt && k < (int64_t)h.size(); ++k) out.push_back(h[k].second);
+  thread_local std::map<std::pair<int64_t, int64_t>, IdxVec> order_of;
+  thread_local size_t cached = 0;
+  auto it = order_of.find({a, b});
+  if (it == order_of.end()) {
+    const uint64_t salt = ((uint64_t)(a & 0xFFFFFFFF) << 32) | (uint64_t)(b & 0xFFFFFFFF);
+    std::vector<std::pair<uint64_t, int32_t>> h;
+    h.reserve(b - a);
+    for (int64_t c = a; c < b; ++c) h.push_back({splitmix(salt ^ ((uint64_t)c * 0x9E3779B97F4A7C15ull)), (int32_t)c});
+    std::sort(h.begin(), h.end());
+    if (cached > (size_t(1) << 24)) {   // bound the cache (entries of all kept ranges)
+      order_of.clear();
+      cached = 0;
+    }
+    IdxVec ord(h.size());
+    for (size_t k = 0; k < h.size(); ++k) ord[k] = h[k].second;
+    cached += ord.size();
+    it = order_of.emplace(std::make_pair(a, b), std::move(ord)).first;
+  }
+  const IdxVec& ord = it->second;
+  const size_t n = (size_t)std::min<int64_t>(cnt, (int64_t)ord.size());
+  IdxVec out(ord.begin(), ord.begin() + n);
   std::sort(out.begin(), out.end());
   return out;
 }
@@ -51,6 +67,7 @@ IdxVec proxies(const IdxVec& X, int64_t a, int64_t b, const std::vector<IdxVec>&
     return out;
   }
   out = uniform_sample(a, b, (int64_t)alpha * X.size());
+  out.reserve(out.size() + (size_t)knn * X.size());
   for (int32_t x : X) {
     if (x < 0 || x >= (int32_t)nn.size()) continue;
     int k = 0;
@@ -1317,13 +1334,14 @@ void BFContext<T>::hodbf_entry_eval_batch(const DExtract<T>& ext, std::vector<HP
         bp.col_off = hp.off + c;
         bp.nn_r.resize(nr);
         bp.nn_c.resize(nc);
+        const std::vector<IdxVec>& nn = *hp.nn;
         for (int x = 0; x < nr; ++x)
-          if (a + x < (int)hp.nn.size())
-            for (int32_t v : hp.nn[a + x])
+          if (a + x < (int)nn.size())
+            for (int32_t v : nn[a + x])
               if (v >= c && v < c + nc) bp.nn_r[x].push_back(v - c);
         for (int y = 0; y < nc; ++y)
-          if (c + y < (int)hp.nn.size())
-            for (int32_t v : hp.nn[c + y])
+          if (c + y < (int)nn.size())
+            for (int32_t v : nn[c + y])
               if (v >= a && v < a + nr) bp.nn_c[y].push_back(v - a);
         where[bp.L].push_back({q, {l, i}});
         groups[bp.L].push_back(std::move(bp));
@@ -1342,7 +1360,7 @@ template <typename T>
 std::unique_ptr<DHODBF<T>> BFContext<T>::hodbf_entry_eval(const DExtract<T>& ext, int n, const Tree& tree,
                                                            const std::vector<IdxVec>& nn, const BFParams& P) {
   std::vector<HProblem<T>> hp(1);
-  hp[0].n = n; hp[0].tree = tree; hp[0].nn = nn; hp[0].off = 0;
+  hp[0].n = n; hp[0].tree = tree; hp[0].nn = &nn; hp[0].off = 0;
   hodbf_entry_eval_batch(ext, hp, P);
   return std::move(hp[0].out);
 }

@@ -168,7 +168,7 @@ struct HProblem {
   int n = 0;
   int64_t off = 0;
   Tree tree;
-  std::vector<IdxVec> nn;             // neighbours in local indices
+  const std::vector<IdxVec>* nn = nullptr;   // neighbours in local indices (owned by the caller)
   std::unique_ptr<DHODBF<T>> out;
 };
 

@@ -141,6 +141,7 @@ int mf_green_build(int32_t nblk, const int32_t* m, double k, double spacing, dou
     s->st = reinterpret_cast<cudaStream_t>(stream);
     s->k = k;
     std::vector<mf::HProblem<float>> probs(nblk);
+    std::vector<std::vector<mf::IdxVec>> nns(nblk);   // the problems' neighbour lists (kept for the build)
     int64_t off = 0;
     for (int b = 0; b < nblk; ++b) {
       const int mb = m[b];
@@ -176,7 +177,8 @@ int mf_green_build(int32_t nblk, const int32_t* m, double k, double spacing, dou
       probs[b].n = n;
       probs[b].off = off;
       probs[b].tree = tree;
-      probs[b].nn = std::move(nn);
+      nns[b] = std::move(nn);
+      probs[b].nn = &nns[b];
       s->off.push_back(off);
       off += n;
     }
