@@ -341,6 +341,7 @@ template <typename T>
 void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
   HostTimer ht_(t_host + H_GEMM);
   std::vector<GemmDesc<T>> D;
+  D.reserve(descs.size());
   int maxn = 0, maxk = 1;
   bool two = false;
   for (auto& d : descs) {
@@ -490,9 +491,13 @@ void BFContext<T>::row_ids(const std::vector<Blk<T>>& Ms, double tol, int max_ra
   // small matrices with their rows in registers, matrices whose QR work fits in shared memory,
   // and the others (work in global memory, a thread-block cluster each): three independent
   // kernels, run side by side on forked streams when more than one kind is present
-  const IdJob<T>* drj = rjobs.empty() ? nullptr : stage(rjobs.data(), rjobs.size());
-  const IdJob<T>* dsj = sjobs.empty() ? nullptr : stage(sjobs.data(), sjobs.size());
-  const IdJob<T>* dgj = jobs.empty() ? nullptr : stage(jobs.data(), jobs.size());
+  auto up = [&](const std::vector<IdJob<T>>& v) {
+    return v.empty() ? nullptr : static_cast<const IdJob<T>*>(upload(v.data(), v.size() * sizeof(IdJob<T>)));
+  };
+  const IdJob<T>* drj = up(rjobs);
+  const IdJob<T>* dsj = up(sjobs);
+  const IdJob<T>* dgj = up(jobs);
+  flush();   // one copy for the three job tables
   const int kinds = (drj ? 1 : 0) + (dsj ? 1 : 0) + (dgj ? 1 : 0);
   const bool fork = kinds > 1 && cap_mode != 2;
   if (fork) {
