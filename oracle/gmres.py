@@ -43,18 +43,20 @@ def gmres_one(A, b, Minv, rtol=1e-8, restart=30, max_iters=300):
             H[j + 1, j] = np.linalg.norm(w)
             if H[j + 1, j] != 0:
                 V[:, j + 1] = w / H[j + 1, j]
-            for i in range(j):                          # previous Givens rotations
-                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
-                H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + np.conj(cs[i]) * H[i + 1, j]
+            # complex Givens rotations G_i = [[conj(c), conj(s)], [-s, c]], c = a / d, s = b / d,
+            # d = sqrt(|a|^2 + |b|^2): G_i (a, b) = (d, 0), so R = G H is upper triangular
+            for i in range(j):                          # previous rotations
+                t = np.conj(cs[i]) * H[i, j] + np.conj(sn[i]) * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
                 H[i, j] = t
             a, bb = H[j, j], H[j + 1, j]
             den = np.sqrt(abs(a) ** 2 + abs(bb) ** 2)
             cs[j] = a / den if den else 1.0
             sn[j] = bb / den if den else 0.0
-            H[j, j] = cs[j] * a + sn[j] * bb
+            H[j, j] = den if den else a
             H[j + 1, j] = 0
-            g[j + 1] = -np.conj(sn[j]) * g[j]
-            g[j] = cs[j] * g[j]
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = np.conj(cs[j]) * g[j]
             its += 1
             j_used = j + 1
             if abs(g[j + 1]) / nb <= rtol or its >= max_iters:

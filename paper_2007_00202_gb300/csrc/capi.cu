@@ -220,19 +220,21 @@ int solve_new_numbering(mf_handle* h, int nrhs, const double* B, double* X, mf_s
           for (int i = 0; i <= j; ++i)
             H[i + (restart + 1) * j] = cplx(hcol[2 * (nrhs * i + c)], hcol[2 * (nrhs * i + c) + 1]);
           H[j + 1 + (restart + 1) * j] = hn;
+          // complex Givens rotations G_i = [[conj(c), conj(s)], [-s, c]], c = a / d, s = b / d,
+          // d = sqrt(|a|^2 + |b|^2): G_i (a, b) = (d, 0), so G H is upper triangular
           for (int i = 0; i < j; ++i) {
             cplx a = H[i + (restart + 1) * j], bb = H[i + 1 + (restart + 1) * j];
-            H[i + (restart + 1) * j] = cs[c][i] * a + sn[c][i] * bb;
-            H[i + 1 + (restart + 1) * j] = -std::conj(sn[c][i]) * a + std::conj(cs[c][i]) * bb;
+            H[i + (restart + 1) * j] = std::conj(cs[c][i]) * a + std::conj(sn[c][i]) * bb;
+            H[i + 1 + (restart + 1) * j] = -sn[c][i] * a + cs[c][i] * bb;
           }
           cplx a = H[j + (restart + 1) * j], bb = H[j + 1 + (restart + 1) * j];
           double den = std::sqrt(std::norm(a) + std::norm(bb));
           cs[c][j] = den > 0 ? a / den : cplx(1);
           sn[c][j] = den > 0 ? bb / den : cplx(0);
-          H[j + (restart + 1) * j] = cs[c][j] * a + sn[c][j] * bb;
+          H[j + (restart + 1) * j] = den > 0 ? cplx(den) : a;
           H[j + 1 + (restart + 1) * j] = 0;
-          g[c][j + 1] = -std::conj(sn[c][j]) * g[c][j];
-          g[c][j] = cs[c][j] * g[c][j];
+          g[c][j + 1] = -sn[c][j] * g[c][j];
+          g[c][j] = std::conj(cs[c][j]) * g[c][j];
           jused[c] = j + 1;
           its_col[c]++;
           if (std::abs(g[c][j + 1]) <= rtol * bn[c] || its_col[c] >= h->opt.max_iters || hn == 0) live[c] = 0;
