@@ -124,6 +124,9 @@ def test_full_size_64cube_helmholtz_to_1e8(g):
     A = p.to_scipy()
     res = np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)
     assert info.converged == 1 and res.max() <= 1e-8
+    # minimal-residual GMRES converges within one restart cycle here (18 iterations measured); a
+    # rotation that does not zero the Hessenberg subdiagonal needed 57
+    assert info.iters <= 30
 
 
 def test_full_size_yee48_maxwell_to_1e8(g):
