@@ -18,6 +18,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -82,7 +83,8 @@ class Clocks:
     def __init__(self, idx):
         self.idx = idx
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to MF_CLOCKS_DIR (default: the system's temporary directory)
+        self.path = os.path.join(os.environ.get("MF_CLOCKS_DIR", tempfile.gettempdir()), f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

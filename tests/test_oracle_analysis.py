@@ -97,7 +97,11 @@ def test_symbolic_equals_bruteforce_elimination():
             assert below - set(idx) == set(f.upd.tolist())
 
 
-def test_survey_shape_table():
+def test_16cube_front_shapes_by_hand():
+    # planar nested dissection of the 16^3 grid (reading A11): the root separator is the plane
+    # x = 8 (16 x 16 = 256 unknowns, no update set); its children split x in [0, 8) and [9, 16),
+    # whose separators are planes of 16 x 8 = 128 and 16 x 7 = 112 unknowns, each updating the
+    # whole root plane (256)
     an = analyze(w.helmholtz7(16, 8), 64, 128, 64)
     assert len(an.fronts) == 101 and len(levels_of_fronts(an)) == 7
     assert an.fronts[-1].s == 256 and an.fronts[-1].u == 0
