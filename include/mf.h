@@ -208,8 +208,10 @@ int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const flo
  *   sk    out, nmat x kmax int32 (first rank_q entries valid), rank out, nmat int32.
  * Matrices with m, n <= 128 keep their rows in registers (1024 threads each); otherwise
  * the QR work matrix (2 m n floats per matrix) lives in shared memory when it fits
- * (2 m n + 2 n + 2 m floats <= 200 KiB), else in scratch allocated by the call.  Runs on `stream`
- * and waits for it.  Errors: MF_ERR_ARG (sizes: n <= 8192, m <= 2048), MF_ERR_OOM, MF_ERR_CUDA.
+ * (2 m n + 2 n + 2 m floats <= 200 KiB), else in scratch allocated by the call, each such
+ * matrix shared by a cluster of 8 thread blocks (same results as one block per matrix).
+ * Runs on `stream` and waits for it.  Errors: MF_ERR_ARG (sizes: n <= 8192, m <= 2048),
+ * MF_ERR_OOM, MF_ERR_CUDA.
  */
 int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol, int32_t max_rank, float* U,
                   int32_t* sk, int32_t* rank, void* stream);
