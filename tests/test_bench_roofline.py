@@ -46,3 +46,15 @@ def test_front_gemm_tensor_roofline_and_empty_profiles():
     assert r["achieved_tensor_passes"] == pytest.approx(300.0) and r["frac"] == pytest.approx(100.0 / 999.0)
     assert bench.roofline({"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0}, PEAKS) is None
     assert bench.roofline_front(None, PEAKS) is None
+
+
+def test_clock_summary_reports_median_max_and_active_reasons(tmp_path):
+    c = bench.Clocks(0)
+    c.path = str(tmp_path / "clocks.csv")
+    rows = ["0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    open(c.path, "w").write("\n".join(rows) + "\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
