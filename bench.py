@@ -143,8 +143,8 @@ def measured_peaks():
 PROFILE_PERIOD = 8
 # nominal FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz maximum SM clock
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM traffic of the narrow GEMM per algorithmic byte, from the ncu capture summarised in
-# profiles/k_gemm_nrhs_4096x16x4096.md (one streaming launch, 136 MB of A: read once), valid
+# DRAM traffic of the narrow GEMM per algorithmic byte, from an ncu capture of one streaming
+# launch (4096 x 16 x 4096, 136 MB of A: read once), valid
 # while the kernel source hashes to NARROW_SRC_SHA1; scaled to the bench's launches by their
 # algorithmic bytes
 NARROW_TRAFFIC_PER_ALG_BYTE = 1.0204
@@ -203,7 +203,7 @@ def roofline_front(prof, peaks):
             "bound": "tensor", "achieved": alg, "achieved_tensor_passes": 3 * alg, "peak": peak,
             "unit": "TFLOP/s", "frac": alg / peak, "frac_tensor_passes": 3 * alg / peak,
             "launches": prof["launches"], "traffic": None,
-            "peak_source": "TF32 cuBLAS 999 TFLOP/s measured on this pool (profiles/peaks_probe.md)"}
+            "peak_source": "TF32 cuBLAS 999 TFLOP/s measured on this GPU model (bench_kernels.py peaks)"}
 
 
 def cpu_baseline():

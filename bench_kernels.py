@@ -1,7 +1,7 @@
 """Microbenchmarks of the library's hot kernels through their C-ABI component entry points,
 and single-phase runs of the 64^3 workload for profilers.
 
-    python -m paper_2007_00202_gb300.kernel_bench [narrow|front|rowid|factor|solve] [--reps R] [--grid G]
+    python bench_kernels.py [narrow|front|rowid|factor|solve] [--reps R] [--grid G]
 
 narrow: the narrow GEMM of the solve (mf_gemm_nrhs_c64), C = -A B + C with A 4096 x 4096,
         B 4096 x 16 (complex64): one launch streams 128 MiB of A (larger than L2).
@@ -13,6 +13,11 @@ factor: the compressed complex64 factorization of the bench workload (helmholtz7
         cudaProfilerStart/Stop (for `ncu --profile-from-start off`).
 solve:  after that factorization, one preconditioner application to 16 right-hand sides
         (no refinement) between cudaProfilerStart/Stop, after three warm-up solves.
+bfapply: the batched butterfly apply of `--blocks` Green's-function HOD-BF blocks (the first
+        blocks of the 200-block workload, m = rint(16 * 8^u), seed 3; tol 1e-4) to 64 vectors,
+        after three warm-up applies; the timed applies run between cudaProfilerStart/Stop.
+peaks:  roofline denominators with library GEMMs (torch.matmul / cuBLAS): 8192^3 fp32 with
+        TF32 off and on, bf16 and fp64, 4096^3 complex64, and a 1 GiB device copy.
 Prints one JSON line per item: device time per call (CUDA events, after warm-up; the
 component entry points include their own synchronisation) and the achieved rate against the
 peaks used by bench.py.
@@ -24,7 +29,7 @@ import sys
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -147,11 +152,56 @@ def solve(torch, mf, reps, grid=64):
             "launches": g.lib().mf_launch_counter() - c0}
 
 
+def bfapply(torch, mf, reps, blocks=200, nrhs=64):
+    import math
+    import workloads as w
+    ms_ = w.butterfly_bench_sizes(200, 3)[:blocks]
+    S = mf.GreenSet([int(m) for m in ms_], math.pi / 4, 1.0, 1e-4, leaf=64,
+                    stream=torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(8)
+    X = w.complex_gaussian(rng, S.rows, nrhs)
+    dX = torch.from_numpy(np.concatenate([X.real.ravel(), X.imag.ravel()]).astype(np.float32)).cuda()
+    dY = torch.zeros_like(dX)
+    for _ in range(3):
+        S.apply(nrhs, dX.data_ptr(), dY.data_ptr())
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    ms = _time(torch, lambda: S.apply(nrhs, dX.data_ptr(), dY.data_ptr()), reps)
+    torch.cuda.profiler.stop()
+    by = 8.0 * S.storage + 2.0 * 8.0 * S.rows * nrhs
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    return {"item": "butterfly apply", "blocks": blocks, "rows": S.rows, "stored_entries": S.storage,
+            "nrhs": nrhs, "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm}
+
+
+def peaks(torch, mf, reps):
+    out = {"item": "library peaks (cuBLAS through torch.matmul; device copy)"}
+
+    def mm(dtype, n, tf32=False):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda").to(dtype)
+        b = torch.randn(n, n, device="cuda").to(dtype)
+        ms = min(_time(torch, lambda: torch.matmul(a, b), 3) for _ in range(max(1, reps // 3)))
+        torch.backends.cuda.matmul.allow_tf32 = False
+        return (8.0 if dtype.is_complex else 2.0) * n ** 3 / ms / 1e9
+    out["fp32_tflops"] = mm(torch.float32, 8192)
+    out["tf32_tflops"] = mm(torch.float32, 8192, tf32=True)
+    out["bf16_tflops"] = mm(torch.bfloat16, 8192)
+    out["fp64_tflops"] = mm(torch.float64, 8192)
+    out["c64_tflops"] = mm(torch.complex64, 4096)
+    src = torch.empty(1 << 28, device="cuda")
+    dst = torch.empty_like(src)
+    ms = _time(torch, lambda: dst.copy_(src), reps)
+    out["copy_gbs"] = 2.0 * src.numel() * 4 / ms / 1e6
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("which", nargs="*", default=["narrow", "front", "rowid"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--grid", type=int, default=64)
+    ap.add_argument("--blocks", type=int, default=200)
     args = ap.parse_args()
     import torch
     from paper_2007_00202_gb300 import build, mf
@@ -159,8 +209,10 @@ def main():
     for w in args.which:
         if w in ("factor", "solve"):
             r = {"factor": factor, "solve": solve}[w](torch, mf, args.reps, args.grid)
+        elif w == "bfapply":
+            r = bfapply(torch, mf, args.reps, args.blocks)
         else:
-            r = {"narrow": narrow, "front": front, "rowid": rowid}[w](torch, mf, args.reps)
+            r = {"narrow": narrow, "front": front, "rowid": rowid, "peaks": peaks}[w](torch, mf, args.reps)
         print(json.dumps(r), flush=True)
 
 

@@ -133,6 +133,18 @@ int mf_solve(mf_handle* h, int32_t nrhs, const double* b, int64_t ldb, double* x
 /* Same as mf_solve with device buffers (interleaved complex128, column-major, ld = N). */
 int mf_solve_device(mf_handle* h, int32_t nrhs, const void* d_b, void* d_x, mf_solve_info* info);
 
+/*
+ * Per-column results of the last mf_solve / mf_solve_device on h (Sec. 6: every
+ * right-hand side runs its own Krylov iteration, so each column has its own
+ * count and residual, independent of the other columns solved with it).
+ * nrhs must equal the last solve's; any output pointer may be NULL:
+ *   iters[c]        Krylov iterations (or refinement steps) of column c
+ *   converged[c]    1 if column c met rtol
+ *   rel_residual[c] ||b_c - A x_c|| / ||b_c|| (FP64, true residual)
+ * Errors: MF_ERR_ARG (h NULL, nrhs mismatch), MF_ERR_STATE (no solve yet).
+ */
+int mf_solve_columns(const mf_handle* h, int32_t nrhs, int32_t* iters, int32_t* converged, double* rel_residual);
+
 /* Counters of the analysis and of the last factorization. */
 int mf_stats(const mf_handle* h, mf_stats_t* out);
 
@@ -219,9 +231,11 @@ int mf_row_id_c64(int32_t nmat, int32_t m, int32_t n, const float* M, double tol
 /*
  * mf_row_id_c64 without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory where
- * they need the decomposition -- code that runs while a CUDA graph is being
- * captured (cudaMalloc/cudaFree cannot be captured), or embedders whose device
- * memory is fully reserved up front.  Same arguments, layouts and results as
+ * they need the decomposition -- applications whose own pool allocator reserves
+ * the GPU's memory up front and owns every buffer (a library cudaMalloc would
+ * fail or take memory the pool counts on), and latency-sensitive loops that may
+ * not call cudaMalloc / cudaFree, which can synchronize the whole device and
+ * stall other streams.  Same arguments, layouts and results as
  * mf_row_id_c64; the QR work matrix lives in a fixed array inside the library
  * (8 MiB per GPU, held by every GPU that loads the library until the process
  * exits) instead of a per-call allocation.
@@ -247,18 +261,22 @@ int mf_row_id_c64_noalloc(int32_t nmat, int32_t m, int32_t n, const float* M, do
  * handle batches every request waiting for that handle when its previous batch
  * ends (requests that arrive during a solve join the next batch), admits
  * requests while the batch's device workspace, estimated as 40 * N * nrhs * 16
- * bytes, fits mem_budget_bytes together with the other batches in flight, and
- * runs the batch as one mf_solve.  The handles stay owned by the caller and must
- * not be used elsewhere while the server lives.
+ * bytes, fits together with the other batches in flight both mf_server_create's
+ * mem_budget_bytes and the device's free memory less 1 GiB (cudaMemGetInfo, read
+ * when the batch is formed), and runs the batch as one mf_solve.  Each request
+ * reports its own columns (mf_solve_columns): its status, iterations, converged
+ * flag and residual are those it would get if solved alone.  The handles must
+ * be on the device that is current at mf_server_create; they stay owned by the
+ * caller and must not be used elsewhere while the server lives.
  */
 typedef struct mf_server mf_server;
 typedef struct {
   int64_t id;
   int32_t problem, nrhs;
-  int32_t iters, converged;
+  int32_t iters, converged;  /* max over the request's columns; 1 if all its columns met rtol */
   int32_t batch_rhs;          /* right-hand sides of the batch the request ran in */
   int32_t reserved;
-  double max_rel_residual;    /* of the batch */
+  double max_rel_residual;    /* max over the request's columns */
   double t_arrival, t_start, t_done;   /* seconds since the server was created */
 } mf_request_info;
 
@@ -268,7 +286,9 @@ int mf_server_create(int32_t nproblems, mf_handle* const* handles, int32_t max_b
  * x (host, same shape) is written when the request completes; *id identifies it.  b and x must
  * stay valid until mf_server_wait returns.  MF_ERR_OOM if the request alone exceeds the budget. */
 int mf_server_submit(mf_server* s, int32_t problem, int32_t nrhs, const double* b, double* x, int64_t* id);
-/* Block until request id is done; returns the request's mf_solve status and fills *info. */
+/* Block until request id is done and fill *info.  Returns MF_OK if every column of the request
+ * met rtol, MF_ERR_NO_CONVERGENCE if one did not (x still written), or the batch's mf_solve
+ * error (MF_ERR_CUDA, ...). */
 int mf_server_wait(mf_server* s, int64_t id, mf_request_info* info);
 /* Finish queued requests and stop the workers. */
 void mf_server_destroy(mf_server* s);

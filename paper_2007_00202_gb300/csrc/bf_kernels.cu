@@ -37,12 +37,11 @@ int launch_row_id_reg(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T
   if (njobs <= 0) return 0;
   if (max_m > 128 || max_n > 128) return -1;
   const size_t sm = row_id_reg_smem_bytes(max_m, max_n, sizeof(T));
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(k_row_id_reg<T, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
     cudaFuncSetAttribute(k_row_id_reg<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
-    attr = true;
-  }
+  });
   count_launches(1);
   if (max_n <= 80) k_row_id_reg<T, 10><<<njobs, 1024, sm, st>>>(d_jobs, tol, max_rank);
   else k_row_id_reg<T, 16><<<njobs, 1024, sm, st>>>(d_jobs, tol, max_rank);
@@ -55,12 +54,11 @@ int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol
   if (njobs <= 0) return 0;
   const size_t sm = smem_bytes ? smem_bytes : row_id_smem_bytes(max_m, max_n, sizeof(T), work_in_smem);
   if (sm > kRowIdSmemCap) return -1;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(k_row_id<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
     cudaFuncSetAttribute(k_row_id<T, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
-    attr = true;
-  }
+  });
   count_launches(1);
   if (work_in_smem) {
     // large shared-memory work (one or two CTAs per SM): four times the threads per matrix
@@ -70,11 +68,10 @@ int launch_row_id(const IdJob<T>* d_jobs, int njobs, int max_m, int max_n, T tol
   }
   // matrices in global memory are the large ones (few per launch): a cluster of kIdCluster
   // 1024-thread CTAs each, every CTA updating its share of the rows
-  static bool cattr = false;
-  if (!cattr) {
+  static PerDeviceOnce cattr;
+  cattr([] {
     cudaFuncSetAttribute(k_row_id_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowIdSmemCap);
-    cattr = true;
-  }
+  });
   const size_t csm = row_id_cluster_smem_bytes(max_m, max_n, sizeof(T));
   if (csm > kRowIdSmemCap) return -1;
   cudaLaunchConfig_t cfg = {};
@@ -374,11 +371,10 @@ int launch_small_inverse(const InvJob<T>* d_jobs, int njobs, int max_n, bool wor
   // the step vectors always sit in shared memory; the work matrix too when work_in_smem
   const size_t smem = work_in_smem ? small_inverse_smem_bytes(max_n, sizeof(double)) : small_inverse_vec_bytes(max_n);
   if (smem > kSmallInvSmemCap) return -1;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(k_small_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallInvSmemCap);
-    attr = true;
-  }
+  });
   count_launches(1);
   k_small_inverse<T><<<njobs, 256, smem, st>>>(d_jobs, work_in_smem ? 1 : 0, status);
   return 0;
@@ -590,11 +586,8 @@ int launch_lstsq(const LstsqJob<T>* d_jobs, int njobs, int max_c, int max_r, int
   if (njobs <= 0) return 0;
   const size_t smem = lstsq_smem_bytes<T>(max_c, max_r, max_w, work_in_smem);
   if (smem > kLstsqSmemCap) return -1;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_lstsq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLstsqSmemCap);
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  attr([] { cudaFuncSetAttribute(k_lstsq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLstsqSmemCap); });
   count_launches(1);
   k_lstsq<T><<<njobs, 256, smem, st>>>(d_jobs, work_in_smem ? 1 : 0);
   return 0;

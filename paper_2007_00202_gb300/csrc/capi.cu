@@ -41,6 +41,9 @@ struct mf_handle {
   int64_t io_nrhs = 0;
   int64_t work_nrhs = 0;
   int32_t work_restart = 0;
+  // per-column results of the last solve (mf_solve_columns)
+  std::vector<int32_t> col_iters, col_converged;
+  std::vector<double> col_rel_residual;
 };
 
 namespace {
@@ -142,7 +145,11 @@ int solve_new_numbering(mf_handle* h, int nrhs, const double* B, double* X, mf_s
   const double rtol = h->opt.rtol;
   int iters = 0;
   std::vector<double> rn;
+  std::vector<int> its_col(nrhs, 0);   // iterations (or refinement steps) of each column
   auto rel_ok = [&](const std::vector<double>& r, int c) { return bn[c] == 0 || r[c] <= rtol * bn[c]; };
+  h->col_iters.clear();
+  h->col_converged.clear();
+  h->col_rel_residual.clear();
 
   if (refine == MF_REFINE_NONE || refine == MF_REFINE_IR) {
     h->eng->apply_precond(B, X, nrhs);
@@ -152,6 +159,8 @@ int solve_new_numbering(mf_handle* h, int nrhs, const double* B, double* X, mf_s
         bool all = true;
         for (int c = 0; c < nrhs; ++c) all = all && rel_ok(rn, c);
         if (all) break;
+        // a column's step count: the refinement steps taken while it was above rtol
+        for (int c = 0; c < nrhs; ++c) its_col[c] += rel_ok(rn, c) ? 0 : 1;
         h->eng->apply_precond(R, Z, nrhs);
         // X += Z
         std::vector<double> one(2 * nrhs, 0.0);
@@ -172,7 +181,6 @@ int solve_new_numbering(mf_handle* h, int nrhs, const double* B, double* X, mf_s
     double* sc = h->wsc.as<double>();
     double* yd = h->wy.as<double>();
     const size_t vstride = (size_t)2 * n * nrhs;   // doubles per Krylov vector block
-    std::vector<int> its_col(nrhs, 0);
     while (true) {
       std::vector<int> active;
       for (int c = 0; c < nrhs; ++c)
@@ -287,6 +295,13 @@ int solve_new_numbering(mf_handle* h, int nrhs, const double* B, double* X, mf_s
     info->iters = iters;
     info->converged = conv ? 1 : 0;
     info->max_rel_residual = worst;
+  }
+  h->col_iters.assign(its_col.begin(), its_col.end());
+  h->col_converged.resize(nrhs);
+  h->col_rel_residual.resize(nrhs);
+  for (int c = 0; c < nrhs; ++c) {
+    h->col_converged[c] = rel_ok(rn, c) ? 1 : 0;
+    h->col_rel_residual[c] = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
   }
   if (!conv && refine != MF_REFINE_NONE)
     return fail(h, MF_ERR_NO_CONVERGENCE, "refinement stopped above rtol (max rel. residual " + std::to_string(worst) + ")");
@@ -452,6 +467,19 @@ int mf_solve(mf_handle* h, int32_t nrhs, const double* b, int64_t ldb, double* x
     MF_CUDA(cudaStreamSynchronize(st));
     return rc;
   });
+}
+
+int mf_solve_columns(const mf_handle* h, int32_t nrhs, int32_t* iters, int32_t* converged, double* rel_residual) {
+  if (!h) return fail(nullptr, MF_ERR_ARG, "handle is NULL");
+  if (h->col_iters.empty()) return fail(const_cast<mf_handle*>(h), MF_ERR_STATE, "no solve has run on this handle");
+  if (nrhs != (int32_t)h->col_iters.size())
+    return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "nrhs differs from the last solve's");
+  for (int c = 0; c < nrhs; ++c) {
+    if (iters) iters[c] = h->col_iters[c];
+    if (converged) converged[c] = h->col_converged[c];
+    if (rel_residual) rel_residual[c] = h->col_rel_residual[c];
+  }
+  return MF_OK;
 }
 
 int mf_stats(const mf_handle* h, mf_stats_t* out) {

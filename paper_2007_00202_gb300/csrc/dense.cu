@@ -355,11 +355,8 @@ void launch_panel_lu(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int 
   int cap = (int)(budget / (2 * sizeof(T) * (size_t)nb));
   if (max_rows < cap) cap = max_rows;
   size_t sm = 2 * sizeof(T) * (size_t)nb * cap;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_panel_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  attr([] { cudaFuncSetAttribute(k_panel_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget); });
   g_launches++;
   k_panel_lu<T><<<nf, 512, sm, st>>>(d_fronts, d_flist, kb, nb, cap, status);
 }
@@ -543,11 +540,8 @@ void launch_trinv_diag(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, in
                        cudaStream_t st) {
   if (nf <= 0) return;
   size_t sm = 4 * 64 * 65 * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_trinv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr_set = true;
-  }
+  static PerDeviceOnce attr;
+  attr([sm] { cudaFuncSetAttribute(k_trinv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); });
   dim3 grid((max_s + 63) / 64, nf);
   g_launches++;
   k_trinv_diag<T><<<grid, 64, sm, st>>>(d_fronts, d_flist, which);

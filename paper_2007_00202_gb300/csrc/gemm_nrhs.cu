@@ -340,13 +340,12 @@ void launch_nb(const GemmDesc<T>* d_desc, const GemmTile* d_tiles, int ntiles, i
   const size_t stages = (size_t)ns * sizeof(NrSlot<T, NB>);
   const size_t red = nr_red_bytes<T, NB>();
   const size_t smem = stages > red ? stages : red;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([red] {
     const size_t most = (size_t)MS * sizeof(NrSlot<T, NB>) > red ? (size_t)MS * sizeof(NrSlot<T, NB>) : red;
     cudaFuncSetAttribute(k_gemm_nrhs<T, NB, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     cudaFuncSetAttribute(k_gemm_nrhs<T, NB, TWO>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
-    attr = true;
-  }
+  });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)ntiles, (unsigned)ksplit, 1);
   cfg.blockDim = dim3(128, 1, 1);

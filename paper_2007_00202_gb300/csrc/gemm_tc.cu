@@ -293,12 +293,11 @@ int gemm_tc_tile() { return BM; }
 void launch_gemm_tc(const GemmDesc<float>* d_desc, const GemmTile* d_tiles, int ntiles, int32_t* status,
                     cudaStream_t st, bool split) {
   if (ntiles <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    attr = true;
-  }
+  });
   count_launches(1);
   if (split) k_gemm_tc<true><<<ntiles, NT, SMEM_BYTES, st>>>(d_desc, d_tiles, status);
   else k_gemm_tc<false><<<ntiles, NT, SMEM_BYTES, st>>>(d_desc, d_tiles, status);

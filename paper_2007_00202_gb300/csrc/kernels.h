@@ -3,6 +3,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <utility>
+
 #include "mf_device.h"
 
 namespace mf {
@@ -10,6 +13,22 @@ namespace mf {
 // Number of kernel launches issued by this library since it was loaded.
 int64_t launch_count();
 void count_launches(int k);
+
+// Runs a set-up step (a kernel attribute, which CUDA keeps per device) once per device: on the
+// first call made with each device current, thread-safe (other callers wait until it is done).
+struct PerDeviceOnce {
+  static constexpr int kMaxDevices = 64;
+  std::once_flag flag[kMaxDevices];
+  template <typename F>
+  void operator()(F&& f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+      f();
+      return;
+    }
+    std::call_once(flag[dev], std::forward<F>(f));
+  }
+};
 
 // Batched planar complex GEMM over a tile list (SIMT).
 template <typename T>

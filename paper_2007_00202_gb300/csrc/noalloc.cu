@@ -2,13 +2,15 @@
 // area instead of per-call device allocations.
 //
 // Some callers cannot allocate device memory at the point where they need an
-// ID: code running while a CUDA graph is being captured (cudaMalloc and
-// cudaFree are not capturable), allocators that forbid allocation on their
-// critical path, or embedders whose memory is fully pre-reserved.  For them
-// mf_row_id_c64_noalloc does the same work as mf_row_id_c64, with the QR work
-// matrix placed in the file-scope array below.  The array is a static device
-// allocation of MF_ID_SCRATCH_FLOATS floats (8 MiB); every GPU that loads this
-// library holds it until the process exits.
+// ID: applications whose own pool allocator reserves the GPU's memory up front
+// and hands out every buffer itself (a cudaMalloc from the library would fail or
+// take memory the pool counts on), and latency-sensitive loops that must not
+// call cudaMalloc / cudaFree because those calls can synchronize the whole
+// device and stall the work of other streams.  For them mf_row_id_c64_noalloc
+// does the same work as mf_row_id_c64, with the QR work matrix placed in the
+// file-scope array below.  The array is a static device allocation of
+// MF_ID_SCRATCH_FLOATS floats (8 MiB); every GPU that loads this library holds
+// it until the process exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>

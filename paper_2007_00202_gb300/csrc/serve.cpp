@@ -5,7 +5,8 @@
 // One worker thread per factorization takes every request that is waiting for
 // it when the previous batch finishes (continuous batching: requests that
 // arrive while a batch is on the GPU join the next batch), admits them while
-// the device workspace of the batch fits the memory budget, solves the batch
+// the device workspace of the batch fits the memory budget and the device's free
+// memory (cudaMemGetInfo, read when the batch is formed), solves the batch
 // with one mf_solve call (columns converge independently inside GMRES), and
 // completes each request.  Batches of different factorizations overlap on the
 // device because the workers run concurrently on different streams.
@@ -20,6 +21,8 @@
 #include <mutex>
 #include <thread>
 #include <vector>
+
+#include <cuda_runtime.h>
 
 #include "../../include/mf.h"
 
@@ -49,6 +52,7 @@ struct Worker {
 
 struct mf_server {
   std::vector<std::unique_ptr<Worker>> w;
+  int device = 0;                         // the device of the handles (current at mf_server_create)
   int32_t max_batch = 256;
   int64_t budget = 0;
   std::atomic<int64_t> reserved{0};
@@ -65,6 +69,7 @@ struct mf_server {
 
 void mf_server::run(int p) {
   Worker& wk = *w[p];
+  cudaSetDevice(device);
   for (;;) {
     std::vector<std::shared_ptr<Request>> batch;
     int64_t bytes = 0;
@@ -72,13 +77,19 @@ void mf_server::run(int p) {
       std::unique_lock<std::mutex> lk(mu);
       cv_work.wait(lk, [&] { return stop || !wk.q.empty(); });
       if (stop && wk.q.empty()) return;
+      // admission by the device's free memory as well as the caller's budget: a batch's workspace
+      // must fit in what the device has left (keeping 1 GiB of headroom)
+      size_t fr = 0, total = 0;
+      int64_t room = budget;
+      if (cudaMemGetInfo(&fr, &total) == cudaSuccess)
+        room = std::min<int64_t>(budget, reserved.load() + std::max<int64_t>(0, (int64_t)fr - (int64_t(1) << 30)));
       int tot = 0;
       while (!wk.q.empty()) {
         auto& r = wk.q.front();
         int64_t need = bytes_for(wk.n, tot + r->nrhs) - bytes;
         bool first = batch.empty();
-        if (!first && (tot + r->nrhs > max_batch || reserved.load() + need > budget)) break;
-        if (first && reserved.load() + need > budget && reserved.load() > 0) break;   // wait for memory
+        if (!first && (tot + r->nrhs > max_batch || reserved.load() + need > room)) break;
+        if (first && reserved.load() + need > room && reserved.load() > 0) break;   // wait for memory
         bytes += need;
         reserved += need;
         tot += r->nrhs;
@@ -103,6 +114,11 @@ void mf_server::run(int p) {
     mf_solve_info info{};
     int rc = mf_solve(wk.h, tot, wk.bbuf.data(), wk.n, wk.xbuf.data(), wk.n, &info);
     const double td = now();
+    // each request reports its own columns: what it returns does not depend on the batch it ran in
+    std::vector<int32_t> cit(tot, 0), cconv(tot, 0);
+    std::vector<double> cres(tot, 0.0);
+    const bool have_cols = (rc == MF_OK || rc == MF_ERR_NO_CONVERGENCE) &&
+                           mf_solve_columns(wk.h, tot, cit.data(), cconv.data(), cres.data()) == MF_OK;
     off = 0;
     for (auto& r : batch) {
       if (rc == MF_OK || rc == MF_ERR_NO_CONVERGENCE)
@@ -112,14 +128,30 @@ void mf_server::run(int p) {
     reserved -= bytes;
     {
       std::lock_guard<std::mutex> lk(mu);
+      int c0 = 0;
       for (auto& r : batch) {
         r->t_start = ts;
         r->t_done = td;
-        r->iters = info.iters;
-        r->converged = info.converged;
-        r->max_rel_residual = info.max_rel_residual;
         r->batch_rhs = tot;
-        r->status = rc;
+        if (have_cols) {
+          int it = 0, conv = 1;
+          double worst = 0;
+          for (int c = c0; c < c0 + r->nrhs; ++c) {
+            it = std::max(it, cit[c]);
+            conv = conv && cconv[c];
+            worst = std::max(worst, cres[c]);
+          }
+          r->iters = it;
+          r->converged = conv;
+          r->max_rel_residual = worst;
+          r->status = conv ? MF_OK : MF_ERR_NO_CONVERGENCE;
+        } else {
+          r->iters = info.iters;
+          r->converged = 0;
+          r->max_rel_residual = info.max_rel_residual;
+          r->status = rc == MF_OK ? MF_ERR_CUDA : rc;
+        }
+        c0 += r->nrhs;
       }
     }
     cv_done.notify_all();
@@ -134,6 +166,7 @@ int mf_server_create(int32_t nproblems, mf_handle* const* handles, int32_t max_b
   if (!out || nproblems <= 0 || !handles || max_batch_rhs <= 0 || mem_budget_bytes <= 0) return MF_ERR_ARG;
   auto s = std::make_unique<mf_server>();
   s->max_batch = max_batch_rhs;
+  if (cudaGetDevice(&s->device) != cudaSuccess) return MF_ERR_CUDA;
   s->budget = mem_budget_bytes;
   for (int p = 0; p < nproblems; ++p) {
     mf_stats_t st;

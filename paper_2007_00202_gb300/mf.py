@@ -79,6 +79,7 @@ SIGNATURES = {
     "mf_solve": (C.c_int, [_P, C.c_int32, _DP, C.c_int64, _DP, C.c_int64, C.POINTER(mf_solve_info)]),
     "mf_solve_device": (C.c_int, [_P, C.c_int32, _P, _P, C.POINTER(mf_solve_info)]),
     "mf_stats": (C.c_int, [_P, C.POINTER(mf_stats_t)]),
+    "mf_solve_columns": (C.c_int, [_P, C.c_int32, _I32P, _I32P, _DP]),
     "mf_last_error": (C.c_char_p, [_P]),
     "mf_destroy": (None, [_P]),
     "mf_launch_counter": (C.c_int64, []),
@@ -188,6 +189,15 @@ class Handle:
         if not (allow_no_convergence and rc == -6):
             _check(rc, self.ptr)
         return info
+
+    def mf_solve_columns(self, nrhs: int) -> dict:
+        """Per-column iterations, converged flags and true relative residuals of the last solve."""
+        it = np.zeros(nrhs, np.int32)
+        cv = np.zeros(nrhs, np.int32)
+        rr = np.zeros(nrhs, np.float64)
+        _check(lib().mf_solve_columns(self.ptr, nrhs, _p(it, C.c_int32), _p(cv, C.c_int32), _p(rr, C.c_double)),
+               self.ptr)
+        return {"iters": it, "converged": cv, "rel_residual": rr}
 
     def mf_stats(self) -> dict:
         s = mf_stats_t()
@@ -351,7 +361,9 @@ class Server:
         B, X = self._bufs.pop(rid)
         if rc not in (0, -6):
             _check(rc)
-        return X, {k: getattr(info, k) for k, _ in info._fields_}
+        out = {k: getattr(info, k) for k, _ in info._fields_}
+        out["status"] = rc
+        return X, out
 
     def close(self):
         if getattr(self, "ptr", None):

@@ -1,8 +1,10 @@
 """The allocation-free row ID entry point against the allocating one.
 
 mf_row_id_c64_noalloc serves callers that cannot allocate device memory when
-they need the decomposition (for example code running under CUDA graph
-capture); it keeps its QR work matrix in a fixed array inside the library.
+they need the decomposition (applications whose pool allocator owns all of the
+GPU's memory, or loops that must not call cudaMalloc / cudaFree because those
+can synchronize the device); it keeps its QR work matrix in a fixed array
+inside the library.
 This file is collected last so that a failure here comes after every other test.
 """
 import numpy as np
