@@ -356,6 +356,27 @@ int mf_analysis_export(const mf_handle* h, int64_t* perm, int64_t* front_parent,
                        int32_t* front_flags, int64_t* upd_ptr, int64_t* upd_idx);
 
 /*
+ * Apply one operator of compressed front f (Alg. 5) to nrhs host vectors, for inspection
+ * (for example the per-front compression error against a dense assembly of the same block):
+ *   which = MF_OP_F11 (0): the HOD-BF F11 (Sec. 4.1), s x s
+ *           MF_OP_F11_INV (1): its Alg. 4 inverse, s x s
+ *           MF_OP_F12 (2): the butterfly F12 (Alg. 2), s x u
+ *           MF_OP_F21 (3): the butterfly F21, u x s
+ *           MF_OP_C (4): the HOD-BF contribution block C = F22 - F21 F11^-1 F12 (kept for the
+ *                        parent; absent at the root), u x u
+ * s = |I^s|, u = |I^u| of front f; rows and columns in the new numbering's order of
+ * [sep_begin, sep_end) and of I^u (see mf_analysis_export).  x: in x nrhs, y: out x nrhs,
+ * host, column-major, interleaved complex128.  Synchronous; allocates device staging.
+ * Errors: MF_ERR_ARG (not a compressed front, no such operator), MF_ERR_STATE (not factored).
+ */
+#define MF_OP_F11 0
+#define MF_OP_F11_INV 1
+#define MF_OP_F12 2
+#define MF_OP_F21 3
+#define MF_OP_C 4
+int mf_front_apply(mf_handle* h, int64_t f, int32_t which, int32_t nrhs, const double* x, double* y);
+
+/*
  * Cluster trees of front f (Sec. 5.1).  nlev[0], nlev[1] receive the number of
  * levels (depth + 1) of the HOD-BF tree T_H of F11 and of the F22 tree (0 for a
  * dense front).  If ranges != NULL it receives, for T_H then the F22 tree,

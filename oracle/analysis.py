@@ -267,8 +267,11 @@ def bfs_nearest(rp, ci, start: int, allowed: np.ndarray, target: np.ndarray, knn
     return out
 
 
-def front_neighbours(an: Analysis, f: Front, knn: int):
+def front_neighbours(an: Analysis, f: Front, knn: int, stride: int = 1):
     """Nearest-neighbour lists of a compressed front (Sec. 5.2).
+
+    stride > 1 computes the lists of every stride-th vertex of I^s and of I^u only (a sample
+    for checks at full size); the lists themselves do not depend on it.
 
     Returns dict with
       nn11[x]  x in I^s : first knn vertices of graph A(I^s,I^s) outside x's T_H leaf,
@@ -289,8 +292,9 @@ def front_neighbours(an: Analysis, f: Front, knn: int):
     leaf_of = np.full(N, -1, np.int64)
     for li, (a, b) in enumerate(f.th_tree[-1] if f.th_tree else [(0, f.s)]):
         leaf_of[f.sep_begin + a: f.sep_begin + b] = li
+    s_sel, u_sel = s_idx[::stride], u_idx[::stride]
     nn11 = {}
-    for x in s_idx:
+    for x in s_sel:
         tgt = in_s & (leaf_of != leaf_of[x])
         nn11[int(x)] = bfs_nearest(rp, ci, int(x), in_s, tgt, knn)
     out["nn11"] = nn11
@@ -299,12 +303,12 @@ def front_neighbours(an: Analysis, f: Front, knn: int):
         for li, (a, b) in enumerate(f.f22_tree[-1] if f.f22_tree else [(0, f.u)]):
             leaf22[u_idx[a:b]] = li
     nn22 = {}
-    for x in u_idx:
+    for x in u_sel:
         tgt = in_u & (leaf22 != leaf22[x])
         nn22[int(x)] = bfs_nearest(rp, ci, int(x), in_u, tgt, knn)
     out["nn22"] = nn22
-    out["nn12"] = {int(x): bfs_nearest(rp, ci, int(x), both, in_u, knn) for x in s_idx}
-    out["nn21"] = {int(y): bfs_nearest(rp, ci, int(y), both, in_s, knn) for y in u_idx}
+    out["nn12"] = {int(x): bfs_nearest(rp, ci, int(x), both, in_u, knn) for x in s_sel}
+    out["nn21"] = {int(y): bfs_nearest(rp, ci, int(y), both, in_s, knn) for y in u_sel}
     return out
 
 

@@ -677,6 +677,17 @@ int mf_analysis_export(const mf_handle* h, int64_t* perm, int64_t* front_parent,
   return MF_OK;
 }
 
+int mf_front_apply(mf_handle* h, int64_t f, int32_t which, int32_t nrhs, const double* x, double* y) {
+  if (!h || !x || !y || nrhs <= 0) return fail(h, MF_ERR_ARG, "invalid argument");
+  if (!h->factored) return fail(h, MF_ERR_STATE, "mf_front_apply before mf_factor");
+  if (f < 0 || f >= (int64_t)h->an.fronts.size()) return fail(h, MF_ERR_ARG, "bad front id");
+  return guarded(h, [&]() -> int {
+    if (h->eng->front_apply((int)f, which, nrhs, x, y) != 0)
+      return fail(h, MF_ERR_ARG, "front is not compressed or has no such operator");
+    return MF_OK;
+  });
+}
+
 int mf_front_trees(const mf_handle* h, int64_t f, int64_t* nlev, int64_t* ranges) {
   if (!h || !nlev) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "NULL argument");
   if (f < 0 || f >= (int64_t)h->an.fronts.size()) return fail(const_cast<mf_handle*>(h), MF_ERR_ARG, "bad front id");

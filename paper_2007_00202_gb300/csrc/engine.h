@@ -190,6 +190,11 @@ class EngineBase {
   virtual int launches_factor() const = 0;
   virtual int launches_solve(int nrhs) = 0;
   virtual int max_rank() const { return 0; }
+  // Inspection of a compressed front's operators: Y = K X with K one of F11 (which 0), F11^-1
+  // (1), F12 (2), F21 (3) or the contribution block C (4) of front fid; X (in x nrhs) and Y
+  // (out x nrhs) host, column-major, interleaved complex128.  Returns 0, or -1 when fid is not a
+  // compressed front or has no such operator.
+  virtual int front_apply(int fid, int which, int nrhs, const double* x, double* y) { return -1; }
   virtual double compressed_seconds() const { return 0; }
   // Event timing of two kernel families (see mf_profile in mf.h):
   // prof[0] the narrow GEMM (k_gemm_nrhs) in factor() and apply_precond(), prof[1] the

@@ -148,6 +148,55 @@ class DenseEngine : public EngineBase {
     return nb;
   }
 
+  int front_apply(int fid, int which, int nrhs, const double* x, double* y) override {
+    if (!comp_ || nrhs <= 0) return -1;
+    auto it = comp_->fronts.find(fid);
+    if (it == comp_->fronts.end()) return -1;
+    CompFront<T>& cf = *it->second;
+    const int s = cf.s, u = cf.u;
+    int rin = s, rout = s;
+    if (which == 2) rin = u;
+    if (which == 3) rout = u;
+    if (which == 4) rin = rout = u;
+    if (which < 0 || which > 4 || rin == 0 || rout == 0) return -1;
+    if ((which == 2 && !cf.F12) || (which == 3 && !cf.F21) || (which == 4 && !cf.C)) return -1;
+    BFContext<T>& cx = comp_->cx;
+    const int ld = (nrhs + 3) & ~3;
+    const int64_t pin = (int64_t)rin * ld, pout = (int64_t)rout * ld;
+    std::vector<T> hx(2 * (size_t)pin, T(0)), hy(2 * (size_t)pout);
+    for (int c = 0; c < nrhs; ++c)
+      for (int r = 0; r < rin; ++r) {
+        hx[(size_t)r * ld + c] = (T)x[2 * ((size_t)c * rin + r)];
+        hx[pin + (size_t)r * ld + c] = (T)x[2 * ((size_t)c * rin + r) + 1];
+      }
+    DevMem dx, dy;
+    dx.alloc(sizeof(T) * hx.size());
+    dy.alloc(sizeof(T) * hy.size());
+    MF_CUDA(cudaMemcpyAsync(dx.p, hx.data(), sizeof(T) * hx.size(), cudaMemcpyHostToDevice, cx.st));
+    Blk<T> X, Y;
+    X.p = dx.as<T>(); X.rows = rin; X.cols = nrhs; X.ld = ld; X.plane = pin;
+    Y.p = dy.as<T>(); Y.rows = rout; Y.cols = nrhs; Y.ld = ld; Y.plane = pout;
+    const size_t mk = cx.scratch.mark();
+    if (which == 0) cx.hodbf_apply(*cf.F11, X, Y, false);
+    if (which == 1) cx.inv_apply(*cf.F11inv, X, Y, false);
+    if (which == 2 || which == 3) {
+      std::vector<const DBF<T>*> b{which == 2 ? cf.F12.get() : cf.F21.get()};
+      std::vector<Blk<T>> xs{X}, ys{Y};
+      cx.apply(b, xs, ys, false, false);
+    }
+    if (which == 4) cx.hodbf_apply(*cf.C, X, Y, false);
+    cx.flush();
+    MF_CUDA(cudaMemcpyAsync(hy.data(), dy.p, sizeof(T) * hy.size(), cudaMemcpyDeviceToHost, cx.st));
+    MF_CUDA(cudaStreamSynchronize(cx.st));
+    cx.scratch.release(mk);
+    for (int c = 0; c < nrhs; ++c)
+      for (int r = 0; r < rout; ++r) {
+        y[2 * ((size_t)c * rout + r)] = (double)hy[(size_t)r * ld + c];
+        y[2 * ((size_t)c * rout + r) + 1] = (double)hy[pout + (size_t)r * ld + c];
+      }
+    return 0;
+  }
+
   void apply_precond(const double* x, double* y, int nrhs) override {
     const int nb = nrhs_bucket(nrhs);
     SolveProg& sp = solve_prog(nb);

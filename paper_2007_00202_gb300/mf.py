@@ -22,6 +22,7 @@ MF_LATTICE_NODE, MF_LATTICE_EDGE = 0, 1
 MF_PREC_C64, MF_PREC_C128 = 0, 1
 MF_REFINE_NONE, MF_REFINE_GMRES, MF_REFINE_IR = 0, 1, 2
 MF_PROF_NARROW_GEMM, MF_PROF_FRONT_GEMM = 0, 1
+MF_OP_F11, MF_OP_F11_INV, MF_OP_F12, MF_OP_F21, MF_OP_C = 0, 1, 2, 3, 4
 MF_OPTIONS_V1 = 1
 
 
@@ -106,6 +107,7 @@ SIGNATURES = {
     "mf_analysis_sizes": (C.c_int, [_P, C.POINTER(mf_analysis_sizes_t)]),
     "mf_analysis_export": (C.c_int, [_P, _I64P, _I64P, _I64P, _I32P, _I64P, _I64P]),
     "mf_front_trees": (C.c_int, [_P, C.c_int64, _I64P, _I64P]),
+    "mf_front_apply": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, _DP, _DP]),
     "mf_front_neighbours": (C.c_int, [_P, C.c_int64, C.c_int32, _I64P, _I64P, _I64P]),
 }
 
@@ -229,6 +231,15 @@ class Handle:
                                         _p(flags, C.c_int32), _p(uptr, C.c_int64), _p(uidx, C.c_int64)), self.ptr)
         return dict(perm=perm, parent=parent, sep=sep.reshape(nf, 2), compressed=flags.astype(bool),
                     upd_ptr=uptr, upd_idx=uidx[:sz.upd_total])
+
+    def mf_front_apply(self, f: int, which: int, x: np.ndarray, out_rows: int) -> np.ndarray:
+        """Y = K x for operator `which` (MF_OP_*) of compressed front f; x: (in, nrhs) complex."""
+        X = np.asfortranarray(np.asarray(x, dtype=np.complex128))
+        Y = np.empty((out_rows, X.shape[1]), np.complex128, order="F")
+        dp = C.POINTER(C.c_double)
+        _check(lib().mf_front_apply(self.ptr, f, which, X.shape[1], C.cast(X.ctypes.data, dp),
+                                    C.cast(Y.ctypes.data, dp)), self.ptr)
+        return Y
 
     def mf_front_trees(self, f: int):
         nlev = np.zeros(2, np.int64)

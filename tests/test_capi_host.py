@@ -50,7 +50,7 @@ def test_argument_errors(g):
     assert (o.leaf_size, o.nmin_sep, o.gmres_restart, o.rtol) == (64, 1024, 30, 1e-8)
 
 
-def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True):
+def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True, stride=1):
     an = analyze(p, leaf, nmin, hleaf)
     h = g.analyze_problem(p, leaf_size=leaf, nmin_sep=nmin, hodbf_leaf=hleaf)
     e = h.mf_analysis_export()
@@ -67,13 +67,13 @@ def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True):
             assert f22 == [list(map(tuple, l)) for l in f.f22_tree]
             if check_nn:
                 nn = h.mf_front_neighbours(f.id, knn, f.s, f.u)
-                on = front_neighbours(an, f, knn)
-                S = range(f.sep_begin, f.sep_end)
-                U = [int(x) for x in f.upd]
-                assert nn["nn11"] == [on["nn11"][x] for x in S]
-                assert nn["nn12"] == [on["nn12"][x] for x in S]
-                assert nn["nn21"] == [on["nn21"][x] for x in U]
-                assert nn["nn22"] == [on["nn22"][x] for x in U]
+                on = front_neighbours(an, f, knn, stride)
+                S = range(f.sep_begin, f.sep_end, stride)
+                U = [int(x) for x in f.upd[::stride]]
+                assert nn["nn11"][::stride] == [on["nn11"][x] for x in S]
+                assert nn["nn12"][::stride] == [on["nn12"][x] for x in S]
+                assert nn["nn21"][::stride] == [on["nn21"][x] for x in U]
+                assert nn["nn22"][::stride] == [on["nn22"][x] for x in U]
     return an
 
 
@@ -91,8 +91,9 @@ def test_analysis_bit_exact_yee(g):
 
 
 def test_analysis_bit_exact_64cube_structure(g):
-    # full-size configuration of the 64^3 workload: ordering and tree only
+    # full-size configuration of the 64^3 workload: ordering, tree, cluster trees, and the
+    # neighbour lists of every compressed front at every 23rd vertex of I^s and of I^u
     p = w.helmholtz7(64, 10)
-    an = _compare(g, p, 64, 1024, 64, check_nn=False)
+    an = _compare(g, p, 64, 1024, 64, stride=23)
     assert len(an.fronts) == 4817
     assert sum(f.compressed for f in an.fronts) == 5

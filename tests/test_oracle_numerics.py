@@ -224,3 +224,33 @@ def test_hodbf_construct_and_invert():
         assert np.linalg.norm(y - np.linalg.solve(F, x)) / np.linalg.norm(np.linalg.solve(F, x)) <= 10 * tol * cond
         xt = inv.applyT(x)
         assert np.linalg.norm(H.applyT(xt) - x) / np.linalg.norm(x) <= 10 * tol * cond
+
+
+def test_oracle_per_front_compression_error_16cube():
+    # Sec. 6.1 / Alg. 5: every compressed front of the 16^3 workload (tol 1e-6) against the same
+    # blocks of the exact elimination in the same ordering (dense assembly, Alg. 1)
+    from oracle import compressed_mf as cm
+    p = w.helmholtz7(16, 8)
+    an = analyze(p, 64, 128, 64)
+    fac, st = cm.compressed_factor(p, an, 1e-6)
+    Ap = dm.permuted_matrix(p, an)
+    cbs, seen = {}, 0
+    for f in an.fronts:
+        F = dm.assemble_sparse(Ap, f)
+        for c in f.children:
+            rel = dm.relative_map(an.fronts[c], f)
+            F[np.ix_(rel, rel)] += cbs.pop(c)
+        s = f.s
+        C = F[s:, s:] - F[s:, :s] @ np.linalg.solve(F[:s, :s], F[:s, s:]) if f.u else None
+        if f.compressed:
+            seen += 1
+            fc = fac[f.id]
+            rel_err = lambda A, B: np.linalg.norm(A - B) / np.linalg.norm(B)
+            assert rel_err(fc.F11.dense(), F[:s, :s]) <= 1e-5
+            if f.u:
+                assert rel_err(fc.F12.dense(), F[:s, s:]) <= 1e-5
+                assert rel_err(fc.F21.dense(), F[s:, :s]) <= 1e-5
+                assert rel_err(fc.C.dense(), C) <= 1e-5
+        if f.parent >= 0:
+            cbs[f.id] = C
+    assert seen == 2
