@@ -190,43 +190,97 @@ def roofline(prof, peaks):
     return r
 
 
+# nominal dense tensor rates of a GB300 (TF32 1.1, bf16 2.25 PFLOP/s): the TF32 ceiling is the
+# measured bf16 peak scaled by their ratio
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak(peaks):
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    return bf16 * TF32_PER_BF16
+
+
 def roofline_front(prof, peaks):
     """The dense fronts' Schur-update GEMMs of the factorization (tcgen05, split TF32: three
-    passes per product) against the TF32 tensor peak, 999 TFLOP/s measured with cuBLAS on this
-    pool (bf16 measured peak x 1/2, the nominal TF32:bf16 ratio, gives 950)."""
+    passes per product) against the TF32 tensor peak (the measured bf16 peak x 1.1 / 2.25)."""
     if not prof or prof["ms"] <= 0:
         return None
     sec = prof["ms"] / 1e3
     alg = prof["flops"] / sec / 1e12
-    peak = 999.0
+    peak = tf32_peak(peaks)
     return {"kernel": "k_gemm_tc<1> (tcgen05 kind::tf32, split precision) + SIMT trailing updates",
             "bound": "tensor", "achieved": alg, "achieved_tensor_passes": 3 * alg, "peak": peak,
             "unit": "TFLOP/s", "frac": alg / peak, "frac_tensor_passes": 3 * alg / peak,
             "launches": prof["launches"], "traffic": None,
-            "peak_source": "TF32 cuBLAS 999 TFLOP/s measured on this GPU model (bench_kernels.py peaks)"}
+            "peak_source": "TF32 = MEASURED_PEAKS.json bf16_tflops x 1.1/2.25 (nominal TF32:bf16 ratio; of measured)"}
 
 
-def cpu_baseline():
-    """The FP64 oracle on a bounded sample of the same workload: the same Helmholtz
-    operator (ppw 10) at 20^3, separators >= 128 HOD-BF compressed at tol 1e-4 with
-    rank cap 64, factor + GMRES(30) solve of 16 RHS to 1e-8, timed on the host cores."""
+def _rel(x, ref):
+    import numpy as np
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+def oracle_sample(n=20, nrhs=16):
+    """The FP64 oracle on a bounded sample of the 64^3 workload: the same Helmholtz operator
+    (ppw 10) at n^3, separators >= 128 HOD-BF compressed at tol 1e-4 with rank cap 64, factor +
+    GMRES(30) solve of nrhs Gaussian RHS (seed 7) to 1e-8, timed on the host cores.  Also returns
+    the oracle's exact solution of the same system (dense multifrontal LU in FP64, untimed), the
+    reference of every GPU result's error."""
     import numpy as np
     import workloads as w
     from oracle.analysis import analyze
-    from oracle import compressed_mf as cm, gmres as gm
-    p = w.helmholtz7(20, 10)
-    b = w.rhs_gaussian(p, 16, 7)
+    from oracle import compressed_mf as cm, dense_mf as dm, gmres as gm
+    p = w.helmholtz7(n, 10)
+    b = w.rhs_gaussian(p, nrhs, 7)
     A = p.to_scipy()
     t0 = time.perf_counter()
     an = analyze(p, 64, 128, 64)
     fac, st = cm.compressed_factor(p, an, 1e-4, max_rank=64)
     X, its, res = gm.gmres(A, b, cm.preconditioner(an, fac), rtol=1e-8)
     dt = time.perf_counter() - t0
+    ane = analyze(p, 64, 10 ** 9)
+    x_exact = dm.solve(p, ane, dm.multifrontal_factor(p, ane)[0], b)
     cores = len(os.sched_getaffinity(0))
-    return {"value": 16 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle: HOD-BF multifrontal factor (tol 1e-4, rank <= 64, separators >= 128) + "
-                      f"GMRES(30) of 16 RHS to 1e-8 on helmholtz7 20^3 (N={p.n}); {dt:.1f} s, "
-                      f"{max(its)} iterations, residual {max(res):.1e}"}
+    return p, b, x_exact, {
+        "value": nrhs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": f"FP64 oracle: HOD-BF multifrontal factor (tol 1e-4, rank <= 64, separators >= 128) + "
+                  f"GMRES(30) of {nrhs} RHS to 1e-8 on helmholtz7 {n}^3 (N={p.n}); {dt:.1f} s, "
+                  f"{max(its)} iterations, residual {max(res):.1e}",
+        "seconds": dt, "err_vs_oracle_exact": _rel(X, x_exact)}
+
+
+def gpu_paths_on(g, torch, p, b, x_exact, nmin, tol=1e-4):
+    """The four GPU variants on one problem: factor s, solve s, solves/s, iterations, residual and
+    the error against the oracle's exact solution x_exact."""
+    import numpy as np
+    nrhs = b.shape[1]
+    stream = torch.cuda.current_stream().cuda_stream
+    variants = {
+        "compressed_c64": dict(nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES),
+        "dense_c64": dict(nmin_sep=10 ** 9, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES),
+        "fp64_exact": dict(nmin_sep=10 ** 9, precision=g.MF_PREC_C128, refine=g.MF_REFINE_IR),
+        "fp64_butterfly": dict(nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C128, refine=g.MF_REFINE_GMRES),
+    }
+    A = p.to_scipy()
+    out = {}
+    for name, kw in variants.items():
+        h = g.analyze_problem(p, stream=stream, **kw)
+        ftol = 0.0 if name == "fp64_exact" else tol
+        h.mf_factor(ftol)                       # warm-up (allocations, graphs)
+        h.mf_solve(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.mf_factor(ftol)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        x, info = h.mf_solve(b)
+        ts = time.perf_counter() - t0
+        res = float(np.max(np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)))
+        out[name] = {"factor_s": tf, "solve_s": ts, "solves_per_s": nrhs / (tf + ts), "iters": int(info.iters),
+                     "max_rel_residual": res, "err_vs_oracle": _rel(x, x_exact)}
+        del h
+    return out
 
 
 def serving(g, w, torch):
@@ -327,7 +381,8 @@ def butterfly_apply(g, w, torch, peaks, nrhs=64):
             "rows": S.rows, "stored_entries": S.storage, "max_rank": S.max_rank, "build_s": S.build_seconds,
             "apply_ms": ms_apply, "alg_gbs": gbs, "hbm_frac": gbs / hbm,
             "tflops": flops / (ms_apply / 1e3) / 1e12, "alu_frac": flops / (ms_apply / 1e3) / 1e12 / FP32_ALU_TFLOPS,
-            "max_rel_err_vs_dense_fp64": err}
+            "max_rel_err_vs_dense_fp64": err, "err_vs_oracle": err,
+            "err_reference": "dense FP64 product K X of the kernel's closed form on three blocks"}
 
 
 def run_reference(args, rank, world):
@@ -335,7 +390,7 @@ def run_reference(args, rank, world):
         return
     vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline()
+        r = oracle_sample()[3]
         if i >= args.warmup:
             vals.append(r["value"])
     v = sum(vals) / len(vals)
@@ -511,7 +566,18 @@ def main():
     if rank == 0 and not args.no_bfapply:
         line["butterfly_apply"] = butterfly_apply(g, w, torch, measured_peaks())
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline()
+        # the cpu_baseline leg: the oracle timed on the 20^3 sample, the GPU paths on the same problem
+        # beside it, and every GPU path's error against the oracle's exact solution of that problem
+        ps, bs, xs, cb = oracle_sample()
+        same = gpu_paths_on(g, torch, ps, bs, xs, nmin=128)
+        cb["gpu_same_problem"] = same
+        cb["gpu_over_oracle"] = same["compressed_c64"]["solves_per_s"] / cb["value"]
+        line["cpu_baseline"] = cb
+        for key, name in (("dense_c64_path", "dense_c64"), ("fp64_path", "fp64_exact"),
+                          ("fp64_butterfly_path", "fp64_butterfly")):
+            if key in line:
+                line[key]["err_vs_oracle_20cube"] = same[name]["err_vs_oracle"]
+        line["err_vs_oracle_20cube"] = same["compressed_c64"]["err_vs_oracle"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(world)
