@@ -107,17 +107,42 @@ def rowid(torch, mf, reps, nmat=256, m=128, n=72):
     return {"kernel": "k_row_id", "shape": [nmat, m, n], "ms": ms, "us_per_matrix": ms * 1e3 / nmat}
 
 
-def _workload(torch, grid):
+def _workload(torch, grid, nmin=1024):
     import workloads as w
     import paper_2007_00202_gb300 as g
     p = w.helmholtz7(grid, 10)
-    h = g.analyze_problem(p, nmin_sep=1024, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_NONE)
+    h = g.analyze_problem(p, nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_NONE)
     return g, p, h
 
 
-def factor(torch, mf, reps, grid=64):
+def extend_add_bytes(h):
+    """Algorithmic bytes of each extend-add launch of the dense levels, in launch order (deepest
+    level first, first then second child): sum of u_child^2 x 24 B (read the child's complex64
+    entry, read and write the parent's)."""
+    ex = h.mf_analysis_export()
+    nf = len(ex["parent"])
+    u = np.diff(ex["upd_ptr"])
+    depth = np.zeros(nf, np.int64)
+    for f in range(nf - 1, -1, -1):
+        if ex["parent"][f] >= 0:
+            depth[f] = depth[ex["parent"][f]] + 1
+    slot = {}
+    seen = {}
+    for f in range(nf):
+        par = int(ex["parent"][f])
+        if par < 0:
+            continue
+        k = seen.get(par, 0)
+        seen[par] = k + 1
+        key = (int(depth[par]), k)
+        slot[key] = slot.get(key, 0) + int(u[f]) ** 2
+    order = sorted(slot, key=lambda t: (-t[0], t[1]))
+    return [(d, k, 24.0 * slot[(d, k)]) for d, k in order]
+
+
+def factor(torch, mf, reps, grid=64, nmin=1024):
     import time
-    g, p, h = _workload(torch, grid)
+    g, p, h = _workload(torch, grid, nmin)
     h.mf_factor(1e-4)
     torch.cuda.synchronize()
     c0 = g.lib().mf_launch_counter()
@@ -127,7 +152,9 @@ def factor(torch, mf, reps, grid=64):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     torch.cuda.profiler.stop()
-    return {"item": "compressed factorization", "grid": grid, "s": dt, "launches": g.lib().mf_launch_counter() - c0}
+    return {"item": "factorization", "grid": grid, "nmin_sep": nmin, "s": dt,
+            "launches": g.lib().mf_launch_counter() - c0,
+            "extend_add_bytes_per_launch": extend_add_bytes(h)[:4]}
 
 
 def solve(torch, mf, reps, grid=64):
@@ -169,9 +196,11 @@ def bfapply(torch, mf, reps, blocks=200, nrhs=64):
     ms = _time(torch, lambda: S.apply(nrhs, dX.data_ptr(), dY.data_ptr()), reps)
     torch.cuda.profiler.stop()
     by = 8.0 * S.storage + 2.0 * 8.0 * S.rows * nrhs
+    fl, lb = S.apply_counts(nrhs)
     hbm = _peaks().get("hbm_gbs", 6800.0)
     return {"item": "butterfly apply", "blocks": blocks, "rows": S.rows, "stored_entries": S.storage,
-            "nrhs": nrhs, "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm}
+            "nrhs": nrhs, "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm,
+            "level_traffic_bytes": lb, "level_traffic_gbs": lb / ms / 1e6, "tflops": fl / ms / 1e9}
 
 
 def peaks(torch, mf, reps):
@@ -202,13 +231,16 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--blocks", type=int, default=200)
+    ap.add_argument("--nmin", type=int, default=1024)
     args = ap.parse_args()
     import torch
     from paper_2007_00202_gb300 import build, mf
     build.build()
     for w in args.which:
-        if w in ("factor", "solve"):
-            r = {"factor": factor, "solve": solve}[w](torch, mf, args.reps, args.grid)
+        if w == "factor":
+            r = factor(torch, mf, args.reps, args.grid, args.nmin)
+        elif w == "solve":
+            r = solve(torch, mf, args.reps, args.grid)
         elif w == "bfapply":
             r = bfapply(torch, mf, args.reps, args.blocks)
         else:

@@ -86,6 +86,8 @@ typedef struct {
   int32_t gpu_launches_factor;  /* kernel launches of one factorization                */
   int32_t gpu_launches_solve;   /* kernel launches of one preconditioner application   */
   int32_t reserved;
+  double arena_peak_bytes;      /* compressed fronts: peak use of the device arenas (factors + work) */
+  double arena_capacity_bytes;  /* compressed fronts: device memory reserved for those arenas      */
 } mf_stats_t;
 
 typedef struct mf_handle mf_handle;
@@ -199,8 +201,11 @@ int mf_gemm_c64(int32_t engine, int32_t m, int32_t n, int32_t k, const float* A,
  *   (trans_a = 1, A stored k x m), B: k x n, C: m x n, all row-major, n <= 128,
  *   each matrix given by its real plane, leading dimension and imaginary-plane offset.
  * ksplit: number of CTAs of a thread-block cluster sharing one 32-row tile's K range
- * (1, 2, 4 or 8), 0 = the library's choice.  No alignment requirements.
- * Runs on `stream` and waits for it.  Errors: MF_ERR_ARG, MF_ERR_CUDA.
+ * (1, 2, 4 or 8), 0 = the library's choice, or -1 for the tensor-core kernel (n <= 64:
+ * tcgen05 kind::tf32, three split-precision passes; the kernel the library uses for
+ * complex64 butterfly level products with at most 64 vectors).  No alignment requirements.
+ * Runs on `stream` and waits for it.  Errors: MF_ERR_ARG, MF_ERR_TIMEOUT (a bounded wait of
+ * the tensor-core kernel expired), MF_ERR_CUDA.
  */
 int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const float* A, int64_t lda, int64_t pla,
                      const float* B, int64_t ldb, int64_t plb, float* C, int64_t ldc, int64_t plc, float alpha,
@@ -312,6 +317,11 @@ int mf_green_build(int32_t nblk, const int32_t* m, double k, double h, double to
 /* rows of the set, stored complex entries, largest ID rank, build wall time */
 int mf_green_info(const mf_bfset* s, int64_t* rows, double* storage_entries, int32_t* max_rank,
                   double* build_seconds);
+/* Work of one mf_green_apply with nrhs vectors (after a first call with that nrhs): real flops
+ * (8 m n k per complex block product) and the bytes its block products move when each level's
+ * vectors go through device memory (factor blocks + input + output vectors of every product);
+ * MF_ERR_STATE before the first call. */
+int mf_green_apply_counts(const mf_bfset* s, int32_t nrhs, double* flops, double* bytes);
 /* host copies of the source (z = 0) and target (z = h) points, rows x 3 each, in the set's row order */
 int mf_green_points(const mf_bfset* s, double* P, double* Q);
 /*

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <type_traits>
 
 #include "bf_engine.h"
 
@@ -334,6 +335,7 @@ void BFContext<T>::check_status() {
   int32_t v = 0;
   MF_CUDA(cudaMemcpyAsync(&v, status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   sync();
+  if (v == 2) throw TimeoutError("a bounded wait in a tensor-core kernel expired");
   if (v != 0) throw SingularError("singular block in a compressed front (zero pivot or indefinite normal equations)");
 }
 
@@ -349,10 +351,38 @@ void BFContext<T>::gemm(std::vector<GemmDesc<T>>& descs) {
     two = two || d.k1 > 0;
     D.push_back(d);
     flops += 8.0 * d.m * d.n * d.k;
+    bytes += gemm_bytes(d);
     maxn = std::max(maxn, (int)d.n);
     maxk = std::max(maxk, (int)d.k);
   }
   if (D.empty()) return;
+  if constexpr (std::is_same<T, float>::value) {
+    // complex64 products of 48 to 64 vectors: the tensor-core kernel (the 64 vectors fill its
+    // M = 128 rows with both planes; narrower blocks run faster on the SIMT kernel's 16- and
+    // 32-column tiles, measured on the solve's 16 right-hand sides)
+    bool tc = maxn >= 48;
+    for (auto& d : D) tc = tc && gemm_nrhs_tc_ok(d);
+    if (tc) {
+      std::vector<GemmTile> tl;
+      for (size_t idx = 0; idx < D.size(); ++idx)
+        for (int i = 0; i < (D[idx].m + gemm_nrhs_tc_rows() - 1) / gemm_nrhs_tc_rows(); ++i)
+        tl.push_back({(int)idx, i, 0, 0});
+      const GemmDesc<T>* dd = static_cast<const GemmDesc<T>*>(upload(D.data(), D.size() * sizeof(GemmDesc<T>)));
+      const GemmTile* dt = stage(tl.data(), tl.size());
+      auto go = [&] { launch_gemm_nrhs_tc(dd, dt, (int)tl.size(), status.template as<int32_t>(), st); };
+      if (prof && prof->on) {
+        double fl = 0, by = 0;
+        for (auto& d : D) {
+          fl += 8.0 * d.m * d.n * d.k;
+          by += gemm_bytes(d);
+        }
+        prof->time(st, fl, by, go);
+      } else {
+        go();
+      }
+      return;
+    }
+  }
   // narrow products (blocks of vectors, n <= 128): 32-row tiles of the streaming kernel; else 64 x 64 tiles
   const int nb = gemm_nrhs_width(maxn, sizeof(T));
   const int tr = nb ? GEMM_NRHS_ROWS : GEMM_TILE;
@@ -589,6 +619,24 @@ void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vecto
         o += ranks[p];
       }
     };
+    // the same with the blocks laid out in the order `order` (a permutation of the block indices)
+    auto vec_buf_ordered = [&](const std::vector<int>& ranks, const std::vector<int>& order,
+                               std::vector<Blk<T>>& out) {
+      size_t tot = 0;
+      for (int r : ranks) tot += (size_t)r;
+      Blk<T> all;
+      all.rows = (int)tot;
+      all.cols = k;
+      all.ld = k;
+      all.plane = (int64_t)std::max<size_t>(tot, 1) * k;
+      all.p = scratch.takeT<T>(2 * (size_t)all.plane);
+      out.resize(ranks.size());
+      size_t o = 0;
+      for (int p : order) {
+        out[p] = all.sub((int)o, 0, ranks[p], k);
+        o += ranks[p];
+      }
+    };
     int stg = 0;
     if (!transpose) {
       // right half: level 0 (V), levels 1..lc (W)
@@ -642,22 +690,30 @@ void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vecto
         std::vector<int> rk;
         for (int i = 0; i < (1 << (l + 1)); ++i)
           for (int j = 0; j < (1 << (L - l - 1)); ++j) rk.push_back(bf.rr(l + 1, i, j));
-        vec_buf(rk, nxt);
         if (two) {
-          for (int i2 = 0; i2 < (1 << (l + 1)); ++i2)
+          // both output halves (2i, j2) and (2i+1, j2) read the same two inputs (i, 2j2), (i, 2j2+1),
+          // and the stored R blocks hold the rows of both halves: one two-term product computes
+          // the pair, into a level buffer laid out so that the pair's blocks are adjacent
+          std::vector<int> order;
+          for (int i = 0; i < (1 << l); ++i)
+            for (int j2 = 0; j2 < (1 << (L - l - 1)); ++j2)
+              for (int h = 0; h < 2; ++h) order.push_back(bf.pidx(l + 1, 2 * i + h, j2));
+          vec_buf_ordered(rk, order, nxt);
+          for (int i = 0; i < (1 << l); ++i)
             for (int j2 = 0; j2 < (1 << (L - l - 1)); ++j2) {
-              const int i = i2 / 2, p0 = bf.pidx(l, i, 2 * j2), p1 = bf.pidx(l, i, 2 * j2 + 1);
-              const int r1 = bf.rr(l + 1, 2 * i, j2);
-              const int rows0 = (i2 % 2 == 0) ? 0 : r1;
-              const int nrow = bf.rr(l + 1, i2, j2);
+              const int p0 = bf.pidx(l, i, 2 * j2), p1 = bf.pidx(l, i, 2 * j2 + 1);
+              const int nrow = bf.rr(l + 1, 2 * i, j2) + bf.rr(l + 1, 2 * i + 1, j2);
               const Blk<T>& R0 = bf.U[l][p0];
               const Blk<T>& R1 = bf.U[l][p1];
+              Blk<T> out = nxt[bf.pidx(l + 1, 2 * i, j2)];
+              out.rows = nrow;
               stages[stg].push_back(gdesc2<T>(nrow, k, bf.rr(l, i, 2 * j2), bf.rr(l, i, 2 * j2 + 1), 0, 0, one, zero,
-                                              R0.sub(rows0, 0, nrow, R0.cols), ys[p0], R1.sub(rows0, 0, nrow, R1.cols),
-                                              ys[p1], nxt[bf.pidx(l + 1, i2, j2)]));
+                                              R0.sub(0, 0, nrow, R0.cols), ys[p0], R1.sub(0, 0, nrow, R1.cols),
+                                              ys[p1], out));
             }
           stg += 1;
         } else {
+          vec_buf(rk, nxt);
           for (int t = 0; t < 2; ++t) {
             for (int i2 = 0; i2 < (1 << (l + 1)); ++i2)
               for (int j2 = 0; j2 < (1 << (L - l - 1)); ++j2) {

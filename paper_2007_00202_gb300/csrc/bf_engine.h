@@ -238,6 +238,7 @@ class BFContext {
   Arena persist, scratch;
   DevMem status;
   double flops = 0;
+  double bytes = 0;   // algorithmic bytes of the products issued (factor blocks, inputs and outputs)
   int max_rank_seen = 0;
   int64_t n_id = 0;
 

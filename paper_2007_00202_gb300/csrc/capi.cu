@@ -62,6 +62,8 @@ int guarded(mf_handle* h, F&& fn) {
     return fn();
   } catch (const mf::SingularError& e) {
     return fail(h, MF_ERR_SINGULAR, e.what());
+  } catch (const mf::TimeoutError& e) {
+    return fail(h, MF_ERR_TIMEOUT, e.what());
   } catch (const CudaError& e) {
     std::string m = e.what();
     int code = (m.find("out of memory") != std::string::npos || m.find("cudaMalloc") != std::string::npos)
@@ -402,6 +404,16 @@ int mf_factor(mf_handle* h, double tol) {
       const size_t per = h->opt.max_rank > 0 ? 10000 : 40000;
       eo.persist_bytes = any_comp ? std::max<size_t>(size_t(8) << 30, comp_n * 20000 * el) : 0;
       eo.scratch_bytes = any_comp ? std::max<size_t>(size_t(4) << 30, comp_n * per * el) : 0;
+      // the two construction contexts hold two such pairs: keep them within 70 % of the free memory
+      size_t fr = 0, tot = 0;
+      if (any_comp && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+        const double want = 2.0 * (double)(eo.persist_bytes + eo.scratch_bytes), room = 0.7 * (double)fr;
+        if (want > room) {
+          const double f = room / want;
+          eo.persist_bytes = (size_t)(f * (double)eo.persist_bytes);
+          eo.scratch_bytes = (size_t)(f * (double)eo.scratch_bytes);
+        }
+      }
       h->eng = h->opt.precision == MF_PREC_C128 ? mf::make_engine_c128(h->an, h->A, h->stream, eo)
                                                : mf::make_engine_c64(h->an, h->A, h->stream, eo);
       h->eng->set_profiling(h->profile);
@@ -497,6 +509,7 @@ int mf_stats(const mf_handle* h, mf_stats_t* out) {
   if (h->eng) {
     out->factor_flops = h->eng->factor_flops();
     out->factor_bytes = h->eng->factor_bytes();
+    h->eng->arena_usage(out->arena_peak_bytes, out->arena_capacity_bytes);
     out->gpu_launches_factor = h->eng->launches_factor();
     out->max_rank = h->eng->max_rank();
   }
@@ -573,8 +586,9 @@ int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const flo
   if (m <= 0 || n <= 0 || n > 128 || k <= 0 || !A || !B || !C || (trans_a != 0 && trans_a != 1) ||
       lda < (trans_a ? m : k) || ldb < n || ldc < n)
     return fail(nullptr, MF_ERR_ARG, "invalid narrow-GEMM arguments");
-  if (ksplit != 0 && ksplit != 1 && ksplit != 2 && ksplit != 4 && ksplit != 8)
-    return fail(nullptr, MF_ERR_ARG, "ksplit must be 0, 1, 2, 4 or 8");
+  if (ksplit != -1 && ksplit != 0 && ksplit != 1 && ksplit != 2 && ksplit != 4 && ksplit != 8)
+    return fail(nullptr, MF_ERR_ARG, "ksplit must be -1, 0, 1, 2, 4 or 8");
+  if (ksplit == -1 && n > 64) return fail(nullptr, MF_ERR_ARG, "the tensor-core kernel takes n <= 64");
   return guarded(nullptr, [&]() -> int {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     mf::GemmDesc<float> d;
@@ -583,6 +597,22 @@ int mf_gemm_nrhs_c64(int32_t trans_a, int32_t m, int32_t n, int32_t k, const flo
     d.B = {const_cast<float*>(B), plb, ldb};
     d.C = {C, plc, ldc};
     std::vector<mf::GemmTile> tl;
+    if (ksplit == -1) {
+      const int tr = mf::gemm_nrhs_tc_rows();
+      for (int i = 0; i < (m + tr - 1) / tr; ++i) tl.push_back({0, i, 0, 0});
+      DevMem dd, dt, ds;
+      mf::upload(dd, std::vector<mf::GemmDesc<float>>{d}, st);
+      mf::upload(dt, tl, st);
+      ds.alloc(sizeof(int32_t));
+      MF_CUDA(cudaMemsetAsync(ds.p, 0, sizeof(int32_t), st));
+      mf::launch_gemm_nrhs_tc(dd.as<mf::GemmDesc<float>>(), dt.as<mf::GemmTile>(), (int)tl.size(), ds.as<int32_t>(), st);
+      MF_CUDA(cudaGetLastError());
+      int32_t stat = 0;
+      MF_CUDA(cudaMemcpyAsync(&stat, ds.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      MF_CUDA(cudaStreamSynchronize(st));
+      if (stat) return fail(nullptr, MF_ERR_TIMEOUT, "a bounded wait in the tensor-core kernel expired");
+      return MF_OK;
+    }
     const int nb = mf::gemm_nrhs_width(n, sizeof(float));
     for (int i = 0; i < (m + mf::GEMM_NRHS_ROWS - 1) / mf::GEMM_NRHS_ROWS; ++i)
       for (int j = 0; j < (n + nb - 1) / nb; ++j) tl.push_back({0, i, j, 0});

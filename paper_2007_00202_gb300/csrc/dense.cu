@@ -184,32 +184,122 @@ void launch_assemble_A(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, in
 
 // ---------------------------------------------------------------------------
 // Extend-add (Sec. 2 step 1): F_parent[rel(i), rel(j)] += C_child[i, j].
-// One warp per child row, coalesced reads along the row.
+// One CTA per EA_TI x EA_TJ tile of a child's block: the tile's rows are read with
+// 16-byte loads (when the block's rows and planes are 16-byte aligned) into shared memory,
+// then scattered.  F11, F21 and C parts of the parent are row-major in the parent's column
+// index, so those entries are written with lanes along the child's columns; the F12 part is
+// stored transposed (row = update position), so its entries are written with lanes along the
+// child's rows, which keeps consecutive lanes on consecutive addresses in both cases.  The
+// two children of a front run as separate launches, so no entry is updated twice at once.
 // ---------------------------------------------------------------------------
+constexpr int EA_TI = 32, EA_TJ = 64;
+
 template <typename T>
-__global__ void k_extend_add(const ExtendAddItem<T>* items, const FrontDev<T>* fronts) {
+__global__ void __launch_bounds__(256) k_extend_add(const ExtendAddItem<T>* items, const FrontDev<T>* fronts,
+                                                    int tiles_j) {
   const ExtendAddItem<T> it = items[blockIdx.y];
+  const int ti = blockIdx.x / tiles_j, tj = blockIdx.x % tiles_j;
+  const int i0 = ti * EA_TI, j0 = tj * EA_TJ;
+  if (i0 >= it.uc || j0 >= it.uc) return;
   const FrontDev<T> f = fronts[it.parent];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (i >= it.uc) return;
-  const int ri = it.rel[i];
-  const T* cr = it.Cc + (int64_t)i * it.ldc;
+  __shared__ T sr[EA_TI][EA_TJ + 1], si[EA_TI][EA_TJ + 1];
+  __shared__ int32_t rr[EA_TI], rc[EA_TJ];
+  const int tid = threadIdx.x;
+  const int ni = min(EA_TI, it.uc - i0), nj = min(EA_TJ, it.uc - j0);
+  if (tid < EA_TI) rr[tid] = tid < ni ? it.rel[i0 + tid] : 0;
+  if (tid < EA_TJ) rc[tid] = tid < nj ? it.rel[j0 + tid] : 0;
+  constexpr int V = 16 / (int)sizeof(T);
+  const bool vec = ((reinterpret_cast<uintptr_t>(it.Cc) | ((uintptr_t)it.ldc * sizeof(T)) |
+                     ((uintptr_t)it.plane_c * sizeof(T))) & 15) == 0;
+  const T* cr = it.Cc + (int64_t)i0 * it.ldc + j0;
   const T* ci = cr + it.plane_c;
-  for (int j = lane; j < it.uc; j += 32) {
-    const int rj = it.rel[j];
-    T vr = cr[j], vi = ci[j];
-    T* dst;
-    int64_t off, pl;
-    if (ri < f.s) {
-      if (rj < f.s) { dst = f.LU; off = (int64_t)ri * f.ls + rj; pl = f.pl_ss; }
-      else { dst = f.F12w; off = (int64_t)(rj - f.s) * f.ls + ri; pl = f.pl_us; }
-    } else {
-      if (rj < f.s) { dst = f.F21w; off = (int64_t)(ri - f.s) * f.ls + rj; pl = f.pl_us; }
-      else { dst = f.C; off = (int64_t)(ri - f.s) * f.lu + (rj - f.s); pl = f.pl_uu; }
+  if (vec && nj == EA_TJ) {
+    constexpr int CH = EA_TI * EA_TJ / V;   // 16-byte chunks per plane
+    for (int c = tid; c < 2 * CH; c += 256) {
+      const int pl = c / CH, cc = c % CH, i = cc / (EA_TJ / V), jv = (cc % (EA_TJ / V)) * V;
+      if (i < ni) {
+        const T* src = (pl ? ci : cr) + (int64_t)i * it.ldc + jv;
+        T buf[V];
+        *reinterpret_cast<uint4*>(buf) = *reinterpret_cast<const uint4*>(src);
+#pragma unroll
+        for (int e = 0; e < V; ++e) (pl ? si : sr)[i][jv + e] = buf[e];
+      }
     }
-    dst[off] += vr;
-    dst[off + pl] += vi;
+  } else {
+    for (int e = tid; e < EA_TI * EA_TJ; e += 256) {
+      const int i = e / EA_TJ, j = e % EA_TJ;
+      if (i < ni && j < nj) {
+        sr[i][j] = cr[(int64_t)i * it.ldc + j];
+        si[i][j] = ci[(int64_t)i * it.ldc + j];
+      }
+    }
+  }
+  __syncthreads();
+  const int s = f.s;
+  // Every parent entry of the tile is distinct (rel is injective), so each thread first gathers
+  // all the parent values it updates, then adds and stores them: the loads of a pass are in
+  // flight together instead of one read-modify-write round trip at a time.
+  constexpr int PER = EA_TI * EA_TJ / 256;   // 8 entries per thread and pass
+  // pass 1, the F11, F21 and C parts: lanes along j
+  {
+    T* dp[PER];
+    int64_t pl[PER];
+    T ar[PER], ai[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q, i = e / EA_TJ, j = e % EA_TJ;
+      dp[q] = nullptr;
+      if (i >= ni || j >= nj) continue;
+      const int ri = rr[i], rj = rc[j];
+      if (ri < s) {
+        if (rj >= s) continue;   // F12: pass 2
+        dp[q] = f.LU + (int64_t)ri * f.ls + rj; pl[q] = f.pl_ss;
+      } else if (rj < s) {
+        dp[q] = f.F21w + (int64_t)(ri - s) * f.ls + rj; pl[q] = f.pl_us;
+      } else {
+        dp[q] = f.C + (int64_t)(ri - s) * f.lu + (rj - s); pl[q] = f.pl_uu;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+      if (dp[q]) {
+        ar[q] = dp[q][0];
+        ai[q] = dp[q][pl[q]];
+      }
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+      if (dp[q]) {
+        const int e = tid + 256 * q, i = e / EA_TJ, j = e % EA_TJ;
+        dp[q][0] = ar[q] + sr[i][j];
+        dp[q][pl[q]] = ai[q] + si[i][j];
+      }
+  }
+  // pass 2, the F12 part (stored transposed, u x s): lanes along i
+  {
+    T* dp[PER];
+    T ar[PER], ai[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q, j = e / EA_TI, i = e % EA_TI;
+      dp[q] = nullptr;
+      if (i >= ni || j >= nj) continue;
+      const int ri = rr[i], rj = rc[j];
+      if (ri >= s || rj < s) continue;
+      dp[q] = f.F12w + (int64_t)(rj - s) * f.ls + ri;
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+      if (dp[q]) {
+        ar[q] = dp[q][0];
+        ai[q] = dp[q][f.pl_us];
+      }
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+      if (dp[q]) {
+        const int e = tid + 256 * q, j = e / EA_TI, i = e % EA_TI;
+        dp[q][0] = ar[q] + sr[i][j];
+        dp[q][f.pl_us] = ai[q] + si[i][j];
+      }
   }
 }
 
@@ -217,9 +307,10 @@ template <typename T>
 void launch_extend_add(const ExtendAddItem<T>* d_items, int nitems, const FrontDev<T>* d_fronts, int max_uc,
                        cudaStream_t st) {
   if (nitems <= 0 || max_uc <= 0) return;
-  dim3 grid((max_uc + 7) / 8, nitems);
+  const int tiles_i = (max_uc + EA_TI - 1) / EA_TI, tiles_j = (max_uc + EA_TJ - 1) / EA_TJ;
+  dim3 grid(tiles_i * tiles_j, nitems);
   g_launches++;
-  k_extend_add<T><<<grid, 256, 0, st>>>(d_items, d_fronts);
+  k_extend_add<T><<<grid, 256, 0, st>>>(d_items, d_fronts, tiles_j);
 }
 
 // ---------------------------------------------------------------------------

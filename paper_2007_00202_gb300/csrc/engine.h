@@ -24,6 +24,10 @@ struct CudaError : std::runtime_error {
 struct SingularError : std::runtime_error {
   using std::runtime_error::runtime_error;
 };
+// a bounded device-side wait expired (MF_ERR_TIMEOUT)
+struct TimeoutError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
 
 #define MF_CUDA(x)                                                                                         \
   do {                                                                                                     \
@@ -196,6 +200,8 @@ class EngineBase {
   // compressed front or has no such operator.
   virtual int front_apply(int fid, int which, int nrhs, const double* x, double* y) { return -1; }
   virtual double compressed_seconds() const { return 0; }
+  // peak use and capacity of the compressed fronts' device arenas (all contexts)
+  virtual void arena_usage(double& peak, double& capacity) const { peak = capacity = 0; }
   // Event timing of two kernel families (see mf_profile in mf.h):
   // prof[0] the narrow GEMM (k_gemm_nrhs) in factor() and apply_precond(), prof[1] the
   // factor's dense front GEMMs (Schur updates).

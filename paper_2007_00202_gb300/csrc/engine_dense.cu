@@ -136,7 +136,7 @@ class DenseEngine : public EngineBase {
     MF_CUDA(cudaStreamSynchronize(st_));
     prof[0].collect();
     prof[1].collect();
-    if (stat == 2) throw CudaError("a bounded wait in the tensor-core GEMM expired (MF_ERR_TIMEOUT)");
+    if (stat == 2) throw TimeoutError("a bounded wait in a tensor-core kernel expired");
     if (stat != DEV_OK) throw SingularError("zero pivot in a dense front");
   }
 
@@ -226,6 +226,15 @@ class DenseEngine : public EngineBase {
 
   double factor_flops() const override { return flops_ + comp_flops_; }
   double factor_bytes() const override { return factor_bytes_; }
+  void arena_usage(double& peak, double& capacity) const override {
+    peak = capacity = 0;
+    if (!comp_) return;
+    for (int w = 0; w < (comp_->cx2 ? 2 : 1); ++w) {
+      const BFContext<T>& c = w == 0 ? comp_->cx : *comp_->cx2;
+      peak += (double)c.persist.peak() + (double)c.scratch.peak();
+      capacity += (double)c.persist.capacity() + (double)c.scratch.capacity();
+    }
+  }
   int launches_factor() const override { return nlaunch_factor_; }
   int launches_solve(int nrhs) override { return solve_prog(nrhs_bucket(nrhs)).nlaunch + 2; }
 

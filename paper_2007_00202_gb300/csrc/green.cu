@@ -98,6 +98,7 @@ struct GreenPlan {
   mf::DevMem dblob;
   cudaGraphExec_t exec = nullptr;
   int glaunch = 0;
+  double flops = 0, bytes = 0;   // counted over the eager first call
   ~GreenPlan() {
     if (exec) cudaGraphExecDestroy(exec);
     if (hblob) cudaFreeHost(hblob);
@@ -244,6 +245,17 @@ int mf_green_info(const mf_bfset* s, int64_t* rows, double* storage, int32_t* ma
   return MF_OK;
 }
 
+int mf_green_apply_counts(const mf_bfset* s, int32_t nrhs, double* flops, double* bytes) {
+  if (!s) return MF_ERR_ARG;
+  for (auto& p : s->plans)
+    if (p->nrhs == nrhs && p->state > 0) {
+      if (flops) *flops = p->flops;
+      if (bytes) *bytes = p->bytes;
+      return MF_OK;
+    }
+  return MF_ERR_STATE;
+}
+
 int mf_green_points(const mf_bfset* s, double* P, double* Q) {
   if (!s) return MF_ERR_ARG;
   if (P) std::memcpy(P, s->P.data(), s->P.size() * sizeof(double));
@@ -279,9 +291,12 @@ int mf_green_apply(mf_bfset* s, int32_t nrhs, const float* x, float* y) {
         }
       }
       cx.gemm(g);
+      // every off-diagonal butterfly of every level in one stage-merged apply: the butterflies of
+      // one block's levels have different level counts, so their last (accumulating) stages fall
+      // in different launches and never write the same rows at once
+      std::vector<const mf::DBF<float>*> bfs;
+      std::vector<Blk<float>> xs, ys;
       for (int l = 1; l <= maxLH; ++l) {
-        std::vector<const mf::DBF<float>*> bfs;
-        std::vector<Blk<float>> xs, ys;
         for (size_t b = 0; b < s->H.size(); ++b) {
           const auto& H = *s->H[b];
           if (l > H.LH) continue;
@@ -292,8 +307,8 @@ int mf_green_apply(mf_bfset* s, int32_t nrhs, const float* x, float* y) {
             ys.push_back(Y.sub((int)(s->off[b] + rr.a), 0, (int)(rr.b - rr.a), nrhs));
           }
         }
-        cx.apply(bfs, xs, ys, false, true);
       }
+      cx.apply(bfs, xs, ys, false, true);
       cx.scratch.release(mk);   // stream order makes later reuse of the scratch safe
     };
     GreenPlan* pl = nullptr;
@@ -308,11 +323,14 @@ int mf_green_apply(mf_bfset* s, int32_t nrhs, const float* x, float* y) {
     }
     if (pl->state == 2 && cx.scratch.mark() != pl->mark) pl->state = 3;   // scratch moved under the graph
     if (pl->state == 0 || pl->state == 3) {
+      const double f0 = cx.flops, b0 = cx.bytes;
       if (pl->state == 0) cx.count_begin();
       body();
       if (pl->state == 0) {
         pl->blob = cx.count_end();
         pl->state = 1;
+        pl->flops = cx.flops - f0;
+        pl->bytes = cx.bytes - b0;
       }
     } else {
       if (pl->state == 1) {   // capture on the private stream

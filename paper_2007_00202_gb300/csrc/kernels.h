@@ -61,6 +61,15 @@ void launch_gemm_tc(const GemmDesc<float>* d_desc, const GemmTile* d_tiles, int 
                     cudaStream_t st, bool split = true);
 int gemm_tc_tile();
 
+// tcgen05 (kind::tf32, split precision) narrow products for complex64 blocks of at most 64 vectors:
+// C = alpha (op(A) B [+ A2 B2]) + beta C, transB = 0, n <= 64, any m and k (tiles {desc, tm, 0}
+// of gemm_nrhs_tc_rows() rows); persistent CTAs, two per SM.  status receives 2 if a bounded
+// wait expired.
+bool gemm_nrhs_tc_ok(const GemmDesc<float>& d);
+int gemm_nrhs_tc_rows();
+void launch_gemm_nrhs_tc(const GemmDesc<float>* d_desc, const GemmTile* d_tiles, int ntiles, int32_t* status,
+                         cudaStream_t st);
+
 // Dense front assembly and extend-add (Sec. 2 step 1).
 template <typename T>
 void launch_assemble_A(FrontDev<T>* d_fronts, const int32_t* d_flist, int nf, int maxrows, const int64_t* rowptr,

@@ -48,7 +48,8 @@ class mf_stats_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("nfronts", C.c_int64), ("ncompressed", C.c_int64), ("tree_levels", C.c_int32),
                 ("max_rank", C.c_int32), ("factor_flops", C.c_double), ("factor_bytes", C.c_double),
                 ("factor_seconds", C.c_double), ("precision", C.c_int32), ("gpu_launches_factor", C.c_int32),
-                ("gpu_launches_solve", C.c_int32), ("reserved", C.c_int32)]
+                ("gpu_launches_solve", C.c_int32), ("reserved", C.c_int32), ("arena_peak_bytes", C.c_double),
+                ("arena_capacity_bytes", C.c_double)]
 
 
 class mf_kernel_profile_t(C.Structure):
@@ -94,6 +95,7 @@ SIGNATURES = {
     "mf_green_info": (C.c_int, [_P, _I64P, _DP, _I32P, _DP]),
     "mf_green_points": (C.c_int, [_P, _DP, _DP]),
     "mf_green_apply": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "mf_green_apply_counts": (C.c_int, [_P, C.c_int32, _DP, _DP]),
     "mf_green_destroy": (None, [_P]),
     "mf_row_id_c64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, C.c_double, C.c_int32, _P, _P, _P, _P]),
     "mf_row_id_c64_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, C.c_double, C.c_int32, _P, _P, _P,
@@ -339,6 +341,12 @@ class GreenSet:
 
     def apply(self, nrhs, d_x, d_y):
         _check(lib().mf_green_apply(self.ptr, nrhs, C.c_void_p(d_x), C.c_void_p(d_y)))
+
+    def apply_counts(self, nrhs):
+        """(flops, bytes) of one apply with nrhs vectors: bytes with each level's vectors in memory."""
+        f, b = C.c_double(), C.c_double()
+        _check(lib().mf_green_apply_counts(self.ptr, nrhs, C.byref(f), C.byref(b)))
+        return f.value, b.value
 
     def __del__(self):
         if getattr(self, "ptr", None):

@@ -75,3 +75,30 @@ def test_gemm_nrhs_against_fp64(tk, trans_a, m, n, k, beta, ksplit):
     scale = np.sqrt(k) * np.abs(A).max() * np.abs(B).max()
     assert np.abs(out - ref).max() / scale < 2e-5
     assert float(dC[0, :, n:].abs().max()) == float(_planar(torch, C0, ldc)[0, :, n:].abs().max())
+
+
+@pytest.mark.parametrize("trans_a", [0, 1])
+@pytest.mark.parametrize("m,n,k,beta", [(1, 1, 1, 0.0), (5, 64, 7, 1.0), (40, 64, 80, 0.0), (100, 64, 37, 1.0),
+                                        (128, 64, 16, 0.0), (129, 64, 33, 1.0), (300, 16, 260, 1.0),
+                                        (77, 3, 1000, 0.0), (600, 64, 64, 1.0)])
+def test_gemm_nrhs_tensor_core_against_fp64(tk, trans_a, m, n, k, beta):
+    # the tcgen05 narrow kernel (ksplit = -1): transposed products with the 64 vectors on the MMA's
+    # M dimension, split TF32; ragged m, n, k (partial 128-row tiles, partial 16-wide K chunks)
+    import paper_2007_00202_gb300.mf as mf
+    torch = tk
+    rng = np.random.default_rng(11 * m + n + 3 * k + trans_a)
+    A = rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))
+    B = rng.standard_normal((k, n)) + 1j * rng.standard_normal((k, n))
+    C0 = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+    As = A.T.copy() if trans_a else A
+    lda = As.shape[1] + 1
+    ldb, ldc = n + 2, n + 1
+    dA, dB, dC = _planar(torch, As, lda), _planar(torch, B, ldb), _planar(torch, C0, ldc)
+    mf.mf_gemm_nrhs_c64(trans_a, m, n, k, dA.data_ptr(), lda, As.shape[0] * lda, dB.data_ptr(), ldb, k * ldb,
+                        dC.data_ptr(), ldc, m * ldc, -1.0, beta, -1, 0)
+    torch.cuda.synchronize()
+    out = dC[0, :, :n].double().cpu().numpy() + 1j * dC[1, :, :n].double().cpu().numpy()
+    ref = -(A @ B) + beta * C0
+    scale = np.sqrt(k) * np.abs(A).max() * np.abs(B).max()
+    assert np.abs(out - ref).max() / scale < 2e-5
+    assert float(dC[0, :, n:].abs().max()) == float(_planar(torch, C0, ldc)[0, :, n:].abs().max())
