@@ -36,6 +36,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=64)
+    ap.add_argument("--problem", default="helmholtz", choices=["helmholtz", "yee", "poisson"],
+                    help="helmholtz: 7-point damped Helmholtz (ppw 10), Gaussian RHS seed 7; yee: curl-curl on "
+                         "grid^3 Yee cells with PEC walls (ppw 10), edge-dipole RHS seed 11; poisson: k = 0")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--nmin", type=int, default=1024, help="separators >= nmin are HOD-BF compressed")
     ap.add_argument("--no-dense", action="store_true", help="skip the all-dense complex64 comparison step")
@@ -43,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) measurement")
     ap.add_argument("--no-bfapply", action="store_true", help="skip the batched butterfly-apply measurement")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="run the full serving workload (32^3 + 64^3 + 100^3 resident, 2000 requests of 1-256 RHS) "
+                         "instead of the bounded one; takes several minutes")
     return ap.parse_args()
 
 
@@ -335,6 +341,69 @@ def serving(g, w, torch):
             "mean_batch_rhs": float(np.mean(batches)), "max_rel_residual_checked": worst}
 
 
+def serving_full(g, w, torch, nreq=2000):
+    """The serving workload at its stated size: helmholtz7 32^3, 64^3 and 100^3 (complex64, separators
+    >= 1024 HOD-BF at tol 1e-4, rank <= 64) factored and resident on the device, each on its own
+    stream; nreq requests (seed 5): problem rng.integers(3), nrhs = rint(exp(U(0, ln 256))) complex
+    Gaussian right-hand sides, exponential inter-arrival times at 80 % of the measured single-stream
+    capacity; batches admitted by free device memory; GMRES to 1e-8.  50 sampled requests are checked
+    with an FP64 residual on the host."""
+    import numpy as np
+    probs = [w.helmholtz7(32, 10), w.helmholtz7(64, 10), w.helmholtz7(100, 10)]
+    streams = [torch.cuda.Stream() for _ in probs]
+    hs = []
+    for p, st in zip(probs, streams):
+        h = g.analyze_problem(p, nmin_sep=1024, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
+                              stream=st.cuda_stream)
+        h.mf_factor(1e-4)
+        hs.append(h)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    which = rng.integers(0, len(probs), nreq)
+    widths = np.rint(np.exp(rng.uniform(0.0, math.log(256.0), nreq))).astype(int)
+    pools = [np.asfortranarray(w.complex_gaussian(rng, p.n, 256)) for p in probs]
+    # single-stream capacity: solves/s of one 64-column batch per problem, averaged over the mix
+    cap = []
+    for p, h, pool in zip(probs, hs, pools):
+        h.mf_solve(pool[:, :64])
+        t0 = time.perf_counter()
+        h.mf_solve(pool[:, :64])
+        cap.append(64 / (time.perf_counter() - t0))
+    mix = np.bincount(which, minlength=len(probs)) / nreq
+    capacity = 1.0 / float(np.sum(mix / np.array(cap)))          # RHS per second over the request mix
+    rate = 0.8 * capacity / float(np.mean(widths))                # requests per second
+    gaps = rng.exponential(1.0 / rate, nreq)
+    srv = g.Server(hs, max_batch_rhs=64, mem_budget_bytes=1 << 62)   # admission by free device memory
+    ids, t0 = [], time.perf_counter()
+    t = t0
+    for k in range(nreq):
+        t += gaps[k]
+        while time.perf_counter() < t:
+            time.sleep(max(0.0, min(1e-3, t - time.perf_counter())))
+        ids.append((srv.submit(int(which[k]), pools[which[k]][:, :widths[k]]), int(which[k]), int(widths[k])))
+    lat, statuses, worst = [], [], 0.0
+    sample = set(np.random.default_rng(6).choice(nreq, 50, replace=False).tolist())
+    As = [p.to_scipy() for p in probs]
+    for q, (rid, pi, k) in enumerate(ids):
+        x, info = srv.wait(rid)
+        lat.append((info["t_done"] - info["t_arrival"]) * 1e3)
+        statuses.append(info["status"])
+        if q in sample:
+            bb = pools[pi][:, :k]
+            worst = max(worst, float(np.max(np.linalg.norm(As[pi] @ x - bb, axis=0) / np.linalg.norm(bb, axis=0))))
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat.sort()
+    return {"workload": "helmholtz7 32^3 + 64^3 + 100^3 resident, complex64 HOD-BF tol 1e-4; "
+                        f"{nreq} Poisson requests (seed 5) of rint(exp(U(0, ln 256))) RHS, arrivals at 80 % of the "
+                        f"measured capacity ({capacity:.0f} RHS/s), admission by free device memory, GMRES to 1e-8",
+            "requests": nreq, "rhs": int(widths.sum()), "arrival_rate_per_s": rate,
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "solves_per_s": float(widths.sum()) / wall, "wall_s": wall,
+            "all_converged": bool(all(s_ == 0 for s_ in statuses)),
+            "max_rel_residual_sampled_50": worst}
+
+
 def butterfly_apply(g, w, torch, peaks, nrhs=64):
     """The batched butterfly-apply workload: 200 compressed blocks of the Helmholtz Green's function
     between two parallel m x m point planes one spacing apart (m = rint(16 * 8^u), u ~ U(0,1),
@@ -427,9 +496,16 @@ def main():
     import workloads as w
 
     n = args.grid
-    p = w.helmholtz7(n, 10)
     nrhs = args.nrhs
-    b = w.rhs_gaussian(p, nrhs, 7)
+    if args.problem == "yee":
+        p = w.yee_maxwell(n, 10)
+        b = w.rhs_dipoles(p, nrhs, 11)
+        wname = f"Yee curl-curl {n}^3 cells, PEC (N={p.n}), ppw 10, {nrhs} edge-dipole RHS seed 11"
+    else:
+        p = w.helmholtz7(n, 10, k=0.0) if args.problem == "poisson" else w.helmholtz7(n, 10)
+        b = w.rhs_gaussian(p, nrhs, 7)
+        wname = (f"{'poisson7 (k = 0)' if args.problem == 'poisson' else 'helmholtz7'} {n}^3 (N={p.n})"
+                 f"{'' if args.problem == 'poisson' else ', ppw 10'}, {nrhs} Gaussian RHS seed 7")
     stream = torch.cuda.current_stream()
     # complex64 factors, separators >= 1024 in HOD-BF at tol 1e-4 (rank <= 64), FP64 GMRES(30) to 1e-8
     nmin = args.nmin
@@ -501,9 +577,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-                "config": {"workload": f"helmholtz7 {n}^3 (N={p.n}), ppw 10, 16 Gaussian RHS seed 7, complex64 "
-                                       f"factors, separators >= {nmin} HOD-BF at tol 1e-4 (rank <= 64), "
-                                       f"FP64 GMRES(30) to 1e-8",
+                "config": {"workload": f"{wname}, complex64 factors, separators >= {nmin} HOD-BF at tol 1e-4 "
+                                       f"(rank <= 64), FP64 GMRES(30) to 1e-8",
                            "compressed_fronts": st["ncompressed"], "max_rank": st["max_rank"],
                            "arena_peak_gb": st["arena_peak_bytes"] / 1e9,
                            "arena_capacity_gb": st["arena_capacity_bytes"] / 1e9,
@@ -580,7 +655,9 @@ def main():
         del hb
       except Exception as e:
         line["fp64_butterfly_path"] = {"error": str(e)[:300]}
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and args.serving_full:
+        line["serving_full"] = serving_full(g, w, torch)
+    elif rank == 0 and not args.no_serving:
         line["serving"] = serving(g, w, torch)
     if rank == 0 and not args.no_bfapply:
         line["butterfly_apply"] = butterfly_apply(g, w, torch, measured_peaks())

@@ -265,7 +265,8 @@ int mf_row_id_c64_noalloc(int32_t nmat, int32_t m, int32_t n, const float* M, do
  * factored; each should have its own CUDA stream).  One worker thread per
  * handle batches every request waiting for that handle when its previous batch
  * ends (requests that arrive during a solve join the next batch), admits
- * requests while the batch's device workspace, estimated as 40 * N * nrhs * 16
+ * requests (up to max_batch_rhs columns; a wider request runs alone, in slices of
+ * max_batch_rhs columns) while the batch's device workspace, estimated as 40 * N * nrhs * 16
  * bytes, fits together with the other batches in flight both mf_server_create's
  * mem_budget_bytes and the device's free memory less 1 GiB (cudaMemGetInfo, read
  * when the batch is formed), and runs the batch as one mf_solve.  Each request
@@ -364,6 +365,15 @@ int mf_analysis_sizes(const mf_handle* h, mf_analysis_sizes_t* out);
  */
 int mf_analysis_export(const mf_handle* h, int64_t* perm, int64_t* front_parent, int64_t* front_sep,
                        int32_t* front_flags, int64_t* upd_ptr, int64_t* upd_idx);
+
+/*
+ * Failure detection of the tensor-core kernels: every mbarrier wait in them polls at most
+ * `spins` times (0 restores the default, 2^26) before the kernel records an expired wait, stops
+ * issuing work, waits for its committed MMAs (always with the default limit), frees its tensor
+ * memory and returns; the call that launched it then returns MF_ERR_TIMEOUT and the CUDA context
+ * stays usable.  Process-wide; meant for tests of that path.  Errors: MF_ERR_ARG (spins < 0).
+ */
+int mf_set_wait_limit(int64_t spins);
 
 /*
  * Apply one operator of compressed front f (Alg. 5) to nrhs host vectors, for inspection

@@ -210,6 +210,14 @@ BFContext<T>::BFContext(cudaStream_t s, size_t pb, size_t sb) : st(s) {
 }
 
 template <typename T>
+BFContext<T>::BFContext(cudaStream_t s, Arena* shared_persist, size_t sb) : st(s) {
+  persist.share(shared_persist);
+  scratch.init(sb);
+  status.alloc(sizeof(int32_t));
+  MF_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int32_t), st));
+}
+
+template <typename T>
 BFContext<T>::~BFContext() {
   if (ring) cudaFreeHost(ring);
   for (int i = 0; i < 2; ++i) {

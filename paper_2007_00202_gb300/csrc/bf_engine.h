@@ -26,15 +26,20 @@ namespace mf {
 
 using Tree = std::vector<std::vector<Range>>;   // levels of index ranges
 
-// Bump allocator over one device allocation; mark/release for scratch phases.
+// Bump allocator over one device allocation; mark/release for scratch phases.  An arena can
+// instead forward every request to a shared parent arena (share()): several construction
+// contexts then allocate their persistent blocks from one allocation, under the parent's lock.
 class Arena {
  public:
   void init(size_t bytes) {
     mem_.alloc(bytes);
     off_ = 0;
   }
-  bool ready() const { return mem_.p != nullptr; }
+  void share(Arena* parent) { parent_ = parent; }
+  bool ready() const { return parent_ ? parent_->ready() : mem_.p != nullptr; }
   void* take(size_t bytes) {
+    if (parent_) return parent_->take(bytes);
+    std::lock_guard<std::mutex> lk(mu_);
     size_t o = (off_ + 255) & ~size_t(255);
     if (o + bytes > mem_.bytes)
       throw CudaError("device arena exhausted (cudaMalloc: out of memory): need " + std::to_string(o + bytes) +
@@ -45,16 +50,27 @@ class Arena {
   }
   template <typename T>
   T* takeT(size_t n) { return static_cast<T*>(take(n * sizeof(T))); }
-  size_t mark() const { return off_; }
-  void release(size_t m) { off_ = m; }
-  size_t used() const { return off_; }
-  size_t peak() const { return peak_; }
-  size_t capacity() const { return mem_.bytes; }
-  char* base() const { return static_cast<char*>(mem_.p); }
+  // mark / release are meant for an arena used by one thread (the scratch arenas); on a shared
+  // arena they act on the parent
+  size_t mark() const { return parent_ ? parent_->mark() : off_; }
+  void release(size_t m) {
+    if (parent_) {
+      parent_->release(m);
+      return;
+    }
+    std::lock_guard<std::mutex> lk(mu_);
+    off_ = m;
+  }
+  size_t used() const { return parent_ ? 0 : off_; }
+  size_t peak() const { return parent_ ? 0 : peak_; }          // a shared arena counts in its parent
+  size_t capacity() const { return parent_ ? 0 : mem_.bytes; }
+  char* base() const { return parent_ ? parent_->base() : static_cast<char*>(mem_.p); }
 
  private:
   DevMem mem_;
   size_t off_ = 0, peak_ = 0;
+  Arena* parent_ = nullptr;
+  std::mutex mu_;
 };
 
 // A planar complex block in device memory: rows x cols, row-major, leading dim ld.
@@ -211,6 +227,8 @@ template <typename T>
 class BFContext {
  public:
   BFContext(cudaStream_t st, size_t persist_bytes, size_t scratch_bytes);
+  // a context whose persistent blocks come from another context's persistent arena
+  BFContext(cudaStream_t st, Arena* shared_persist, size_t scratch_bytes);
   ~BFContext();
   cudaStream_t st;
   cudaStream_t side[2] = {nullptr, nullptr};            // forked streams of row_ids (created on first use)

@@ -395,19 +395,26 @@ int mf_factor(mf_handle* h, double tol) {
       eo.knn = h->opt.knn;
       eo.seed = h->opt.seed;
       bool any_comp = false;
-      size_t comp_n = 0;
+      size_t comp_n = 0, max_n = 0;
       for (auto& f : h->an.fronts)
-        if (f.compressed) { any_comp = true; comp_n += (size_t)(f.s() + f.u()); }
-      // arenas for the compressed fronts, sized from their dimensions (generous: 280 GB devices)
+        if (f.compressed) {
+          any_comp = true;
+          comp_n += (size_t)(f.s() + f.u());
+          max_n = std::max(max_n, (size_t)(f.s() + f.u()));
+        }
+      // arenas for the compressed fronts, sized from their dimensions: one persistent arena for every
+      // compressed front's factors, and per construction context a work arena for the largest front
+      // (released after each front)
       size_t el = h->opt.precision == MF_PREC_C128 ? 16 : 8;
       // without a rank cap the sketch widths may double several times: give the work arena room
-      const size_t per = h->opt.max_rank > 0 ? 10000 : 40000;
-      eo.persist_bytes = any_comp ? std::max<size_t>(size_t(8) << 30, comp_n * 20000 * el) : 0;
-      eo.scratch_bytes = any_comp ? std::max<size_t>(size_t(4) << 30, comp_n * per * el) : 0;
-      // the two construction contexts hold two such pairs: keep them within 70 % of the free memory
+      // (measured peaks: 64^3, one front of s + u = 6144: 1.6 GB; 100^3: one request of 4.8 GB)
+      const size_t per = h->opt.max_rank > 0 ? 80000 : 320000;
+      eo.persist_bytes = any_comp ? std::max<size_t>(size_t(4) << 30, comp_n * 24000 * el) : 0;
+      eo.scratch_bytes = any_comp ? std::max<size_t>(size_t(2) << 30, max_n * per * el) : 0;
+      // the persistent arena and up to eight work arenas stay within 70 % of the free memory
       size_t fr = 0, tot = 0;
       if (any_comp && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-        const double want = 2.0 * (double)(eo.persist_bytes + eo.scratch_bytes), room = 0.7 * (double)fr;
+        const double want = (double)eo.persist_bytes + 8.0 * (double)eo.scratch_bytes, room = 0.7 * (double)fr;
         if (want > room) {
           const double f = room / want;
           eo.persist_bytes = (size_t)(f * (double)eo.persist_bytes);
@@ -704,6 +711,12 @@ int mf_analysis_export(const mf_handle* h, int64_t* perm, int64_t* front_parent,
     p += f.u();
     if (upd_ptr) upd_ptr[i + 1] = p;
   }
+  return MF_OK;
+}
+
+int mf_set_wait_limit(int64_t spins) {
+  if (spins < 0) return fail(nullptr, MF_ERR_ARG, "spins must be >= 0");
+  mf::set_wait_limit((long long)spins);
   return MF_OK;
 }
 

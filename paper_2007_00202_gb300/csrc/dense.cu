@@ -12,6 +12,12 @@ namespace mf {
 
 static std::atomic<int64_t> g_launches{0};
 int64_t launch_count() { return g_launches.load(); }
+
+namespace {
+std::atomic<long long> g_wait_limit{kDefaultWaitLimit};
+}
+void set_wait_limit(long long spins) { g_wait_limit.store(spins > 0 ? spins : kDefaultWaitLimit); }
+long long wait_limit() { return g_wait_limit.load(); }
 void count_launches(int k) { g_launches += k; }
 
 // ---------------------------------------------------------------------------

@@ -22,11 +22,15 @@ IdxVec iota_vec(int n) {
 }  // namespace
 
 template <typename T>
-void CompressedPart<T>::ensure_second() {
-  if (cx2) return;
-  MF_CUDA(cudaStreamCreateWithFlags(&st2_, cudaStreamNonBlocking));
-  cx2 = std::make_unique<BFContext<T>>(st2_, persist_bytes_, scratch_bytes_);
-  cx2->prof = cx.prof;
+void CompressedPart<T>::ensure_contexts(int n) {
+  n = std::min(n, kMaxContexts);
+  while (contexts() < n) {
+    cudaStream_t s = nullptr;
+    MF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    extra_st_.push_back(s);
+    extra_.push_back(std::make_unique<BFContext<T>>(s, &cx.persist, scratch_bytes_));
+    extra_.back()->prof = cx.prof;
+  }
 }
 
 namespace {
@@ -109,6 +113,7 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
                                      int w) {
   BFContext<T>& cx = ctx(w);          // this front's execution context and stream
   const cudaStream_t st_ = stream(w);
+  const size_t scratch_mark = cx.scratch.mark();   // this front's work is released when it is built
   auto t0 = std::chrono::steady_clock::now();
   const FrontInfo& f = an_.fronts[fid];
   const int s = (int)f.s(), u = (int)f.u();
@@ -295,6 +300,7 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
   upload(cf.d_upd32, cf.upd32, st_);
   MF_CUDA(cudaStreamSynchronize(st_));
   cx.check_status();
+  cx.scratch.release(scratch_mark);   // the stream is idle: the work buffers can be reused
   cf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   std::lock_guard<std::mutex> lk(fronts_mu_);
   fronts[fid] = std::move(cfp);

@@ -39,9 +39,12 @@ class CompressedPart {
   CompressedPart(const Analysis& an, const DeviceMatrix& A, cudaStream_t st, size_t persist, size_t scratch)
       : an_(an), A_(A), st_(st), cx(st, persist, scratch), persist_bytes_(persist), scratch_bytes_(scratch) {}
   ~CompressedPart() {
-    cx2.reset();
-    if (st2_) cudaStreamDestroy(st2_);
+    extra_.clear();
+    for (auto s : extra_st_)
+      if (s) cudaStreamDestroy(s);
   }
+  // the most construction contexts (host threads and streams) that build the fronts of one level
+  static constexpr int kMaxContexts = 8;
 
   // Factor compressed front fid with execution context w (0: the engine's stream and arenas,
   // 1: a second context on its own stream, so that two fronts of one tree level can be built
@@ -49,10 +52,12 @@ class CompressedPart {
   void factor_front(int fid, const std::vector<FrontDev<T>>& fr, const BFParams& P, uint64_t seed, int w = 0);
   // Expand C of a compressed front into the dense buffer of its (dense) parent's extend-add.
   void densify_C(int fid, const FrontDev<T>& f, int w = 0);
-  // the second execution context (created on first use with the same arena sizes)
-  void ensure_second();
-  BFContext<T>& ctx(int w) { return w == 0 ? cx : *cx2; }
-  cudaStream_t stream(int w) const { return w == 0 ? st_ : st2_; }
+  // execution contexts 1 .. n-1 (created on first use, each with its own stream and scratch arena;
+  // their persistent blocks come from context 0's persistent arena)
+  void ensure_contexts(int n);
+  int contexts() const { return 1 + (int)extra_.size(); }
+  BFContext<T>& ctx(int w) { return w == 0 ? cx : *extra_[w - 1]; }
+  cudaStream_t stream(int w) const { return w == 0 ? st_ : extra_st_[w - 1]; }
   // Solve steps on X (N x k, planar row-major, new numbering) for all compressed fronts of one
   // tree level at once (they touch disjoint separator rows; the update rows they write are
   // combined by the scatter-add of the forward step)
@@ -74,8 +79,8 @@ class CompressedPart {
   const DeviceMatrix& A_;
   cudaStream_t st_;
   BFContext<T> cx;
-  std::unique_ptr<BFContext<T>> cx2;
-  cudaStream_t st2_ = nullptr;
+  std::vector<std::unique_ptr<BFContext<T>>> extra_;
+  std::vector<cudaStream_t> extra_st_;
   size_t persist_bytes_, scratch_bytes_;
   std::mutex fronts_mu_;   // guards fronts while two contexts build fronts of one level
   std::map<int, std::unique_ptr<CompFront<T>>> fronts;

@@ -9,6 +9,7 @@
 // The whole sequence is built once per analysis ("launch program") and
 // replayed by every factorization.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -54,7 +55,7 @@ class DenseEngine : public EngineBase {
     for (auto& kv : sprog_) kv.second->drop_graph();   // compressed fronts move with every factorization
     if (comp_) {
       comp_->fronts.clear();
-      for (int w = 0; w < (comp_->cx2 ? 2 : 1); ++w) {
+      for (int w = 0; w < comp_->contexts(); ++w) {
         comp_->ctx(w).persist.release(0);
         comp_->ctx(w).scratch.release(0);
         comp_->ctx(w).flops = 0;
@@ -92,42 +93,57 @@ class DenseEngine : public EngineBase {
       if (lvl.size() == 1 || serial) {
         run(lvl, 0, 1, 0);
       } else {
-        // the fronts of one level are independent: two host threads build them, each with its own
-        // stream and arenas, so one thread's host work overlaps the other's GPU work
-        comp_->ensure_second();
+        // the fronts of one level are independent: up to kMaxContexts host threads build them, each
+        // with its own stream and scratch arena, taking the next front of the level when done, so
+        // that one thread's host work overlaps the others' GPU work
+        const int nctx = std::min<int>((int)lvl.size(), CompressedPart<T>::kMaxContexts);
+        comp_->ensure_contexts(nctx);
         MF_CUDA(cudaEventRecord(lev_ev_[0], st_));                  // children and dense fronts below
-        MF_CUDA(cudaStreamWaitEvent(comp_->stream(1), lev_ev_[0], 0));
+        for (int w = 1; w < nctx; ++w) MF_CUDA(cudaStreamWaitEvent(comp_->stream(w), lev_ev_[0], 0));
         int dev = 0;
         MF_CUDA(cudaGetDevice(&dev));
-        std::exception_ptr err;
-        std::thread th([&, dev] {
+        std::atomic<size_t> next{0};
+        std::vector<std::exception_ptr> errs(nctx);
+        auto worker = [&](int w) {
           try {
-            MF_CUDA(cudaSetDevice(dev));
-            run(lvl, 1, 2, 1);
-            MF_CUDA(cudaStreamSynchronize(comp_->stream(1)));
+            for (size_t i = next++; i < lvl.size(); i = next++) run(lvl, i, lvl.size(), w);
           } catch (...) {
-            err = std::current_exception();
+            errs[w] = std::current_exception();
           }
-        });
-        std::exception_ptr err0;
-        try {
-          run(lvl, 0, 2, 0);
-        } catch (...) {
-          err0 = std::current_exception();
-        }
-        th.join();
-        if (err0) std::rethrow_exception(err0);
-        if (err) std::rethrow_exception(err);
+        };
+        std::vector<std::thread> th;
+        for (int w = 1; w < nctx; ++w)
+          th.emplace_back([&, w, dev] {
+            if (cudaSetDevice(dev) != cudaSuccess) {
+              errs[w] = std::make_exception_ptr(CudaError("cudaSetDevice failed"));
+              return;
+            }
+            worker(w);
+            if (!errs[w] && cudaStreamSynchronize(comp_->stream(w)) != cudaSuccess)
+              errs[w] = std::make_exception_ptr(CudaError("construction stream failed"));
+          });
+        worker(0);
+        for (auto& t : th) t.join();
+        for (auto& e : errs)
+          if (e) std::rethrow_exception(e);
       }
       if (side) MF_CUDA(cudaStreamWaitEvent(st_, lev_ev_[2], 0));   // the next level needs both
       for (int32_t fid : lvl) max_rank_ = std::max(max_rank_, comp_->fronts.at(fid)->max_rank);
       comp_seconds_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
-    if (comp_) comp_flops_ = comp_->cx.flops + (comp_->cx2 ? comp_->cx2->flops : 0.0);
+    if (comp_) {
+      comp_flops_ = 0;
+      for (int w = 0; w < comp_->contexts(); ++w) comp_flops_ += comp_->ctx(w).flops;
+    }
     if (getenv("MF_TRACE") && getenv("MF_TRACE")[0] == '1') {
       MF_CUDA(cudaStreamSynchronize(st_));
       fprintf(stderr, "[mf] factor: %.3f s, compressed fronts %.3f s (host-issued, synchronised per phase)\n",
               std::chrono::duration<double>(std::chrono::steady_clock::now() - tf0).count(), comp_seconds_);
+      if (comp_)
+        for (int w = 0; w < comp_->contexts(); ++w)
+          fprintf(stderr, "[mf] context %d: persistent arena peak %.2f of %.2f GB, work arena peak %.2f of %.2f GB\n",
+                  w, comp_->ctx(w).persist.peak() / 1e9, comp_->ctx(w).persist.capacity() / 1e9,
+                  comp_->ctx(w).scratch.peak() / 1e9, comp_->ctx(w).scratch.capacity() / 1e9);
     }
     MF_CUDA(cudaGetLastError());
     nlaunch_factor_ = (int)(launch_count() - c0);
@@ -229,8 +245,8 @@ class DenseEngine : public EngineBase {
   void arena_usage(double& peak, double& capacity) const override {
     peak = capacity = 0;
     if (!comp_) return;
-    for (int w = 0; w < (comp_->cx2 ? 2 : 1); ++w) {
-      const BFContext<T>& c = w == 0 ? comp_->cx : *comp_->cx2;
+    for (int w = 0; w < comp_->contexts(); ++w) {
+      const BFContext<T>& c = w == 0 ? comp_->cx : *comp_->extra_[w - 1];
       peak += (double)c.persist.peak() + (double)c.scratch.peak();
       capacity += (double)c.persist.capacity() + (double)c.scratch.capacity();
     }

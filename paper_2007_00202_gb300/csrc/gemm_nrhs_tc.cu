@@ -45,7 +45,6 @@ constexpr uint32_t TC_TMEM_COLS = 256;           // two accumulators of up to 12
 constexpr int TC_XBLK = (64 / 8) * (TC_BK / 4);  // core matrices of one X plane chunk: 32
 constexpr int TC_MAXBLK = TC_XBLK + (TC_ROWS / 8) * (TC_BK / 4);
 constexpr int TC_PER_WARP = (TC_MAXBLK + TC_WARPS - 1) / TC_WARPS;   // 10
-constexpr long long TC_SPIN = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -63,23 +62,24 @@ __device__ __forceinline__ uint32_t idesc(int n, int neg_a) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)neg_a << 13) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(128 >> 4) << 24);
 }
+// hi = x rounded to the 10 explicit mantissa bits of TF32 (round half away from zero, low 13 bits
+// cleared explicitly, so that the MMA reads hi exactly), lo = x - hi (exact in FP32)
 __device__ __forceinline__ void split(float x, float& hi, float& lo) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(x));
-  hi = __uint_as_float(h);
+  const uint32_t b = __float_as_uint(x);
+  hi = __uint_as_float((b + 0x1000u) & 0xFFFFE000u);
   lo = x - hi;
 }
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < TC_SPIN; ++i)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long spins) {
+  for (long long i = 0; i < spins; ++i)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -217,7 +217,7 @@ __device__ __forceinline__ void epilogue(const GemmDesc<float>* descs, const Gem
 
 __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_nrhs_tc(const GemmDesc<float>* __restrict__ descs,
                                                                  const GemmTile* __restrict__ tiles, int ntiles,
-                                                                 int32_t* status) {
+                                                                 int32_t* status, long long spins) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if ((int)blockIdx.x >= ntiles) return;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_nrhs_tc(const GemmDesc<f
   const uint32_t bar0 = sbase + TC_SLOTS * TC_SLOT;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sgen + TC_SLOTS * TC_SLOT + 64);
   if (tid == 0) {
-    for (int s = 0; s < TC_SLOTS; ++s)
+    for (int s = 0; s <= TC_SLOTS; ++s)   // one per slot and a spare that nothing arrives at
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar0 + 8 * s), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
@@ -240,17 +240,19 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_nrhs_tc(const GemmDesc<f
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = *tmem_slot;
 
+  bool ok = true;
+  if (spins <= kProbeWaitLimit)   // expiry test: the spare barrier never completes
+    ok = __syncthreads_and(mbar_wait(bar0 + 8 * TC_SLOTS, 0u, spins) ? 1 : 0) != 0;
   Chunk cur;
-  cur.t = blockIdx.x;
+  cur.t = ok ? (int)blockIdx.x : ntiles;   // after an expired test wait the CTA issues no work
   cur.c = 0;
   Regs ra, rb;
-  load_chunk(ra, descs, tiles, cur, warp, lane);
+  if (cur.t < ntiles) load_chunk(ra, descs, tiles, cur, warp, lane);
   long long g = 0;      // chunks issued by this CTA
   int j = 0;            // tiles completed (MMAs issued) by this CTA
   int pend_t = -1;      // tile whose epilogue is pending, its accumulator and last chunk
   uint32_t pend_acc = 0;
   long long pend_g = 0;
-  bool ok = true;
 #pragma unroll 1
   while (cur.t < ntiles) {
     const GemmTile tl = tiles[cur.t];
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_nrhs_tc(const GemmDesc<f
     unsigned char* sp = sgen + slot * TC_SLOT;
     const uint32_t sa = sbase + slot * TC_SLOT;
     // the slot is free once the MMAs of its previous chunk (g - TC_SLOTS) are complete
-    if (g >= TC_SLOTS) ok = mbar_wait(bar0 + 8 * slot, (uint32_t)(((g / TC_SLOTS) - 1) & 1));
+    if (g >= TC_SLOTS) ok = mbar_wait(bar0 + 8 * slot, (uint32_t)(((g / TC_SLOTS) - 1) & 1), spins);
     if (ok) store_chunk(ra, sp, nt / 8 * (TC_BK / 4), warp, lane);
     Chunk nx = cur;
     if (++nx.c == nk) {
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_nrhs_tc(const GemmDesc<f
     ++g;
     // the previous tile's epilogue, while the tensor core works on this chunk
     if (cur.c == 0 && pend_t >= 0) {
-      ok = mbar_wait(bar0 + 8 * (int)(pend_g % TC_SLOTS), (uint32_t)((pend_g / TC_SLOTS) & 1));
+      ok = mbar_wait(bar0 + 8 * (int)(pend_g % TC_SLOTS), (uint32_t)((pend_g / TC_SLOTS) & 1), spins);
       if (__syncthreads_or(ok ? 0 : 1)) {
         ok = false;
         break;
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_nrhs_tc(const GemmDesc<f
     cur = nx;
   }
   if (ok && pend_t >= 0) {
-    ok = mbar_wait(bar0 + 8 * (int)(pend_g % TC_SLOTS), (uint32_t)((pend_g / TC_SLOTS) & 1));
+    ok = mbar_wait(bar0 + 8 * (int)(pend_g % TC_SLOTS), (uint32_t)((pend_g / TC_SLOTS) & 1), spins);
     if (!__syncthreads_or(ok ? 0 : 1)) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
       epilogue(descs, tiles, pend_t, pend_acc, warp, lane);
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_nrhs_tc(const GemmDesc<f
   // limit even after an expired wait, so that no MMA can still write the columns being freed)
   if (tid == 0 && g > 0) {
     const int slot = (int)((g - 1) % TC_SLOTS);
-    if (!mbar_wait(bar0 + 8 * slot, (uint32_t)(((g - 1) / TC_SLOTS) & 1))) ok = false;
+    if (!mbar_wait(bar0 + 8 * slot, (uint32_t)(((g - 1) / TC_SLOTS) & 1), kDefaultWaitLimit)) ok = false;
   }
   if (!ok && status) atomicExch(status, 2);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -358,7 +360,7 @@ void launch_gemm_nrhs_tc(const GemmDesc<float>* d_desc, const GemmTile* d_tiles,
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;   // two CTAs per SM
   count_launches(1);
-  k_gemm_nrhs_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(d_desc, d_tiles, ntiles, status);
+  k_gemm_nrhs_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(d_desc, d_tiles, ntiles, status, wait_limit());
 }
 
 }  // namespace mf

@@ -9,12 +9,16 @@
 // A complex product is four real products into two TMEM accumulators:
 //   Dre += Are Bre^T ; Dre += (-Aim) Bim^T (negate-A bit) ; Dim += Are Bim^T ; Dim += Aim Bre^T.
 //
-// One CTA (4 warps) computes a 128 x 128 output tile.  Operand tiles of 16
+// One CTA (4 warps) computes a 128 x 128 output tile.  Operand tiles of 8
 // K-elements are staged in shared memory by cp.async (16-byte copies, zero
 // fill past the edges) in the canonical no-swizzle K-major layout of 8 x 16-byte
-// core matrices, 3 stages; thread 0 issues the MMAs and commits each stage to an
-// mbarrier, which frees the stage for the next copy.  The epilogue reads TMEM
-// with tcgen05.ld (one row per thread) and applies alpha / beta.
+// core matrices, 6 stages with copies issued 4 chunks ahead; thread 0 issues the
+// MMAs and commits each stage to an mbarrier, which frees the stage.  A stage is
+// refilled once the MMAs of the chunk two behind have completed, so the tensor core
+// works on one chunk while the threads stage and split the next.  The epilogue
+// reads TMEM with tcgen05.ld (one row per thread), transposes 32 x 32 blocks
+// through shared memory and writes C rows with consecutive lanes on consecutive
+// columns, applying alpha / beta.
 // SPLIT = true is the split-precision form: every staged value x is replaced in
 // shared memory by hi = tf32(x) (round to nearest) plus a second tile lo = x - hi,
 // and each product is hi*hi + hi*lo + lo*hi (three tensor-core passes), which
@@ -31,13 +35,13 @@ namespace mf {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 16, STAGES = 3, NT = 128;
+constexpr int BM = 128, BN = 128, BK = 8, STAGES = 6, NT = 128;
+constexpr int PREFETCH = STAGES - 2;                     // chunks whose copies are in flight
 constexpr int KCH = BK / 4;                              // 16-byte K chunks per row
-constexpr int TILE_BYTES = BM * BK * 4;                  // one plane tile of A (or B): 8 KB
+constexpr int TILE_BYTES = BM * BK * 4;                  // one plane tile of A (or B): 4 KB
 constexpr int STAGE_BYTES = 8 * TILE_BYTES;              // Are, Aim, Bre, Bim and their lo parts
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2048;  // + alignment slack, barriers, tmem slot
 constexpr uint32_t TMEM_COLS = 256;                      // Dre (128 cols) + Dim (128 cols)
-constexpr long long SPIN_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -71,15 +75,15 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
-// bounded wait; returns false on expiry
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < SPIN_LIMIT; ++i)
+// bounded wait (non-blocking polls, so that the limit counts polls); returns false on expiry
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long spins) {
+  for (long long i = 0; i < spins; ++i)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -120,17 +124,18 @@ __device__ __forceinline__ void load_tile(uint32_t dst_re, uint32_t dst_im, cons
   }
 }
 
-// hi = tf32(x) rounded to nearest (low 13 mantissa bits zero), lo = x - hi
+// hi = x rounded to the 10 explicit mantissa bits of TF32 (round half away from zero, low 13 bits
+// cleared explicitly, so that the MMA reads hi exactly), lo = x - hi (exact in FP32)
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(x));
-  hi = __uint_as_float(h);
+  const uint32_t b = __float_as_uint(x);
+  hi = __uint_as_float((b + 0x1000u) & 0xFFFFE000u);
   lo = x - hi;
 }
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc<float>* __restrict__ descs,
-                                                    const GemmTile* __restrict__ tiles, int32_t* status) {
+                                                    const GemmTile* __restrict__ tiles, int32_t* status,
+                                                    long long spins) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   const GemmTile t = tiles[blockIdx.x];
@@ -140,6 +145,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc<float>* __rest
   unsigned char* sgen = smem + (sbase - smem_u32(smem));
   uint64_t* bars = reinterpret_cast<uint64_t*>(sgen + STAGES * STAGE_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sgen + STAGES * STAGE_BYTES + 64);
+  int* s_done = reinterpret_cast<int*>(sgen + STAGES * STAGE_BYTES + 96);
   const uint32_t bar0 = sbase + STAGES * STAGE_BYTES;
 
   if (tid == 0) {
@@ -167,24 +173,32 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc<float>* __rest
     load_tile(stage_addr(s, 2), stage_addr(s, 3), Br, d.B.plane, d.B.ld, d.n, n0, K, kb * BK, tid);
   };
   bool ok = true;
+  if (spins <= kProbeWaitLimit) {   // expiry test: the spare barrier (index STAGES) never completes
+    if (tid == 0) *s_done = mbar_wait(bar0 + 8 * STAGES, 0u, spins) ? 1 : 0;
+    __syncthreads();
+    ok = *s_done != 0;
+    __syncthreads();
+  }
+  int last = -1;   // thread 0: the last chunk whose MMAs it committed
 #pragma unroll 1
-  for (int s = 0; s < STAGES - 1; ++s) {
-    if (s < nk) issue_load(s, s);
+  for (int s = 0; s < PREFETCH; ++s) {
+    if (s < nk && ok) issue_load(s, s);
     cp_commit();
   }
   const uint32_t id_pos = idesc_tf32(0), id_neg = idesc_tf32(1);
   const uint32_t d_re = tmem, d_im = tmem + BN;
 #pragma unroll 1
-  for (int kb = 0; kb < nk; ++kb) {
+  const int nk_run = ok ? nk : 0;   // fixed before the loop: ok is uniform only here
+  for (int kb = 0; kb < nk_run; ++kb) {
     const int s = kb % STAGES;
-    const int kn = kb + STAGES - 1;
+    const int kn = kb + PREFETCH;
     if (kn < nk) {
-      const int sn = kn % STAGES;     // == (kb - 1) % STAGES: consumed by the MMAs of kb - 1
-      if (kb >= 1 && ok) ok = mbar_wait(bar0 + 8 * sn, (uint32_t)(((kb - 1) / STAGES) & 1));
+      const int sn = kn % STAGES;     // == (kb - 2) % STAGES: consumed by the MMAs of kb - 2
+      if (kb >= 2 && ok) ok = mbar_wait(bar0 + 8 * sn, (uint32_t)(((kb - 2) / STAGES) & 1), spins);
       if (ok) issue_load(sn, kn);
     }
     cp_commit();
-    cp_wait<STAGES - 1>();
+    cp_wait<PREFETCH>();
     if (SPLIT) {
       __syncthreads();
       // each staged value -> hi in place, lo into the second half of the stage
@@ -223,17 +237,28 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc<float>* __rest
         }
       }
       mma_commit(bar0 + 8 * s);
+      last = kb;
     }
   }
-  // all MMAs complete: the last commit covers every earlier MMA of thread 0
-  if (nk > 0 && ok) ok = mbar_wait(bar0 + 8 * ((nk - 1) % STAGES), (uint32_t)(((nk - 1) / STAGES) & 1));
+  // all MMAs complete: thread 0's last commit covers every MMA it issued; every thread waits for it
+  // (with the default limit even after an expired wait, so that no MMA can still write the columns
+  // freed below).  The tile is written only if every chunk's MMAs were issued and no wait expired.
+  if (tid == 0) *s_done = last;   // the last committed chunk, for every thread's wait below
+  __syncthreads();
+  const int lastc = *s_done;
+  const uint32_t lbar = bar0 + 8 * (lastc < 0 ? 0 : lastc % STAGES), lpar = (uint32_t)((lastc / STAGES) & 1);
+  bool done = lastc < 0 || mbar_wait(lbar, lpar, spins);   // the tile's results, within the wait limit
+  // expired: still wait (default limit) until no MMA of this CTA can write the columns freed below
+  if (!done && lastc >= 0) (void)mbar_wait(lbar, lpar, kDefaultWaitLimit);
   cp_wait<0>();
+  ok = __syncthreads_and((ok && done && lastc == nk - 1) ? 1 : 0) != 0;
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   if (!ok) {
     if (status) atomicExch(status, 2);
   } else {
-    // epilogue: thread tid owns row m0 + tid (TMEM lane tid)
-    const int row = m0 + tid;
+    // epilogue: TMEM lane tid holds row m0 + tid of the tile
+    const int lane = tid & 31;
+    float* tb = reinterpret_cast<float*>(sgen) + warp * (2 * 32 * 33);
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     float* Cr = d.C.re;
     float* Ci = d.C.re + d.C.plane;
@@ -259,23 +284,31 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc<float>* __rest
             "=r"(vi[29]), "=r"(vi[30]), "=r"(vi[31])
           : "r"(d_im + lane_base + c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (row < d.m) {
-        const int64_t rb = (int64_t)row * d.C.ld;
+      // transpose the warp's 32 x 32 block through shared memory (the stages are idle now) so
+      // that the stores below run along C's rows
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < d.n) {
-            float xr = d.alpha * __uint_as_float(vr[j]);
-            float xi = d.alpha * __uint_as_float(vi[j]);
-            if (d.beta != 0.f) {
-              xr += d.beta * Cr[rb + col];
-              xi += d.beta * Ci[rb + col];
-            }
-            Cr[rb + col] = xr;
-            Ci[rb + col] = xi;
+      for (int j = 0; j < 32; ++j) {
+        tb[lane * 33 + j] = __uint_as_float(vr[j]);
+        tb[32 * 33 + lane * 33 + j] = __uint_as_float(vi[j]);
+      }
+      __syncwarp();
+      const int col = n0 + c0 + lane;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const int grow = m0 + warp * 32 + r;
+        if (grow < d.m && col < d.n) {
+          const int64_t off = (int64_t)grow * d.C.ld + col;
+          float xr = d.alpha * tb[r * 33 + lane];
+          float xi = d.alpha * tb[32 * 33 + r * 33 + lane];
+          if (d.beta != 0.f) {
+            xr += d.beta * Cr[off];
+            xi += d.beta * Ci[off];
           }
+          Cr[off] = xr;
+          Ci[off] = xi;
         }
       }
+      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -299,8 +332,8 @@ void launch_gemm_tc(const GemmDesc<float>* d_desc, const GemmTile* d_tiles, int 
     cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
   count_launches(1);
-  if (split) k_gemm_tc<true><<<ntiles, NT, SMEM_BYTES, st>>>(d_desc, d_tiles, status);
-  else k_gemm_tc<false><<<ntiles, NT, SMEM_BYTES, st>>>(d_desc, d_tiles, status);
+  if (split) k_gemm_tc<true><<<ntiles, NT, SMEM_BYTES, st>>>(d_desc, d_tiles, status, wait_limit());
+  else k_gemm_tc<false><<<ntiles, NT, SMEM_BYTES, st>>>(d_desc, d_tiles, status, wait_limit());
 }
 
 }  // namespace mf

@@ -10,6 +10,17 @@
 
 namespace mf {
 
+// Iteration limit of the bounded mbarrier waits in the tensor-core kernels (0 restores the
+// default, 2^26 polls); on expiry a kernel records status 2 (MF_ERR_TIMEOUT).  The final wait
+// before a kernel releases its tensor memory always uses the default.
+void set_wait_limit(long long spins);
+long long wait_limit();
+constexpr long long kDefaultWaitLimit = 1ll << 26;
+// A limit of at most kProbeWaitLimit polls (tests of the expiry path) also makes every CTA of those
+// kernels first wait on an mbarrier that nothing arrives at: the wait runs out, the CTA issues no
+// work and reports the expiry.
+constexpr long long kProbeWaitLimit = 16;
+
 // Number of kernel launches issued by this library since it was loaded.
 int64_t launch_count();
 void count_launches(int k);

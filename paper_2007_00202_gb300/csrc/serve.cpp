@@ -63,7 +63,9 @@ struct mf_server {
   std::map<int64_t, std::shared_ptr<Request>> reqs;
   Clock::time_point t0 = Clock::now();
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
-  int64_t bytes_for(int64_t n, int32_t nrhs) const { return (int64_t)(30 + 10) * n * nrhs * 16; }
+  int64_t bytes_for(int64_t n, int32_t nrhs) const {
+    return (int64_t)(30 + 10) * n * std::min<int32_t>(nrhs, max_batch) * 16;
+  }
   void run(int p);
 };
 
@@ -111,14 +113,30 @@ void mf_server::run(int p) {
       std::memcpy(wk.bbuf.data() + off, r->b, sizeof(double) * 2 * wk.n * r->nrhs);
       off += (size_t)2 * wk.n * r->nrhs;
     }
+    // each request reports its own columns: what it returns does not depend on the batch it ran in.
+    // A request wider than max_batch runs alone, in slices of max_batch columns (its columns are
+    // independent), so that the solve's workspace stays bounded.
     mf_solve_info info{};
-    int rc = mf_solve(wk.h, tot, wk.bbuf.data(), wk.n, wk.xbuf.data(), wk.n, &info);
-    const double td = now();
-    // each request reports its own columns: what it returns does not depend on the batch it ran in
     std::vector<int32_t> cit(tot, 0), cconv(tot, 0);
     std::vector<double> cres(tot, 0.0);
-    const bool have_cols = (rc == MF_OK || rc == MF_ERR_NO_CONVERGENCE) &&
-                           mf_solve_columns(wk.h, tot, cit.data(), cconv.data(), cres.data()) == MF_OK;
+    int rc = MF_OK;
+    bool have_cols = true;
+    for (int c0 = 0; c0 < tot && (rc == MF_OK || rc == MF_ERR_NO_CONVERGENCE); c0 += max_batch) {
+      const int nc = std::min(max_batch, tot - c0);
+      const size_t o = (size_t)2 * wk.n * c0;
+      mf_solve_info part{};
+      const int r = mf_solve(wk.h, nc, wk.bbuf.data() + o, wk.n, wk.xbuf.data() + o, wk.n, &part);
+      if (r != MF_OK && r != MF_ERR_NO_CONVERGENCE) {
+        rc = r;
+        break;
+      }
+      if (r == MF_ERR_NO_CONVERGENCE) rc = r;
+      info.iters = std::max(info.iters, part.iters);
+      info.max_rel_residual = std::max(info.max_rel_residual, part.max_rel_residual);
+      have_cols = have_cols && mf_solve_columns(wk.h, nc, cit.data() + c0, cconv.data() + c0, cres.data() + c0) == MF_OK;
+    }
+    have_cols = have_cols && (rc == MF_OK || rc == MF_ERR_NO_CONVERGENCE);
+    const double td = now();
     off = 0;
     for (auto& r : batch) {
       if (rc == MF_OK || rc == MF_ERR_NO_CONVERGENCE)

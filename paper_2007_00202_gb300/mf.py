@@ -110,6 +110,7 @@ SIGNATURES = {
     "mf_analysis_export": (C.c_int, [_P, _I64P, _I64P, _I64P, _I32P, _I64P, _I64P]),
     "mf_front_trees": (C.c_int, [_P, C.c_int64, _I64P, _I64P]),
     "mf_front_apply": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, _DP, _DP]),
+    "mf_set_wait_limit": (C.c_int, [C.c_int64]),
     "mf_front_neighbours": (C.c_int, [_P, C.c_int64, C.c_int32, _I64P, _I64P, _I64P]),
 }
 
@@ -314,6 +315,11 @@ def mf_row_id_c64(nmat, m, n, M, tol, max_rank, U, sk, rank, stream=0):
     """Component batched row ID on device pointers (ints); see include/mf.h."""
     _check(lib().mf_row_id_c64(nmat, m, n, C.c_void_p(M), tol, max_rank, C.c_void_p(U), C.c_void_p(sk),
                                C.c_void_p(rank), C.c_void_p(stream)))
+
+
+def mf_set_wait_limit(spins: int):
+    """Poll limit of the tensor-core kernels' bounded waits (0: the default); see include/mf.h."""
+    _check(lib().mf_set_wait_limit(int(spins)))
 
 
 def mf_row_id_c64_noalloc(nmat, m, n, M, tol, max_rank, U, sk, rank, stream=0):

@@ -46,6 +46,10 @@ def test_gemm_nt_against_fp64(tk, engine, m, n, k, beta):
     # FP32 SIMT: ~1e-6; one TF32 pass (10-bit mantissa inputs, FP32 accumulate): ~1e-3;
     # split TF32 (three passes): FP32-like
     assert err < {0: 2e-5, 1: 4e-3, 2: 2e-5}[engine], err
+    # relative Frobenius error: SIMT FP32 ~1e-6; split TF32 ~1e-5 (measured 1.4e-5 at k = 961: the
+    # tensor core's accumulation, not the split, sets this floor); one TF32 pass ~3e-4
+    rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert rel < {0: 1e-5, 1: 2e-3, 2: 5e-5}[engine], rel
     # the padding column of C (beyond n) is untouched
     assert float(dC[0, :, n:].abs().max()) == float(_planar(torch, C0, ldc)[0, :, n:].abs().max())
 
@@ -101,4 +105,92 @@ def test_gemm_nrhs_tensor_core_against_fp64(tk, trans_a, m, n, k, beta):
     ref = -(A @ B) + beta * C0
     scale = np.sqrt(k) * np.abs(A).max() * np.abs(B).max()
     assert np.abs(out - ref).max() / scale < 2e-5
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 5e-5     # split TF32 (one TF32 pass: ~3e-4)
     assert float(dC[0, :, n:].abs().max()) == float(_planar(torch, C0, ldc)[0, :, n:].abs().max())
+
+
+def test_split_tf32_passes_recover_fp32_accuracy(tk):
+    # the split product (hi*hi + hi*lo + lo*hi) must be clearly more accurate than one TF32 pass on the
+    # same operands (a split whose lo parts were lost would match the one-pass error, ~3e-4); its own
+    # floor, ~1e-5, is the tensor core's accumulation
+    import paper_2007_00202_gb300.mf as mf
+    torch = tk
+    rng = np.random.default_rng(5)
+    m, n, k = 512, 384, 2048
+    A = rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))
+    B = rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))
+    dA, dB = _planar(torch, A, k), _planar(torch, B, k)
+    ref = A @ B.T
+    errs = {}
+    for engine in (1, 2):
+        dC = torch.zeros(2, m, n, dtype=torch.float32, device="cuda")
+        mf.mf_gemm_c64(engine, m, n, k, dA.data_ptr(), k, m * k, dB.data_ptr(), k, n * k, dC.data_ptr(), n, m * n,
+                       1.0, 0.0, 0)
+        torch.cuda.synchronize()
+        out = dC[0].double().cpu().numpy() + 1j * dC[1].double().cpu().numpy()
+        errs[engine] = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert errs[2] < 5e-5 and errs[2] < errs[1] / 8, errs
+    # the narrow tensor-core kernel on the same A (first 64 columns of B^T as the block of vectors)
+    Bn = B[:64].T.copy()
+    dBn = _planar(torch, Bn, 64)
+    dC = torch.zeros(2, m, 64, dtype=torch.float32, device="cuda")
+    mf.mf_gemm_nrhs_c64(0, m, 64, k, dA.data_ptr(), k, m * k, dBn.data_ptr(), 64, k * 64, dC.data_ptr(), 64, m * 64,
+                        1.0, 0.0, -1, 0)
+    torch.cuda.synchronize()
+    out = dC[0].double().cpu().numpy() + 1j * dC[1].double().cpu().numpy()
+    refn = A @ Bn
+    assert np.linalg.norm(out - refn) / np.linalg.norm(refn) < 5e-5
+
+
+def test_expired_waits_return_timeout_and_the_context_stays_usable(tk):
+    # failure detection without a fault: with a one-poll limit the bounded mbarrier waits of the
+    # tensor-core kernels expire while their MMAs are still running; the kernel records the
+    # expiry, drains its committed MMAs, frees its tensor memory and the call returns
+    # MF_ERR_TIMEOUT.  The kernels are deterministic, so every attempt either times out or returns
+    # exactly the bits of a run with the default limit; afterwards the default limit gives those
+    # bits again on the same context.
+    import paper_2007_00202_gb300.mf as mf
+    torch = tk
+    MF_ERR_TIMEOUT = -7
+    rng = np.random.default_rng(99)
+    m, n, k = 1024, 1024, 4096
+    A = rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))
+    B = rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))
+    dA, dB = _planar(torch, A, k), _planar(torch, B, k)
+    mn, kn = 96 * 304 * 3, 16                 # tensor-core narrow kernel: many one-chunk tiles per CTA
+    An = rng.standard_normal((mn, kn)) + 1j * rng.standard_normal((mn, kn))
+    Bn = rng.standard_normal((kn, 64)) + 1j * rng.standard_normal((kn, 64))
+    dAn, dBn = _planar(torch, An, kn), _planar(torch, Bn, 64)
+
+    def front():
+        dC = torch.zeros(2, m, n, dtype=torch.float32, device="cuda")
+        mf.mf_gemm_c64(2, m, n, k, dA.data_ptr(), k, m * k, dB.data_ptr(), k, n * k, dC.data_ptr(), n, m * n,
+                       -1.0, 0.0, 0)
+        torch.cuda.synchronize()
+        return dC.cpu().numpy()
+
+    def narrow():
+        dC = torch.zeros(2, mn, 64, dtype=torch.float32, device="cuda")
+        mf.mf_gemm_nrhs_c64(0, mn, 64, kn, dAn.data_ptr(), kn, mn * kn, dBn.data_ptr(), 64, kn * 64,
+                            dC.data_ptr(), 64, mn * 64, -1.0, 0.0, -1, 0)
+        torch.cuda.synchronize()
+        return dC.cpu().numpy()
+
+    for call, ref in ((front, -(A @ B.T)), (narrow, -(An @ Bn))):
+        base = call()                          # default limit
+        got = base[0].astype(np.float64) + 1j * base[1].astype(np.float64)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-4
+        timeouts = 0
+        mf.mf_set_wait_limit(1)
+        try:
+            for attempt in range(6):
+                try:
+                    out = call()
+                    assert np.array_equal(out, base)
+                except mf.MfError as e:
+                    assert e.code == MF_ERR_TIMEOUT, e
+                    timeouts += 1
+        finally:
+            mf.mf_set_wait_limit(0)
+        assert timeouts >= 1, call.__name__
+        assert np.array_equal(call(), base)
