@@ -407,19 +407,23 @@ int mf_factor(mf_handle* h, double tol) {
       // (released after each front)
       size_t el = h->opt.precision == MF_PREC_C128 ? 16 : 8;
       // without a rank cap the sketch widths may double several times: give the work arena room
-      // (measured peaks: 64^3, one front of s + u = 6144: 1.6 GB; 100^3: one request of 4.8 GB)
-      const size_t per = h->opt.max_rank > 0 ? 80000 : 320000;
+      // (measured work of one front: 1.6 GB at s + u = 6144 (64^3), more than 9.6 GB at 15000 (100^3))
+      const size_t per = h->opt.max_rank > 0 ? 320000 : 1280000;
       eo.persist_bytes = any_comp ? std::max<size_t>(size_t(4) << 30, comp_n * 24000 * el) : 0;
       eo.scratch_bytes = any_comp ? std::max<size_t>(size_t(2) << 30, max_n * per * el) : 0;
-      // the persistent arena and up to eight work arenas stay within 70 % of the free memory
+      // the persistent arena takes at most 40 % of the free memory; as many work arenas as fit in
+      // 70 % of it beside it (1 to 8) set the number of construction contexts
       size_t fr = 0, tot = 0;
       if (any_comp && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-        const double want = (double)eo.persist_bytes + 8.0 * (double)eo.scratch_bytes, room = 0.7 * (double)fr;
-        if (want > room) {
-          const double f = room / want;
-          eo.persist_bytes = (size_t)(f * (double)eo.persist_bytes);
-          eo.scratch_bytes = (size_t)(f * (double)eo.scratch_bytes);
+        const double room = 0.7 * (double)fr;
+        eo.persist_bytes = std::min(eo.persist_bytes, (size_t)(0.4 * (double)fr));
+        const double left = room - (double)eo.persist_bytes;
+        int nc = (int)(left / (double)eo.scratch_bytes);
+        if (nc < 1) {
+          nc = 1;
+          eo.scratch_bytes = (size_t)std::max(0.0, left);
         }
+        eo.max_contexts = std::min(nc, 8);
       }
       h->eng = h->opt.precision == MF_PREC_C128 ? mf::make_engine_c128(h->an, h->A, h->stream, eo)
                                                : mf::make_engine_c64(h->an, h->A, h->stream, eo);

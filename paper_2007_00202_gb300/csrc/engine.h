@@ -217,7 +217,8 @@ struct EngineOptions {
   int alpha = 2, knn = 8;
   uint64_t seed = 1;
   size_t persist_bytes = size_t(24) << 30;   // device arena for compressed factors
-  size_t scratch_bytes = size_t(12) << 30;   // device arena for construction work
+  size_t scratch_bytes = size_t(12) << 30;   // device arena for construction work, per context
+  int max_contexts = 8;                        // construction contexts (host threads) per tree level
 };
 
 std::unique_ptr<EngineBase> make_engine_c64(const Analysis& an, const DeviceMatrix& A, cudaStream_t st,

@@ -90,13 +90,13 @@ class DenseEngine : public EngineBase {
           if (F[fid].parent >= 0 && !F[F[fid].parent].compressed) comp_->densify_C(fid, fr_[fid], w);
         }
       };
-      if (lvl.size() == 1 || serial) {
+      if (lvl.size() == 1 || serial || eo_.max_contexts <= 1) {
         run(lvl, 0, 1, 0);
       } else {
         // the fronts of one level are independent: up to kMaxContexts host threads build them, each
         // with its own stream and scratch arena, taking the next front of the level when done, so
         // that one thread's host work overlaps the others' GPU work
-        const int nctx = std::min<int>((int)lvl.size(), CompressedPart<T>::kMaxContexts);
+        const int nctx = std::min<int>({(int)lvl.size(), CompressedPart<T>::kMaxContexts, std::max(1, eo_.max_contexts)});
         comp_->ensure_contexts(nctx);
         MF_CUDA(cudaEventRecord(lev_ev_[0], st_));                  // children and dense fronts below
         for (int w = 1; w < nctx; ++w) MF_CUDA(cudaStreamWaitEvent(comp_->stream(w), lev_ev_[0], 0));

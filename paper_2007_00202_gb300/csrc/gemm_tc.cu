@@ -9,14 +9,14 @@
 // A complex product is four real products into two TMEM accumulators:
 //   Dre += Are Bre^T ; Dre += (-Aim) Bim^T (negate-A bit) ; Dim += Are Bim^T ; Dim += Aim Bre^T.
 //
-// One CTA (4 warps) computes a 128 x 128 output tile.  Operand tiles of 8
+// One CTA (8 warps) computes a 128 x 128 output tile.  Operand tiles of 8
 // K-elements are staged in shared memory by cp.async (16-byte copies, zero
 // fill past the edges) in the canonical no-swizzle K-major layout of 8 x 16-byte
 // core matrices, 6 stages with copies issued 4 chunks ahead; thread 0 issues the
 // MMAs and commits each stage to an mbarrier, which frees the stage.  A stage is
 // refilled once the MMAs of the chunk two behind have completed, so the tensor core
 // works on one chunk while the threads stage and split the next.  The epilogue
-// reads TMEM with tcgen05.ld (one row per thread), transposes 32 x 32 blocks
+// reads TMEM with tcgen05.ld (a lane per row, half the columns per warpgroup), transposes 32 x 32 blocks
 // through shared memory and writes C rows with consecutive lanes on consecutive
 // columns, applying alpha / beta.
 // SPLIT = true is the split-precision form: every staged value x is replaced in
@@ -35,7 +35,7 @@ namespace mf {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 8, STAGES = 6, NT = 128;
+constexpr int BM = 128, BN = 128, BK = 8, STAGES = 6, NT = 256;
 constexpr int PREFETCH = STAGES - 2;                     // chunks whose copies are in flight
 constexpr int KCH = BK / 4;                              // 16-byte K chunks per row
 constexpr int TILE_BYTES = BM * BK * 4;                  // one plane tile of A (or B): 4 KB
@@ -256,14 +256,15 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc<float>* __rest
   if (!ok) {
     if (status) atomicExch(status, 2);
   } else {
-    // epilogue: TMEM lane tid holds row m0 + tid of the tile
+    // epilogue: TMEM lane q holds row m0 + q of the tile
     const int lane = tid & 31;
     float* tb = reinterpret_cast<float*>(sgen) + warp * (2 * 32 * 33);
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows); the two warpgroups take half the columns each
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     float* Cr = d.C.re;
     float* Ci = d.C.re + d.C.plane;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
+    for (int c0 = (warp >> 2) * (BN / 2); c0 < (warp >> 2) * (BN / 2) + BN / 2; c0 += 32) {
       uint32_t vr[32], vi[32];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc<float>* __rest
       const int col = n0 + c0 + lane;
 #pragma unroll 4
       for (int r = 0; r < 32; ++r) {
-        const int grow = m0 + warp * 32 + r;
+        const int grow = m0 + (warp & 3) * 32 + r;
         if (grow < d.m && col < d.n) {
           const int64_t off = (int64_t)grow * d.C.ld + col;
           float xr = d.alpha * tb[r * 33 + lane];
