@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) measurement")
     ap.add_argument("--no-bfapply", action="store_true", help="skip the batched butterfly-apply measurement")
     ap.add_argument("--serving-full", action="store_true",
-                    help="run the full serving workload (32^3 + 64^3 + 100^3 resident, 2000 requests of 1-256 RHS) "
-                         "instead of the bounded one; takes several minutes")
+                    help="run only the full serving workload (32^3 + 64^3 + 100^3 resident, 2000 requests of "
+                         "1-256 RHS) and print its JSON line; takes several minutes")
     return ap.parse_args()
 
 
@@ -255,6 +255,39 @@ def oracle_sample(n=20, nrhs=16):
         "seconds": dt, "err_vs_oracle_exact": _rel(X, x_exact)}
 
 
+def direct_16cube(g, torch):
+    """The 16^3 direct-solver configuration: helmholtz7 16^3 (ppw 8), separators >= 128 HOD-BF at
+    tol 1e-6, complex128 factors, no refinement, RHS a point source at (8, 8, 8) plus a Gaussian
+    column (seed 42); error against the oracle's exact solution (Alg. 1, FP64)."""
+    import numpy as np
+    import workloads as w
+    from oracle.analysis import analyze
+    from oracle import dense_mf as dm
+    p = w.helmholtz7(16, 8)
+    b = w.rhs_point_plus_gaussian(p, 42)
+    an = analyze(p, 64, 10 ** 9)
+    xe = dm.solve(p, an, dm.multifrontal_factor(p, an)[0], b)
+    h = g.analyze_problem(p, nmin_sep=128, precision=g.MF_PREC_C128, refine=g.MF_REFINE_NONE,
+                          stream=torch.cuda.current_stream().cuda_stream)
+    h.mf_factor(1e-6)
+    h.mf_solve(b, allow_no_convergence=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.mf_factor(1e-6)
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, _ = h.mf_solve(b, allow_no_convergence=True)
+    ts = time.perf_counter() - t0
+    A = p.to_scipy()
+    st = h.mf_stats()
+    return {"workload": "helmholtz7 16^3 (N=4096), ppw 8, separators >= 128 HOD-BF at tol 1e-6, complex128, "
+                        "no refinement, point source + Gaussian RHS (seed 42)",
+            "compressed_fronts": st["ncompressed"], "factor_s": tf, "solve_s": ts,
+            "max_rel_residual": float(np.max(np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0))),
+            "err_vs_oracle": _rel(x, xe)}
+
+
 def gpu_paths_on(g, torch, p, b, x_exact, nmin, tol=1e-4):
     """The four GPU variants on one problem: factor s, solve s, solves/s, iterations, residual and
     the error against the oracle's exact solution x_exact."""
@@ -349,6 +382,9 @@ def serving_full(g, w, torch, nreq=2000):
     capacity; batches admitted by free device memory; GMRES to 1e-8.  50 sampled requests are checked
     with an FP64 residual on the host."""
     import numpy as np
+    # three factorizations stay resident: one construction context each (one work arena per handle),
+    # so that the batches' GMRES workspace fits beside them
+    os.environ["MF_SERIAL_FRONTS"] = "1"
     probs = [w.helmholtz7(32, 10), w.helmholtz7(64, 10), w.helmholtz7(100, 10)]
     streams = [torch.cuda.Stream() for _ in probs]
     hs = []
@@ -362,18 +398,18 @@ def serving_full(g, w, torch, nreq=2000):
     which = rng.integers(0, len(probs), nreq)
     widths = np.rint(np.exp(rng.uniform(0.0, math.log(256.0), nreq))).astype(int)
     pools = [np.asfortranarray(w.complex_gaussian(rng, p.n, 256)) for p in probs]
-    # single-stream capacity: solves/s of one 64-column batch per problem, averaged over the mix
+    # single-stream capacity: solves/s of one 32-column batch per problem, averaged over the mix
     cap = []
     for p, h, pool in zip(probs, hs, pools):
-        h.mf_solve(pool[:, :64])
+        h.mf_solve(pool[:, :32])
         t0 = time.perf_counter()
-        h.mf_solve(pool[:, :64])
-        cap.append(64 / (time.perf_counter() - t0))
+        h.mf_solve(pool[:, :32])
+        cap.append(32 / (time.perf_counter() - t0))
     mix = np.bincount(which, minlength=len(probs)) / nreq
     capacity = 1.0 / float(np.sum(mix / np.array(cap)))          # RHS per second over the request mix
     rate = 0.8 * capacity / float(np.mean(widths))                # requests per second
     gaps = rng.exponential(1.0 / rate, nreq)
-    srv = g.Server(hs, max_batch_rhs=64, mem_budget_bytes=1 << 62)   # admission by free device memory
+    srv = g.Server(hs, max_batch_rhs=32, mem_budget_bytes=1 << 62)   # admission by free device memory
     ids, t0 = [], time.perf_counter()
     t = t0
     for k in range(nreq):
@@ -494,6 +530,13 @@ def main():
     barrier(world)
     import paper_2007_00202_gb300 as g
     import workloads as w
+
+    if args.serving_full:
+        if rank == 0:
+            print(json.dumps({"metric": "serving p50/p99 latency and solves/s (full serving workload)",
+                              "serving_full": serving_full(g, w, torch)}), flush=True)
+        barrier(world)
+        return
 
     n = args.grid
     nrhs = args.nrhs
@@ -655,9 +698,7 @@ def main():
         del hb
       except Exception as e:
         line["fp64_butterfly_path"] = {"error": str(e)[:300]}
-    if rank == 0 and args.serving_full:
-        line["serving_full"] = serving_full(g, w, torch)
-    elif rank == 0 and not args.no_serving:
+    if rank == 0 and not args.no_serving:
         line["serving"] = serving(g, w, torch)
     if rank == 0 and not args.no_bfapply:
         line["butterfly_apply"] = butterfly_apply(g, w, torch, measured_peaks())
@@ -674,6 +715,7 @@ def main():
             if key in line:
                 line[key]["err_vs_oracle_20cube"] = same[name]["err_vs_oracle"]
         line["err_vs_oracle_20cube"] = same["compressed_c64"]["err_vs_oracle"]
+        line["direct_16cube"] = direct_16cube(g, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(world)

@@ -7,7 +7,8 @@ narrow: the narrow GEMM of the solve (mf_gemm_nrhs_c64), C = -A B + C with A 409
         B 4096 x 16 (complex64): one launch streams 128 MiB of A (larger than L2).
 front:  the split-TF32 tcgen05 front GEMM (mf_gemm_c64 engine 2), 4096 x 4096 x 4096.
 rowid:  the batched row ID (mf_row_id_c64) of 256 matrices of 128 x 72 (the randomized
-        construction's sketch blocks).
+        construction's sketch blocks); rowid_big: 8 matrices of 256 x 1024 (the entry
+        evaluation's large proxy blocks, one thread-block cluster each).
 factor: the compressed complex64 factorization of the bench workload (helmholtz7 G^3, ppw 10,
         separators >= 1024 HOD-BF at tol 1e-4, rank <= 64), once to warm up, then once between
         cudaProfilerStart/Stop (for `ncu --profile-from-start off`).
@@ -90,6 +91,13 @@ def front(torch, mf, reps, m=4096, n=4096, k=4096):
     return {"kernel": "k_gemm_tc<1> (split TF32, 3 passes)", "shape": [m, n, k], "ms": ms,
             "tflops": flops / ms / 1e9, "tensor_tflops": 3 * flops / ms / 1e9,
             "tf32_frac": 3 * flops / ms / 1e9 / 999.0}
+
+
+def rowid_big(torch, mf, reps):
+    """The large-block row ID (8 matrices of 256 x 1024, rank <= 64): a thread-block cluster each."""
+    r = rowid(torch, mf, reps, nmat=8, m=256, n=1024)
+    r["kernel"] = "k_row_id_cluster"
+    return r
 
 
 def rowid(torch, mf, reps, nmat=256, m=128, n=72):
@@ -244,7 +252,8 @@ def main():
         elif w == "bfapply":
             r = bfapply(torch, mf, args.reps, args.blocks)
         else:
-            r = {"narrow": narrow, "front": front, "rowid": rowid, "peaks": peaks}[w](torch, mf, args.reps)
+            r = {"narrow": narrow, "front": front, "rowid": rowid, "rowid_big": rowid_big,
+                 "peaks": peaks}[w](torch, mf, args.reps)
         print(json.dumps(r), flush=True)
 
 

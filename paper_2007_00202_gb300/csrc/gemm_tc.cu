@@ -99,17 +99,21 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
 }
 
-// Stage one 128 x 32 tile of a planar operand (rows r0.., K from k0) into smem.
+// The 16-byte chunk (row r, K chunk) of a staged tile that thread tid copies in its e-th copy.
+__device__ __forceinline__ void chunk_of(int tid, int e, int& r, int& chunk) {
+  const int idx = tid + e * NT;
+  chunk = (idx >> 3) % KCH;               // 16-byte K chunk
+  r = (idx / (8 * KCH)) * 8 + (idx & 7);  // 8-row group, row within it
+}
+
+// Stage one 128 x BK tile of a planar operand (rows r0.., K from k0) into smem.
 __device__ __forceinline__ void load_tile(uint32_t dst_re, uint32_t dst_im, const float* re, int64_t plane, int64_t ld,
                                           int rows, int r0, int K, int k0, int tid) {
-  // 128 rows x KCH chunks of 16 B per plane; 128 threads
+  // 128 rows x KCH chunks of 16 B per plane, (BM * KCH) / NT per thread
 #pragma unroll
   for (int e = 0; e < (BM * KCH) / NT; ++e) {
-    int idx = tid + e * NT;
-    int lane_r = idx & 7;                 // row within the 8-row group
-    int chunk = (idx >> 3) % KCH;         // 16-byte K chunk
-    int grp = idx / (8 * KCH);            // 8-row group (0..15)
-    int r = grp * 8 + lane_r;
+    int r, chunk;
+    chunk_of(tid, e, r, chunk);
     int gr = r0 + r, gk = k0 + chunk * 4;
     uint32_t bytes = 0;
     const float* src = re;
@@ -200,15 +204,26 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc<float>* __rest
     cp_commit();
     cp_wait<PREFETCH>();
     if (SPLIT) {
-      __syncthreads();
-      // each staged value -> hi in place, lo into the second half of the stage
-      float* st4 = reinterpret_cast<float*>(sgen + s * STAGE_BYTES);
-#pragma unroll 4
-      for (int e = tid; e < 4 * BM * BK; e += NT) {
-        float hi, lo;
-        split_tf32(st4[e], hi, lo);
-        st4[e] = hi;
-        st4[e + 4 * BM * BK] = lo;
+      // the chunks this thread copied (its own copies are complete): hi in place, lo into the
+      // second half of the stage; no barrier is needed before, the one below orders all of them
+      // before the MMAs
+#pragma unroll
+      for (int e = 0; e < (BM * KCH) / NT; ++e) {
+        int r, chunk;
+        chunk_of(tid, e, r, chunk);
+        const uint32_t off = tile_off(r, chunk);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {   // A re, A im, B re, B im
+          float4* p = reinterpret_cast<float4*>(sgen + s * STAGE_BYTES + t * TILE_BYTES + off);
+          float4* q = reinterpret_cast<float4*>(sgen + s * STAGE_BYTES + (4 + t) * TILE_BYTES + off);
+          float4 x = *p, h, l;
+          split_tf32(x.x, h.x, l.x);
+          split_tf32(x.y, h.y, l.y);
+          split_tf32(x.z, h.z, l.z);
+          split_tf32(x.w, h.w, l.w);
+          *p = h;
+          *q = l;
+        }
       }
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");

@@ -1,5 +1,5 @@
 """3D Poisson (Sec. 6.3: the same solver with k = 0) on the GPU compressed path: complex64 HOD-BF
-fronts at tol 1e-4, FP64 GMRES to 1e-8, compared with the exact multifrontal solution."""
+fronts at tol 1e-4, FP64 GMRES to 1e-8, compared with the oracle's exact multifrontal solution."""
 import numpy as np
 import pytest
 
@@ -30,6 +30,10 @@ def test_poisson_32cube_compressed_gmres_to_1e8(g):
     A = p.to_scipy()
     res = np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)
     assert info.converged == 1 and res.max() <= 1e-8
-    import scipy.sparse.linalg as sla
-    xe = sla.spsolve(A.tocsc(), b)
+    # the oracle's exact multifrontal solution (Alg. 1, FP64) of the same system
+    from oracle.analysis import analyze
+    from oracle import dense_mf as dm
+    an = analyze(p, 64, 10 ** 9)
+    xe = dm.solve(p, an, dm.multifrontal_factor(p, an)[0], b)
+    assert np.linalg.norm(A @ xe - b) / np.linalg.norm(b) <= 1e-12
     assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-6

@@ -105,3 +105,23 @@ def test_request_status_does_not_depend_on_its_batch(env):
     srv.close()
     assert ib["status"] == -6 and ib["converged"] == 0
     assert iz["status"] == 0 and iz["converged"] == 1 and np.all(xz == 0)
+
+
+def test_wide_request_runs_in_slices_like_alone(env):
+    # a request wider than the batch limit runs alone, in slices of max_batch_rhs columns; its
+    # columns are independent, so its solution, status and per-column results match one solve
+    g, probs, hs, streams = env
+    import paper_2007_00202_gb300.mf as mf
+    p = probs[1]
+    rng = np.random.default_rng(17)
+    b = w.complex_gaussian(rng, p.n, 11)
+    xa, ia = hs[1].mf_solve(b)
+    srv = mf.Server(hs, max_batch_rhs=4, mem_budget_bytes=8 << 30)
+    x, info = srv.wait(srv.submit(1, b))
+    srv.close()
+    A = p.to_scipy()
+    res = np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)
+    assert info["status"] == 0 and info["converged"] == 1 and info["batch_rhs"] == 11
+    assert res.max() <= 1e-8 and abs(info["max_rel_residual"] - res.max()) <= 1e-9
+    assert np.linalg.norm(x - xa) / np.linalg.norm(xa) <= 1e-6
+
