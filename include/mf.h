@@ -64,7 +64,7 @@ typedef struct {
   int32_t lattice;        /* [MF_LATTICE_NODE] how coords are read (see mf_analyze)             */
   double rtol;            /* [1e-8] target ||b - A x|| / ||b||                                  */
   uint64_t seed;          /* [1]    seed of the random sketches                                 */
-  const int32_t* coords;  /* [NULL] N x 3 integer lattice coordinates, required                 */
+  const int32_t* coords;  /* [NULL] N x 3 integer lattice coordinates; NULL: graph ordering    */
 } mf_options;
 
 typedef struct {
@@ -96,15 +96,19 @@ typedef struct mf_handle mf_handle;
 int mf_options_init(mf_options* opt);
 
 /*
- * Symbolic analysis (Alg. 1 lines 2-3, Alg. 5 line 2; Sec. 2, 5.1, 5.2).
+ * Symbolic analysis (the ordering and symbolic steps of Alg. 1 and Alg. 5; Sec. 2, 5.1, 5.2).
  *   n, rowptr[n+1] (int64), colind[nnz] (int32, 0-based), vals[2*nnz] (re, im):
  *     the CSR matrix A; the pattern must be structurally symmetric.
- *   opt->coords (N x 3 int32, required): lattice coordinates of the unknowns.
+ *   opt->coords (N x 3 int32, optional): lattice coordinates of the unknowns.
  *     MF_LATTICE_NODE: grid indices (separator planes are layers of unknowns);
  *     MF_LATTICE_EDGE: doubled coordinates of a Yee edge lattice (an edge at
  *     (i+1/2, j, k) is (2i+1, 2j, 2k)); separators are node planes.
+ *     NULL: general CSR input, ordered by graph nested dissection (breadth-first
+ *     level structures from a pseudo-peripheral vertex; separator = the level
+ *     where half of the reached vertices are passed; compressed separators
+ *     ordered by a breadth-first search of their own subgraph).
  *   cuda_stream: the CUDA stream all device work of this handle runs on (NULL = default).
- * Computes the planar nested-dissection ordering, the assembly tree, the
+ * Computes the nested-dissection ordering (planar or graph), the assembly tree, the
  * update sets, the HOD-BF cluster trees and the neighbour lists on the host;
  * no device memory is touched until mf_factor.  *out receives a new handle.
  * Errors: MF_ERR_ARG (bad pointers/sizes/CSR), MF_ERR_UNSUPPORTED (a box with

@@ -5,9 +5,13 @@ tests, the smoke check and the benchmark's CPU-baseline leg may use it.  It
 shares no code with the GPU path (whose host analysis is written separately
 in C++ from the same rules) and must agree with it bit for bit.
 
-Rules implemented (Sec. 2; Sec. 5.1; Sec. 5.2; Alg. 1 lines 2-3; Alg. 5 line 2):
+Rules implemented (Sec. 2; Sec. 5.1; Sec. 5.2; the ordering and symbolic steps of Alg. 1 and Alg. 5):
   * nested dissection by planar separators on lattice boxes (the Helmholtz runs
-    of Sec. 6 use planar separators),
+    of Sec. 6 use planar separators), or, for a general CSR input without
+    coordinates, by graph level structures (breadth-first search from a
+    pseudo-peripheral vertex; the separator is the level where half of the
+    reached vertices are passed; compressed separators ordered by a
+    breadth-first search of their own subgraph, balanced cluster tree),
   * post-order assembly tree, I^s (a separator) and I^u (update set) per front,
     with  I^u_nu  contained in  I^s_tau U I^u_tau  (Sec. 2),
   * rank-reducing separator reordering P-hat by recursive geometric bisection
@@ -149,16 +153,95 @@ def cluster_tree_balanced(npts: int, leaf: int):
     return levels
 
 
-def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64) -> Analysis:
-    """Nested dissection + assembly tree + symbolic factorization (Alg. 1 l.2-3, Alg. 5 l.2)."""
-    coords = prob.coords.astype(np.int64)
+def _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts):
+    """Graph nested dissection of a CSR pattern (no coordinates).
+
+    The fill-reducing ordering of a general sparse matrix comes from nested dissection of its
+    graph (Sec. 2; the Maxwell experiment of Sec. 6.2 is ordered this way).  The graph is the
+    (structurally symmetric) pattern of A without self loops.  The bisection rule here is a level-structure one
+    (METIS's multilevel partitioner, which the paper names, is a library this project does not
+    reproduce); the rule is deterministic, so the GPU analysis can be compared with it exactly.
+    A set of more than leaf_size vertices: breadth-first search inside the set from its smallest
+    vertex, neighbours visited in increasing index; p = the smallest vertex of the last level;
+    search again from p.  The separator is level m, the first level at which levels 0..m hold at
+    least half of the vertices reached from p, kept in 1 .. (number of levels - 2); levels below m
+    form the first child, levels above m and the vertices not reached from p (other components)
+    the second.  With fewer than three levels the set is a front of its own.  A separator at or
+    above nmin_sep is ordered by breadth-first search of its own subgraph before the balanced
+    bisection that defines its HOD-BF tree: the paper bisects the graph of A(I^s, I^s) for that
+    hierarchy in the algebraic setting (Sec. 5.1), and a breadth-first order keeps graph
+    neighbours at nearby positions, so each contiguous cluster is a connected piece."""
+    adj = [sorted(set(int(c) for c in ci[rp[i]:rp[i + 1]]) - {i}) for i in range(N)]
+
+    def bfs(start, inside, seen):
+        levels = [[start]]
+        seen.add(start)
+        while True:
+            nxt = []
+            for v in levels[-1]:
+                for w in adj[v]:
+                    if w in inside and w not in seen:
+                        seen.add(w)
+                        nxt.append(w)
+            if not nxt:
+                return levels
+            levels.append(nxt)
+
+    def new_front(sep, kids, compressed, th):
+        sep = np.asarray(sep, dtype=np.int64)
+        fronts_sep.append((sep, kids, compressed, th))
+        perm_parts.append(sep)
+        return len(fronts_sep) - 1
+
+    def nd(ids):                     # ids: sorted list of vertices
+        if len(ids) <= leaf_size:
+            return new_front(ids, [], False, None)
+        inside = set(ids)
+        lv0 = bfs(ids[0], inside, set())
+        p = min(lv0[-1])
+        reached = set()
+        lv = bfs(p, inside, reached)
+        nl = len(lv)
+        if nl < 3:
+            return new_front(ids, [], False, None)
+        total = sum(len(l) for l in lv)
+        acc, m = 0, 0
+        while m < nl:
+            acc += len(lv[m])
+            if 2 * acc >= total:
+                break
+            m += 1
+        m = max(1, min(m, nl - 2))
+        left = sorted(v for i in range(m) for v in lv[i])
+        right = sorted([v for i in range(m + 1, nl) for v in lv[i]] + [v for v in ids if v not in reached])
+        sep = sorted(lv[m])
+        kids = []
+        if left:
+            kids.append(nd(left))
+        if right:
+            kids.append(nd(right))
+        if len(sep) >= nmin_sep:
+            inside_sep, done, order = set(sep), set(), []
+            for s0 in sep:           # components of the separator's subgraph, from their smallest vertex
+                if s0 in done:
+                    continue
+                for level in bfs(s0, inside_sep, done):
+                    order += level
+            return new_front(order, kids, True, cluster_tree_balanced(len(order), hodbf_leaf))
+        return new_front(sep, kids, False, None)
+
+    nd(list(range(N)))
+
+
+def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False) -> Analysis:
+    """Nested dissection + assembly tree + symbolic factorization (the ordering and symbolic steps of Alg. 1 and Alg. 5).
+    graph=True ignores the coordinates (graph nested dissection of the pattern)."""
     lattice = prob.lattice
     N = prob.n
     rp, ci = prob.rowptr, prob.colind
 
     fronts_sep = []     # list of (old ids of separator in front order, children front ids, compressed)
     perm_parts = []
-    counter = [0]
 
     def nd(ids, lo, hi):
         """Returns the front id of the subtree root."""
@@ -194,8 +277,12 @@ def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64) -> Analysis:
         perm_parts.append(sep)
         return fid
 
-    lo, hi = _initial_box(coords, lattice)
-    nd(np.arange(N, dtype=np.int64), lo, hi)
+    if graph:
+        _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts)
+    else:
+        coords = prob.coords.astype(np.int64)
+        lo, hi = _initial_box(coords, lattice)
+        nd(np.arange(N, dtype=np.int64), lo, hi)
 
     perm = np.concatenate(perm_parts).astype(np.int64)
     assert len(perm) == N

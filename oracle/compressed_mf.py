@@ -4,7 +4,7 @@ Test infrastructure only (see oracle/analysis.py).
 
 For every front in topological order (Alg. 5):
   * separator smaller than nmin_sep: dense front, Alg. 1 (dense_mf.py);
-  * otherwise (Sec. 5, steps after Eq. (5.1); Alg. 5 lines 8-12):
+  * otherwise (Sec. 5, steps after Eq. (5.1); the large-front branch of Alg. 5):
       F11   <- HODBF_entry_eval(A(Is,Is) (+) C_nu1 (+) C_nu2)
       F11^-1<- HODBF_invert(F11)                                   (Alg. 4)
       F12   <- BF_entry_eval(A(Is,Iu) (+) C_nu1 (+) C_nu2)          (Alg. 2)

@@ -1,5 +1,16 @@
-// Host-side symbolic analysis (Sec. 2; Sec. 5.1; Sec. 5.2; Alg. 1 lines 2-3; Alg. 5 line 2).
+// Host-side symbolic analysis (Sec. 2; Sec. 5.1; Sec. 5.2; the ordering and symbolic steps of Alg. 1 and Alg. 5).
 //
+// * Without coordinates (general CSR input), nested dissection by graph level
+//   structures (Sec. 2): a set of more than leaf_size vertices is split by a
+//   breadth-first search (restricted to the set, neighbours in increasing index)
+//   from a pseudo-peripheral vertex (the smallest vertex of the last level of a
+//   search from the set's smallest vertex); the separator is the first level
+//   at which the levels so far hold at least half of the reached vertices
+//   (kept between the first and the last level), the lower levels form the first
+//   child and the higher levels plus any unreached vertices the second.  Fronts
+//   list their vertices in increasing index; a compressed separator is ordered
+//   by a breadth-first search of its own subgraph and clustered in balanced
+//   halves of that order.
 // * Nested dissection by planar separators on integer lattice boxes.  A box is
 //   half-open [lo, hi) per axis.  The separator axis is the first axis of
 //   largest extent (x, then y, then z); for the node lattice the extent is
@@ -24,6 +35,8 @@
 
 namespace mf {
 
+std::vector<std::vector<Range>> cluster_tree_balanced(int64_t npts, int64_t leaf);
+
 namespace {
 
 using C3 = std::array<int64_t, 3>;
@@ -32,6 +45,11 @@ struct Builder {
   const int32_t* coords;
   int lattice;
   int leaf, nmin, hleaf;
+  // graph mode: adjacency with sorted neighbour lists, set membership marks
+  std::vector<int64_t> adj_ptr;
+  std::vector<int32_t> adj;
+  std::vector<int64_t> mark;   // mark[v] == tag: v in the current set
+  int64_t tag = 0;
   struct Raw {
     std::vector<int64_t> sep;  // old ids in front order
     std::vector<int64_t> kids;
@@ -99,6 +117,92 @@ struct Builder {
     return order;
   }
 
+  // breadth-first search from s over the vertices with mark == t; returns the levels
+  std::vector<std::vector<int64_t>> bfs_levels(int64_t s, int64_t t, std::vector<int64_t>& seen, int64_t stamp) const {
+    std::vector<std::vector<int64_t>> lv{{s}};
+    seen[s] = stamp;
+    for (;;) {
+      std::vector<int64_t> nxt;
+      for (int64_t v : lv.back())
+        for (int64_t k = adj_ptr[v]; k < adj_ptr[v + 1]; ++k) {
+          const int64_t w = adj[k];
+          if (mark[w] == t && seen[w] != stamp) {
+            seen[w] = stamp;
+            nxt.push_back(w);
+          }
+        }
+      if (nxt.empty()) break;
+      lv.push_back(std::move(nxt));
+    }
+    return lv;
+  }
+  std::vector<int64_t> seen_;
+  int64_t stamp_ = 0;
+
+  // breadth-first order of a separator's own subgraph (components from their smallest vertex)
+  std::vector<int64_t> bfs_order(const std::vector<int64_t>& sorted_ids) {
+    const int64_t t = ++tag;
+    for (int64_t v : sorted_ids) mark[v] = t;
+    const int64_t st = ++stamp_;
+    std::vector<int64_t> order;
+    for (int64_t s0 : sorted_ids) {
+      if (seen_[s0] == st) continue;
+      auto lv = bfs_levels(s0, t, seen_, st);
+      for (auto& l : lv) order.insert(order.end(), l.begin(), l.end());
+    }
+    return order;
+  }
+
+  int64_t nd_graph(std::vector<int64_t>& ids) {   // ids sorted ascending
+    auto leaf_front = [&](std::vector<int64_t>& v) {
+      Raw r;
+      r.sep = std::move(v);
+      r.compressed = false;
+      raw.push_back(std::move(r));
+      return (int64_t)raw.size() - 1;
+    };
+    if ((int64_t)ids.size() <= leaf) return leaf_front(ids);
+    const int64_t t = ++tag;
+    for (int64_t v : ids) mark[v] = t;
+    auto lv0 = bfs_levels(ids[0], t, seen_, ++stamp_);
+    const int64_t p = *std::min_element(lv0.back().begin(), lv0.back().end());
+    auto lv = bfs_levels(p, t, seen_, ++stamp_);
+    const int64_t nl = (int64_t)lv.size();
+    if (nl < 3) return leaf_front(ids);   // no level strictly inside the structure
+    int64_t reached = 0;
+    for (auto& l : lv) reached += (int64_t)l.size();
+    int64_t m = 0, acc = 0;
+    for (; m < nl; ++m) {
+      acc += (int64_t)lv[m].size();
+      if (2 * acc >= reached) break;
+    }
+    m = std::max<int64_t>(1, std::min<int64_t>(m, nl - 2));
+    std::vector<int64_t> left, right, sep = lv[m];
+    const int64_t st = stamp_;   // seen_[v] == st: v reached from p
+    for (int64_t i = 0; i < m; ++i) left.insert(left.end(), lv[i].begin(), lv[i].end());
+    for (int64_t i = m + 1; i < nl; ++i) right.insert(right.end(), lv[i].begin(), lv[i].end());
+    for (int64_t v : ids)
+      if (seen_[v] != st) right.push_back(v);
+    std::vector<int64_t>().swap(ids);
+    std::sort(left.begin(), left.end());
+    std::sort(right.begin(), right.end());
+    std::sort(sep.begin(), sep.end());
+    std::vector<int64_t> kids;
+    if (!left.empty()) kids.push_back(nd_graph(left));
+    if (!right.empty()) kids.push_back(nd_graph(right));
+    Raw r;
+    r.compressed = (int64_t)sep.size() >= nmin;
+    if (r.compressed) {
+      r.sep = bfs_order(sep);
+      r.th = cluster_tree_balanced((int64_t)r.sep.size(), hleaf);
+    } else {
+      r.sep = std::move(sep);
+    }
+    r.kids = std::move(kids);
+    raw.push_back(std::move(r));
+    return (int64_t)raw.size() - 1;
+  }
+
   int64_t nd(std::vector<int64_t>& ids, C3 lo, C3 hi) {
     if ((int64_t)ids.size() <= leaf) {
       Raw r;
@@ -164,7 +268,7 @@ std::vector<std::vector<Range>> cluster_tree_balanced(int64_t npts, int64_t leaf
 
 void analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* coords, int lattice,
              int leaf_size, int nmin_sep, int hodbf_leaf, Analysis& out) {
-  if (n <= 0 || !rowptr || !colind || !coords) throw std::runtime_error("invalid CSR or coordinates");
+  if (n <= 0 || !rowptr || !colind) throw std::runtime_error("invalid CSR");
   if (lattice != LATTICE_NODE && lattice != LATTICE_EDGE) throw std::runtime_error("unknown lattice");
   if (leaf_size < 1 || hodbf_leaf < 1 || nmin_sep < 1) throw std::runtime_error("invalid sizes in options");
   if (rowptr[0] != 0) throw std::runtime_error("rowptr[0] must be 0");
@@ -174,11 +278,35 @@ void analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const int3
       if (colind[k] < 0 || colind[k] >= n) throw std::runtime_error("column index out of range");
   }
   Builder b;
+  // sorted off-diagonal neighbour lists; the pattern must be structurally symmetric
+  b.adj_ptr.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<int32_t> nb;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+      if (colind[k] != i) nb.push_back(colind[k]);
+    std::sort(nb.begin(), nb.end());
+    nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+    b.adj.insert(b.adj.end(), nb.begin(), nb.end());
+    b.adj_ptr[i + 1] = (int64_t)b.adj.size();
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = b.adj_ptr[i]; k < b.adj_ptr[i + 1]; ++k) {
+      const int64_t j = b.adj[k];
+      if (!std::binary_search(b.adj.begin() + b.adj_ptr[j], b.adj.begin() + b.adj_ptr[j + 1], (int32_t)i))
+        throw std::runtime_error("pattern not structurally symmetric");
+    }
   b.coords = coords;
   b.lattice = lattice;
   b.leaf = leaf_size;
   b.nmin = nmin_sep;
   b.hleaf = hodbf_leaf;
+  if (!coords) {
+    b.mark.assign(n, 0);
+    b.seen_.assign(n, 0);
+    std::vector<int64_t> all(n);
+    std::iota(all.begin(), all.end(), 0);
+    b.nd_graph(all);
+  } else {
   C3 mn{INT64_MAX, INT64_MAX, INT64_MAX}, mx{INT64_MIN, INT64_MIN, INT64_MIN};
   for (int64_t i = 0; i < n; ++i)
     for (int d = 0; d < 3; ++d) {
@@ -197,6 +325,7 @@ void analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const int3
   std::vector<int64_t> all(n);
   std::iota(all.begin(), all.end(), 0);
   b.nd(all, lo, hi);
+  }
 
   out = Analysis();
   out.n = n;

@@ -341,17 +341,19 @@ int mf_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const do
   *out = nullptr;
   if (!opt || opt->version != MF_OPTIONS_V1) return fail(nullptr, MF_ERR_ARG, "options missing or wrong version");
   if (n <= 0 || !rowptr || !colind || !vals) return fail(nullptr, MF_ERR_ARG, "invalid CSR arguments");
-  if (!opt->coords) return fail(nullptr, MF_ERR_UNSUPPORTED, "lattice coordinates are required for the ordering");
   std::unique_ptr<mf_handle> h(new (std::nothrow) mf_handle());
   if (!h) return fail(nullptr, MF_ERR_OOM, "host allocation failed");
   int rc = guarded(h.get(), [&]() -> int {
     h->opt = *opt;
-    h->coords.assign(opt->coords, opt->coords + 3 * n);
-    h->opt.coords = h->coords.data();
+    if (opt->coords) {
+      h->coords.assign(opt->coords, opt->coords + 3 * n);
+      h->opt.coords = h->coords.data();
+    }
     h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     try {
-      mf::analyze(n, rowptr, colind, h->coords.data(), opt->lattice, opt->leaf_size, opt->nmin_sep, opt->hodbf_leaf,
-                  h->an);
+      // with lattice coordinates: planar separators; without: graph nested dissection
+      mf::analyze(n, rowptr, colind, opt->coords ? h->coords.data() : nullptr, opt->lattice, opt->leaf_size,
+                  opt->nmin_sep, opt->hodbf_leaf, h->an);
     } catch (const std::runtime_error& e) {
       std::string m = e.what();
       if (m.find("empty separator") != std::string::npos) return fail(h.get(), MF_ERR_UNSUPPORTED, m);

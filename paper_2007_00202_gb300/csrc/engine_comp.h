@@ -1,4 +1,4 @@
-// Compressed fronts of the multifrontal factorization (Alg. 5, lines 8-12) on the GPU:
+// Compressed fronts of the multifrontal factorization (the large-front branch of Alg. 5) on the GPU:
 //   F11   <- HODBF_entry_eval(A(Is,Is) (+) C_nu1 (+) C_nu2)
 //   F11^-1<- HODBF_invert(F11)                                 (Alg. 4)
 //   F12   <- BF_entry_eval(A(Is,Iu) (+) C_nu1 (+) C_nu2)        (Alg. 2)

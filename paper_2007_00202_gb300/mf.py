@@ -282,11 +282,12 @@ def mf_analyze(n, rowptr, colind, vals, coords, lattice=MF_LATTICE_NODE, stream=
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     vals = np.ascontiguousarray(vals, dtype=np.complex128)
-    coords = np.ascontiguousarray(coords, dtype=np.int32)
-    if coords.shape != (n, 3):
-        raise ValueError("coords must be N x 3")
     o = mf_options_init(lattice=lattice, **opts)
-    o.coords = _p(coords, C.c_int32)
+    if coords is not None:          # None: general CSR input, graph nested dissection
+        coords = np.ascontiguousarray(coords, dtype=np.int32)
+        if coords.shape != (n, 3):
+            raise ValueError("coords must be N x 3")
+        o.coords = _p(coords, C.c_int32)
     h = C.c_void_p()
     rc = lib().mf_analyze(n, _p(rowptr, C.c_int64), _p(colind, C.c_int32), C.cast(vals.ctypes.data, C.POINTER(C.c_double)),
                           C.byref(o), C.c_void_p(stream), C.byref(h))
@@ -294,9 +295,11 @@ def mf_analyze(n, rowptr, colind, vals, coords, lattice=MF_LATTICE_NODE, stream=
     return Handle(h, (rowptr, colind, vals, coords))
 
 
-def analyze_problem(prob, **opts) -> Handle:
-    """mf_analyze on a workloads.SparseProblem-like object (n, rowptr, colind, vals, coords, lattice)."""
-    return mf_analyze(prob.n, prob.rowptr, prob.colind, prob.vals, prob.coords, prob.lattice, **opts)
+def analyze_problem(prob, graph=False, **opts) -> Handle:
+    """mf_analyze on a workloads.SparseProblem-like object (n, rowptr, colind, vals, coords, lattice);
+    graph=True withholds the coordinates (graph nested dissection of the CSR pattern)."""
+    return mf_analyze(prob.n, prob.rowptr, prob.colind, prob.vals, None if graph else prob.coords, prob.lattice,
+                      **opts)
 
 
 def mf_gemm_c64(engine, m, n, k, A, lda, pla, B, ldb, plb, C_, ldc, plc, alpha, beta, stream=0):

@@ -42,6 +42,15 @@ def test_argument_errors(g):
     with pytest.raises(MfError) as e:
         g.mf_analyze(p.n, p.rowptr, np.full_like(p.colind, p.n + 5), p.vals, p.coords)
     assert e.value.code == -1
+    # an unsymmetric pattern (row 0 loses one off-diagonal entry) is rejected
+    rp, ci, v = p.rowptr.copy(), p.colind.copy(), p.vals.copy()
+    k = int(np.flatnonzero(ci[rp[0]:rp[1]] != 0)[0])
+    keep = np.ones(len(ci), bool)
+    keep[k] = False
+    rp[1:] -= 1
+    with pytest.raises(MfError) as e:
+        g.mf_analyze(p.n, rp, ci[keep], v[keep], None)
+    assert e.value.code == -1 and "symmetric" in str(e.value)
     h = g.analyze_problem(p)
     with pytest.raises(MfError) as e:
         h.mf_solve(np.ones(p.n, complex))
@@ -50,9 +59,9 @@ def test_argument_errors(g):
     assert (o.leaf_size, o.nmin_sep, o.gmres_restart, o.rtol) == (64, 1024, 30, 1e-8)
 
 
-def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True, stride=1):
-    an = analyze(p, leaf, nmin, hleaf)
-    h = g.analyze_problem(p, leaf_size=leaf, nmin_sep=nmin, hodbf_leaf=hleaf)
+def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True, stride=1, graph=False):
+    an = analyze(p, leaf, nmin, hleaf, graph=graph)
+    h = g.analyze_problem(p, graph=graph, leaf_size=leaf, nmin_sep=nmin, hodbf_leaf=hleaf)
     e = h.mf_analysis_export()
     assert np.array_equal(e["perm"], an.perm)
     assert len(e["parent"]) == len(an.fronts)
@@ -97,3 +106,15 @@ def test_analysis_bit_exact_64cube_structure(g):
     an = _compare(g, p, 64, 1024, 64, stride=23)
     assert len(an.fronts) == 4817
     assert sum(f.compressed for f in an.fronts) == 5
+
+
+@pytest.mark.parametrize("which", ["helmholtz13", "yee8", "rgg"])
+def test_graph_analysis_bit_exact(g, which):
+    # general CSR input (coordinates withheld): the graph nested dissection of the C++ host analysis
+    # equals the oracle's bit for bit, including cluster trees and neighbour lists
+    from test_oracle_analysis import random_graph
+    p = {"helmholtz13": lambda: w.helmholtz7(13, 8), "yee8": lambda: w.yee_maxwell(8, 10),
+         "rgg": random_graph}[which]()
+    an = _compare(g, p, 24, 40, 16, knn=6, graph=True)
+    assert sum(f.compressed for f in an.fronts) >= 1
+

@@ -56,6 +56,32 @@ def test_mixed_compressed_gmres_to_1e8(g):
     assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-6
 
 
+@pytest.mark.parametrize("which", ["helmholtz16", "yee10"])
+def test_graph_nested_dissection_compressed_gmres_to_1e8(g, which):
+    # general sparse input: coordinates withheld, the ordering and the separators' cluster trees
+    # come from the matrix graph alone; the compressed solve still reaches 1e-8 and the oracle's
+    # exact multifrontal solution in the same graph ordering
+    if which == "helmholtz16":
+        p = w.helmholtz7(16, 8)
+        b = w.rhs_gaussian(p, 3, 17)
+    else:
+        p = w.yee_maxwell(10, 10)
+        b = w.rhs_dipoles(p, 3, 19)
+    h = g.analyze_problem(p, graph=True, leaf_size=32, nmin_sep=64, hodbf_leaf=32,
+                          precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES)
+    an = analyze(p, 32, 64, 32, graph=True)
+    assert np.array_equal(h.mf_analysis_export()["perm"], an.perm)
+    h.mf_factor(1e-4)
+    assert h.mf_stats()["ncompressed"] >= 1
+    x, info = h.mf_solve(b)
+    A = p.to_scipy()
+    assert info.converged == 1
+    assert np.max(np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)) <= 1e-8
+    an_exact = analyze(p, 32, 10 ** 9, graph=True)
+    xe = dm.solve(p, an_exact, dm.multifrontal_factor(p, an_exact)[0], b)
+    assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-6
+
+
 def test_compressed_yee(g):
     p = w.yee_maxwell(10, 10)
     b = w.rhs_dipoles(p, 3, 11)

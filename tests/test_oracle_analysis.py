@@ -144,3 +144,86 @@ def test_neighbour_lists_respect_targets():
     assert all(set(v) <= u_set and len(v) == 4 for v in nn["nn12"].values())
     assert all(set(v) <= s_set and len(v) == 4 for v in nn["nn21"].values())
     assert all(set(v) <= s_set for v in nn["nn11"].values())
+
+
+# ---------------- graph nested dissection (general CSR input, no coordinates) ----------------
+def _pattern_problem(n, edges, name="graph"):
+    """A SparseProblem from an undirected edge list (unit off-diagonal, diagonal n), no coordinates."""
+    import scipy.sparse as sp
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    r = np.concatenate([e[:, 0], e[:, 1], np.arange(n)])
+    c = np.concatenate([e[:, 1], e[:, 0], np.arange(n)])
+    v = np.concatenate([-np.ones(2 * len(e)), np.full(n, float(n))]).astype(complex)
+    A = sp.csr_matrix((v, (r, c)), shape=(n, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    return w.SparseProblem(name, n, A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data,
+                           np.zeros((n, 3), np.int32), w.LATTICE_NODE)
+
+
+def random_graph(seed=4, n1=700, n2=120):
+    """Two components: a random geometric graph in the unit square and a smaller one far away."""
+    rng = np.random.default_rng(seed)
+    pts = np.concatenate([rng.random((n1, 2)), 10.0 + rng.random((n2, 2))])
+    d = np.sqrt(((pts[:, None, :] - pts[None, :, :]) ** 2).sum(-1))
+    i, j = np.nonzero(np.triu(d < 0.075, 1))
+    return _pattern_problem(n1 + n2, np.stack([i, j], 1), "rgg")
+
+
+def test_graph_nd_path_by_hand():
+    # path 0-1-...-9, leaf 3: the search from 0 ends at 9; from 9 the levels are 9, 8, ..., 0 and the
+    # fifth level (vertex 5) is where half of the ten vertices are passed -> root separator {5};
+    # [6..9]: levels from 9 are 9, 8, 7, 6 -> separator {8}, children [9] and [6, 7];
+    # [0..4]: from 4 the levels are 4, 3, 2, 1, 0 -> separator {2}, children [3, 4] and [0, 1]
+    p = _pattern_problem(10, [(k, k + 1) for k in range(9)])
+    an = analyze(p, leaf_size=3, nmin_sep=10 ** 9, graph=True)
+    assert an.perm.tolist() == [9, 6, 7, 8, 3, 4, 0, 1, 2, 5]
+    assert [f.s for f in an.fronts] == [1, 2, 1, 2, 2, 1, 1]
+    assert an.fronts[-1].children == [2, 5]
+
+
+@pytest.mark.parametrize("gen", [lambda: w.helmholtz7(12, 8), lambda: w.yee_maxwell(6, 10), random_graph])
+def test_graph_nd_structure_invariants(gen):
+    p = gen()
+    an = analyze(p, leaf_size=16, nmin_sep=40, hodbf_leaf=8, graph=True)
+    N = p.n
+    assert np.array_equal(np.sort(an.perm), np.arange(N))
+    assert sum(f.s for f in an.fronts) == N
+    A = p.to_scipy()[an.perm][:, an.perm].tocoo()
+    owner = np.empty(N, np.int64)
+    for f in an.fronts:
+        owner[f.sep_begin:f.sep_end] = f.id
+    anc = {}
+    for f in an.fronts:
+        a, q = set(), f.id
+        while q >= 0:
+            a.add(q); q = an.fronts[q].parent
+        anc[f.id] = a
+    for r, c in zip(A.row, A.col):        # separators separate: no entry couples unrelated fronts
+        fr, fc = owner[r], owner[c]
+        assert fr in anc[fc] or fc in anc[fr]
+    for f in an.fronts:
+        ok = set(range(f.sep_begin, f.sep_end)) | set(f.upd.tolist())
+        for c in f.children:
+            assert set(an.fronts[c].upd.tolist()) <= ok
+        if f.compressed:
+            assert max(b - a for a, b in f.th_tree[-1]) <= 8
+    assert sum(f.compressed for f in an.fronts) >= 1
+
+
+def test_graph_nd_symbolic_equals_bruteforce_elimination():
+    for p in (w.helmholtz7(6, 8), w.yee_maxwell(4, 10), random_graph(5, 150, 30)):
+        an = analyze(p, leaf_size=10, nmin_sep=10 ** 9, graph=True)
+        N = p.n
+        P = (p.to_scipy()[an.perm][:, an.perm].toarray() != 0)
+        S = P.copy()
+        for k in range(N):
+            rows = np.nonzero(S[k + 1:, k])[0] + k + 1
+            cols = np.nonzero(S[k, k + 1:])[0] + k + 1
+            S[np.ix_(rows, cols)] = True
+        for f in an.fronts:
+            idx = list(range(f.sep_begin, f.sep_end))
+            below = set()
+            for k in idx:
+                below |= set((np.nonzero(S[k + 1:, k])[0] + k + 1).tolist())
+            assert below - set(idx) == set(f.upd.tolist())
