@@ -105,8 +105,8 @@ int mf_options_init(mf_options* opt);
  *     (i+1/2, j, k) is (2i+1, 2j, 2k)); separators are node planes.
  *     NULL: general CSR input, ordered by graph nested dissection (breadth-first
  *     level structures from a pseudo-peripheral vertex; separator = the level
- *     where half of the reached vertices are passed; compressed separators
- *     ordered by a breadth-first search of their own subgraph).
+ *     where half of the reached vertices are passed; a compressed separator's
+ *     HOD-BF tree comes from recursive bisection of its two-hop graph).
  *   cuda_stream: the CUDA stream all device work of this handle runs on (NULL = default).
  * Computes the nested-dissection ordering (planar or graph), the assembly tree, the
  * update sets, the HOD-BF cluster trees and the neighbour lists on the host;

@@ -153,6 +153,64 @@ def cluster_tree_balanced(npts: int, leaf: int):
     return levels
 
 
+def _separator_bisection(sep, adj, th):
+    """Order a graph separator by recursive bisection along its HOD-BF tree th (Sec. 5.1).
+
+    In the algebraic setting the paper takes the HOD-BF hierarchy of F11 from a recursive
+    bisection of the graph of A(I^s, I^s).  A level-structure separator of a 7-point stencil has
+    no edges inside it (its vertices all lie at one distance from p), so the graph bisected here
+    is the two-hop graph of the separator: u ~ v when A(u, v) != 0 or u and v share a neighbour
+    in A.  Bisection of a node's vertex set (sorted): breadth-first search from its smallest
+    vertex (neighbours in increasing index), p = the smallest vertex of the last level, search
+    again from p; the sequence is the levels from p, each sorted, then the vertices not reached
+    (sorted).  The node's first child takes the first (child size) vertices of the sequence, the
+    second child the rest; leaves are sorted.  Returns the separator in HOD-BF order."""
+    S = set(sep)
+    adj2 = {}
+    for v in sep:
+        nb = set()
+        for x in adj[v]:
+            if x in S:
+                nb.add(x)
+            for y in adj[x]:
+                if y in S and y != v:
+                    nb.add(y)
+        adj2[v] = sorted(nb)
+
+    def levels_from(start, inside, seen):
+        lv = [[start]]
+        seen.add(start)
+        while True:
+            nxt = []
+            for v in lv[-1]:
+                for x in adj2[v]:
+                    if x in inside and x not in seen:
+                        seen.add(x)
+                        nxt.append(x)
+            if not nxt:
+                return lv
+            lv.append(nxt)
+
+    def split(vs, h):
+        if not vs:
+            return [], []
+        inside = set(vs)
+        p = min(levels_from(vs[0], inside, set())[-1])
+        reached = set()
+        seq = [v for level in levels_from(p, inside, reached) for v in sorted(level)]
+        seq += [v for v in vs if v not in reached]
+        return sorted(seq[:h]), sorted(seq[h:])
+
+    def order(vs, lvl, k):
+        if lvl == len(th) - 1:
+            return vs
+        a, m = th[lvl + 1][2 * k]
+        left, right = split(vs, m - a)
+        return order(left, lvl + 1, 2 * k) + order(right, lvl + 1, 2 * k + 1)
+
+    return order(sorted(sep), 0, 0)
+
+
 def _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts):
     """Graph nested dissection of a CSR pattern (no coordinates).
 
@@ -167,10 +225,7 @@ def _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts
     least half of the vertices reached from p, kept in 1 .. (number of levels - 2); levels below m
     form the first child, levels above m and the vertices not reached from p (other components)
     the second.  With fewer than three levels the set is a front of its own.  A separator at or
-    above nmin_sep is ordered by breadth-first search of its own subgraph before the balanced
-    bisection that defines its HOD-BF tree: the paper bisects the graph of A(I^s, I^s) for that
-    hierarchy in the algebraic setting (Sec. 5.1), and a breadth-first order keeps graph
-    neighbours at nearby positions, so each contiguous cluster is a connected piece."""
+    above nmin_sep is ordered by _separator_bisection along its balanced HOD-BF tree."""
     adj = [sorted(set(int(c) for c in ci[rp[i]:rp[i + 1]]) - {i}) for i in range(N)]
 
     def bfs(start, inside, seen):
@@ -221,13 +276,8 @@ def _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts
         if right:
             kids.append(nd(right))
         if len(sep) >= nmin_sep:
-            inside_sep, done, order = set(sep), set(), []
-            for s0 in sep:           # components of the separator's subgraph, from their smallest vertex
-                if s0 in done:
-                    continue
-                for level in bfs(s0, inside_sep, done):
-                    order += level
-            return new_front(order, kids, True, cluster_tree_balanced(len(order), hodbf_leaf))
+            th = cluster_tree_balanced(len(sep), hodbf_leaf)
+            return new_front(_separator_bisection(sep, adj, th), kids, True, th)
         return new_front(sep, kids, False, None)
 
     nd(list(range(N)))

@@ -139,19 +139,93 @@ struct Builder {
   std::vector<int64_t> seen_;
   int64_t stamp_ = 0;
 
-  // breadth-first order of a separator's own subgraph (components from their smallest vertex)
-  std::vector<int64_t> bfs_order(const std::vector<int64_t>& sorted_ids) {
+  // HOD-BF order of a graph separator: recursive bisection of its two-hop graph (u ~ v when
+  // A(u, v) != 0 or u and v share a neighbour) along the balanced tree th.  A node's vertex set
+  // (sorted) is searched breadth-first from its smallest vertex, then again from p = the smallest
+  // vertex of the last level; the sequence is the levels from p, each sorted, then the vertices not
+  // reached (sorted); the first child takes the first (child size) vertices, the second the rest.
+  std::vector<int64_t> sep_order(const std::vector<int64_t>& sep, const std::vector<std::vector<Range>>& th) {
+    const int64_t ns = (int64_t)sep.size();
     const int64_t t = ++tag;
-    for (int64_t v : sorted_ids) mark[v] = t;
-    const int64_t st = ++stamp_;
-    std::vector<int64_t> order;
-    for (int64_t s0 : sorted_ids) {
-      if (seen_[s0] == st) continue;
-      auto lv = bfs_levels(s0, t, seen_, st);
-      for (auto& l : lv) order.insert(order.end(), l.begin(), l.end());
+    if ((int64_t)loc_.size() < (int64_t)mark.size()) loc_.assign(mark.size(), 0);
+    for (int64_t i = 0; i < ns; ++i) { mark[sep[i]] = t; loc_[sep[i]] = i; }
+    // two-hop graph in local indices (local order = increasing vertex id)
+    std::vector<int64_t> p2(ns + 1, 0);
+    std::vector<int64_t> a2;
+    std::vector<int64_t> nb;
+    for (int64_t i = 0; i < ns; ++i) {
+      const int64_t v = sep[i];
+      nb.clear();
+      for (int64_t k = adj_ptr[v]; k < adj_ptr[v + 1]; ++k) {
+        const int64_t x = adj[k];
+        if (mark[x] == t) nb.push_back(loc_[x]);
+        for (int64_t k2 = adj_ptr[x]; k2 < adj_ptr[x + 1]; ++k2) {
+          const int64_t y = adj[k2];
+          if (mark[y] == t && y != v) nb.push_back(loc_[y]);
+        }
+      }
+      std::sort(nb.begin(), nb.end());
+      nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+      a2.insert(a2.end(), nb.begin(), nb.end());
+      p2[i + 1] = (int64_t)a2.size();
     }
-    return order;
+    std::vector<int64_t> in(ns, 0), seen(ns, 0);
+    int64_t in_tag = 0, seen_tag = 0;
+    auto levels_from = [&](int64_t s0, int64_t it, int64_t st) {
+      std::vector<std::vector<int64_t>> lv{{s0}};
+      seen[s0] = st;
+      for (;;) {
+        std::vector<int64_t> nxt;
+        for (int64_t v : lv.back())
+          for (int64_t k = p2[v]; k < p2[v + 1]; ++k) {
+            const int64_t x = a2[k];
+            if (in[x] == it && seen[x] != st) { seen[x] = st; nxt.push_back(x); }
+          }
+        if (nxt.empty()) break;
+        lv.push_back(std::move(nxt));
+      }
+      return lv;
+    };
+    std::vector<int64_t> out;
+    out.reserve(ns);
+    // explicit recursion over (vertex set, level, node)
+    std::function<void(std::vector<int64_t>&, size_t, size_t)> order = [&](std::vector<int64_t>& vs, size_t lvl,
+                                                                            size_t k) {
+      if (lvl + 1 == th.size()) { out.insert(out.end(), vs.begin(), vs.end()); return; }
+      const int64_t h = th[lvl + 1][2 * k].b - th[lvl + 1][2 * k].a;
+      std::vector<int64_t> left, right;
+      if (!vs.empty()) {
+        const int64_t it = ++in_tag;
+        for (int64_t v : vs) in[v] = it;
+        auto lv0 = levels_from(vs[0], it, ++seen_tag);
+        const int64_t p = *std::min_element(lv0.back().begin(), lv0.back().end());
+        const int64_t st = ++seen_tag;
+        auto lv = levels_from(p, it, st);
+        std::vector<int64_t> seq;
+        seq.reserve(vs.size());
+        for (auto& l : lv) {
+          std::sort(l.begin(), l.end());
+          seq.insert(seq.end(), l.begin(), l.end());
+        }
+        for (int64_t v : vs)
+          if (seen[v] != st) seq.push_back(v);
+        const int64_t hh = std::min<int64_t>(h, (int64_t)seq.size());
+        left.assign(seq.begin(), seq.begin() + hh);
+        right.assign(seq.begin() + hh, seq.end());
+        std::sort(left.begin(), left.end());
+        std::sort(right.begin(), right.end());
+      }
+      std::vector<int64_t>().swap(vs);
+      order(left, lvl + 1, 2 * k);
+      order(right, lvl + 1, 2 * k + 1);
+    };
+    std::vector<int64_t> all(ns);
+    std::iota(all.begin(), all.end(), 0);
+    order(all, 0, 0);
+    for (auto& v : out) v = sep[v];
+    return out;
   }
+  std::vector<int64_t> loc_;
 
   int64_t nd_graph(std::vector<int64_t>& ids) {   // ids sorted ascending
     auto leaf_front = [&](std::vector<int64_t>& v) {
@@ -193,8 +267,8 @@ struct Builder {
     Raw r;
     r.compressed = (int64_t)sep.size() >= nmin;
     if (r.compressed) {
-      r.sep = bfs_order(sep);
-      r.th = cluster_tree_balanced((int64_t)r.sep.size(), hleaf);
+      r.th = cluster_tree_balanced((int64_t)sep.size(), hleaf);
+      r.sep = sep_order(sep, r.th);
     } else {
       r.sep = std::move(sep);
     }

@@ -227,3 +227,26 @@ def test_graph_nd_symbolic_equals_bruteforce_elimination():
             for k in idx:
                 below |= set((np.nonzero(S[k + 1:, k])[0] + k + 1).tolist())
             assert below - set(idx) == set(f.upd.tolist())
+
+
+def test_graph_separator_bisection_gives_compact_clusters():
+    # Sec. 5.1: the HOD-BF hierarchy of a separator comes from recursive bisection of its graph, so
+    # that the clusters are compact pieces of the separator surface (the off-diagonal ranks depend
+    # on it).  The root separator of the level-structure ordering of a 24^3 grid is a diagonal
+    # plane; every cluster of its tree keeps diameter / sqrt(size) below 3, as a disc-like piece of
+    # a plane does, while the same tree over index order (strips) passes 4 at its leaves
+    p = w.helmholtz7(24, 8)
+    an = analyze(p, 64, 200, 32, graph=True)
+    f = an.fronts[-1]
+    assert f.compressed and len(f.th_tree) >= 5
+    X = p.coords[an.perm].astype(float)
+
+    def worst(S, lvl):
+        return max(np.sqrt(((S[a:b, None] - S[None, a:b]) ** 2).sum(-1)).max() / np.sqrt(b - a)
+                   for a, b in f.th_tree[lvl])
+    S = X[f.sep_begin:f.sep_end]
+    assert all(worst(S, lvl) < 3.0 for lvl in range(1, len(f.th_tree)))
+    assert worst(X[np.sort(an.perm[f.sep_begin:f.sep_end])], len(f.th_tree) - 1) > 4.0
+    # the separator is a level set of the 7-point graph: no edge joins two of its vertices
+    A = p.to_scipy()[an.perm][:, an.perm].tocsr()[f.sep_begin:f.sep_end, f.sep_begin:f.sep_end]
+    assert A.nnz == f.s
