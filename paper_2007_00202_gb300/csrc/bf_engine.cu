@@ -339,6 +339,62 @@ void BFContext<T>::h2d(void* dst, const void* src, size_t bytes) {
 }
 
 template <typename T>
+void BFContext<T>::gemm_stages(std::map<int, std::vector<GemmDesc<T>>>& stages) {
+  if constexpr (std::is_same<T, float>::value) {
+    std::vector<GemmDesc<T>> D;
+    std::vector<GemmTile> tl;
+    std::vector<std::pair<size_t, size_t>> span;   // tiles of each launch: [first, last)
+    bool tc = true;
+    for (auto& kv : stages) {
+      int maxn = 0;
+      const size_t t0 = tl.size();
+      for (auto& d : kv.second) {
+        if (d.m <= 0 || d.n <= 0) continue;
+        tc = tc && gemm_nrhs_tc_ok(d);
+        maxn = std::max(maxn, (int)d.n);
+        for (int i = 0; i < (d.m + gemm_nrhs_tc_rows() - 1) / gemm_nrhs_tc_rows(); ++i)
+          tl.push_back({(int)D.size(), i, 0, 0});
+        D.push_back(d);
+      }
+      tc = tc && (maxn == 0 || maxn >= 48);
+      if (!tc) break;
+      if (tl.size() > t0) span.push_back({t0, tl.size()});
+    }
+    if (tc) {
+      if (D.empty()) return;
+      HostTimer ht_(t_host + H_GEMM);
+      double fl = 0, by = 0;
+      for (auto& d : D) {
+        fl += 8.0 * d.m * d.n * d.k;
+        by += gemm_bytes(d);
+      }
+      flops += fl;
+      bytes += by;
+      const GemmDesc<T>* dd = static_cast<const GemmDesc<T>*>(upload(D.data(), D.size() * sizeof(GemmDesc<T>)));
+      const GemmTile* dt = stage(tl.data(), tl.size());
+      for (auto& sp : span) {
+        auto go = [&] {
+          launch_gemm_nrhs_tc(dd, dt + sp.first, (int)(sp.second - sp.first), status.template as<int32_t>(), st);
+        };
+        if (prof && prof->on) {
+          double f1 = 0, b1 = 0;
+          for (size_t t = sp.first; t < sp.second; ++t)
+            if (tl[t].tm == 0) {
+              f1 += 8.0 * D[tl[t].desc].m * D[tl[t].desc].n * D[tl[t].desc].k;
+              b1 += gemm_bytes(D[tl[t].desc]);
+            }
+          prof->time(st, f1, b1, go);
+        } else {
+          go();
+        }
+      }
+      return;
+    }
+  }
+  for (auto& kv : stages) gemm(kv.second);
+}
+
+template <typename T>
 void BFContext<T>::check_status() {
   int32_t v = 0;
   MF_CUDA(cudaMemcpyAsync(&v, status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -855,7 +911,7 @@ void BFContext<T>::apply(const std::vector<const DBF<T>*>& bfs, const std::vecto
   // The final stage of each butterfly writes its output; butterflies with fewer stages finish earlier,
   // which is fine because outputs of different butterflies in one call are disjoint or accumulated in
   // separate calls by the callers.
-  for (auto& kv : stages) gemm(kv.second);
+  gemm_stages(stages);
 }
 
 template <typename T>

@@ -16,6 +16,7 @@
 #include <memory>
 #include <chrono>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "analysis.h"
@@ -292,6 +293,9 @@ class BFContext {
   int cap_mode = 0;                 // 0 eager, 1 counting, 2 capturing
   void sync();                      // stream synchronize, timed into t_wait
   void gemm(std::vector<GemmDesc<T>>& descs);             // one launch for all descs
+  // consecutive dependent launches (stage s reads what stage s - 1 wrote): one upload of every
+  // stage's descriptors and tiles when all run on the tensor-core kernel, else gemm() per stage
+  void gemm_stages(std::map<int, std::vector<GemmDesc<T>>>& stages);
   void zero(Blk<T>& b);                                   // b: a whole block from new_blk
   // row IDs of the given matrices (device); results on host (ranks, skeletons) and U in persist
   // centre blocks by least squares, one launch for all jobs (work from scratch when shared memory is short)
