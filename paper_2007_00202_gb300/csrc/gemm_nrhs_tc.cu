@@ -20,10 +20,12 @@
 //    into shared-memory rings (16-byte cp.async) several tiles ahead, so that no global load
 //    sits on the producers' path.  Each thread splits the elements it staged itself (no barrier
 //    between copy and split) and writes them by whole 8 x 4 core matrices (conflict-free) into
-//    one of two shared memory slots in the canonical no-swizzle K-major layout; after a named
-//    barrier of the 8 warps, thread 0 issues the chunk's MMAs and commits them to the slot's
-//    mbarrier, which frees the slot, and after a tile's last chunk to the accumulator's "full"
-//    mbarrier, beside the tile's epilogue record.  Tiles rotate over four TMEM accumulators.
+//    one of two shared memory slots in the canonical no-swizzle K-major layout, then meet the
+//    MMA warp at a named barrier.
+//  * 1 MMA warp: after the barrier of chunk g, while the producers stage chunk g + 1, one lane
+//    issues chunk g's MMAs and commits them to the slot's mbarrier, which frees the slot, and
+//    after a tile's last chunk to the accumulator's "full" mbarrier, beside the tile's epilogue
+//    record.  Tiles rotate over four TMEM accumulators.
 //  * 4 epilogue warps (TMEM lanes 0-127, lane = right-hand side and plane) wait for a tile's
 //    accumulator, read it with tcgen05.ld 32 rows at a time, write C rows with consecutive lanes
 //    on consecutive columns and release the accumulator ("empty" mbarrier) while later tiles are
@@ -42,7 +44,9 @@ namespace {
 
 constexpr int TC_PROD = 256;                     // producer threads (8 warps)
 constexpr int TC_EPI = 128;                      // epilogue threads (4 warps)
-constexpr int TC_THREADS = TC_PROD + TC_EPI;
+constexpr int TC_MMA_WARP = (TC_PROD + TC_EPI) / 32;   // warp 12 issues the MMAs
+constexpr int TC_THREADS = TC_PROD + TC_EPI + 32;
+constexpr int TC_SYNC = TC_PROD + 32;            // producers and the MMA warp meet once per chunk
 constexpr int TC_WARPS = TC_PROD / 32;           // producer warps
 constexpr int TC_BK = 16;                        // K elements per chunk
 constexpr int TC_GRP = (TC_BK / 4) * 128;        // bytes per 8-row group of a tile (4 core matrices)
@@ -83,10 +87,6 @@ static_assert(TC_DAHEAD > TC_NRAW && TC_TAHEAD - TC_DAHEAD > TC_NRAW, "records f
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-// byte offset of element (r, k) of a canonical no-swizzle K-major tile with 16-wide K chunks
-__device__ __forceinline__ uint32_t cano(int r, int k) {
-  return (uint32_t)((r >> 3) * TC_GRP + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
-}
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   const uint64_t lbo = 128, sbo = TC_GRP;
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46);
@@ -117,25 +117,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
     if (mbar_try(bar, parity)) return true;
   return false;
 }
-// bounded wait that also gives up when another role has recorded a failure
+// bounded wait for the long waits (epilogue warps, accumulator reuse) that also gives up when
+// another role has recorded a failure; after a few polls it sleeps between polls, so that the
+// waiting warp leaves its issue slots to the producers
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, long long spins,
                                                    const volatile int* abort) {
   for (long long i = 0; i < spins; ++i) {
     if (mbar_try(bar, parity)) return true;
     if ((i & 63) == 63 && *abort) return false;
+    if (i >= 8) __nanosleep(32);
   }
   return false;
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
 }
-// barrier of the TC_PROD producer threads (named barrier 1) that also ORs a flag over them
-__device__ __forceinline__ bool producers_sync_or(bool v) {
+// barrier of the producer threads and the MMA warp (named barrier 1, TC_SYNC threads) that also
+// ORs a flag over them
+__device__ __forceinline__ bool chunk_sync_or(bool v) {
   uint32_t r;
   asm volatile(
       "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(r)
-      : "r"((uint32_t)v), "n"(TC_PROD)
+      : "r"((uint32_t)v), "n"(TC_SYNC)
       : "memory");
   return r != 0;
 }
@@ -185,8 +189,10 @@ __device__ __forceinline__ void fetch_records(int i, int ntiles, const GemmDesc<
 }
 
 // Asynchronous copy of chunk c of a tile into raw stage `raw` (shared address), d and tl the
-// tile's descriptor and record (shared memory): core matrix b of the chunk (b < TC_XBLK: X, else
-// W rows), lane -> (row 8 g + lane / 4, k 4 kg + lane % 4); value i of this thread goes to floats
+// tile's descriptor and record (shared memory).  Thread (warp, lane) takes K index
+// kq = 4 (warp % 4) + lane % 4 of the chunk and the 8-row groups g0 + 2 i (g0 = warp / 4):
+// values i = 0..3 are X columns 8 (g0 + 2 i) + lane / 4, values i = 4..9 are W rows
+// 8 (g0 + 2 (i - 4)) + lane / 4 (row groups of the tile only).  Value i goes to floats
 // (2 i + plane) * TC_PROD + tid.  Elements outside the operands are zero-filled (source size 0,
 // source address a valid dummy).  Does not commit.
 __device__ __forceinline__ void copy_chunk(uint32_t raw, const GemmDesc<float>& d, const GemmTile tl, int c,
@@ -199,73 +205,83 @@ __device__ __forceinline__ void copy_chunk(uint32_t raw, const GemmDesc<float>& 
   const PMat<float> A = second ? d.A2 : d.A, B = second ? d.B2 : d.B;
   const int m0 = tl.tm * TC_ROWS;
   const int rows = min(TC_ROWS, d.m - m0);
-  const int nwb = ((rows + 15) & ~15) / 8 * (TC_BK / 4);
-  const int n = d.n, transA = d.transA;
-  const int r8 = lane >> 2, k4 = lane & 3;
+  const int ngw = (rows + 15) / 16 * 2;                       // 8-row groups of W in the tile
+  const int n = d.n;
+  const int r8 = lane >> 2, g0 = warp >> 2;
+  const int k = kc + (warp & 3) * 4 + (lane & 3);
+  const bool kin = k < kt;
+  const float* fdummy = static_cast<const float*>(dummy);
+  const uint32_t dst0 = raw + (uint32_t)(tid * 4);
+  {
+    const float* px = B.re + (int64_t)(kin ? k : 0) * B.ld + 8 * g0 + r8;
 #pragma unroll
-  for (int i = 0; i < TC_PER_WARP; ++i) {
-    const int b = warp + TC_WARPS * i;
-    const float* p = static_cast<const float*>(dummy);
-    int64_t pl = 0;
-    uint32_t bytes = 0;
-    if (b < TC_XBLK) {
-      const int col = (b >> 2) * 8 + r8, k = kc + (b & 3) * 4 + k4;   // X: 8 column groups x 4 k groups
-      if (col < n && k < kt) {
-        p = B.re + (int64_t)k * B.ld + col;
-        pl = B.plane;
-        bytes = 4;
-      }
-    } else if (b - TC_XBLK < nwb) {
-      const int bw = b - TC_XBLK;
-      const int r = (bw >> 2) * 8 + r8, k = kc + (bw & 3) * 4 + k4;
-      if (r < rows && k < kt) {
-        p = transA ? A.re + (int64_t)k * A.ld + m0 + r : A.re + (int64_t)(m0 + r) * A.ld + k;
-        pl = A.plane;
-        bytes = 4;
-      }
-    } else {
-      continue;   // no element of this chunk: the raw value is never read
+    for (int i = 0; i < 4; ++i) {
+      const bool v = kin && 8 * (g0 + 2 * i) + r8 < n;
+      const float* p = v ? px + 16 * i : fdummy;
+      const uint32_t bytes = v ? 4u : 0u;
+      const uint32_t dst = dst0 + (uint32_t)((2 * i) * TC_PROD * 4);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(p), "r"(bytes) : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst + TC_PROD * 4), "l"(v ? p + B.plane : p),
+                   "r"(bytes)
+                   : "memory");
     }
-    const uint32_t dst = raw + (uint32_t)(((2 * i) * TC_PROD + tid) * 4);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(p), "r"(bytes) : "memory");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst + TC_PROD * 4), "l"(p + pl), "r"(bytes)
-                 : "memory");
+  }
+  {
+    const int r0 = 8 * g0 + r8;
+    const int64_t step = d.transA ? 16 : 16 * A.ld;
+    const float* pw = d.transA ? A.re + (int64_t)(kin ? k : 0) * A.ld + m0 + r0
+                               : A.re + (int64_t)(m0 + (r0 < rows ? r0 : 0)) * A.ld + (kin ? k : 0);
+#pragma unroll
+    for (int j = 0; j < TC_PER_WARP - 4; ++j) {
+      if (g0 + 2 * j >= ngw) continue;   // no element of this chunk: the raw value is never read
+      const bool v = kin && r0 + 16 * j < rows;
+      const float* p = v ? pw + step * j : fdummy;
+      const uint32_t bytes = v ? 4u : 0u;
+      const uint32_t dst = dst0 + (uint32_t)((2 * (4 + j)) * TC_PROD * 4);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(p), "r"(bytes) : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst + TC_PROD * 4), "l"(v ? p + A.plane : p),
+                   "r"(bytes)
+                   : "memory");
+    }
   }
 }
 
-// Split this thread's staged values of a chunk into hi / lo and write them to slot s
-// (conflict-free: a warp writes whole core matrices)
-__device__ __forceinline__ void store_chunk(const float* raw, unsigned char* slot, int nwb, int warp, int lane,
+// Split this thread's staged values of a chunk into hi / lo and write them to slot s, at the
+// positions copy_chunk gave them (conflict-free: a warp writes whole core matrices).  Element
+// (r, k) of a canonical no-swizzle K-major tile with 16-wide K chunks sits at byte
+// (r / 8) TC_GRP + (k / 4) 128 + (r % 8) 16 + (k % 4) 4.
+__device__ __forceinline__ void store_chunk(const float* raw, unsigned char* slot, int ngw, int warp, int lane,
                                             int tid) {
-  const int r8 = lane >> 2, k4 = lane & 3;
+  const int g0 = warp >> 2;
+  const uint32_t base = (uint32_t)(g0 * TC_GRP + (warp & 3) * 128 + (lane >> 2) * 16 + (lane & 3) * 4) >> 2;
+  float* xh = reinterpret_cast<float*>(slot);
+  float* xl = reinterpret_cast<float*>(slot + TC_XTILE);
+  float* w = reinterpret_cast<float*>(slot + 2 * TC_XTILE);
 #pragma unroll
-  for (int i = 0; i < TC_PER_WARP; ++i) {
-    const int b = warp + TC_WARPS * i;
-    if (b >= TC_XBLK && b - TC_XBLK >= nwb) continue;
+  for (int i = 0; i < 4; ++i) {
     float rh, rl, ih, il;
     split(raw[(2 * i) * TC_PROD + tid], rh, rl);
     split(raw[(2 * i + 1) * TC_PROD + tid], ih, il);
-    if (b < TC_XBLK) {
-      const int col = (b >> 2) * 8 + r8, k = (b & 3) * 4 + k4;
-      float* xh = reinterpret_cast<float*>(slot);
-      float* xl = reinterpret_cast<float*>(slot + TC_XTILE);
-      const uint32_t o0 = cano(col, k) >> 2, o1 = cano(64 + col, k) >> 2, o2 = cano(128 + col, k) >> 2;
-      xh[o0] = rh;
-      xl[o0] = rl;
-      xh[o1] = ih;
-      xl[o1] = il;
-      xh[o2] = -rh;
-      xl[o2] = -rl;
-    } else {
-      const int bw = b - TC_XBLK;
-      const int r = (bw >> 2) * 8 + r8, k = (bw & 3) * 4 + k4;
-      const uint32_t o = cano(r, k) >> 2;
-      float* w = reinterpret_cast<float*>(slot + 2 * TC_XTILE);
-      w[o] = rh;
-      w[o + TC_WTILE / 4] = rl;
-      w[o + 2 * TC_WTILE / 4] = ih;
-      w[o + 3 * TC_WTILE / 4] = il;
-    }
+    const uint32_t o0 = base + (uint32_t)(2 * i * TC_GRP / 4);   // rows col, 64 + col, 128 + col
+    const uint32_t o1 = o0 + 8 * TC_GRP / 4, o2 = o0 + 16 * TC_GRP / 4;
+    xh[o0] = rh;
+    xl[o0] = rl;
+    xh[o1] = ih;
+    xl[o1] = il;
+    xh[o2] = -rh;
+    xl[o2] = -rl;
+  }
+#pragma unroll
+  for (int j = 0; j < TC_PER_WARP - 4; ++j) {
+    if (g0 + 2 * j >= ngw) continue;
+    float rh, rl, ih, il;
+    split(raw[(2 * (4 + j)) * TC_PROD + tid], rh, rl);
+    split(raw[(2 * (4 + j) + 1) * TC_PROD + tid], ih, il);
+    const uint32_t o = base + (uint32_t)(2 * j * TC_GRP / 4);
+    w[o] = rh;
+    w[o + TC_WTILE / 4] = rl;
+    w[o + 2 * TC_WTILE / 4] = ih;
+    w[o + 3 * TC_WTILE / 4] = il;
   }
 }
 
@@ -382,7 +398,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_nrhs_tc(const GemmDesc<f
   if (spins <= kProbeWaitLimit)   // expiry test: the spare barrier never completes
     ok = __syncthreads_and(mbar_wait(bar_spare, 0u, spins) ? 1 : 0) != 0;
   long long g = 0;      // chunks taken by this CTA (producers)
-  long long gi = 0;     // chunks whose MMAs thread 0 issued (g - 1 at most after an expired wait)
+  long long gi = 0;     // chunks whose MMAs the MMA warp issued (g - 1 at most after an expired wait)
   if (tid < TC_PROD) {
     // ---------------- producers ----------------
     Cursor cur;
@@ -406,7 +422,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_nrhs_tc(const GemmDesc<f
       const int nt = (rows + 15) & ~15;
       const int slot = (int)(g % TC_SLOTS);
       unsigned char* sp = sgen + slot * TC_SLOT;
-      const uint32_t sa = sbase + slot * TC_SLOT;
       const bool last = cur.c + 1 == nk;
       // request chunk g + TC_NRAW - 1 (and records), then wait for this thread's copies of chunk g
       if (cp.t < ntiles) {
@@ -419,15 +434,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_nrhs_tc(const GemmDesc<f
       asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_NRAW - 1) : "memory");
       // the slot is free once the MMAs of its previous chunk (g - TC_SLOTS) are complete
       if (ok && g >= TC_SLOTS) ok = mbar_wait(bar0 + 8 * slot, (uint32_t)(((g / TC_SLOTS) - 1) & 1), spins);
-      if (ok) store_chunk(rawg + (size_t)(g % TC_NRAW) * (TC_RAW / 4), sp, nt / 8 * (TC_BK / 4), warp, lane, tid);
+      if (ok) store_chunk(rawg + (size_t)(g % TC_NRAW) * (TC_RAW / 4), sp, nt / 8, warp, lane, tid);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      if (producers_sync_or(!ok || *abort_flag)) {
+      if (chunk_sync_or(!ok || *abort_flag)) {
+        ok = false;
+        break;
+      }
+      ++g;
+      if (last) {
+        cur.c = 0;
+        cur.t += gridDim.x;
+        ++cur.i;
+      } else {
+        ++cur.c;
+      }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy may land after the CTA is gone
+    if (!ok) *abort_flag = 1;
+  } else if (warp == TC_MMA_WARP) {
+    // ---------------- MMA warp: the producers' cursor, one chunk behind them ----------------
+    Cursor cur;
+    cur.t = ok ? (int)blockIdx.x : ntiles;
+#pragma unroll 1
+    while (cur.t < ntiles) {
+      const GemmDesc<float>& d = sd[cur.i % TC_DRING];
+      const GemmTile tl = st[cur.i % TC_TRING];
+      const int nk = tile_chunks(d);
+      const int rows = min(TC_ROWS, d.m - tl.tm * TC_ROWS);
+      const int nt = (rows + 15) & ~15;
+      const int slot = (int)(g % TC_SLOTS);
+      const uint32_t sa = sbase + slot * TC_SLOT;
+      const bool last = cur.c + 1 == nk;
+      if (chunk_sync_or(!ok || *abort_flag)) {   // chunk g is in its slot
         ok = false;
         break;
       }
       const int a = cur.i % TC_NACC;
       const uint32_t acc_tm = tmem + (uint32_t)(a * 128);
-      if (tid == 0) {
+      if (lane == 0) {
         // a tile's first chunk reuses the accumulator of tile i - TC_NACC: wait until it has been read
         if (cur.c == 0 && cur.i >= TC_NACC)
           ok = mbar_wait_or_abort(bar_empty + 8 * a, (uint32_t)(((cur.i / TC_NACC) - 1) & 1), spins, abort_flag);
@@ -471,6 +515,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_nrhs_tc(const GemmDesc<f
           *abort_flag = 1;
         }
       }
+      __syncwarp();   // the warp meets the next aligned barrier converged
       ++g;
       if (last) {
         cur.c = 0;
@@ -480,7 +525,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_nrhs_tc(const GemmDesc<f
         ++cur.c;
       }
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy may land after the CTA is gone
     if (!ok) *abort_flag = 1;
   } else {
     // ---------------- epilogue warps ----------------
@@ -505,11 +549,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_nrhs_tc(const GemmDesc<f
   __syncthreads();
   // drain: every MMA this CTA issued has completed before TMEM is released (with the default
   // limit even after an expired wait, so that no MMA can still write the columns being freed)
-  if (tid == 0 && gi > 0) {
+  if (warp == TC_MMA_WARP && lane == 0 && gi > 0) {
     const int slot = (int)((gi - 1) % TC_SLOTS);
     if (!mbar_wait(bar0 + 8 * slot, (uint32_t)(((gi - 1) / TC_SLOTS) & 1), kDefaultWaitLimit)) ok = false;
   }
-  if (tid == 0 && *abort_flag) ok = false;
+  if (*abort_flag) ok = false;
   if (!ok && status) atomicExch(status, 2);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
