@@ -23,9 +23,11 @@
 //    one of two shared memory slots in the canonical no-swizzle K-major layout, then meet the
 //    MMA warp at a named barrier.
 //  * 1 MMA warp: after the barrier of chunk g, while the producers stage chunk g + 1, one lane
-//    issues chunk g's MMAs and commits them to the slot's mbarrier, which frees the slot, and
-//    after a tile's last chunk to the accumulator's "full" mbarrier, beside the tile's epilogue
-//    record.  Tiles rotate over four TMEM accumulators.
+//    issues chunk g's MMAs and commits them to the slot's mbarrier, and after a tile's last
+//    chunk to the accumulator's "full" mbarrier, beside the tile's epilogue record; it joins
+//    the next barrier only once those MMAs are complete, so that the producers, who refill the
+//    slot after that barrier, never wait on it themselves.  Tiles rotate over four TMEM
+//    accumulators.
 //  * 4 epilogue warps (TMEM lanes 0-127, lane = right-hand side and plane) wait for a tile's
 //    accumulator, read it with tcgen05.ld 32 rows at a time, write C rows with consecutive lanes
 //    on consecutive columns and release the accumulator ("empty" mbarrier) while later tiles are
@@ -117,15 +119,25 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
     if (mbar_try(bar, parity)) return true;
   return false;
 }
-// bounded wait for the long waits (epilogue warps, accumulator reuse) that also gives up when
-// another role has recorded a failure; after a few polls it sleeps between polls, so that the
-// waiting warp leaves its issue slots to the producers
+// Bounded wait that suspends the thread in the barrier (try_wait with a time hint of 1 us)
+// instead of polling, so that the waiting warp leaves its issue slots to the producers; a
+// suspended try counts as 64 polls of the limit, so the wait ends after about spins / 64 us.  It
+// also gives up when another role has recorded a failure.
+__device__ __forceinline__ bool mbar_try_suspend(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(1000u)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, long long spins,
                                                    const volatile int* abort) {
-  for (long long i = 0; i < spins; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if ((i & 63) == 63 && *abort) return false;
-    if (i >= 8) __nanosleep(32);
+  const long long tries = spins > 64 ? spins >> 6 : 1;
+  for (long long i = 0; i < tries; ++i) {
+    if (mbar_try_suspend(bar, parity)) return true;
+    if (*abort) return false;
   }
   return false;
 }
@@ -432,8 +444,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_nrhs_tc(const GemmDesc<f
       }
       asm volatile("cp.async.commit_group;\n" ::: "memory");
       asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_NRAW - 1) : "memory");
-      // the slot is free once the MMAs of its previous chunk (g - TC_SLOTS) are complete
-      if (ok && g >= TC_SLOTS) ok = mbar_wait(bar0 + 8 * slot, (uint32_t)(((g / TC_SLOTS) - 1) & 1), spins);
+      // the slot is free: the MMA warp passed the last barrier after chunk g - 2's MMAs completed
       if (ok) store_chunk(rawg + (size_t)(g % TC_NRAW) * (TC_RAW / 4), sp, nt / 8, warp, lane, tid);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       if (chunk_sync_or(!ok || *abort_flag)) {
@@ -465,6 +476,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_nrhs_tc(const GemmDesc<f
       const int slot = (int)(g % TC_SLOTS);
       const uint32_t sa = sbase + slot * TC_SLOT;
       const bool last = cur.c + 1 == nk;
+      // chunk g - 1's MMAs complete before the barrier, after which the producers refill its slot
+      if (lane == 0 && ok && g >= 1)
+        ok = mbar_wait_or_abort(bar0 + 8 * (int)((g - 1) % TC_SLOTS), (uint32_t)(((g - 1) / TC_SLOTS) & 1), spins,
+                                abort_flag);
+      __syncwarp();
       if (chunk_sync_or(!ok || *abort_flag)) {   // chunk g is in its slot
         ok = false;
         break;
