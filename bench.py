@@ -53,7 +53,11 @@ def parse():
     ap.add_argument("--no-bfapply", action="store_true", help="skip the batched butterfly-apply measurement")
     ap.add_argument("--serving-full", action="store_true",
                     help="run only the full serving workload (32^3 + 64^3 + 100^3 resident, 2000 requests of "
-                         "1-256 RHS) and print its JSON line; takes several minutes")
+                         "1-256 RHS) and print its JSON line; at 80 % of the measured capacity the 2000 requests "
+                         "take about 40 minutes")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="with --serving-full: serve the first N requests of the seed-5 stream (the stream, its "
+                         "arrival rate and the problems are those of the full workload)")
     return ap.parse_args()
 
 
@@ -379,7 +383,7 @@ def serving(g, w, torch):
             "mean_batch_rhs": float(np.mean(batches)), "max_rel_residual_checked": worst}
 
 
-def serving_full(g, w, torch, nreq=2000):
+def serving_full(g, w, torch, nserve=2000, nreq=2000):
     """The serving workload at its stated size: helmholtz7 32^3, 64^3 and 100^3 (complex64, separators
     >= 1024 HOD-BF at tol 1e-4, rank <= 64) factored and resident on the device, each on its own
     stream; nreq requests (seed 5): problem rng.integers(3), nrhs = rint(exp(U(0, ln 256))) complex
@@ -403,18 +407,21 @@ def serving_full(g, w, torch, nreq=2000):
     which = rng.integers(0, len(probs), nreq)
     widths = np.rint(np.exp(rng.uniform(0.0, math.log(256.0), nreq))).astype(int)
     pools = [np.asfortranarray(w.complex_gaussian(rng, p.n, 256)) for p in probs]
-    # single-stream capacity: solves/s of one 32-column batch per problem, averaged over the mix
+    # single-stream capacity: solves/s of one full batch (64 columns: the tensor-core width of the
+    # preconditioner's level products) per problem, averaged over the mix
+    batch = 64
     cap = []
     for p, h, pool in zip(probs, hs, pools):
-        h.mf_solve(pool[:, :32])
+        h.mf_solve(pool[:, :batch])
         t0 = time.perf_counter()
-        h.mf_solve(pool[:, :32])
-        cap.append(32 / (time.perf_counter() - t0))
+        h.mf_solve(pool[:, :batch])
+        cap.append(batch / (time.perf_counter() - t0))
     mix = np.bincount(which, minlength=len(probs)) / nreq
     capacity = 1.0 / float(np.sum(mix / np.array(cap)))          # RHS per second over the request mix
     rate = 0.8 * capacity / float(np.mean(widths))                # requests per second
     gaps = rng.exponential(1.0 / rate, nreq)
-    srv = g.Server(hs, max_batch_rhs=32, mem_budget_bytes=1 << 62)   # admission by free device memory
+    print(f"serving: capacity {cap} RHS/s per problem", file=sys.stderr, flush=True)
+    srv = g.Server(hs, max_batch_rhs=batch, mem_budget_bytes=1 << 62)   # admission by free device memory
     sample = set(np.random.default_rng(6).choice(nreq, 50, replace=False).tolist())
     As = [p.to_scipy() for p in probs]
     # results are collected while requests keep arriving (each solution is dropped once checked),
@@ -445,6 +452,12 @@ def serving_full(g, w, torch, nreq=2000):
         while time.perf_counter() < t:
             time.sleep(max(0.0, min(1e-3, t - time.perf_counter())))
         pending.put((k, srv.submit(int(which[k]), pools[which[k]][:, :widths[k]]), int(which[k]), int(widths[k])))
+        if k % 100 == 99:
+            done = sorted(lat)
+            pq = (f", p50 {done[len(done) // 2]:.0f} ms, p99 {done[min(len(done) - 1, int(0.99 * len(done)))]:.0f} ms"
+                  if done else "")
+            print(f"serving: {k + 1} requests submitted, {len(done)} done, {time.perf_counter() - t0:.0f} s{pq}",
+                  file=sys.stderr, flush=True)
     pending.put(None)
     collector.join()
     wall = time.perf_counter() - t0
@@ -454,7 +467,8 @@ def serving_full(g, w, torch, nreq=2000):
     return {"workload": "helmholtz7 32^3 + 64^3 + 100^3 resident, complex64 HOD-BF tol 1e-4; "
                         f"{nreq} Poisson requests (seed 5) of rint(exp(U(0, ln 256))) RHS, arrivals at 80 % of the "
                         f"measured capacity ({capacity:.0f} RHS/s), admission by free device memory, GMRES to 1e-8",
-            "requests": nreq, "rhs": int(widths.sum()), "arrival_rate_per_s": rate,
+            "requests": nreq, "rhs": int(widths.sum()), "arrival_rate_per_s": rate, "max_batch_rhs": batch,
+            "capacity_rhs_per_s": capacity,
             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "solves_per_s": float(widths.sum()) / wall, "wall_s": wall,
             "all_converged": bool(all(s_ == 0 for s_ in statuses)),
@@ -555,7 +569,7 @@ def main():
     if args.serving_full:
         if rank == 0:
             print(json.dumps({"metric": "serving p50/p99 latency and solves/s (full serving workload)",
-                              "serving_full": serving_full(g, w, torch)}), flush=True)
+                              "serving_full": serving_full(g, w, torch, args.serving_requests)}), flush=True)
         barrier(world)
         return
 
