@@ -43,9 +43,10 @@ def parse():
                          "grid^3 Yee cells with PEC walls (ppw 10), edge-dipole RHS seed 11; poisson: k = 0")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--nmin", type=int, default=1024, help="separators >= nmin are HOD-BF compressed")
-    ap.add_argument("--ordering", default="planar", choices=["planar", "graph"],
-                    help="planar: nested dissection by lattice planes; graph: level-structure nested dissection "
-                         "of the matrix graph (coordinates withheld)")
+    ap.add_argument("--ordering", default="planar", choices=["planar", "hybrid", "graph"],
+                    help="planar: nested dissection by lattice planes; hybrid: lattice planes while the separators "
+                         "are compressed, graph nested dissection inside boxes whose planar separator would stay "
+                         "dense; graph: level-structure nested dissection of the matrix graph (coordinates withheld)")
     ap.add_argument("--no-dense", action="store_true", help="skip the all-dense complex64 comparison step")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -590,8 +591,8 @@ def main():
     # complex64 factors, separators >= 1024 in HOD-BF at tol 1e-4 (rank <= 64), FP64 GMRES(30) to 1e-8
     nmin = args.nmin
     tol = 1e-4
-    graph = args.ordering == "graph"
-    h = g.analyze_problem(p, graph=graph, nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
+    okw = {"planar": {}, "graph": {"graph": True}, "hybrid": {"ordering": g.MF_ORDER_HYBRID}}[args.ordering]
+    h = g.analyze_problem(p, **okw, nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
                           stream=stream.cuda_stream)
     bd = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()     # N x nrhs column-major, resident
     xd = torch.empty_like(bd)
@@ -682,7 +683,7 @@ def main():
     # all-dense complex64 path (same solver without compression), one step
     if rank == 0 and not args.no_dense:
       try:
-        hd = g.analyze_problem(p, graph=graph, nmin_sep=10 ** 9, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
+        hd = g.analyze_problem(p, **okw, nmin_sep=10 ** 9, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
                                stream=stream.cuda_stream)
         hd.mf_factor(tol)
         torch.cuda.synchronize()
@@ -702,7 +703,7 @@ def main():
     # FP64 GPU path (same code in complex128), one step, for the mixed-vs-FP64 comparison
     if rank == 0 and not args.no_fp64:
       try:
-        h64 = g.analyze_problem(p, graph=graph, nmin_sep=10 ** 9, precision=g.MF_PREC_C128, refine=g.MF_REFINE_IR,
+        h64 = g.analyze_problem(p, **okw, nmin_sep=10 ** 9, precision=g.MF_PREC_C128, refine=g.MF_REFINE_IR,
                                 stream=stream.cuda_stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -721,7 +722,7 @@ def main():
         line["fp64_path"] = {"error": str(e)[:300]}
       try:
         # FP64 butterfly variant: the compressed path in complex128 + GMRES
-        hb = g.analyze_problem(p, graph=graph, nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C128, refine=g.MF_REFINE_GMRES,
+        hb = g.analyze_problem(p, **okw, nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C128, refine=g.MF_REFINE_GMRES,
                                stream=stream.cuda_stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

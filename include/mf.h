@@ -46,11 +46,20 @@ enum { MF_LATTICE_NODE = 0, MF_LATTICE_EDGE = 1 };
 enum { MF_PREC_C64 = 0 /* complex64 factors + FP64 refinement */, MF_PREC_C128 = 1 /* all complex128 */ };
 enum { MF_REFINE_NONE = 0, MF_REFINE_GMRES = 1, MF_REFINE_IR = 2 };
 
-#define MF_OPTIONS_V1 1
+#define MF_OPTIONS_V1 1   /* the options up to coords */
+#define MF_OPTIONS_V2 2   /* adds ordering; mf_options_init fills version 2 */
+
+/* Nested-dissection ordering (mf_options.ordering):
+ *   MF_ORDER_AUTO: planar separators when coords are given, graph nested dissection otherwise;
+ *   MF_ORDER_HYBRID: planar separators while they are compressed (|I^s| >= nmin_sep); a box
+ *     whose planar separator would be smaller (a dense front) is ordered by graph nested
+ *     dissection of its unknowns, which leaves less fill in the dense fronts (needs coords);
+ *   MF_ORDER_GRAPH: graph nested dissection even when coords are given. */
+enum { MF_ORDER_AUTO = 0, MF_ORDER_HYBRID = 1, MF_ORDER_GRAPH = 2 };
 
 /* Options.  mf_options_init() fills the defaults given in brackets. */
 typedef struct {
-  int32_t version;        /* MF_OPTIONS_V1                                                      */
+  int32_t version;        /* MF_OPTIONS_V2 (MF_OPTIONS_V1: the fields up to coords)             */
   int32_t leaf_size;      /* [64]   nested-dissection leaf (unknowns per leaf front)            */
   int32_t nmin_sep;       /* [1024] fronts with |I^s| >= nmin_sep are HOD-BF compressed (Alg. 5) */
   int32_t hodbf_leaf;     /* [64]   leaf size of the HOD-BF and butterfly cluster trees          */
@@ -65,6 +74,8 @@ typedef struct {
   double rtol;            /* [1e-8] target ||b - A x|| / ||b||                                  */
   uint64_t seed;          /* [1]    seed of the random sketches                                 */
   const int32_t* coords;  /* [NULL] N x 3 integer lattice coordinates; NULL: graph ordering    */
+  int32_t ordering;       /* [MF_ORDER_AUTO] MF_ORDER_*                                         */
+  int32_t reserved_;      /* 0                                                                  */
 } mf_options;
 
 typedef struct {
@@ -108,10 +119,11 @@ int mf_options_init(mf_options* opt);
  *     where half of the reached vertices are passed; a compressed separator's
  *     HOD-BF tree comes from recursive bisection of its two-hop graph).
  *   cuda_stream: the CUDA stream all device work of this handle runs on (NULL = default).
- * Computes the nested-dissection ordering (planar or graph), the assembly tree, the
+ * Computes the nested-dissection ordering (planar, hybrid or graph: opt->ordering), the assembly tree, the
  * update sets, the HOD-BF cluster trees and the neighbour lists on the host;
  * no device memory is touched until mf_factor.  *out receives a new handle.
- * Errors: MF_ERR_ARG (bad pointers/sizes/CSR), MF_ERR_UNSUPPORTED (a box with
+ * Errors: MF_ERR_ARG (bad pointers/sizes/CSR, an unknown ordering, MF_ORDER_HYBRID without
+ * coords), MF_ERR_UNSUPPORTED (a box with
  * an empty separator), MF_ERR_OOM.
  */
 int mf_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,

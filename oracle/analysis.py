@@ -212,7 +212,8 @@ def _separator_bisection(sep, adj, th):
 
 
 def _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts):
-    """Graph nested dissection of a CSR pattern (no coordinates).
+    """Graph nested dissection of a CSR pattern (no coordinates); returns the recursion nd(ids),
+    which orders the vertex set ids (sorted) and returns the front id of its subtree root.
 
     The fill-reducing ordering of a general sparse matrix comes from nested dissection of its
     graph (Sec. 2; the Maxwell experiment of Sec. 6.2 is ordered this way).  The graph is the
@@ -280,15 +281,24 @@ def _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts
             return new_front(_separator_bisection(sep, adj, th), kids, True, th)
         return new_front(sep, kids, False, None)
 
-    nd(list(range(N)))
+    return nd
 
 
-def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False) -> Analysis:
+def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False, ordering="auto") -> Analysis:
     """Nested dissection + assembly tree + symbolic factorization (the ordering and symbolic steps of Alg. 1 and Alg. 5).
-    graph=True ignores the coordinates (graph nested dissection of the pattern)."""
+    ordering: "auto" (planar separators), "graph" (graph nested dissection of the pattern, the
+    coordinates ignored; also graph=True) or "hybrid" (planar separators while they are compressed,
+    |sep| >= nmin_sep; a box whose planar separator would be smaller, a dense front, is ordered by
+    graph nested dissection of its vertices).  Nested dissection is the paper's fill-reducing
+    ordering (Sec. 2); the choice of separators below the compressed levels is free."""
+    if graph:
+        ordering = "graph"
+    if ordering not in ("auto", "hybrid", "graph"):
+        raise ValueError(f"unknown ordering {ordering}")
     lattice = prob.lattice
     N = prob.n
     rp, ci = prob.rowptr, prob.colind
+    gnd = None
 
     fronts_sep = []     # list of (old ids of separator in front order, children front ids, compressed)
     perm_parts = []
@@ -303,6 +313,8 @@ def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False) -> An
             return fid
         a, mid = _split(lo, hi, lattice)
         ca = coords[ids, a]
+        if ordering == "hybrid" and int(np.count_nonzero(ca == mid)) < nmin_sep:
+            return gnd(sorted(int(v) for v in ids))   # the box's planar separator would stay dense
         left = ids[ca < mid]
         right = ids[ca > mid]
         sep = ids[ca == mid]
@@ -327,8 +339,10 @@ def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False) -> An
         perm_parts.append(sep)
         return fid
 
-    if graph:
-        _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts)
+    if ordering != "auto":
+        gnd = _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts)
+    if ordering == "graph":
+        gnd(list(range(N)))
     else:
         coords = prob.coords.astype(np.int64)
         lo, hi = _initial_box(coords, lattice)

@@ -45,6 +45,7 @@ struct Builder {
   const int32_t* coords;
   int lattice;
   int leaf, nmin, hleaf;
+  bool hybrid = false;
   // graph mode: adjacency with sorted neighbour lists, set membership marks
   std::vector<int64_t> adj_ptr;
   std::vector<int32_t> adj;
@@ -292,6 +293,15 @@ struct Builder {
     for (int d = 1; d < 3; ++d)
       if (ext[d] > ext[a]) a = d;
     int64_t mid = lattice == LATTICE_NODE ? lo[a] + ext[a] / 2 : (lo[a] - 1) + 2 * (ext[a] / 2);
+    if (hybrid) {
+      // a box whose planar separator would stay dense is ordered by graph nested dissection
+      int64_t ns = 0;
+      for (int64_t id : ids) ns += coords[3 * id + a] == mid;
+      if (ns < nmin) {
+        std::sort(ids.begin(), ids.end());
+        return nd_graph(ids);
+      }
+    }
     std::vector<int64_t> left, right, sep;
     for (int64_t id : ids) {
       int64_t c = coords[3 * id + a];
@@ -341,7 +351,10 @@ std::vector<std::vector<Range>> cluster_tree_balanced(int64_t npts, int64_t leaf
 }
 
 void analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* coords, int lattice,
-             int leaf_size, int nmin_sep, int hodbf_leaf, Analysis& out) {
+             int leaf_size, int nmin_sep, int hodbf_leaf, Analysis& out, int ordering) {
+  if (ordering != ORDER_AUTO && ordering != ORDER_HYBRID && ordering != ORDER_GRAPH)
+    throw std::runtime_error("unknown ordering");
+  if (ordering == ORDER_HYBRID && !coords) throw std::runtime_error("the hybrid ordering needs lattice coordinates");
   if (n <= 0 || !rowptr || !colind) throw std::runtime_error("invalid CSR");
   if (lattice != LATTICE_NODE && lattice != LATTICE_EDGE) throw std::runtime_error("unknown lattice");
   if (leaf_size < 1 || hodbf_leaf < 1 || nmin_sep < 1) throw std::runtime_error("invalid sizes in options");
@@ -374,9 +387,10 @@ void analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const int3
   b.leaf = leaf_size;
   b.nmin = nmin_sep;
   b.hleaf = hodbf_leaf;
-  if (!coords) {
-    b.mark.assign(n, 0);
-    b.seen_.assign(n, 0);
+  b.hybrid = ordering == ORDER_HYBRID;
+  b.mark.assign(n, 0);
+  b.seen_.assign(n, 0);
+  if (!coords || ordering == ORDER_GRAPH) {
     std::vector<int64_t> all(n);
     std::iota(all.begin(), all.end(), 0);
     b.nd_graph(all);

@@ -35,8 +35,12 @@ struct Analysis {
 enum { LATTICE_NODE = 0, LATTICE_EDGE = 1 };
 
 // Throws std::runtime_error on invalid input.
+// ordering: ORDER_AUTO (planar with coords, graph without), ORDER_HYBRID (planar separators while
+// they are compressed, graph nested dissection of every box whose planar separator is smaller
+// than nmin_sep), ORDER_GRAPH (graph nested dissection even with coords)
+enum { ORDER_AUTO = 0, ORDER_HYBRID = 1, ORDER_GRAPH = 2 };
 void analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* coords, int lattice,
-             int leaf_size, int nmin_sep, int hodbf_leaf, Analysis& out);
+             int leaf_size, int nmin_sep, int hodbf_leaf, Analysis& out, int ordering = ORDER_AUTO);
 
 std::vector<std::vector<Range>> cluster_tree_balanced(int64_t npts, int64_t leaf);
 

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstddef>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -317,7 +318,7 @@ extern "C" {
 int mf_options_init(mf_options* o) {
   if (!o) return fail(nullptr, MF_ERR_ARG, "opt is NULL");
   std::memset(o, 0, sizeof(*o));
-  o->version = MF_OPTIONS_V1;
+  o->version = MF_OPTIONS_V2;
   o->leaf_size = 64;
   o->nmin_sep = 1024;
   o->hodbf_leaf = 64;
@@ -332,6 +333,7 @@ int mf_options_init(mf_options* o) {
   o->rtol = 1e-8;
   o->seed = 1;
   o->coords = nullptr;
+  o->ordering = MF_ORDER_AUTO;
   return MF_OK;
 }
 
@@ -339,12 +341,21 @@ int mf_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const do
                void* cuda_stream, mf_handle** out) {
   if (!out) return fail(nullptr, MF_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (!opt || opt->version != MF_OPTIONS_V1) return fail(nullptr, MF_ERR_ARG, "options missing or wrong version");
+  if (!opt || (opt->version != MF_OPTIONS_V1 && opt->version != MF_OPTIONS_V2))
+    return fail(nullptr, MF_ERR_ARG, "options missing or wrong version");
+  const int ordering = opt->version >= MF_OPTIONS_V2 ? opt->ordering : MF_ORDER_AUTO;   // V1 structs end at coords
   if (n <= 0 || !rowptr || !colind || !vals) return fail(nullptr, MF_ERR_ARG, "invalid CSR arguments");
   std::unique_ptr<mf_handle> h(new (std::nothrow) mf_handle());
   if (!h) return fail(nullptr, MF_ERR_OOM, "host allocation failed");
   int rc = guarded(h.get(), [&]() -> int {
-    h->opt = *opt;
+    if (opt->version >= MF_OPTIONS_V2) {
+      h->opt = *opt;
+    } else {   // a version-1 struct ends at coords
+      std::memset(&h->opt, 0, sizeof(h->opt));
+      std::memcpy(&h->opt, opt, offsetof(mf_options, ordering));
+      h->opt.version = MF_OPTIONS_V2;
+      h->opt.ordering = MF_ORDER_AUTO;
+    }
     if (opt->coords) {
       h->coords.assign(opt->coords, opt->coords + 3 * n);
       h->opt.coords = h->coords.data();
@@ -353,7 +364,7 @@ int mf_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const do
     try {
       // with lattice coordinates: planar separators; without: graph nested dissection
       mf::analyze(n, rowptr, colind, opt->coords ? h->coords.data() : nullptr, opt->lattice, opt->leaf_size,
-                  opt->nmin_sep, opt->hodbf_leaf, h->an);
+                  opt->nmin_sep, opt->hodbf_leaf, h->an, ordering);
     } catch (const std::runtime_error& e) {
       std::string m = e.what();
       if (m.find("empty separator") != std::string::npos) return fail(h.get(), MF_ERR_UNSUPPORTED, m);

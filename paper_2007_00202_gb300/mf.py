@@ -23,7 +23,8 @@ MF_PREC_C64, MF_PREC_C128 = 0, 1
 MF_REFINE_NONE, MF_REFINE_GMRES, MF_REFINE_IR = 0, 1, 2
 MF_PROF_NARROW_GEMM, MF_PROF_FRONT_GEMM = 0, 1
 MF_OP_F11, MF_OP_F11_INV, MF_OP_F12, MF_OP_F21, MF_OP_C = 0, 1, 2, 3, 4
-MF_OPTIONS_V1 = 1
+MF_OPTIONS_V1, MF_OPTIONS_V2 = 1, 2
+MF_ORDER_AUTO, MF_ORDER_HYBRID, MF_ORDER_GRAPH = 0, 1, 2
 
 
 class MfError(RuntimeError):
@@ -37,7 +38,7 @@ class mf_options(C.Structure):
                 ("hodbf_leaf", C.c_int32), ("max_rank", C.c_int32), ("alpha", C.c_int32), ("knn", C.c_int32),
                 ("precision", C.c_int32), ("refine", C.c_int32), ("gmres_restart", C.c_int32),
                 ("max_iters", C.c_int32), ("lattice", C.c_int32), ("rtol", C.c_double), ("seed", C.c_uint64),
-                ("coords", C.POINTER(C.c_int32))]
+                ("coords", C.POINTER(C.c_int32)), ("ordering", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class mf_solve_info(C.Structure):
@@ -297,7 +298,8 @@ def mf_analyze(n, rowptr, colind, vals, coords, lattice=MF_LATTICE_NODE, stream=
 
 def analyze_problem(prob, graph=False, **opts) -> Handle:
     """mf_analyze on a workloads.SparseProblem-like object (n, rowptr, colind, vals, coords, lattice);
-    graph=True withholds the coordinates (graph nested dissection of the CSR pattern)."""
+    graph=True withholds the coordinates (graph nested dissection of the CSR pattern); the ordering
+    option (MF_ORDER_*) picks planar, hybrid or graph nested dissection when coordinates are given."""
     return mf_analyze(prob.n, prob.rowptr, prob.colind, prob.vals, None if graph else prob.coords, prob.lattice,
                       **opts)
 

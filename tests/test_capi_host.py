@@ -59,9 +59,10 @@ def test_argument_errors(g):
     assert (o.leaf_size, o.nmin_sep, o.gmres_restart, o.rtol) == (64, 1024, 30, 1e-8)
 
 
-def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True, stride=1, graph=False):
-    an = analyze(p, leaf, nmin, hleaf, graph=graph)
-    h = g.analyze_problem(p, graph=graph, leaf_size=leaf, nmin_sep=nmin, hodbf_leaf=hleaf)
+def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True, stride=1, graph=False, ordering="auto"):
+    an = analyze(p, leaf, nmin, hleaf, graph=graph, ordering=ordering)
+    code = {"auto": g.MF_ORDER_AUTO, "hybrid": g.MF_ORDER_HYBRID, "graph": g.MF_ORDER_GRAPH}[ordering]
+    h = g.analyze_problem(p, graph=graph, leaf_size=leaf, nmin_sep=nmin, hodbf_leaf=hleaf, ordering=code)
     e = h.mf_analysis_export()
     assert np.array_equal(e["perm"], an.perm)
     assert len(e["parent"]) == len(an.fronts)
@@ -117,4 +118,43 @@ def test_graph_analysis_bit_exact(g, which):
          "rgg": random_graph}[which]()
     an = _compare(g, p, 24, 40, 16, knn=6, graph=True)
     assert sum(f.compressed for f in an.fronts) >= 1
+
+
+@pytest.mark.parametrize("which", ["helmholtz13", "helmholtz16", "yee8"])
+def test_hybrid_analysis_bit_exact(g, which):
+    # planar separators while compressed, graph nested dissection inside boxes whose planar
+    # separator would stay dense: the host analysis equals the oracle's bit for bit
+    p, args = {"helmholtz13": (w.helmholtz7(13, 8), (24, 40, 16)), "helmholtz16": (w.helmholtz7(16, 8), (32, 100, 16)),
+               "yee8": (w.yee_maxwell(8, 10), (24, 40, 16))}[which]
+    an = _compare(g, p, *args, knn=6, ordering="hybrid")
+    assert sum(f.compressed for f in an.fronts) >= 1
+
+
+def test_graph_ordering_with_coordinates_bit_exact(g):
+    # MF_ORDER_GRAPH ignores the coordinates it is given
+    _compare(g, w.helmholtz7(12, 8), 24, 40, 16, knn=6, ordering="graph")
+    h = g.analyze_problem(w.helmholtz7(12, 8), graph=True, leaf_size=24, nmin_sep=40, hodbf_leaf=16)
+    h2 = g.analyze_problem(w.helmholtz7(12, 8), leaf_size=24, nmin_sep=40, hodbf_leaf=16, ordering=g.MF_ORDER_GRAPH)
+    assert np.array_equal(h.mf_analysis_export()["perm"], h2.mf_analysis_export()["perm"])
+
+
+def test_version_1_options_ignore_the_ordering_field(g):
+    # a caller built against the first options layout (ending at coords) gets the planar ordering
+    import ctypes as C
+    import paper_2007_00202_gb300.mf as mf
+    p = w.helmholtz7(12, 8)
+    o = mf.mf_options_init(leaf_size=24, nmin_sep=40, hodbf_leaf=16, ordering=mf.MF_ORDER_HYBRID)
+    o.version = mf.MF_OPTIONS_V1
+    coords = np.ascontiguousarray(p.coords, dtype=np.int32)
+    o.coords = coords.ctypes.data_as(C.POINTER(C.c_int32))
+    vals = np.ascontiguousarray(p.vals, dtype=np.complex128)
+    h = C.c_void_p()
+    rc = mf.lib().mf_analyze(p.n, p.rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                             np.ascontiguousarray(p.colind, dtype=np.int32).ctypes.data_as(C.POINTER(C.c_int32)),
+                             C.cast(vals.ctypes.data, C.POINTER(C.c_double)), C.byref(o), None, C.byref(h))
+    assert rc == 0
+    hv1 = mf.Handle(h, (coords, vals))
+    assert np.array_equal(hv1.mf_analysis_export()["perm"], analyze(p, 24, 40, 16).perm)
+    with pytest.raises(mf.MfError):   # the hybrid rule reads coordinates
+        g.analyze_problem(p, graph=True, ordering=mf.MF_ORDER_HYBRID)
 

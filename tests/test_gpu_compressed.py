@@ -82,6 +82,29 @@ def test_graph_nested_dissection_compressed_gmres_to_1e8(g, which):
     assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-6
 
 
+def test_hybrid_ordering_same_compressed_fronts_to_1e8(g):
+    # planar separators while compressed, graph nested dissection below: the compressed fronts are
+    # the planar ordering's, so GMRES needs about as many iterations, and the solution matches the
+    # oracle's exact multifrontal solution in the hybrid ordering
+    p = w.helmholtz7(20, 8)
+    b = w.rhs_gaussian(p, 3, 23)
+    A = p.to_scipy()
+    its = {}
+    for lab, kw in (("planar", {}), ("hybrid", {"ordering": g.MF_ORDER_HYBRID})):
+        h = g.analyze_problem(p, leaf_size=32, nmin_sep=150, hodbf_leaf=32, max_rank=64,
+                              precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES, **kw)
+        h.mf_factor(1e-4)
+        assert h.mf_stats()["ncompressed"] >= 3
+        x, info = h.mf_solve(b)
+        assert info.converged == 1
+        assert np.max(np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)) <= 1e-8
+        its[lab] = int(info.iters)
+    assert abs(its["hybrid"] - its["planar"]) <= 2, its
+    an = analyze(p, 32, 10 ** 9, 32, ordering="hybrid")
+    xe = dm.solve(p, an, dm.multifrontal_factor(p, an)[0], b)
+    assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-6
+
+
 def test_compressed_yee(g):
     p = w.yee_maxwell(10, 10)
     b = w.rhs_dipoles(p, 3, 11)

@@ -250,3 +250,66 @@ def test_graph_separator_bisection_gives_compact_clusters():
     # the separator is a level set of the 7-point graph: no edge joins two of its vertices
     A = p.to_scipy()[an.perm][:, an.perm].tocsr()[f.sep_begin:f.sep_end, f.sep_begin:f.sep_end]
     assert A.nnz == f.s
+
+
+# ---------------- hybrid ordering: planar while compressed, graph nested dissection below ----------------
+@pytest.mark.parametrize("gen", [lambda: w.helmholtz7(14, 8), lambda: w.yee_maxwell(6, 10)])
+def test_hybrid_structure_invariants_and_symbolic(gen):
+    p = gen()
+    an = analyze(p, leaf_size=16, nmin_sep=40, hodbf_leaf=8, ordering="hybrid")
+    N = p.n
+    assert np.array_equal(np.sort(an.perm), np.arange(N))
+    P = (p.to_scipy()[an.perm][:, an.perm].toarray() != 0)
+    S = P.copy()
+    for k in range(N):                      # brute-force symbolic elimination
+        rows = np.nonzero(S[k + 1:, k])[0] + k + 1
+        cols = np.nonzero(S[k, k + 1:])[0] + k + 1
+        S[np.ix_(rows, cols)] = True
+    # a part beyond a level-structure separator can fall apart into pieces that stay one subtree
+    # (a front has at most two children), so an update set may also hold indices of the other
+    # pieces' neighbours with no fill (structural zeros): it must contain the fill and lie in the
+    # ancestors' separators
+    owner = np.empty(N, np.int64)
+    for f in an.fronts:
+        owner[f.sep_begin:f.sep_end] = f.id
+    extra = total = 0
+    for f in an.fronts:
+        idx = list(range(f.sep_begin, f.sep_end))
+        below = set()
+        for k in idx:
+            below |= set((np.nonzero(S[k + 1:, k])[0] + k + 1).tolist())
+        upd = set(f.upd.tolist())
+        assert below - set(idx) <= upd
+        anc, q = set(), f.parent
+        while q >= 0:
+            anc.add(q)
+            q = an.fronts[q].parent
+        assert all(int(owner[x]) in anc for x in upd)
+        extra += len(upd - below)
+        total += len(upd)
+    assert extra <= 0.02 * total
+
+
+def test_hybrid_keeps_the_compressed_fronts_of_the_planar_ordering():
+    # the rule only reorders boxes whose planar separator would stay dense, so every compressed
+    # front (its separator in HOD-BF order, its cluster trees and its update set, in original
+    # numbering) is the planar ordering's, while the dense fronts hold less fill
+    p = w.helmholtz7(24, 8)
+    a0 = analyze(p, 32, 200, 32)
+    a1 = analyze(p, 32, 200, 32, ordering="hybrid")
+
+    def compressed(an):
+        out = []
+        for f in an.fronts:
+            if f.compressed:
+                out.append((an.perm[f.sep_begin:f.sep_end].tolist(), sorted(an.perm[f.upd].tolist()),
+                            f.th_tree, f.f22_tree))
+        return out
+    c0, c1 = compressed(a0), compressed(a1)
+    assert len(c0) >= 3 and len(c0) == len(c1)
+    for x, y in zip(c0, c1):
+        assert x[0] == y[0] and x[1] == y[1] and x[2] == y[2] and x[3] == y[3]
+
+    def dense_fill(an):
+        return sum(f.s * f.s + 2 * f.s * len(f.upd) for f in an.fronts if not f.compressed)
+    assert dense_fill(a1) < 0.95 * dense_fill(a0)
