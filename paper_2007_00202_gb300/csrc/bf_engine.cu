@@ -245,6 +245,10 @@ void BFContext<T>::sync() {
 template <typename T>
 void BFContext<T>::flush() {
   if (!pend || cap_mode == 2) return;
+  if (ring_dev) {   // mapped ring: the kernels read the staged bytes in place
+    pend = false;
+    return;
+  }
   MF_CUDA(cudaMemcpyAsync(dring.as<char>() + pend_begin, ring + pend_begin, ring_off - pend_begin,
                           cudaMemcpyHostToDevice, st));
   ++n_copies;
@@ -266,12 +270,23 @@ const void* BFContext<T>::upload(const void* src, size_t bytes) {
   }
   if (cap_mode == 1) cap_off = ((cap_off + 15) & ~size_t(15)) + bytes;
   if (!ring) {
-    if (cudaHostAlloc(reinterpret_cast<void**>(&ring), kRingBytes, cudaHostAllocDefault) != cudaSuccess)
-      throw CudaError("cudaHostAlloc of the staging ring failed");
-    dring.alloc(kRingBytes);
+    // Mapped pinned memory: a launch's descriptors are written on the host and read by the kernel
+    // in place (coherent host memory on the GPU's side), which saves one copy per launch; host
+    // writes before a launch are visible to it, and the ring is reused only after the stream has
+    // drained.  Without mapping, a device mirror receives one copy before each launch.
+    if (cudaHostAlloc(reinterpret_cast<void**>(&ring), kRingBytes, cudaHostAllocMapped) == cudaSuccess) {
+      void* d = nullptr;
+      if (cudaHostGetDevicePointer(&d, ring, 0) == cudaSuccess && d) ring_dev = static_cast<char*>(d);
+    } else {
+      cudaGetLastError();
+      ring = nullptr;
+      if (cudaHostAlloc(reinterpret_cast<void**>(&ring), kRingBytes, cudaHostAllocDefault) != cudaSuccess)
+        throw CudaError("cudaHostAlloc of the staging ring failed");
+    }
+    if (!ring_dev) dring.alloc(kRingBytes);
     ring_cap = kRingBytes;
   }
-  if (bytes == 0) return dring.p;
+  if (bytes == 0) return ring_dev ? static_cast<const void*>(ring_dev) : dring.p;
   if (bytes > ring_cap / 4) {   // large: a scratch copy of its own
     void* d = scratch.take(bytes);
     flush();
@@ -292,7 +307,7 @@ const void* BFContext<T>::upload(const void* src, size_t bytes) {
     pend = true;
   }
   ring_off = o + bytes;
-  return dring.as<char>() + o;
+  return (ring_dev ? ring_dev : dring.as<char>()) + o;
 }
 
 template <typename T>

@@ -235,7 +235,8 @@ class BFContext {
   cudaStream_t side[2] = {nullptr, nullptr};            // forked streams of row_ids (created on first use)
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   char* ring = nullptr;             // pinned host staging ring
-  DevMem dring;                     // its device mirror (targets of upload())
+  char* ring_dev = nullptr;         // the ring's device-mapped address (kernels read it in place)
+  DevMem dring;                     // a device mirror of the ring, where mapping is not available
   size_t ring_cap = 0, ring_off = 0, pend_begin = 0;
   bool pend = false;
   int64_t n_copies = 0;             // host -> device copies issued
