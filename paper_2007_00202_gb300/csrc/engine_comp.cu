@@ -110,7 +110,7 @@ const typename CompressedPart<T>::Neigh& CompressedPart<T>::neighbours(int fid, 
 
 template <typename T>
 void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr, const BFParams& P, uint64_t seed,
-                                     int w) {
+                                     int w, int helper) {
   BFContext<T>& cx = ctx(w);          // this front's execution context and stream
   const cudaStream_t st_ = stream(w);
   const size_t scratch_mark = cx.scratch.mark();   // this front's work is released when it is built
@@ -173,9 +173,11 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
   const FrontCtx<T>* dctx = d_ctx.template as<FrontCtx<T>>();
   const DBF<T>* Sptr = nullptr;
   // extraction over front positions; shifts map the caller's local indices to front positions
-  auto make_ext = [&, dctx](int rs, int cs, bool with_A, bool minus_S) -> DExtract<T> {
-    return [&, dctx, rs, cs, with_A, minus_S](const std::vector<std::pair<IdxVec, IdxVec>>& lst,
-                                              std::vector<Blk<T>>& dst) {
+  // (on: the context that issues the extraction's work, this front's own by default)
+  auto make_ext = [&, dctx](int rs, int cs, bool with_A, bool minus_S, BFContext<T>* on = nullptr) -> DExtract<T> {
+    BFContext<T>* ec = on ? on : &cx;
+    return [&, dctx, rs, cs, with_A, minus_S, ec](const std::vector<std::pair<IdxVec, IdxVec>>& lst,
+                                                  std::vector<Blk<T>>& dst) {
       std::vector<FrontEntryJob<T>> jobs;
       int64_t mx = 0;
       std::vector<std::pair<IdxVec, IdxVec>> g(lst);
@@ -187,8 +189,8 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
         if (g[q].first.empty() || g[q].second.empty()) continue;
         FrontEntryJob<T> j;
         j.ctx = 0;
-        j.X = static_cast<const int32_t*>(cx.upload(g[q].first.data(), g[q].first.size() * 4));
-        j.Y = static_cast<const int32_t*>(cx.upload(g[q].second.data(), g[q].second.size() * 4));
+        j.X = static_cast<const int32_t*>(ec->upload(g[q].first.data(), g[q].first.size() * 4));
+        j.Y = static_cast<const int32_t*>(ec->upload(g[q].second.data(), g[q].second.size() * 4));
         j.nx = (int)g[q].first.size(); j.ny = (int)g[q].second.size();
         j.dst = dst[q].p; j.dplane = dst[q].plane; j.dld = dst[q].ld;
         j.with_A = with_A ? 1 : 0;
@@ -197,9 +199,9 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
         mx = std::max<int64_t>(mx, (int64_t)j.nx * j.ny);
       }
       if (!jobs.empty()) {
-        const FrontEntryJob<T>* dj = cx.stage(jobs.data(), jobs.size());
+        const FrontEntryJob<T>* dj = ec->stage(jobs.data(), jobs.size());
         launch_front_entries<T>(dj, (int)jobs.size(), mx, dctx, A_.rowptr.template as<int64_t>(),
-                                A_.col32.template as<int32_t>(), A_.vals.template as<double>(), st_);
+                                A_.col32.template as<int32_t>(), A_.vals.template as<double>(), ec->st);
       }
       for (auto& k : kids) {
         if (!k.compressed) continue;
@@ -210,7 +212,7 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
           for (int32_t y : g[q].second) m[q].second.push_back(y >= 0 && y < s + u ? k.inv[y] : -1);
           any = true;
         }
-        if (any) cx.hodbf_extract(*k.cf->C, m, dst, T(1));
+        if (any) ec->hodbf_extract(*k.cf->C, m, dst, T(1));
       }
       if (minus_S && Sptr) {
         std::vector<std::pair<IdxVec, IdxVec>> m(g);
@@ -218,7 +220,7 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
           for (auto& x : pr.first) x -= s;
           for (auto& y : pr.second) y -= s;
         }
-        cx.extract_bf(*Sptr, m, dst, T(-1));
+        ec->extract_bf(*Sptr, m, dst, T(-1));
       }
     };
   };
@@ -256,14 +258,54 @@ void CompressedPart<T>::factor_front(int fid, const std::vector<FrontDev<T>>& fr
     wp = cx.t_wait;
     hp.assign(cx.t_host, cx.t_host + BFContext<T>::H_N);
   };
+  const int LH = (int)th.size() - 1, L22 = (int)t22.size() - 1, L = std::min(LH, L22);
+  // F12 and F21 do not depend on F11 or its inverse: with a helper context they are built by a
+  // second host thread on its own stream while this thread builds F11 and F11^-1 (the phase trace
+  // keeps them sequential)
+  std::thread helper_th;
+  std::exception_ptr helper_err;
+  cudaEvent_t setup_ev = nullptr;
+  struct Join {
+    std::thread& t;
+    cudaEvent_t& e;
+    ~Join() {
+      if (t.joinable()) t.join();
+      if (e) cudaEventDestroy(e);
+    }
+  } join_guard{helper_th, setup_ev};
+  if (helper >= 0 && u > 0 && !trace) {
+    MF_CUDA(cudaEventCreateWithFlags(&setup_ev, cudaEventDisableTiming));
+    MF_CUDA(cudaEventRecord(setup_ev, st_));   // the front's uploads (relative maps, gather context)
+    int dev = 0;
+    MF_CUDA(cudaGetDevice(&dev));
+    helper_th = std::thread([&, dev] {
+      try {
+        MF_CUDA(cudaSetDevice(dev));
+        BFContext<T>& hc = this->ctx(helper);
+        MF_CUDA(cudaStreamWaitEvent(hc.st, setup_ev, 0));
+        const size_t hm = hc.scratch.mark();
+        cf.F12 = hc.entry_eval(make_ext(0, s, true, false, &hc), s, u, th, t22, L, nn12, nn21, P);
+        cf.F21 = hc.entry_eval(make_ext(s, 0, true, false, &hc), u, s, t22, th, L, nn21, nn12, P);
+        hc.flush();
+        MF_CUDA(cudaStreamSynchronize(hc.st));
+        hc.scratch.release(hm);
+      } catch (...) {
+        helper_err = std::current_exception();
+      }
+    });
+  }
   cf.F11 = cx.hodbf_entry_eval(make_ext(0, 0, true, false), s, th, nn11, P);
   phase("F11");
   cf.F11inv = cx.hodbf_invert(*cf.F11, P, (uint32_t)((seed * 7 + fid) & 0xFFFFF));
   phase("F11inv");
   if (u > 0) {
-    const int LH = (int)th.size() - 1, L22 = (int)t22.size() - 1, L = std::min(LH, L22);
-    cf.F12 = cx.entry_eval(make_ext(0, s, true, false), s, u, th, t22, L, nn12, nn21, P);
-    cf.F21 = cx.entry_eval(make_ext(s, 0, true, false), u, s, t22, th, L, nn21, nn12, P);
+    if (helper_th.joinable()) {
+      helper_th.join();
+      if (helper_err) std::rethrow_exception(helper_err);
+    } else {
+      cf.F12 = cx.entry_eval(make_ext(0, s, true, false), s, u, th, t22, L, nn12, nn21, P);
+      cf.F21 = cx.entry_eval(make_ext(s, 0, true, false), u, s, t22, th, L, nn21, nn12, P);
+    }
     phase("F12,F21");
     const DBF<T>* F12p = cf.F12.get();
     const DBF<T>* F21p = cf.F21.get();

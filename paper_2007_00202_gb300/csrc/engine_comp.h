@@ -49,7 +49,10 @@ class CompressedPart {
   // Factor compressed front fid with execution context w (0: the engine's stream and arenas,
   // 1: a second context on its own stream, so that two fronts of one tree level can be built
   // by two host threads at once).  fr: dense-front descriptors (children's dense C blocks).
-  void factor_front(int fid, const std::vector<FrontDev<T>>& fr, const BFParams& P, uint64_t seed, int w = 0);
+  // w: the context that builds the front; helper >= 0: a second context that builds F12 and F21
+  // at the same time
+  void factor_front(int fid, const std::vector<FrontDev<T>>& fr, const BFParams& P, uint64_t seed, int w = 0,
+                    int helper = -1);
   // Expand C of a compressed front into the dense buffer of its (dense) parent's extend-add.
   void densify_C(int fid, const FrontDev<T>& f, int w = 0);
   // execution contexts 1 .. n-1 (created on first use, each with its own stream and scratch arena;

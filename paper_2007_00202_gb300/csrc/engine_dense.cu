@@ -82,22 +82,27 @@ class DenseEngine : public EngineBase {
       if (lvl.empty()) continue;
       auto t0 = std::chrono::steady_clock::now();
       const auto& F = an_.fronts;
-      // front list[i] with execution context w; densify on the same context
-      auto run = [&](const std::vector<int32_t>& list, size_t i0, size_t step, int w) {
+      // front list[i] with execution context w (and helper context `helper` for its F12 / F21, -1:
+      // none); densify on the same context
+      const int ctx_cap = std::min<int>(CompressedPart<T>::kMaxContexts, std::max(1, eo_.max_contexts));
+      auto run = [&](const std::vector<int32_t>& list, size_t i0, size_t step, int w, int helper) {
         for (size_t i = i0; i < list.size(); i += step) {
           const int fid = list[i];
-          comp_->factor_front(fid, fr_, P, eo_.seed, w);
+          comp_->factor_front(fid, fr_, P, eo_.seed, w, helper);
           if (F[fid].parent >= 0 && !F[F[fid].parent].compressed) comp_->densify_C(fid, fr_[fid], w);
         }
       };
       if (lvl.size() == 1 || serial || eo_.max_contexts <= 1) {
-        run(lvl, 0, 1, 0);
+        const int helper = (!serial && ctx_cap >= 2) ? 1 : -1;
+        if (helper > 0) comp_->ensure_contexts(2);
+        run(lvl, 0, 1, 0, helper);
       } else {
         // the fronts of one level are independent: up to kMaxContexts host threads build them, each
         // with its own stream and scratch arena, taking the next front of the level when done, so
         // that one thread's host work overlaps the others' GPU work
-        const int nctx = std::min<int>({(int)lvl.size(), CompressedPart<T>::kMaxContexts, std::max(1, eo_.max_contexts)});
-        comp_->ensure_contexts(nctx);
+        const int nctx = std::min<int>((int)lvl.size(), ctx_cap);
+        const int nhelp = std::max(0, std::min(nctx, ctx_cap - nctx));   // contexts left for F12 / F21
+        comp_->ensure_contexts(nctx + nhelp);
         MF_CUDA(cudaEventRecord(lev_ev_[0], st_));                  // children and dense fronts below
         for (int w = 1; w < nctx; ++w) MF_CUDA(cudaStreamWaitEvent(comp_->stream(w), lev_ev_[0], 0));
         int dev = 0;
@@ -106,7 +111,7 @@ class DenseEngine : public EngineBase {
         std::vector<std::exception_ptr> errs(nctx);
         auto worker = [&](int w) {
           try {
-            for (size_t i = next++; i < lvl.size(); i = next++) run(lvl, i, lvl.size(), w);
+            for (size_t i = next++; i < lvl.size(); i = next++) run(lvl, i, lvl.size(), w, w < nhelp ? nctx + w : -1);
           } catch (...) {
             errs[w] = std::current_exception();
           }
