@@ -109,6 +109,16 @@ def test_analysis_bit_exact_64cube_structure(g):
     assert sum(f.compressed for f in an.fronts) == 5
 
 
+def test_hybrid_analysis_bit_exact_64cube(g):
+    # the 64^3 workload in the hybrid ordering: graph nested dissection below the compressed
+    # levels, the same 5 compressed fronts; tree, update sets and cluster trees in full (the
+    # neighbour lists are covered by the planar test above, the compressed fronts being the same)
+    p = w.helmholtz7(64, 10)
+    an = _compare(g, p, 64, 1024, 64, check_nn=False, ordering="hybrid")
+    assert len(an.fronts) == 7847
+    assert sum(f.compressed for f in an.fronts) == 5
+
+
 @pytest.mark.parametrize("which", ["helmholtz13", "yee8", "rgg"])
 def test_graph_analysis_bit_exact(g, which):
     # general CSR input (coordinates withheld): the graph nested dissection of the C++ host analysis
