@@ -43,6 +43,8 @@ def parse():
                          "grid^3 Yee cells with PEC walls (ppw 10), edge-dipole RHS seed 11; poisson: k = 0")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--nmin", type=int, default=1024, help="separators >= nmin are HOD-BF compressed")
+    ap.add_argument("--parallel-levels", type=int, default=0,
+                    help="planar rule: cut the top N levels along the root separator's axis (parallel separators)")
     ap.add_argument("--ordering", default="planar", choices=["planar", "hybrid", "graph"],
                     help="planar: nested dissection by lattice planes; hybrid: lattice planes while the separators "
                          "are compressed, graph nested dissection inside boxes whose planar separator would stay "
@@ -592,6 +594,8 @@ def main():
     nmin = args.nmin
     tol = 1e-4
     okw = {"planar": {}, "graph": {"graph": True}, "hybrid": {"ordering": g.MF_ORDER_HYBRID}}[args.ordering]
+    if args.parallel_levels:
+        okw = dict(okw, parallel_levels=args.parallel_levels)
     h = g.analyze_problem(p, **okw, nmin_sep=nmin, max_rank=64, precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES,
                           stream=stream.cuda_stream)
     bd = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()     # N x nrhs column-major, resident
@@ -665,6 +669,7 @@ def main():
                            "arena_peak_gb": st["arena_peak_bytes"] / 1e9,
                            "arena_capacity_gb": st["arena_capacity_bytes"] / 1e9,
                            "nrhs": nrhs, "nmin_sep": nmin, "ordering": args.ordering,
+                           "parallel_levels": args.parallel_levels,
                            "l2": "inputs larger than L2 (factors "
                            f"{st['factor_bytes'] / 1e9:.1f} GB)", "parallelism": "replicas" if world > 1 else "1gpu"},
                 "factor_s": factor_s, "solve_s": solve_s, "solve_iters": int(info.iters),

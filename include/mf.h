@@ -75,7 +75,10 @@ typedef struct {
   uint64_t seed;          /* [1]    seed of the random sketches                                 */
   const int32_t* coords;  /* [NULL] N x 3 integer lattice coordinates; NULL: graph ordering    */
   int32_t ordering;       /* [MF_ORDER_AUTO] MF_ORDER_*                                         */
-  int32_t reserved_;      /* 0                                                                  */
+  int32_t parallel_levels;/* [0] the planar rule cuts the top parallel_levels levels along the root
+                           * separator's axis (while a box extends >= 3 units along it): parallel
+                           * instead of crossing separators there (the remedy of the remark in
+                           * Sec. 5.3 for F12 / F21 ranks between crossing separators)            */
 } mf_options;
 
 typedef struct {

@@ -85,13 +85,16 @@ def _initial_box(coords: np.ndarray, lattice: int):
     return lo, hi
 
 
-def _split(lo, hi, lattice):
-    """Separator axis and plane coordinate for a box [lo, hi) (half-open per axis)."""
+def _split(lo, hi, lattice, axis=None):
+    """Separator axis and plane coordinate for a box [lo, hi) (half-open per axis).  axis: cut along
+    this axis instead when the box extends 3 or more units along it (parallel separators)."""
     if lattice == LATTICE_NODE:
         ext = hi - lo
     else:
         ext = (hi - lo + 1) // 2          # number of lattice cells
     a = int(np.argmax(ext))               # first axis of largest extent: x, then y, then z
+    if axis is not None and ext[axis] >= 3:
+        a = int(axis)
     if lattice == LATTICE_NODE:
         mid = int(lo[a] + ext[a] // 2)
     else:
@@ -284,13 +287,17 @@ def _graph_nd(N, rp, ci, leaf_size, nmin_sep, hodbf_leaf, fronts_sep, perm_parts
     return nd
 
 
-def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False, ordering="auto") -> Analysis:
+def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False, ordering="auto",
+            parallel_levels=0) -> Analysis:
     """Nested dissection + assembly tree + symbolic factorization (the ordering and symbolic steps of Alg. 1 and Alg. 5).
     ordering: "auto" (planar separators), "graph" (graph nested dissection of the pattern, the
     coordinates ignored; also graph=True) or "hybrid" (planar separators while they are compressed,
     |sep| >= nmin_sep; a box whose planar separator would be smaller, a dense front, is ordered by
     graph nested dissection of its vertices).  Nested dissection is the paper's fill-reducing
-    ordering (Sec. 2); the choice of separators below the compressed levels is free."""
+    ordering (Sec. 2); the choice of separators below the compressed levels is free.
+    parallel_levels: the planar rule cuts the boxes of the top parallel_levels levels along the
+    root's axis, so that those separators are parallel planes rather than crossing ones (the
+    remedy the remark of Sec. 5.3 gives for the ranks of F12 / F21 between crossing separators)."""
     if graph:
         ordering = "graph"
     if ordering not in ("auto", "hybrid", "graph"):
@@ -303,7 +310,9 @@ def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False, order
     fronts_sep = []     # list of (old ids of separator in front order, children front ids, compressed)
     perm_parts = []
 
-    def nd(ids, lo, hi):
+    root_axis = [0]
+
+    def nd(ids, lo, hi, depth=0):
         """Returns the front id of the subtree root."""
         if len(ids) <= leaf_size:
             sep = _lex_order(coords, ids)
@@ -311,7 +320,9 @@ def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False, order
             fronts_sep.append((sep, [], False, None))
             perm_parts.append(sep)
             return fid
-        a, mid = _split(lo, hi, lattice)
+        a, mid = _split(lo, hi, lattice, root_axis[0] if 0 < depth < parallel_levels else None)
+        if depth == 0:
+            root_axis[0] = a
         ca = coords[ids, a]
         if ordering == "hybrid" and int(np.count_nonzero(ca == mid)) < nmin_sep:
             return gnd(sorted(int(v) for v in ids))   # the box's planar separator would stay dense
@@ -321,10 +332,10 @@ def analyze(prob, leaf_size=64, nmin_sep=1024, hodbf_leaf=64, graph=False, order
         kids = []
         if len(left):
             hi2 = hi.copy(); hi2[a] = mid
-            kids.append(nd(left, lo.copy(), hi2))
+            kids.append(nd(left, lo.copy(), hi2, depth + 1))
         if len(right):
             lo2 = lo.copy(); lo2[a] = mid + 1
-            kids.append(nd(right, lo2, hi.copy()))
+            kids.append(nd(right, lo2, hi.copy(), depth + 1))
         if len(sep) == 0:
             raise ValueError("empty separator: the lattice rule does not apply to this input")
         compressed = len(sep) >= nmin_sep

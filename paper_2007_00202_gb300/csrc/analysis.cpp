@@ -46,6 +46,8 @@ struct Builder {
   int lattice;
   int leaf, nmin, hleaf;
   bool hybrid = false;
+  int par_levels = 0;    // top levels cut along the root's axis (parallel separators)
+  int root_axis = 0;
   // graph mode: adjacency with sorted neighbour lists, set membership marks
   std::vector<int64_t> adj_ptr;
   std::vector<int32_t> adj;
@@ -278,7 +280,7 @@ struct Builder {
     return (int64_t)raw.size() - 1;
   }
 
-  int64_t nd(std::vector<int64_t>& ids, C3 lo, C3 hi) {
+  int64_t nd(std::vector<int64_t>& ids, C3 lo, C3 hi, int depth = 0) {
     if ((int64_t)ids.size() <= leaf) {
       Raw r;
       r.sep = ids;
@@ -292,6 +294,8 @@ struct Builder {
     int a = 0;
     for (int d = 1; d < 3; ++d)
       if (ext[d] > ext[a]) a = d;
+    if (depth == 0) root_axis = a;
+    else if (depth < par_levels && ext[root_axis] >= 3) a = root_axis;   // parallel to the root separator
     int64_t mid = lattice == LATTICE_NODE ? lo[a] + ext[a] / 2 : (lo[a] - 1) + 2 * (ext[a] / 2);
     if (hybrid) {
       // a box whose planar separator would stay dense is ordered by graph nested dissection
@@ -313,11 +317,11 @@ struct Builder {
     std::vector<int64_t> kids;
     if (!left.empty()) {
       C3 h2 = hi; h2[a] = mid;
-      kids.push_back(nd(left, lo, h2));
+      kids.push_back(nd(left, lo, h2, depth + 1));
     }
     if (!right.empty()) {
       C3 l2 = lo; l2[a] = mid + 1;
-      kids.push_back(nd(right, l2, hi));
+      kids.push_back(nd(right, l2, hi, depth + 1));
     }
     if (sep.empty()) throw std::runtime_error("empty separator: the lattice rule does not apply to this input");
     Raw r;
@@ -351,7 +355,8 @@ std::vector<std::vector<Range>> cluster_tree_balanced(int64_t npts, int64_t leaf
 }
 
 void analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* coords, int lattice,
-             int leaf_size, int nmin_sep, int hodbf_leaf, Analysis& out, int ordering) {
+             int leaf_size, int nmin_sep, int hodbf_leaf, Analysis& out, int ordering, int parallel_levels) {
+  if (parallel_levels < 0) throw std::runtime_error("parallel_levels must be >= 0");
   if (ordering != ORDER_AUTO && ordering != ORDER_HYBRID && ordering != ORDER_GRAPH)
     throw std::runtime_error("unknown ordering");
   if (ordering == ORDER_HYBRID && !coords) throw std::runtime_error("the hybrid ordering needs lattice coordinates");
@@ -388,6 +393,7 @@ void analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const int3
   b.nmin = nmin_sep;
   b.hleaf = hodbf_leaf;
   b.hybrid = ordering == ORDER_HYBRID;
+  b.par_levels = parallel_levels;
   b.mark.assign(n, 0);
   b.seen_.assign(n, 0);
   if (!coords || ordering == ORDER_GRAPH) {

@@ -39,8 +39,11 @@ enum { LATTICE_NODE = 0, LATTICE_EDGE = 1 };
 // they are compressed, graph nested dissection of every box whose planar separator is smaller
 // than nmin_sep), ORDER_GRAPH (graph nested dissection even with coords)
 enum { ORDER_AUTO = 0, ORDER_HYBRID = 1, ORDER_GRAPH = 2 };
+// parallel_levels: the planar rule cuts the boxes of the top parallel_levels levels along the root's
+// axis (while they extend 3 or more units along it), so that those separators are parallel planes
 void analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* coords, int lattice,
-             int leaf_size, int nmin_sep, int hodbf_leaf, Analysis& out, int ordering = ORDER_AUTO);
+             int leaf_size, int nmin_sep, int hodbf_leaf, Analysis& out, int ordering = ORDER_AUTO,
+             int parallel_levels = 0);
 
 std::vector<std::vector<Range>> cluster_tree_balanced(int64_t npts, int64_t leaf);
 

@@ -364,7 +364,8 @@ int mf_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const do
     try {
       // with lattice coordinates: planar separators; without: graph nested dissection
       mf::analyze(n, rowptr, colind, opt->coords ? h->coords.data() : nullptr, opt->lattice, opt->leaf_size,
-                  opt->nmin_sep, opt->hodbf_leaf, h->an, ordering);
+                  opt->nmin_sep, opt->hodbf_leaf, h->an, ordering,
+                  opt->version >= MF_OPTIONS_V2 ? opt->parallel_levels : 0);
     } catch (const std::runtime_error& e) {
       std::string m = e.what();
       if (m.find("empty separator") != std::string::npos) return fail(h.get(), MF_ERR_UNSUPPORTED, m);

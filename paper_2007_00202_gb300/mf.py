@@ -38,7 +38,7 @@ class mf_options(C.Structure):
                 ("hodbf_leaf", C.c_int32), ("max_rank", C.c_int32), ("alpha", C.c_int32), ("knn", C.c_int32),
                 ("precision", C.c_int32), ("refine", C.c_int32), ("gmres_restart", C.c_int32),
                 ("max_iters", C.c_int32), ("lattice", C.c_int32), ("rtol", C.c_double), ("seed", C.c_uint64),
-                ("coords", C.POINTER(C.c_int32)), ("ordering", C.c_int32), ("reserved_", C.c_int32)]
+                ("coords", C.POINTER(C.c_int32)), ("ordering", C.c_int32), ("parallel_levels", C.c_int32)]
 
 
 class mf_solve_info(C.Structure):

@@ -59,10 +59,11 @@ def test_argument_errors(g):
     assert (o.leaf_size, o.nmin_sep, o.gmres_restart, o.rtol) == (64, 1024, 30, 1e-8)
 
 
-def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True, stride=1, graph=False, ordering="auto"):
-    an = analyze(p, leaf, nmin, hleaf, graph=graph, ordering=ordering)
+def _compare(g, p, leaf, nmin, hleaf, knn=8, check_nn=True, stride=1, graph=False, ordering="auto", parallel=0):
+    an = analyze(p, leaf, nmin, hleaf, graph=graph, ordering=ordering, parallel_levels=parallel)
     code = {"auto": g.MF_ORDER_AUTO, "hybrid": g.MF_ORDER_HYBRID, "graph": g.MF_ORDER_GRAPH}[ordering]
-    h = g.analyze_problem(p, graph=graph, leaf_size=leaf, nmin_sep=nmin, hodbf_leaf=hleaf, ordering=code)
+    h = g.analyze_problem(p, graph=graph, leaf_size=leaf, nmin_sep=nmin, hodbf_leaf=hleaf, ordering=code,
+                          parallel_levels=parallel)
     e = h.mf_analysis_export()
     assert np.array_equal(e["perm"], an.perm)
     assert len(e["parent"]) == len(an.fronts)
@@ -167,4 +168,14 @@ def test_version_1_options_ignore_the_ordering_field(g):
     assert np.array_equal(hv1.mf_analysis_export()["perm"], analyze(p, 24, 40, 16).perm)
     with pytest.raises(mf.MfError):   # the hybrid rule reads coordinates
         g.analyze_problem(p, graph=True, ordering=mf.MF_ORDER_HYBRID)
+
+
+@pytest.mark.parametrize("which,parallel", [("helmholtz24", 2), ("helmholtz24", 3), ("yee10", 3), ("hybrid20", 3)])
+def test_parallel_levels_analysis_bit_exact(g, which, parallel):
+    # parallel separators at the top levels (planar rule along the root's axis): bit for bit
+    p, args, o = {"helmholtz24": (w.helmholtz7(24, 8), (32, 150, 32), "auto"),
+                  "yee10": (w.yee_maxwell(10, 10), (32, 100, 32), "auto"),
+                  "hybrid20": (w.helmholtz7(20, 8), (32, 150, 32), "hybrid")}[which]
+    an = _compare(g, p, *args, knn=6, ordering=o, parallel=parallel)
+    assert sum(f.compressed for f in an.fronts) >= 2
 

@@ -105,6 +105,26 @@ def test_hybrid_ordering_same_compressed_fronts_to_1e8(g):
     assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-6
 
 
+def test_parallel_separators_compressed_gmres_to_1e8(g):
+    # parallel separators at the top three levels (the remedy of the remark in Sec. 5.3): the
+    # compressed solve reaches 1e-8 and the oracle's exact solution in the same ordering
+    p = w.helmholtz7(20, 8)
+    b = w.rhs_gaussian(p, 2, 29)
+    h = g.analyze_problem(p, leaf_size=32, nmin_sep=150, hodbf_leaf=32, max_rank=64, parallel_levels=3,
+                          precision=g.MF_PREC_C64, refine=g.MF_REFINE_GMRES)
+    an = analyze(p, 32, 150, 32, parallel_levels=3)
+    assert np.array_equal(h.mf_analysis_export()["perm"], an.perm)
+    h.mf_factor(1e-4)
+    assert h.mf_stats()["ncompressed"] >= 3
+    x, info = h.mf_solve(b)
+    A = p.to_scipy()
+    assert info.converged == 1
+    assert np.max(np.linalg.norm(A @ x - b, axis=0) / np.linalg.norm(b, axis=0)) <= 1e-8
+    ae = analyze(p, 32, 10 ** 9, 32, parallel_levels=3)
+    xe = dm.solve(p, ae, dm.multifrontal_factor(p, ae)[0], b)
+    assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-6
+
+
 def test_compressed_yee(g):
     p = w.yee_maxwell(10, 10)
     b = w.rhs_dipoles(p, 3, 11)

@@ -313,3 +313,32 @@ def test_hybrid_keeps_the_compressed_fronts_of_the_planar_ordering():
     def dense_fill(an):
         return sum(f.s * f.s + 2 * f.s * len(f.upd) for f in an.fronts if not f.compressed)
     assert dense_fill(a1) < 0.95 * dense_fill(a0)
+
+
+# ---------------- parallel separators at the top levels (the remedy of the remark in Sec. 5.3) ----------------
+@pytest.mark.parametrize("gen,args", [(lambda: w.helmholtz7(24, 8), (32, 150, 32)), (lambda: w.yee_maxwell(10, 10), (32, 100, 32))])
+def test_parallel_levels_cut_along_the_root_axis(gen, args):
+    p = gen()
+    P = 3
+    an = analyze(p, *args, parallel_levels=P)
+    a0 = analyze(p, *args)
+    assert np.array_equal(np.sort(an.perm), np.arange(p.n))
+    # depth of every front below the root
+    depth = {}
+    for f in reversed(an.fronts):
+        depth[f.id] = 0 if f.parent < 0 else depth[f.parent] + 1
+
+    def axis(f):
+        c = p.coords[an.perm[f.sep_begin:f.sep_end]]
+        return int(np.argmin(c.max(0) - c.min(0)))   # the separator plane's constant coordinate
+    root = an.fronts[-1]
+    for f in an.fronts:
+        if 0 < depth[f.id] < P and f.s > an.leaf_size:
+            assert axis(f) == axis(root)
+    # the default rule alternates: some separator of depth 1 or 2 crosses the root separator
+    d0 = {}
+    for f in reversed(a0.fronts):
+        d0[f.id] = 0 if f.parent < 0 else d0[f.parent] + 1
+    c = [int(np.argmin(np.ptp(p.coords[a0.perm[f.sep_begin:f.sep_end]], axis=0)))
+         for f in a0.fronts if d0[f.id] in (1, 2) and f.s > a0.leaf_size]
+    assert any(x != axis(a0.fronts[-1]) for x in c)
