@@ -168,6 +168,10 @@ def test_version_1_options_ignore_the_ordering_field(g):
     assert np.array_equal(hv1.mf_analysis_export()["perm"], analyze(p, 24, 40, 16).perm)
     with pytest.raises(mf.MfError):   # the hybrid rule reads coordinates
         g.analyze_problem(p, graph=True, ordering=mf.MF_ORDER_HYBRID)
+    for bad in ({"ordering": 7}, {"parallel_levels": -1}):
+        with pytest.raises(mf.MfError) as e:
+            g.analyze_problem(p, **bad)
+        assert e.value.code == -1, bad
 
 
 @pytest.mark.parametrize("which,parallel", [("helmholtz24", 2), ("helmholtz24", 3), ("yee10", 3), ("hybrid20", 3)])
