@@ -162,19 +162,24 @@ PROFILE_PERIOD = 8
 # nominal FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz maximum SM clock
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM traffic of the narrow GEMM per algorithmic byte, from an ncu capture of one streaming
-# launch (4096 x 16 x 4096, 136 MB of A: read once), valid
-# while the kernel source hashes to NARROW_SRC_SHA1; scaled to the bench's launches by their
-# algorithmic bytes
+# launch (4096 x 16 x 4096, 136 MB of A: read once), valid while the kernel's device code (the
+# source file up to its first host launch function) hashes to NARROW_SRC_SHA1; scaled to the
+# bench's launches by their algorithmic bytes
 NARROW_TRAFFIC_PER_ALG_BYTE = 1.0204
-NARROW_SRC_SHA1 = "ab8525938375ca8924e77b137cf439837fbf15df"
+NARROW_SRC_SHA1 = "d006306299d40ec83fe95f1fbcfd4d36babf87c6"
 
 
-def _src_sha1(name):
+def _device_code_sha1(name, launcher):
+    """SHA-1 of a kernel source file up to the template line that introduces its host function
+    `launcher` (the device code; edits of the host launch code leave it unchanged)."""
     import hashlib
     path = os.path.join(ROOT, "paper_2007_00202_gb300", "csrc", name)
     try:
-        return hashlib.sha1(open(path, "rb").read()).hexdigest()
-    except OSError:
+        text = open(path).read()
+        i = text.index(f"void {launcher}(")
+        i = text.rfind("\ntemplate", 0, i)
+        return hashlib.sha1(text[:i].encode()).hexdigest() if i >= 0 else None
+    except (OSError, ValueError):
         return None
 
 
@@ -191,7 +196,7 @@ def roofline(prof, peaks):
     hbm = peaks.get("hbm_gbs") or 6800.0
     ai = prof["flops"] / max(prof["bytes"], 1.0)
     traffic = None
-    if NARROW_TRAFFIC_PER_ALG_BYTE is not None and _src_sha1("gemm_nrhs.cu") == NARROW_SRC_SHA1:
+    if NARROW_TRAFFIC_PER_ALG_BYTE is not None and _device_code_sha1("gemm_nrhs.cu", "launch_nb") == NARROW_SRC_SHA1:
         traffic = NARROW_TRAFFIC_PER_ALG_BYTE * prof["bytes"] / max(prof["launches"], 1)
     alu_bound = ai * hbm / 1e3 > FP32_ALU_TFLOPS
     r = {"kernel": "k_gemm_nrhs (narrow planar complex GEMM: solve front products, butterfly level products)",

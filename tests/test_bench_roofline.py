@@ -23,11 +23,24 @@ def test_narrow_gemm_alu_bound_arithmetic():
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["hbm_frac"] == pytest.approx(prof["bytes"] / 2e-3 / 1e9 / 6756.5)
     assert r["ms_per_launch"] == pytest.approx(0.2)
-    matches = bench._src_sha1("gemm_nrhs.cu") == bench.NARROW_SRC_SHA1
+    matches = bench._device_code_sha1("gemm_nrhs.cu", "launch_nb") == bench.NARROW_SRC_SHA1
     if matches:
         assert r["traffic"] == pytest.approx(bench.NARROW_TRAFFIC_PER_ALG_BYTE * prof["bytes"] / 10)
     else:
         assert r["traffic"] is None
+
+
+def test_traffic_hash_covers_the_device_code_only():
+    # the counters stay valid across edits of the host launch code and lapse with any edit of the
+    # kernels: the hash covers the source up to the first host launch function
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2007_00202_gb300", "csrc", "gemm_nrhs.cu")
+    text = open(path).read()
+    i = text.index("void launch_nb(")
+    cut = text.rfind("\ntemplate", 0, i)
+    assert 0 < cut < i
+    assert "__global__" in text[:cut] and "__global__" not in text[cut:]
 
 
 def test_narrow_gemm_hbm_bound_below_the_ridge():
